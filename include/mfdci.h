@@ -1,0 +1,243 @@
+/*
+ * mfdci.h -- C ABI of the GB300 (sm_103a) library for the hot path of
+ * MFDn-style nuclear configuration interaction (CI):
+ *
+ *   enumerate the proton x neutron Slater-determinant basis as bit strings,
+ *   filter determinant pairs by XOR + popcount, count -> scan -> fill the
+ *   sparse Hamiltonian H, apply it to a block of vectors (SpMM), and find
+ *   its lowest eigenpairs by block Lanczos; plus a batched form and a
+ *   submit/poll solve queue.
+ *
+ * Paper: B. Cook, P. J. Fasano, P. Maris, C. Yang, D. Oryspayev,
+ * "Accelerating quantum many-body configuration interaction with
+ * directives" (2021): Fig. 1 (the matrix-construction and eigensolve
+ * pipeline), Sec. 2.1 (bit representation, popcount filter, Listing 2),
+ * Sec. 2.2 (counts -> offsets, Eq. 1), Sec. 2.3 (filling shared arrays,
+ * Listing 7), Sec. 2 (SpMV/SpMM and LOBPCG/Lanczos eigensolvers).
+ *
+ * Conventions (every function):
+ *   - returns ci_status; CI_OK is 0.  On error, ci_last_error() gives a
+ *     message for the calling thread.  No exception crosses the ABI and the
+ *     library never aborts the process.
+ *   - handles (ci_problem, ci_matrix, ci_batch, ci_queue) are owned by the
+ *     library and freed by their *_destroy call.  Buffers passed in are
+ *     owned by the caller; the library copies what it keeps.
+ *   - "device" pointers are CUDA global-memory pointers of the current
+ *     device (e.g. torch.Tensor.data_ptr()); "host" pointers are ordinary
+ *     process memory.  Where a parameter says "host or device" the library
+ *     tells them apart with cudaPointerGetAttributes.
+ *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy
+ *     default stream.  Calls that return host results synchronise the
+ *     stream before returning.
+ *   - all matrices and vectors are row-major; indices are 0-based.
+ *
+ * Single-particle (s.p.) states: the caller lists them (S <= 128 per
+ * species) with their HO shell N and 2m.  A species determinant is a bit
+ * string with bit a set when state a is occupied (Sec. 2.1), stored as
+ * W = ceil(S/64) little-endian 64-bit words.  A basis state is a pair (p, n)
+ * of a proton and a neutron determinant, |p;n> = (prod_{a in p, ascending}
+ * a+_{a,p}) (prod_{b in n, ascending} a+_{b,n}) |0>.
+ *
+ * Hamiltonian:  H = sum_a eps_a a+_a a_a  (both species)
+ *   + 1/4 sum V^pp_abcd a+_a a+_b a_d a_c  + (the same for nn)
+ *   + sum V^pn_abcd a+_{a,p} a+_{b,n} a_{d,n} a_{c,p},
+ * V^pp and V^nn antisymmetrised, all three real, Hermitian and conserving m.
+ */
+#ifndef MFDCI_H
+#define MFDCI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CI_OK = 0,
+    CI_ERR_INVALID_ARG = 1,  /* a bad argument; nothing was changed        */
+    CI_ERR_OOM = 2,          /* a device or host allocation failed         */
+    CI_ERR_CUDA = 3,         /* a CUDA call failed (message names it)      */
+    CI_ERR_CAPACITY = 4,     /* a size beyond a documented limit           */
+    CI_ERR_TIMEOUT = 5,      /* a bounded wait gave up                     */
+    CI_NOT_READY = 6,        /* ci_poll: the request is still running      */
+    CI_ERR_CANCELLED = 7,    /* the request was cancelled                  */
+    CI_ERR_INTERNAL = 8,     /* an internal consistency check failed      */
+    CI_ERR_NOT_CONVERGED = 9,/* eigensolver hit its iteration limit        */
+    CI_ERR_STATE = 10        /* call order violated (e.g. no basis yet)    */
+} ci_status;
+
+/* Precision of the stored H values (and of the arithmetic that makes them).
+ * CI_F32: float values, FP32 accumulation of matrix-element terms.
+ * CI_F64: double values, FP64 accumulation (the plain FP64 form).
+ * CI_BF16_ROWSCALE: bf16 values times a per-row float scale (FP32 compute). */
+typedef enum { CI_F32 = 0, CI_F64 = 1, CI_BF16_ROWSCALE = 2 } ci_value_type;
+
+/* Where the two-body matrix elements come from. */
+typedef enum {
+    CI_TBME_TABLES = 0,  /* caller's flat tables v_pp, v_nn, v_pn            */
+    CI_TBME_SEED = 1     /* counter-based generator from tbme_seed (below)   */
+} ci_tbme_source;
+
+typedef struct ci_problem ci_problem;
+typedef struct ci_matrix ci_matrix;
+typedef struct ci_batch ci_batch;
+typedef struct ci_queue ci_queue;
+
+/* Problem description (Sec. 2: many-body basis of A = Z + N nucleons).
+ *
+ * n_sp        S, s.p. states per species, 1..128.
+ * sp_N        host [S]: HO shell N of each state (>= 0).
+ * sp_twom     host [S]: 2m of each state (odd).
+ * sp_energy   host [S]: one-body energies eps_a (both species).
+ * Z, N        protons and neutrons, 0..min(S, 16).
+ * nmax        Nmax cut on the total excess HO quanta q_p + q_n (q = sum of
+ *             shells minus the lowest possible sum); -1 for no cut.
+ * twoM        total 2M of the basis.
+ * tbme_source CI_TBME_TABLES or CI_TBME_SEED.
+ * tbme_dtype  CI_F32 or CI_F64: element type of v_pp / v_nn / v_pn.
+ * v_pp, v_nn, v_pn  flat tables V[((a*S+b)*S+c)*S+d], S^4 entries each, host
+ *             or device memory, read during ci_problem_create only.
+ * tbme_seed   with CI_TBME_SEED: V is drawn from SplitMix64 as follows.
+ *             Like pairs a<b have index P = b(b-1)/2 + a, pn pairs (a,b)
+ *             P = a*S + b; for pair indices P <= Q of pairs with equal
+ *             m_a+m_b, counter c = (ch<<32)|(P<<16)|Q with ch = 0 (pp),
+ *             1 (nn), 2 (pn); g = sum_{k=0..11} (mix(seed + (12c+k+1)*
+ *             0x9E3779B97F4A7C15) >> 32) * 2^-32 - 6 (exact in binary64);
+ *             V_abcd = V_cdab = g, completed by antisymmetry for pp, nn;
+ *             the float32 table is g rounded to nearest. */
+typedef struct {
+    int32_t n_sp;
+    const int32_t *sp_N;
+    const int32_t *sp_twom;
+    const double *sp_energy;
+    int32_t Z, N;
+    int32_t nmax;
+    int32_t twoM;
+    int32_t tbme_source;
+    int32_t tbme_dtype;
+    const void *v_pp, *v_nn, *v_pn;
+    uint64_t tbme_seed;
+} ci_problem_desc;
+
+/* ---------------------------------------------------------------- errors */
+
+/* Message of the last failed call on this thread ("" if none).  The
+ * pointer stays valid until the next call on this thread. */
+const char *ci_last_error(void);
+/* Static name of a status code. */
+const char *ci_status_string(ci_status s);
+/* Library version string. */
+const char *ci_version(void);
+
+/* ---------------------------------------------------------------- problem */
+
+/* Validate desc, copy the s.p. table, and stage the interaction on the
+ * current device as compact m-blocked tables.  Errors: INVALID_ARG (bad
+ * sizes, S > 128, Z or N > 16 or > S, missing tables), OOM, CUDA. */
+ci_status ci_problem_create(const ci_problem_desc *desc, ci_problem **out);
+void ci_problem_destroy(ci_problem *p);
+
+/* Step 1 of Fig. 1: enumerate the species determinant lists and the
+ * product basis (Sec. 2.1).  Each species list holds every A-particle
+ * determinant with q <= nmax, sorted by (2M, q, value of the bit string).
+ * The basis is p-major: for each proton determinant p (list order), every
+ * neutron determinant n with 2M_p + 2M_n = twoM and q_p + q_n <= nmax, in
+ * list order.  *dim receives the basis dimension.  Idempotent. */
+ci_status ci_enumerate_basis(ci_problem *p, int64_t *dim, void *stream);
+
+/* Size of a species list (species 0 = protons, 1 = neutrons) and its words
+ * per bit string. Needs ci_enumerate_basis. */
+ci_status ci_species_size(const ci_problem *p, int32_t species, int64_t *n, int32_t *words);
+/* Copy a species list to host arrays of cap >= n entries: bits [n][words],
+ * q [n], twoM [n]; any pointer may be NULL. */
+ci_status ci_get_species(const ci_problem *p, int32_t species, uint64_t *bits,
+                         int32_t *q, int32_t *twoM, int64_t cap);
+/* Copy the basis to host arrays [dim]: the proton and neutron list index of
+ * every basis state.  cap must be >= dim. */
+ci_status ci_get_basis(const ci_problem *p, int32_t *p_idx, int32_t *n_idx, int64_t cap);
+
+/* Fig. 1 lines 2-5 (tiles) at the species level: for every determinant s of
+ * a species, the determinants s' it can connect to through H, found by
+ * popcount(BIN(s) XOR BIN(s')) (Sec. 2.1, Listing 2).  Kept: all s' with
+ * 0 or 2 differing states, and s' with 4 differing states and 2M_s' =
+ * 2M_s (a two-particle move of one species leaves the other species fixed,
+ * so only equal-M partners can pair up in the basis).  Idempotent; called
+ * by ci_count_nnz if needed. */
+ci_status ci_species_filter(ci_problem *p, void *stream);
+/* Copy species `species`' connectivity to host arrays: ptr [n+1] (int64),
+ * idx [total] and d [total] (number of differing s.p. states: 0, 2, 4),
+ * each row in ascending s'.  *total receives the entry count; with idx ==
+ * NULL only *total and ptr are written. */
+ci_status ci_get_species_conn(const ci_problem *p, int32_t species, int64_t *ptr,
+                              int32_t *idx, int8_t *d, int64_t cap, int64_t *total);
+
+/* Fig. 1 lines 6-8: number of structurally nonzero entries of every row,
+ * i.e. basis states (p', n') within 4 differing s.p. states of the row
+ * state (Listing 2's test, p and n bits side by side).  *nnz receives the
+ * total; row_cnt (nullable, host or device, int32 [dim]) the per-row counts. */
+ci_status ci_count_nnz(ci_problem *p, int64_t *nnz, int32_t *row_cnt, void *stream);
+
+/* Eq. 1 / Alg. 1 (Sec. 2.2): exclusive prefix sum of n int32 counts into
+ * n+1 int64 offsets, offsets[0] = 0 and offsets[n] = total.  counts and
+ * offsets are device pointers; n >= 0 (n = 0 writes offsets[0] = 0).
+ * Uses a library-owned scratch buffer, grown on demand. */
+ci_status ci_exclusive_scan(const int32_t *counts, int64_t n, int64_t *offsets, void *stream);
+
+/* Fig. 1 lines 9-14 (Sec. 2.3, Listing 7): build H in CSR form on the
+ * device.  Row i holds every column j with at most 4 differing s.p. states
+ * (stored even when its value is 0), columns ascending.  H_ij = <Phi_i|H|Phi_j>
+ * by the Slater-Condon rules, the phase from masked popcounts.  The matrix
+ * is library-owned (int64 row_ptr [dim+1], int32 col [nnz], values of vtype;
+ * CI_BF16_ROWSCALE adds float row_scale [dim]). */
+ci_status ci_build_H(ci_problem *p, int32_t vtype, ci_matrix **out, void *stream);
+void ci_matrix_destroy(ci_matrix *m);
+ci_status ci_matrix_info(const ci_matrix *m, int64_t *dim, int64_t *nnz, int32_t *vtype);
+/* Copy H out to caller buffers (each host or device, each nullable):
+ * row_ptr [dim+1] int64, col [nnz] int32, val [nnz] (float, double or
+ * uint16 bf16 bits by vtype), row_scale [dim] float (BF16 only). */
+ci_status ci_matrix_export(const ci_matrix *m, int64_t *row_ptr, int32_t *col,
+                           void *val, float *row_scale, void *stream);
+
+/* Fig. 2 line 5 (Sec. 2): Y = H X for a block of nvec vectors (1..8), X and
+ * Y device arrays [dim][nvec] (float for CI_F32 / CI_BF16_ROWSCALE, double
+ * for CI_F64), not overlapping.  Each row is accumulated in the value
+ * precision in ascending column order within each of 32 lanes. */
+ci_status ci_apply_H(const ci_matrix *m, const void *X, void *Y, int32_t nvec, void *stream);
+
+/* ---------------------------------------------------------------- eigensolver */
+
+/* Options of ci_lowest_eigs; zero fields take the defaults in brackets. */
+typedef struct {
+    int32_t k;            /* eigenpairs wanted, 1..32                      [5]  */
+    int32_t block;        /* block size b, 1..8                            [8]  */
+    int32_t max_basis;    /* Krylov vectors kept before a thick restart  [128] */
+    int32_t max_iter;     /* block steps in total                       [2000] */
+    double tol;           /* converged when ||H x - theta x|| <= tol*||H||[1e-8] */
+    uint64_t seed;        /* seed of the start block                      [1]  */
+    int32_t reorth_passes;/* full Gram-Schmidt passes per step, 1..2      [2]  */
+    int32_t check_every;  /* block steps between convergence checks       [2]  */
+} ci_eig_opts;
+
+typedef struct {
+    int32_t iterations;   /* block steps taken                                  */
+    int32_t restarts;     /* thick restarts                                     */
+    int32_t converged;    /* number of converged pairs among the k              */
+    int32_t basis_size;   /* Krylov vectors at the end                          */
+    double hnorm_est;     /* estimate of ||H||_2 (largest |Ritz value| seen)    */
+    double residual[32];  /* ||H x_i - theta_i x_i||_2, FP64, with the stored H */
+    double seconds;       /* wall time of the call                              */
+} ci_eig_info;
+
+/* Fig. 1 line 15 (Sec. 2): lowest k eigenvalues of H by block Lanczos with
+ * full FP64 reorthogonalisation and thick restart.  SpMM in the matrix's
+ * precision, everything else in FP64.  evals: host [k], ascending.  evecs:
+ * nullable device double [dim][k], unit norm.  info: nullable.  Returns
+ * CI_ERR_NOT_CONVERGED (with the best estimates written) if max_iter is hit. */
+ci_status ci_lowest_eigs(const ci_matrix *m, const ci_eig_opts *opts, double *evals,
+                         double *evecs, ci_eig_info *info, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MFDCI_H */

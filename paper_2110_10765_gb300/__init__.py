@@ -1,0 +1,223 @@
+"""GB300 (sm_103a) library for the hot path of MFDn-style configuration
+interaction: bit-string basis, XOR+popcount filter, count -> scan -> fill of
+the sparse Hamiltonian, SpMM and block Lanczos, behind the C ABI of
+``include/mfdci.h``.
+
+This module is the thin Python binding: the functions carry the C names
+(``enumerate_basis``, ``count_nnz``, ``build_H``, ``apply_H``,
+``lowest_eigs``, ...) and only marshal arguments.  Device buffers are torch
+CUDA tensors (PyTorch provides memory and streams only); host arrays are
+numpy arrays.
+"""
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+from ._lib import (CIError, CI_F32, CI_F64, CI_BF16_ROWSCALE, CI_TBME_TABLES,
+                   CI_TBME_SEED, check, lib)
+
+__all__ = ["Problem", "Matrix", "exclusive_scan", "CIError", "CI_F32", "CI_F64",
+           "CI_BF16_ROWSCALE", "VTYPES", "lib", "current_stream"]
+
+VTYPES = {"f32": CI_F32, "f64": CI_F64, "bf16": CI_BF16_ROWSCALE}
+
+
+def current_stream():
+    """cudaStream_t of torch's current stream, as an int (0 = default)."""
+    import torch
+    return int(torch.cuda.current_stream().cuda_stream)
+
+
+def _stream(stream):
+    if stream is None:
+        return C.c_void_p(current_stream())
+    if hasattr(stream, "cuda_stream"):
+        return C.c_void_p(int(stream.cuda_stream))
+    return C.c_void_p(int(stream))
+
+
+def _ptr(x):
+    """Address of a numpy array or torch tensor (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return C.c_void_p(x.ctypes.data)
+    if not x.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return C.c_void_p(x.data_ptr())
+
+
+class Problem:
+    """A CI problem (``ci_problem``).
+
+    sp: dict with int arrays ``N``, ``twom`` (HO shell and 2m of each s.p.
+    state); eps: one-body energies; tables: dict ``pp``/``nn``/``pn`` of flat
+    S**4 numpy arrays or torch tensors (float32 or float64), or None with
+    ``seed`` to draw the TBMEs on the device.
+    """
+
+    def __init__(self, sp, Z, N, nmax, twoM, eps, tables=None, seed=None):
+        L = lib()
+        S = len(sp["N"])
+        self._keep = []
+        spN = np.ascontiguousarray(sp["N"], dtype=np.int32)
+        spm = np.ascontiguousarray(sp["twom"], dtype=np.int32)
+        e = np.ascontiguousarray(eps, dtype=np.float64)
+        self._keep += [spN, spm, e]
+        d = _lib.ProblemDesc()
+        d.n_sp = S
+        d.sp_N = spN.ctypes.data_as(C.POINTER(C.c_int32))
+        d.sp_twom = spm.ctypes.data_as(C.POINTER(C.c_int32))
+        d.sp_energy = e.ctypes.data_as(C.POINTER(C.c_double))
+        d.Z, d.N, d.nmax, d.twoM = int(Z), int(N), int(nmax), int(twoM)
+        if tables is not None:
+            d.tbme_source = CI_TBME_TABLES
+            arrs = []
+            for k in ("pp", "nn", "pn"):
+                t = tables[k]
+                if isinstance(t, np.ndarray):
+                    t = np.ascontiguousarray(t)
+                    dt = t.dtype
+                else:
+                    dt = np.dtype(str(t.dtype).replace("torch.", ""))
+                if dt not in (np.float32, np.float64):
+                    raise ValueError("TBME tables must be float32 or float64")
+                arrs.append(t)
+            d.tbme_dtype = CI_F32 if dt == np.float32 else CI_F64
+            d.v_pp, d.v_nn, d.v_pn = [_ptr(a) for a in arrs]
+            self._keep += arrs
+        else:
+            if seed is None:
+                raise ValueError("give TBME tables or a seed")
+            d.tbme_source = CI_TBME_SEED
+            d.tbme_dtype = CI_F32
+            d.tbme_seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+        h = C.c_void_p()
+        check(L.ci_problem_create(C.byref(d), C.byref(h)), "ci_problem_create")
+        self._h = h
+        self.S = S
+        self._keep = []  # the library copied what it keeps
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().ci_problem_destroy(h)
+            self._h = None
+
+    # -- Fig. 1 line 1 ---------------------------------------------------
+    def enumerate_basis(self, stream=None):
+        dim = C.c_int64()
+        check(lib().ci_enumerate_basis(self._h, C.byref(dim), _stream(stream)), "ci_enumerate_basis")
+        return dim.value
+
+    def species(self, s):
+        n, w = C.c_int64(), C.c_int32()
+        check(lib().ci_species_size(self._h, s, C.byref(n), C.byref(w)), "ci_species_size")
+        bits = np.zeros((n.value, w.value), np.uint64)
+        q = np.zeros(n.value, np.int32)
+        m = np.zeros(n.value, np.int32)
+        check(lib().ci_get_species(self._h, s, _ptr(bits), _ptr(q), _ptr(m), n.value), "ci_get_species")
+        return {"bits": bits, "q": q, "twoM": m}
+
+    def basis(self):
+        dim = self.enumerate_basis()
+        p = np.zeros(max(dim, 1), np.int32)
+        n = np.zeros(max(dim, 1), np.int32)
+        check(lib().ci_get_basis(self._h, _ptr(p), _ptr(n), dim), "ci_get_basis")
+        return p[:dim], n[:dim]
+
+    # -- Fig. 1 lines 2-5 ------------------------------------------------
+    def species_filter(self, stream=None):
+        check(lib().ci_species_filter(self._h, _stream(stream)), "ci_species_filter")
+
+    def species_conn(self, s):
+        n, w = C.c_int64(), C.c_int32()
+        check(lib().ci_species_size(self._h, s, C.byref(n), C.byref(w)), "ci_species_size")
+        ptr = np.zeros(n.value + 1, np.int64)
+        total = C.c_int64()
+        check(lib().ci_get_species_conn(self._h, s, _ptr(ptr), None, None, 0, C.byref(total)),
+              "ci_get_species_conn")
+        idx = np.zeros(max(total.value, 1), np.int32)
+        d = np.zeros(max(total.value, 1), np.int8)
+        check(lib().ci_get_species_conn(self._h, s, _ptr(ptr), _ptr(idx), _ptr(d), total.value,
+                                        C.byref(total)), "ci_get_species_conn")
+        return ptr, idx[: total.value], d[: total.value]
+
+    # -- Fig. 1 lines 6-8 ------------------------------------------------
+    def count_nnz(self, row_cnt=None, stream=None):
+        nnz = C.c_int64()
+        check(lib().ci_count_nnz(self._h, C.byref(nnz), _ptr(row_cnt), _stream(stream)), "ci_count_nnz")
+        return nnz.value
+
+    # -- Fig. 1 lines 9-14 -----------------------------------------------
+    def build_H(self, vtype="f32", stream=None):
+        h = C.c_void_p()
+        check(lib().ci_build_H(self._h, VTYPES.get(vtype, vtype), C.byref(h), _stream(stream)), "ci_build_H")
+        return Matrix(h)
+
+
+class Matrix:
+    """A library-owned CSR Hamiltonian (``ci_matrix``)."""
+
+    def __init__(self, handle):
+        self._h = handle
+        dim, nnz, vt = C.c_int64(), C.c_int64(), C.c_int32()
+        check(lib().ci_matrix_info(handle, C.byref(dim), C.byref(nnz), C.byref(vt)), "ci_matrix_info")
+        self.dim, self.nnz, self.vtype = dim.value, nnz.value, vt.value
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().ci_matrix_destroy(h)
+            self._h = None
+
+    @property
+    def value_dtype(self):
+        return {CI_F32: np.float32, CI_F64: np.float64, CI_BF16_ROWSCALE: np.uint16}[self.vtype]
+
+    def export(self, stream=None):
+        """Host copies (row_ptr int64, col int32, val, row_scale or None)."""
+        rp = np.zeros(self.dim + 1, np.int64)
+        col = np.zeros(max(self.nnz, 1), np.int32)
+        val = np.zeros(max(self.nnz, 1), self.value_dtype)
+        rs = np.zeros(max(self.dim, 1), np.float32) if self.vtype == CI_BF16_ROWSCALE else None
+        check(lib().ci_matrix_export(self._h, _ptr(rp), _ptr(col), _ptr(val), _ptr(rs), _stream(stream)),
+              "ci_matrix_export")
+        return rp, col[: self.nnz], val[: self.nnz], rs
+
+    def export_device(self, row_ptr, col, val, row_scale=None, stream=None):
+        check(lib().ci_matrix_export(self._h, _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(row_scale),
+                                     _stream(stream)), "ci_matrix_export")
+
+    # -- Fig. 2 line 5 -------------------------------------------------------
+    def apply_H(self, X, Y, stream=None):
+        """Y = H X for device tensors [dim, nvec] (nvec 1..8)."""
+        nvec = 1 if X.dim() == 1 else int(X.shape[1])
+        check(lib().ci_apply_H(self._h, _ptr(X), _ptr(Y), nvec, _stream(stream)), "ci_apply_H")
+
+    # -- Fig. 1 line 15 ------------------------------------------------------
+    def lowest_eigs(self, k=5, block=8, max_basis=0, max_iter=0, tol=0.0, seed=1, reorth_passes=0,
+                    check_every=0, evecs=None, stream=None, allow_unconverged=False):
+        """Lowest k eigenvalues (numpy, ascending) and the solve info dict.
+
+        evecs: optional device float64 tensor [dim, k] for the eigenvectors."""
+        o = _lib.EigOpts(k, block, max_basis, max_iter, tol, seed, reorth_passes, check_every)
+        ev = np.zeros(k, np.float64)
+        info = _lib.EigInfo()
+        st = lib().ci_lowest_eigs(self._h, C.byref(o), _ptr(ev), _ptr(evecs), C.byref(info), _stream(stream))
+        if not (allow_unconverged and st == _lib.CI_ERR_NOT_CONVERGED):
+            check(st, "ci_lowest_eigs")
+        out = {"iterations": info.iterations, "restarts": info.restarts, "converged": info.converged,
+               "basis_size": info.basis_size, "hnorm_est": info.hnorm_est,
+               "residual": list(info.residual)[:k], "seconds": info.seconds, "status": st}
+        return ev, out
+
+
+def exclusive_scan(counts, offsets, stream=None):
+    """Eq. 1 on the device: int32 counts [n] -> int64 offsets [n+1]."""
+    check(lib().ci_exclusive_scan(_ptr(counts), int(counts.numel()), _ptr(offsets), _stream(stream)),
+          "ci_exclusive_scan")

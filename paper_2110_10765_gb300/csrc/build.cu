@@ -1,0 +1,267 @@
+// Count -> scan -> fill of the Hamiltonian rows (Fig. 1 lines 6-14,
+// Sec. 2.2-2.3).  One warp owns one row (p, n).  The row's partners are
+// the proton connectivity list of p (ascending p') crossed with segments of
+// the neutron lists of n: for p' two states away, the L2(n) entries in the
+// 2M block that pairs with p' and within the Nmax cut; for p' = p, the
+// L4(n) entries; for p' four states away, n itself.  Columns therefore come
+// out ascending without sorting, and every lane writes its own slot of a
+// coalesced run (the deterministic counterpart of Listing 7's atomic
+// capture).
+#include "problem.cuh"
+
+namespace ci {
+
+template <class T>
+struct RowArgs {
+    int64_t dim;
+    int S, W, nq, nds, K, nmax, twoM;
+    const int32_t *row_p, *row_n;
+    const int64_t *p_row_base;
+    const int32_t *p_q, *p_twoM, *n_q, *n_twoM, *n_local;
+    const uint64_t *p_bits, *n_bits;
+    const int64_t *o_ptr, *l2_ptr, *l4_ptr;
+    const ConnEntry<T> *o_ent, *l2_ent, *l4_ent;
+    const int32_t *seg2, *seg4;
+    const T *Upn, *Wpn, *Dpn, *Cpn;
+    const int32_t *pn_row, *pn_col;
+    int32_t *row_cnt;          // count pass
+    const int64_t *row_ptr;    // fill pass
+    int32_t *col;
+    T *val;
+};
+
+// Segment of neutron partners that the proton partner entry e opens for
+// row (p, n).  kind 0: n itself (one entry); 1: L2(n)[beg, beg+len);
+// 2: L4(n)[0, len).
+template <class T>
+__device__ __forceinline__ void partner_segment(const RowArgs<T> &a, int p, int n, const ConnEntry<T> &e,
+                                                int &kind, int &beg, int &len) {
+    const int dc = info_dcode(e.info);
+    const int pp = e.tgt;
+    kind = 0; beg = 0; len = 0;
+    if (dc == 2) {  // four states moved among protons: the neutrons stay put
+        if (a.nmax < 0 || a.p_q[pp] + a.n_q[n] <= a.nmax) len = 1;
+        return;
+    }
+    int c = 0;
+    if (a.nmax >= 0) {
+        c = a.nmax - a.p_q[pp];
+        if (c < 0) return;
+        if (c > a.nq - 1) c = a.nq - 1;
+    }
+    if (dc == 0) {  // p' = p: every same-2M neutron partner of n
+        kind = 2;
+        len = a.seg4[(int64_t)n * a.nq + c];
+        return;
+    }
+    kind = 1;       // one proton moved: neutron partners at most one move away
+    int ds = ((a.twoM - a.p_twoM[pp]) - a.n_twoM[n]) / 2 + a.K;
+    if (ds < 0 || ds >= a.nds) return;
+    const int32_t *sg = a.seg2 + (int64_t)n * a.nds * a.nq;
+    beg = ds == 0 ? 0 : sg[(ds - 1) * a.nq + (a.nq - 1)];
+    int end = sg[ds * a.nq + c];
+    len = end > beg ? end - beg : 0;
+}
+
+__device__ __forceinline__ int warp_incl_scan_i32(int v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+    }
+    return v;
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_count_rows(RowArgs<T> a) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = warp; r < a.dim; r += nwarps) {
+        const int p = a.row_p[r], n = a.row_n[r];
+        const int64_t e0 = a.o_ptr[p], e1 = a.o_ptr[p + 1];
+        int cnt = 0;
+        for (int64_t e = e0 + lane; e < e1; e += 32) {
+            int kind, beg, len;
+            partner_segment<T>(a, p, n, a.o_ent[e], kind, beg, len);
+            cnt += len;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        if (lane == 0) a.row_cnt[r] = cnt;
+    }
+}
+
+// sum over the set bits k of a (W-word) bit string of tab[k]
+template <class T>
+__device__ __forceinline__ T sum_over_bits(const T *tab, uint64_t w0, uint64_t w1) {
+    T s = 0;
+    while (w0) { int k = __ffsll((long long)w0) - 1; w0 &= w0 - 1; s += tab[k]; }
+    while (w1) { int k = __ffsll((long long)w1) - 1; w1 &= w1 - 1; s += tab[64 + k]; }
+    return s;
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_fill_rows(RowArgs<T> a) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int S = a.S;
+    for (int64_t r = warp; r < a.dim; r += nwarps) {
+        const int p = a.row_p[r], n = a.row_n[r];
+        const uint64_t pb0 = a.p_bits[(int64_t)p * a.W], pb1 = a.W > 1 ? a.p_bits[(int64_t)p * a.W + 1] : 0;
+        const uint64_t nb0 = a.n_bits[(int64_t)n * a.W], nb1 = a.W > 1 ? a.n_bits[(int64_t)n * a.W + 1] : 0;
+        const int n_local = a.n_local[n];
+        const int64_t l2b = a.l2_ptr[n], l4b = a.l4_ptr[n];
+        const int64_t e0 = a.o_ptr[p], e1 = a.o_ptr[p + 1];
+        int64_t out = a.row_ptr[r];
+        for (int64_t c0 = e0; c0 < e1; c0 += 32) {
+            ConnEntry<T> ep;
+            int kind = 0, beg = 0, len = 0;
+            if (c0 + lane < e1) {
+                ep = a.o_ent[c0 + lane];
+                partner_segment<T>(a, p, n, ep, kind, beg, len);
+            } else {
+                ep.tgt = 0; ep.local = 0; ep.info = 0; ep.val = 0;
+            }
+            const int incl = warp_incl_scan_i32(len);
+            const int excl = incl - len;
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            for (int t0 = 0; t0 < total; t0 += 32) {
+                const int t = t0 + lane;
+                int j = 0;  // last lane whose segment starts at or before t
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    int v = __shfl_sync(0xffffffffu, excl, j + step);
+                    if (v <= t) j += step;
+                }
+                const int k = t - __shfl_sync(0xffffffffu, excl, j);
+                const int pt = __shfl_sync(0xffffffffu, ep.tgt, j);
+                const uint32_t pinfo = __shfl_sync(0xffffffffu, ep.info, j);
+                const T pval = __shfl_sync(0xffffffffu, ep.val, j);
+                const int jkind = __shfl_sync(0xffffffffu, kind, j);
+                const int jbeg = __shfl_sync(0xffffffffu, beg, j);
+                if (t < total) {
+                    const int64_t colbase = a.p_row_base[pt];
+                    int colv;
+                    T v;
+                    if (jkind == 0) {               // (4,0): n' = n
+                        colv = (int)colbase + n_local;
+                        v = pval;
+                    } else if (jkind == 1) {        // one proton move (a -> c)
+                        const ConnEntry<T> en = a.l2_ent[l2b + jbeg + k];
+                        colv = (int)colbase + en.local;
+                        const int ap = info_a(pinfo), cp = info_c(pinfo);
+                        if (info_dcode(en.info) == 0) {   // (2,0): neutrons are spectators
+                            const T *u = a.Upn + ((int64_t)cp * S + ap) * S;
+                            T h = pval + sum_over_bits<T>(u, nb0, nb1);
+                            v = info_neg(pinfo) ? -h : h;
+                        } else {                          // (2,2): V^pn_{c d, a b}
+                            const int an = info_a(en.info), cn = info_c(en.info);
+                            T w = a.Cpn[a.pn_row[cp * S + cn] + a.pn_col[ap * S + an]];
+                            v = (info_neg(pinfo) ^ info_neg(en.info)) ? -w : w;
+                        }
+                    } else {                        // p' = p
+                        const ConnEntry<T> en = a.l4_ent[l4b + k];
+                        colv = (int)colbase + en.local;
+                        const int dn = info_dcode(en.info);
+                        if (dn == 0) {                    // diagonal
+                            T h = pval + en.val;
+                            uint64_t x0 = pb0, x1 = pb1;
+                            while (x0 | x1) {
+                                int kp;
+                                if (x0) { kp = __ffsll((long long)x0) - 1; x0 &= x0 - 1; }
+                                else { kp = 64 + __ffsll((long long)x1) - 1; x1 &= x1 - 1; }
+                                h += sum_over_bits<T>(a.Dpn + (int64_t)kp * S, nb0, nb1);
+                            }
+                            v = h;
+                        } else if (dn == 1) {             // (0,2): protons are spectators
+                            const int an = info_a(en.info), cn = info_c(en.info);
+                            const T *w = a.Wpn + ((int64_t)cn * S + an) * S;
+                            T h = en.val + sum_over_bits<T>(w, pb0, pb1);
+                            v = info_neg(en.info) ? -h : h;
+                        } else {                          // (0,4)
+                            v = en.val;
+                        }
+                    }
+                    a.col[out + t] = colv;
+                    a.val[out + t] = v;
+                }
+            }
+            out += total;
+        }
+    }
+}
+
+template <class T>
+static RowArgs<T> row_args(Problem *p) {
+    Connectivity<T> &c = p->conn<T>();
+    Tables<T> &t = p->tables<T>();
+    SpeciesList &P = p->sp[0], &Nn = p->sp[1];
+    RowArgs<T> a;
+    a.dim = p->dim; a.S = p->S; a.W = P.W; a.nq = Nn.nq; a.nds = p->nds; a.K = p->K;
+    a.nmax = p->nmax; a.twoM = p->twoM;
+    a.row_p = p->d_row_p.ptr; a.row_n = p->d_row_n.ptr; a.p_row_base = p->d_p_row_base.ptr;
+    a.p_q = P.d_q.ptr; a.p_twoM = P.d_twoM.ptr; a.n_q = Nn.d_q.ptr; a.n_twoM = Nn.d_twoM.ptr;
+    a.n_local = Nn.d_local.ptr; a.p_bits = P.d_bits.ptr; a.n_bits = Nn.d_bits.ptr;
+    a.o_ptr = c.outer.ptr.ptr; a.l2_ptr = c.l2.ptr.ptr; a.l4_ptr = c.l4.ptr.ptr;
+    a.o_ent = c.outer.ent.ptr; a.l2_ent = c.l2.ent.ptr; a.l4_ent = c.l4.ent.ptr;
+    a.seg2 = c.seg2.ptr; a.seg4 = c.seg4.ptr;
+    a.Upn = t.Upn.ptr; a.Wpn = t.Wpn.ptr; a.Dpn = t.Dpn.ptr; a.Cpn = t.Cpn.ptr;
+    a.pn_row = p->pn_row.ptr; a.pn_col = p->pn_col.ptr;
+    a.row_cnt = p->row_cnt.ptr; a.row_ptr = nullptr; a.col = nullptr; a.val = nullptr;
+    return a;
+}
+
+static int row_grid(int64_t dim) { return grid_for(dim * 32, 256, sm_count() * 8); }
+
+template <class T>
+static void count_rows_t(Problem *p, cudaStream_t s) {
+    species_filter<T>(p, s);
+    p->row_cnt.alloc(p->dim);
+    if (p->dim > 0) {
+        RowArgs<T> a = row_args<T>(p);
+        k_count_rows<T><<<row_grid(p->dim), 256, 0, s>>>(a);
+        CI_CHECK_LAUNCH();
+    }
+    p->conn_prec = sizeof(T) == 4 ? 0 : 1;
+    p->counted = true;
+}
+
+void count_rows(Problem *p, int prec, cudaStream_t s) {
+    if (p->counted && p->conn_prec == prec) return;
+    if (prec == 0) count_rows_t<float>(p, s);
+    else count_rows_t<double>(p, s);
+}
+
+void build_matrix(Problem *p, int vtype, Matrix *m, cudaStream_t s) {
+    if (vtype != CI_F32 && vtype != CI_F64)
+        fail(CI_ERR_INVALID_ARG, "value type %d is not supported by ci_build_H", vtype);
+    const int prec = vtype == CI_F64 ? 1 : 0;
+    enumerate_basis(p, s);
+    count_rows(p, prec, s);
+    m->dim = p->dim;
+    m->vtype = vtype;
+    m->row_ptr.alloc(p->dim + 1);
+    exclusive_scan_i32(p->row_cnt.ptr, p->dim, m->row_ptr.ptr, p->scan_scratch, s);
+    CI_CUDA(cudaMemcpyAsync(&m->nnz, m->row_ptr.ptr + p->dim, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CI_CUDA(cudaStreamSynchronize(s));
+    p->nnz = m->nnz;
+    m->col.alloc(m->nnz);
+    const size_t esz = prec ? sizeof(double) : sizeof(float);
+    m->val.alloc(m->nnz * esz);
+    if (p->dim == 0) return;
+    if (prec == 0) {
+        RowArgs<float> a = row_args<float>(p);
+        a.row_ptr = m->row_ptr.ptr; a.col = m->col.ptr; a.val = (float *)m->val.ptr;
+        k_fill_rows<float><<<row_grid(p->dim), 256, 0, s>>>(a);
+    } else {
+        RowArgs<double> a = row_args<double>(p);
+        a.row_ptr = m->row_ptr.ptr; a.col = m->col.ptr; a.val = (double *)m->val.ptr;
+        k_fill_rows<double><<<row_grid(p->dim), 256, 0, s>>>(a);
+    }
+    CI_CHECK_LAUNCH();
+}
+
+}  // namespace ci

@@ -1,0 +1,138 @@
+// Shared internals of libmfdci: status handling, device buffers, bit helpers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/mfdci.h"
+
+namespace ci {
+
+// ------------------------------------------------------------------ errors
+
+// Exception used inside the library; converted to ci_status at the ABI.
+struct Error : std::runtime_error {
+    ci_status status;
+    Error(ci_status s, const std::string &m) : std::runtime_error(m), status(s) {}
+};
+
+[[noreturn]] void fail(ci_status s, const char *fmt, ...);
+void set_last_error(const std::string &m);
+
+#define CI_CUDA(call)                                                              \
+    do {                                                                           \
+        cudaError_t e_ = (call);                                                   \
+        if (e_ != cudaSuccess) {                                                   \
+            ::ci::fail(e_ == cudaErrorMemoryAllocation ? CI_ERR_OOM : CI_ERR_CUDA, \
+                       "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),     \
+                       __FILE__, __LINE__);                                        \
+        }                                                                          \
+    } while (0)
+
+#define CI_CHECK_LAUNCH() CI_CUDA(cudaGetLastError())
+
+// Run f and convert exceptions to a status (the body of every ABI call).
+template <class F>
+ci_status guard(F &&f) {
+    try {
+        f();
+        return CI_OK;
+    } catch (const Error &e) {
+        set_last_error(e.what());
+        return e.status;
+    } catch (const std::bad_alloc &) {
+        set_last_error("host allocation failed");
+        return CI_ERR_OOM;
+    } catch (const std::exception &e) {
+        set_last_error(e.what());
+        return CI_ERR_INTERNAL;
+    } catch (...) {
+        set_last_error("unknown exception");
+        return CI_ERR_INTERNAL;
+    }
+}
+
+// ------------------------------------------------------------------ memory
+
+// Owning device buffer (cudaMalloc / cudaFree).
+template <class T>
+struct DevBuf {
+    T *ptr = nullptr;
+    size_t n = 0;
+    DevBuf() = default;
+    explicit DevBuf(size_t count) { alloc(count); }
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    DevBuf(DevBuf &&o) noexcept : ptr(o.ptr), n(o.n) { o.ptr = nullptr; o.n = 0; }
+    DevBuf &operator=(DevBuf &&o) noexcept {
+        if (this != &o) { release(); ptr = o.ptr; n = o.n; o.ptr = nullptr; o.n = 0; }
+        return *this;
+    }
+    ~DevBuf() { release(); }
+    void alloc(size_t count) {
+        release();
+        if (count == 0) count = 1;  // keep a valid pointer for empty arrays
+        CI_CUDA(cudaMalloc(&ptr, count * sizeof(T)));
+        n = count;
+    }
+    void ensure(size_t count) { if (n < count || ptr == nullptr) alloc(count); }
+    void release() {
+        if (ptr) cudaFree(ptr);
+        ptr = nullptr;
+        n = 0;
+    }
+    void upload(const std::vector<T> &h, cudaStream_t s) {
+        alloc(h.size());
+        if (!h.empty())
+            CI_CUDA(cudaMemcpyAsync(ptr, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+    }
+    size_t bytes() const { return n * sizeof(T); }
+};
+
+bool is_device_pointer(const void *p);
+
+// Copy count elements to a destination that may be host or device memory.
+void copy_out(void *dst, const void *src_dev, size_t bytes, cudaStream_t s);
+
+inline int grid_for(int64_t work, int per_block, int cap = 152 * 16) {
+    int64_t g = (work + per_block - 1) / per_block;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (int)g;
+}
+
+int sm_count();
+
+// ------------------------------------------------------------------ bits
+
+constexpr int kMaxWords = 2;   // S <= 128
+constexpr int kMaxA = 16;      // particles per species
+
+// Bit string of one species determinant (W <= 2 words).
+struct Bits {
+    uint64_t w[kMaxWords];
+};
+
+__host__ __device__ inline int popc64(uint64_t x) {
+#ifdef __CUDA_ARCH__
+    return __popcll(x);
+#else
+    return __builtin_popcountll(x);
+#endif
+}
+
+// Mask of the states strictly below state o (o < 64*W).
+__host__ __device__ inline uint64_t below_mask_word(int o, int word) {
+    int lo = word * 64;
+    if (o <= lo) return 0ull;
+    if (o >= lo + 64) return ~0ull;
+    return (1ull << (o - lo)) - 1ull;
+}
+
+}  // namespace ci

@@ -1,0 +1,523 @@
+// Lowest eigenpairs of H (Fig. 1 line 15): block Lanczos with full FP64
+// reorthogonalisation (classical Gram-Schmidt, repeated), thick restart,
+// and a rank-revealing block QR that completes a deflated block with
+// random directions.  H is applied by the SpMM in the matrix's precision;
+// the Krylov basis, projections, Gram matrices, Ritz vectors and residuals
+// are FP64.  The projected matrix T = Q^T H Q is assembled on the host
+// from the Gram-Schmidt coefficients and diagonalised there (dense.h).
+#include <chrono>
+#include <cmath>
+
+#include "dense.h"
+#include "problem.cuh"
+
+namespace ci {
+
+// ------------------------------------------------------------------ kernels
+
+constexpr int kTnThreads = 256;   // 8 warps: warp v owns column v of B
+constexpr int kMaxNa = 256;       // columns of A in one product
+
+// part[blk][u][v] = sum_{i in rows of blk} A[i][u] B[i][v], u < na, v < nb <= 8
+__global__ void __launch_bounds__(kTnThreads) k_tn_partial(int64_t dim, const double *__restrict__ A, int lda, int na,
+                                                           const double *__restrict__ B, int ldb, int nb,
+                                                           double *__restrict__ part, int64_t rows_per_blk) {
+    const int v = threadIdx.x >> 5, u0 = threadIdx.x & 31;
+    double acc[kMaxNa / 32];
+#pragma unroll
+    for (int j = 0; j < kMaxNa / 32; ++j) acc[j] = 0.0;
+    const int64_t r0 = blockIdx.x * rows_per_blk;
+    const int64_t r1 = min(dim, r0 + rows_per_blk);
+    if (v < nb) {
+        for (int64_t i = r0; i < r1; ++i) {
+            const double bv = B[i * ldb + v];
+            const double *Ai = A + i * lda;
+#pragma unroll
+            for (int j = 0; j < kMaxNa / 32; ++j) {
+                const int u = u0 + 32 * j;
+                if (u < na) acc[j] = fma(Ai[u], bv, acc[j]);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kMaxNa / 32; ++j) {
+            const int u = u0 + 32 * j;
+            if (u < na) part[((int64_t)blockIdx.x * na + u) * nb + v] = acc[j];
+        }
+    }
+}
+
+// out[e] = sum_blk part[blk][e] in block order (deterministic)
+__global__ void k_reduce_partial(const double *__restrict__ part, int nblk, int n, double *__restrict__ out) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < nblk; ++b) s += part[(int64_t)b * n + e];
+        out[e] = s;
+    }
+}
+
+// W[i][v] = beta W[i][v] + alpha sum_u A[i][u] C[u][v]   (beta == 0: W not read)
+__global__ void __launch_bounds__(256) k_nn_update(int64_t dim, const double *__restrict__ A, int lda, int na,
+                                                   const double *__restrict__ C, int nb, double *__restrict__ W,
+                                                   int ldw, double alpha, double beta) {
+    __shared__ double Cs[kMaxNa * 8];
+    for (int e = threadIdx.x; e < na * nb; e += blockDim.x) Cs[e] = C[e];
+    __syncthreads();
+    const int64_t total = dim * nb;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / nb;
+        const int v = (int)(t % nb);
+        const double *Ai = A + i * lda;
+        double s = 0.0;
+        for (int u = 0; u < na; ++u) s = fma(Ai[u], Cs[u * nb + v], s);
+        double *w = W + i * ldw + v;
+        *w = beta == 0.0 ? alpha * s : fma(beta, *w, alpha * s);
+    }
+}
+
+__global__ void k_cvt_to_f32(int64_t dim, int nb, const double *__restrict__ src, int lds, float *__restrict__ dst) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < dim * nb; t += (int64_t)gridDim.x * blockDim.x)
+        dst[t] = (float)src[(t / nb) * lds + t % nb];
+}
+
+__global__ void k_cvt_to_f64(int64_t dim, int nb, const float *__restrict__ src, double *__restrict__ dst, int ldd) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < dim * nb; t += (int64_t)gridDim.x * blockDim.x)
+        dst[(t / nb) * ldd + t % nb] = (double)src[t];
+}
+
+__global__ void k_copy_cols(int64_t dim, int nb, const double *__restrict__ src, int lds, double *__restrict__ dst,
+                            int ldd) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < dim * nb; t += (int64_t)gridDim.x * blockDim.x)
+        dst[(t / nb) * ldd + t % nb] = src[(t / nb) * lds + t % nb];
+}
+
+__global__ void k_zero_cols(int64_t dim, int nb, double *dst, int ldd) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < dim * nb; t += (int64_t)gridDim.x * blockDim.x)
+        dst[(t / nb) * ldd + t % nb] = 0.0;
+}
+
+// Uniform(-1, 1) entries from SplitMix64 at position (i*nb + v) of stream seed.
+__global__ void k_random_cols(int64_t dim, int nb, uint64_t seed, double *dst, int ldd) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < dim * nb; t += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t z = seed + (uint64_t)(t + 1) * 0x9E3779B97F4A7C15ull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        dst[(t / nb) * ldd + t % nb] = (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+    }
+}
+
+// R = HX - X diag(theta): R[i][v] = HX[i][v] - theta[v] X[i][v]
+template <class TX>
+__global__ void k_residual(int64_t dim, int nb, const TX *__restrict__ HX, const double *__restrict__ X, int ldx,
+                           const double *__restrict__ theta, double *__restrict__ R) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < dim * nb; t += (int64_t)gridDim.x * blockDim.x) {
+        const int v = (int)(t % nb);
+        R[t] = (double)HX[t] - theta[v] * X[(t / nb) * ldx + v];
+    }
+}
+
+// ------------------------------------------------------------------ driver
+
+namespace {
+
+struct Solver {
+    const Matrix *H;
+    cudaStream_t s;
+    int64_t dim;
+    int b, k, mmax;
+    bool f64;
+    int nblk;
+    int64_t rows_per_blk;
+    DevBuf<double> Q, W, tmp, part, Cdev, Mdev, theta_dev;
+    DevBuf<float> X32, Y32;
+    DevBuf<double> X64;
+    double hnorm = 0.0;
+
+    Solver(const Matrix *H_, cudaStream_t s_, int b_, int k_, int mmax_)
+        : H(H_), s(s_), dim(H_->dim), b(b_), k(k_), mmax(mmax_), f64(H_->vtype == CI_F64) {
+        int sms = sm_count();
+        nblk = (int)std::min<int64_t>((int64_t)sms * 4, (dim + 63) / 64);
+        if (nblk < 1) nblk = 1;
+        rows_per_blk = (dim + nblk - 1) / nblk;
+        Q.alloc((size_t)dim * mmax);
+        W.alloc((size_t)dim * b);
+        tmp.alloc((size_t)dim * std::max(mmax, b));
+        part.alloc((size_t)nblk * kMaxNa * 8);
+        Cdev.alloc((size_t)kMaxNa * 8);
+        Mdev.alloc((size_t)kMaxNa * 8);
+        theta_dev.alloc(64);
+        if (f64) X64.alloc((size_t)dim * b);
+        else { X32.alloc((size_t)dim * b); Y32.alloc((size_t)dim * b); }
+    }
+
+    int grid(int64_t work) const { return grid_for(work, 256, sm_count() * 8); }
+
+    // C (na x nb) = A^T B over all rows; result in Cout (device) and, if
+    // host != null, copied to host.
+    void tn(const double *A, int lda, int na, const double *B, int ldb, int nb, double *Cout,
+            std::vector<double> *host) {
+        k_tn_partial<<<nblk, kTnThreads, 0, s>>>(dim, A, lda, na, B, ldb, nb, part.ptr, rows_per_blk);
+        k_reduce_partial<<<grid_for(na * nb, 128, 64), 128, 0, s>>>(part.ptr, nblk, na * nb, Cout);
+        CI_CHECK_LAUNCH();
+        if (host) {
+            host->resize((size_t)na * nb);
+            CI_CUDA(cudaMemcpyAsync(host->data(), Cout, sizeof(double) * na * nb, cudaMemcpyDeviceToHost, s));
+            CI_CUDA(cudaStreamSynchronize(s));
+        }
+    }
+
+    void nn(const double *A, int lda, int na, const double *C, int nb, double *Wout, int ldw, double alpha,
+            double beta) {
+        k_nn_update<<<grid(dim * nb), 256, 0, s>>>(dim, A, lda, na, C, nb, Wout, ldw, alpha, beta);
+        CI_CHECK_LAUNCH();
+    }
+
+    void upload(const std::vector<double> &h, double *d) {
+        CI_CUDA(cudaMemcpyAsync(d, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice, s));
+    }
+
+    // Wout [dim][nb] (contiguous) = H V, V with leading dimension ldv.
+    void apply(const double *V, int ldv, int nb, double *Wout) {
+        if (f64) {
+            k_copy_cols<<<grid(dim * nb), 256, 0, s>>>(dim, nb, V, ldv, X64.ptr, nb);
+            apply_matrix(H, X64.ptr, Wout, nb, s);
+        } else {
+            k_cvt_to_f32<<<grid(dim * nb), 256, 0, s>>>(dim, nb, V, ldv, X32.ptr);
+            apply_matrix(H, X32.ptr, Y32.ptr, nb, s);
+            k_cvt_to_f64<<<grid(dim * nb), 256, 0, s>>>(dim, nb, Y32.ptr, Wout, nb);
+        }
+        CI_CHECK_LAUNCH();
+    }
+
+    // Project the block Wb [dim][nb] (ld nb) against Q[:, 0:m], `passes`
+    // times; returns the summed coefficients (m x nb, host).
+    void project(double *Wb, int nb, int m, int passes, std::vector<double> *coef) {
+        if (coef) coef->assign((size_t)m * nb, 0.0);
+        if (m == 0) return;
+        std::vector<double> c;
+        for (int p = 0; p < passes; ++p) {
+            tn(Q.ptr, mmax, m, Wb, nb, nb, Cdev.ptr, coef ? &c : nullptr);
+            nn(Q.ptr, mmax, m, Cdev.ptr, nb, Wb, nb, -1.0, 1.0);
+            if (coef)
+                for (size_t e = 0; e < c.size(); ++e) (*coef)[e] += c[e];
+        }
+    }
+
+    // Orthonormalise Wb [dim][b] (already orthogonal to Q[:, 0:m]) into
+    // Q[:, m:m+b].  R (b x b, row-major) receives the coupling Wb = V R.
+    // Directions below the deflation threshold are replaced by random
+    // vectors orthogonal to Q and V (their coupling is zero).
+    void block_qr(double *Wb, int m, uint64_t seed, std::vector<double> &R) {
+        std::vector<double> G, w, U;
+        tn(Wb, b, b, Wb, b, b, Cdev.ptr, &G);
+        sym_eig(b, G, w, U);
+        const double lmax = std::max(w[b - 1], 0.0);
+        const double scale = std::max(hnorm, std::sqrt(lmax));
+        const double thr = 1e-20 * scale * scale + 1e-300;
+        std::vector<double> M((size_t)b * b, 0.0);
+        R.assign((size_t)b * b, 0.0);
+        int r = 0;
+        for (int i = b - 1; i >= 0; --i) {  // largest first
+            if (w[i] <= thr) break;
+            double sq = std::sqrt(w[i]);
+            for (int a = 0; a < b; ++a) {
+                M[(size_t)a * b + r] = U[(size_t)a * b + i] / sq;
+                R[(size_t)r * b + a] = U[(size_t)a * b + i] * sq;
+            }
+            ++r;
+        }
+        double *V = Q.ptr + m;
+        upload(M, Mdev.ptr);
+        nn(Wb, b, b, Mdev.ptr, b, V, mmax, 1.0, 0.0);
+        if (r < b) {
+            // random completion of columns r..b-1
+            double *Vr = tmp.ptr;
+            int nr = b - r;
+            k_random_cols<<<grid(dim * nr), 256, 0, s>>>(dim, nr, seed, Vr, nr);
+            CI_CHECK_LAUNCH();
+            for (int pass = 0; pass < 2; ++pass) {
+                if (m > 0) {
+                    tn(Q.ptr, mmax, m, Vr, nr, nr, Cdev.ptr, nullptr);
+                    nn(Q.ptr, mmax, m, Cdev.ptr, nr, Vr, nr, -1.0, 1.0);
+                }
+                if (r > 0) {
+                    tn(V, mmax, r, Vr, nr, nr, Cdev.ptr, nullptr);
+                    nn(V, mmax, r, Cdev.ptr, nr, Vr, nr, -1.0, 1.0);
+                }
+            }
+            k_copy_cols<<<grid(dim * nr), 256, 0, s>>>(dim, nr, Vr, nr, V + r, mmax);
+            CI_CHECK_LAUNCH();
+        }
+        // second pass: V <- V G2^{-1/2}, R <- G2^{1/2} R
+        tn(V, mmax, b, V, mmax, b, Cdev.ptr, &G);
+        sym_eig(b, G, w, U);
+        std::vector<double> Mi((size_t)b * b, 0.0), Ms((size_t)b * b, 0.0);
+        for (int a = 0; a < b; ++a)
+            for (int c = 0; c < b; ++c) {
+                double x = 0.0, y = 0.0;
+                for (int i = 0; i < b; ++i) {
+                    double wi = std::max(w[i], 1e-300);
+                    x += U[(size_t)a * b + i] * U[(size_t)c * b + i] / std::sqrt(wi);
+                    y += U[(size_t)a * b + i] * U[(size_t)c * b + i] * std::sqrt(wi);
+                }
+                Mi[(size_t)a * b + c] = x;
+                Ms[(size_t)a * b + c] = y;
+            }
+        upload(Mi, Mdev.ptr);
+        nn(V, mmax, b, Mdev.ptr, b, tmp.ptr, b, 1.0, 0.0);
+        k_copy_cols<<<grid(dim * b), 256, 0, s>>>(dim, b, tmp.ptr, b, V, mmax);
+        CI_CHECK_LAUNCH();
+        std::vector<double> R2((size_t)b * b, 0.0);
+        for (int a = 0; a < b; ++a)
+            for (int c = 0; c < b; ++c) {
+                double x = 0.0;
+                for (int i = 0; i < b; ++i) x += Ms[(size_t)a * b + i] * R[(size_t)i * b + c];
+                R2[(size_t)a * b + c] = x;
+            }
+        R.swap(R2);
+    }
+};
+
+// Ritz analysis of T[0:m, 0:m] with last-block coupling R (b x b).
+struct Ritz {
+    std::vector<double> theta, S, res;
+};
+
+Ritz ritz(const std::vector<double> &T, int ldt, int m, int b, const std::vector<double> &R, int k) {
+    Ritz o;
+    std::vector<double> A((size_t)m * m);
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) A[(size_t)i * m + j] = 0.5 * (T[(size_t)i * ldt + j] + T[(size_t)j * ldt + i]);
+    sym_eig(m, A, o.theta, o.S);
+    o.res.assign(std::min(k, m), 0.0);
+    for (int i = 0; i < (int)o.res.size(); ++i) {
+        double ss = 0.0;
+        for (int r = 0; r < b; ++r) {
+            double x = 0.0;
+            for (int c = 0; c < b; ++c) x += R[(size_t)r * b + c] * o.S[(size_t)(m - b + c) * m + i];
+            ss += x * x;
+        }
+        o.res[i] = std::sqrt(ss);
+    }
+    return o;
+}
+
+}  // namespace
+
+void lowest_eigs(const Matrix *H, const ci_eig_opts *opts_in, double *evals, double *evecs, ci_eig_info *info,
+                 cudaStream_t s) {
+    auto t_start = std::chrono::steady_clock::now();
+    if (!H) fail(CI_ERR_INVALID_ARG, "matrix is NULL");
+    if (!evals) fail(CI_ERR_INVALID_ARG, "evals is NULL");
+    ci_eig_opts o = opts_in ? *opts_in : ci_eig_opts{};
+    if (o.k == 0) o.k = 5;
+    if (o.block == 0) o.block = 8;
+    if (o.max_basis == 0) o.max_basis = 128;
+    if (o.max_iter == 0) o.max_iter = 2000;
+    if (o.tol == 0.0) o.tol = H->vtype == CI_F64 ? 1e-10 : 1e-7;
+    if (o.seed == 0) o.seed = 1;
+    if (o.reorth_passes == 0) o.reorth_passes = 2;
+    if (o.check_every == 0) o.check_every = 2;
+    if (o.k < 1 || o.k > 32) fail(CI_ERR_INVALID_ARG, "k must be 1..32");
+    if (o.block < 1 || o.block > 8) fail(CI_ERR_INVALID_ARG, "block must be 1..8");
+    if (o.reorth_passes < 1 || o.reorth_passes > 2) fail(CI_ERR_INVALID_ARG, "reorth_passes must be 1..2");
+    if (o.max_basis > kMaxNa) fail(CI_ERR_CAPACITY, "max_basis above %d", kMaxNa);
+    const int64_t dim = H->dim;
+    if (dim < o.k) fail(CI_ERR_INVALID_ARG, "k = %d exceeds the dimension %lld", o.k, (long long)dim);
+    int b = o.block;
+    int mmax = (o.max_basis / b) * b;
+    if (mmax < o.k + 2 * b) fail(CI_ERR_INVALID_ARG, "max_basis must be >= k + 2*block");
+    const int k = o.k;
+    ci_eig_info inf{};
+
+    // small spaces: Rayleigh-Ritz on the whole space (Q = I, so the
+    // projection Q^T H Q is H itself, applied to identity blocks)
+    if (dim <= (int64_t)mmax + 2 * b) {
+        const int n = (int)dim;
+        const int bb = std::min<int>(b, n);
+        DevBuf<double> E((size_t)n * bb), Wd((size_t)n * bb);
+        DevBuf<float> E32((size_t)n * bb), W32((size_t)n * bb);
+        std::vector<double> T((size_t)n * n, 0.0), Eh((size_t)n * bb), Wh((size_t)n * bb);
+        for (int j0 = 0; j0 < n; j0 += bb) {
+            int nb = std::min(bb, n - j0);
+            std::fill(Eh.begin(), Eh.end(), 0.0);
+            for (int v = 0; v < nb; ++v) Eh[(size_t)(j0 + v) * nb + v] = 1.0;
+            if (H->vtype == CI_F64) {
+                CI_CUDA(cudaMemcpyAsync(E.ptr, Eh.data(), sizeof(double) * n * nb, cudaMemcpyHostToDevice, s));
+                apply_matrix(H, E.ptr, Wd.ptr, nb, s);
+                CI_CUDA(cudaMemcpyAsync(Wh.data(), Wd.ptr, sizeof(double) * n * nb, cudaMemcpyDeviceToHost, s));
+                CI_CUDA(cudaStreamSynchronize(s));
+            } else {
+                std::vector<float> Ef(Eh.begin(), Eh.begin() + (size_t)n * nb), Wf((size_t)n * nb);
+                CI_CUDA(cudaMemcpyAsync(E32.ptr, Ef.data(), sizeof(float) * n * nb, cudaMemcpyHostToDevice, s));
+                apply_matrix(H, E32.ptr, W32.ptr, nb, s);
+                CI_CUDA(cudaMemcpyAsync(Wf.data(), W32.ptr, sizeof(float) * n * nb, cudaMemcpyDeviceToHost, s));
+                CI_CUDA(cudaStreamSynchronize(s));
+                for (size_t e = 0; e < Wf.size(); ++e) Wh[e] = Wf[e];
+            }
+            for (int i = 0; i < n; ++i)
+                for (int v = 0; v < nb; ++v) T[(size_t)i * n + j0 + v] = Wh[(size_t)i * nb + v];
+        }
+        std::vector<double> A((size_t)n * n), w, Z;
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) A[(size_t)i * n + j] = 0.5 * (T[(size_t)i * n + j] + T[(size_t)j * n + i]);
+        sym_eig(n, A, w, Z);
+        for (int i = 0; i < k; ++i) evals[i] = w[i];
+        if (evecs) {
+            std::vector<double> X((size_t)n * k);
+            for (int r = 0; r < n; ++r)
+                for (int i = 0; i < k; ++i) X[(size_t)r * k + i] = Z[(size_t)r * n + i];
+            CI_CUDA(cudaMemcpyAsync(evecs, X.data(), sizeof(double) * n * k, cudaMemcpyHostToDevice, s));
+        }
+        // residuals of the Ritz pairs against the dense projection (exact space)
+        for (int i = 0; i < k; ++i) {
+            double ss = 0.0;
+            for (int r = 0; r < n; ++r) {
+                double x = 0.0;
+                for (int c = 0; c < n; ++c) x += T[(size_t)r * n + c] * Z[(size_t)c * n + i];
+                x -= w[i] * Z[(size_t)r * n + i];
+                ss += x * x;
+            }
+            inf.residual[i] = std::sqrt(ss);
+        }
+        inf.iterations = (n + bb - 1) / bb;
+        inf.converged = k;
+        inf.basis_size = n;
+        inf.hnorm_est = std::max(std::fabs(w.front()), std::fabs(w.back()));
+        CI_CUDA(cudaStreamSynchronize(s));
+        inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+        if (info) *info = inf;
+        return;
+    }
+
+    Solver sv(H, s, b, k, mmax);
+    std::vector<double> T((size_t)mmax * mmax, 0.0);
+    std::vector<double> R, coef;
+    // start block
+    k_random_cols<<<sv.grid(dim * b), 256, 0, s>>>(dim, b, o.seed, sv.W.ptr, b);
+    CI_CHECK_LAUNCH();
+    sv.block_qr(sv.W.ptr, 0, o.seed ^ 0x5bd1e995ull, R);
+    int m_cur = b, j0 = 0;
+    int it = 0, since_check = 0;
+    bool converged = false;
+    Ritz last;
+    int m_act = 0;
+    std::vector<double> Rlast;
+    while (true) {
+        // W = H V_j, orthogonalised against the whole basis
+        sv.apply(sv.Q.ptr + j0, mmax, b, sv.W.ptr);
+        sv.project(sv.W.ptr, b, m_cur, o.reorth_passes, &coef);
+        for (int i = 0; i < j0; ++i)
+            for (int v = 0; v < b; ++v) {
+                T[(size_t)i * mmax + j0 + v] = coef[(size_t)i * b + v];
+                T[(size_t)(j0 + v) * mmax + i] = coef[(size_t)i * b + v];
+            }
+        for (int u = 0; u < b; ++u)  // diagonal block, symmetrised
+            for (int v = 0; v < b; ++v)
+                T[(size_t)(j0 + u) * mmax + j0 + v] =
+                    0.5 * (coef[(size_t)(j0 + u) * b + v] + coef[(size_t)(j0 + v) * b + u]);
+        ++it;
+        // next block
+        sv.block_qr(sv.W.ptr, m_cur, o.seed + 0x9E37ull * (uint64_t)(it + 1), Rlast);
+        for (int r = 0; r < b; ++r)
+            for (int c = 0; c < b; ++c) {
+                T[(size_t)(m_cur + r) * mmax + j0 + c] = Rlast[(size_t)r * b + c];
+                T[(size_t)(j0 + c) * mmax + m_cur + r] = Rlast[(size_t)r * b + c];
+            }
+        m_act = m_cur;
+        j0 = m_cur;
+        m_cur += b;
+        const bool full = m_cur + b > mmax;
+        ++since_check;
+        if (since_check >= o.check_every || full || it >= o.max_iter) {
+            since_check = 0;
+            last = ritz(T, mmax, m_act, b, Rlast, k);
+            sv.hnorm = std::max(sv.hnorm, std::max(std::fabs(last.theta.front()), std::fabs(last.theta.back())));
+            converged = (int)last.res.size() >= k;
+            for (int i = 0; i < k && converged; ++i)
+                if (last.res[i] > o.tol * sv.hnorm) converged = false;
+            if (converged || it >= o.max_iter) break;
+        }
+        if (full) {
+            // thick restart: keep the lowest Ritz vectors and the new block
+            int keep = std::max(k + b, m_act / 2);
+            keep = std::min(keep, m_act - b);
+            std::vector<double> Sk((size_t)m_act * keep);
+            for (int r = 0; r < m_act; ++r)
+                for (int i = 0; i < keep; ++i) Sk[(size_t)r * keep + i] = last.S[(size_t)r * m_act + i];
+            for (int c0 = 0; c0 < keep; c0 += 8) {
+                int nc = std::min(8, keep - c0);
+                std::vector<double> Sc((size_t)m_act * nc);
+                for (int r = 0; r < m_act; ++r)
+                    for (int i = 0; i < nc; ++i) Sc[(size_t)r * nc + i] = Sk[(size_t)r * keep + c0 + i];
+                sv.upload(Sc, sv.Mdev.ptr);
+                sv.nn(sv.Q.ptr, mmax, m_act, sv.Mdev.ptr, nc, sv.tmp.ptr + c0, keep, 1.0, 0.0);
+            }
+            // new block Q[:, m_act:m_act+b] -> Q[:, keep:keep+b]; Ritz vectors -> Q[:, 0:keep]
+            k_copy_cols<<<sv.grid(dim * b), 256, 0, s>>>(dim, b, sv.Q.ptr + m_act, mmax, sv.Q.ptr + keep, mmax);
+            k_copy_cols<<<sv.grid(dim * keep), 256, 0, s>>>(dim, keep, sv.tmp.ptr, keep, sv.Q.ptr, mmax);
+            CI_CHECK_LAUNCH();
+            std::fill(T.begin(), T.end(), 0.0);
+            for (int i = 0; i < keep; ++i) T[(size_t)i * mmax + i] = last.theta[i];
+            for (int r = 0; r < b; ++r)
+                for (int i = 0; i < keep; ++i) {
+                    double x = 0.0;
+                    for (int c = 0; c < b; ++c) x += Rlast[(size_t)r * b + c] * last.S[(size_t)(m_act - b + c) * m_act + i];
+                    T[(size_t)(keep + r) * mmax + i] = x;
+                    T[(size_t)i * mmax + keep + r] = x;
+                }
+            m_cur = keep + b;
+            j0 = keep;
+            ++inf.restarts;
+        }
+    }
+    // Ritz pairs, eigenvectors and FP64 residuals with the stored H
+    for (int i = 0; i < k; ++i) evals[i] = last.theta[i];
+    std::vector<double> Sk((size_t)m_act * k);
+    for (int r = 0; r < m_act; ++r)
+        for (int i = 0; i < k; ++i) Sk[(size_t)r * k + i] = last.S[(size_t)r * m_act + i];
+    double *X = sv.tmp.ptr;  // [dim][k]
+    for (int c0 = 0; c0 < k; c0 += 8) {
+        int nc = std::min(8, k - c0);
+        std::vector<double> Sc((size_t)m_act * nc);
+        for (int r = 0; r < m_act; ++r)
+            for (int i = 0; i < nc; ++i) Sc[(size_t)r * nc + i] = Sk[(size_t)r * k + c0 + i];
+        sv.upload(Sc, sv.Mdev.ptr);
+        sv.nn(sv.Q.ptr, mmax, m_act, sv.Mdev.ptr, nc, X + c0, k, 1.0, 0.0);
+    }
+    for (int c0 = 0; c0 < k; c0 += b) {
+        int nc = std::min(b, k - c0);
+        sv.apply(X + c0, k, nc, sv.W.ptr);  // W [dim][nc] = H x
+        std::vector<double> th(last.theta.begin() + c0, last.theta.begin() + c0 + nc);
+        sv.upload(th, sv.theta_dev.ptr);
+        double *Rr = sv.Q.ptr;  // basis no longer needed: scratch [dim][nc]
+        k_residual<double><<<sv.grid(dim * nc), 256, 0, s>>>(dim, nc, sv.W.ptr, X + c0, k, sv.theta_dev.ptr, Rr);
+        CI_CHECK_LAUNCH();
+        std::vector<double> G;
+        sv.tn(Rr, nc, nc, Rr, nc, nc, sv.Cdev.ptr, &G);
+        for (int i = 0; i < nc; ++i) inf.residual[c0 + i] = std::sqrt(std::max(G[(size_t)i * nc + i], 0.0));
+    }
+    if (evecs) CI_CUDA(cudaMemcpyAsync(evecs, X, sizeof(double) * dim * k, cudaMemcpyDeviceToDevice, s));
+    CI_CUDA(cudaStreamSynchronize(s));
+    inf.iterations = it;
+    inf.basis_size = m_act;
+    inf.hnorm_est = sv.hnorm;
+    inf.converged = 0;
+    for (int i = 0; i < k; ++i)
+        if (last.res[i] <= o.tol * sv.hnorm) ++inf.converged;
+    inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+    if (info) *info = inf;
+    if (!converged) fail(CI_ERR_NOT_CONVERGED, "block Lanczos stopped after %d steps (%d of %d converged)", it,
+                         inf.converged, k);
+}
+
+}  // namespace ci
+
+extern "C" ci_status ci_lowest_eigs(const ci_matrix *m, const ci_eig_opts *opts, double *evals, double *evecs,
+                                    ci_eig_info *info, void *stream) {
+    return ci::guard([&] {
+        if (!m) ci::fail(CI_ERR_INVALID_ARG, "matrix is NULL");
+        ci::lowest_eigs(&m->impl, opts, evals, evecs, info, reinterpret_cast<cudaStream_t>(stream));
+    });
+}

@@ -1,0 +1,448 @@
+// Problem set-up: validation, the host planner of the species lists and the
+// product basis (Fig. 1 line 1), and the staging of the interaction into
+// compact device tables.
+#include <algorithm>
+#include <cstring>
+#include <functional>
+#include <map>
+#include <numeric>
+
+#include "problem.cuh"
+
+namespace ci {
+
+// ------------------------------------------------------------------ errors
+
+static thread_local std::string g_last_error;
+
+void set_last_error(const std::string &m) { g_last_error = m; }
+const char *last_error_cstr() { return g_last_error.c_str(); }
+
+void fail(ci_status s, const char *fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    throw Error(s, buf);
+}
+
+bool is_device_pointer(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+void copy_out(void *dst, const void *src_dev, size_t bytes, cudaStream_t s) {
+    if (!dst || bytes == 0) return;
+    CI_CUDA(cudaMemcpyAsync(dst, src_dev, bytes, cudaMemcpyDefault, s));
+}
+
+int sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        CI_CUDA(cudaGetDevice(&dev));
+        CI_CUDA(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+    }
+    return n;
+}
+
+// ------------------------------------------------------------------ TBME source
+
+// Parameters every staging thread needs to fetch V_abcd of one channel.
+struct TbmeSrc {
+    int S;
+    int source;         // CI_TBME_TABLES / CI_TBME_SEED
+    int dtype;          // CI_F32 / CI_F64 of the flat table
+    const void *flat;   // S^4 entries (tables) or null
+    uint64_t seed;
+    int channel;        // 0 pp, 1 nn, 2 pn
+    const int32_t *twom;
+};
+
+__device__ __forceinline__ uint64_t splitmix64_mix(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// g(seed, channel, P, Q) of the counter-based recipe in mfdci.h; the
+// integer sum is exact, so the double result is exact.
+__device__ double tbme_draw(uint64_t seed, int channel, uint32_t P, uint32_t Q) {
+    uint64_t c = ((uint64_t)channel << 32) | ((uint64_t)P << 16) | (uint64_t)Q;
+    uint64_t acc = 0;
+    for (int k = 0; k < 12; ++k)
+        acc += splitmix64_mix(seed + (12ull * c + (uint64_t)(k + 1)) * 0x9E3779B97F4A7C15ull) >> 32;
+    return (double)acc * (1.0 / 4294967296.0) - 6.0;
+}
+
+// V_abcd of one channel, exact in binary64 (a float table is widened).
+__device__ double tbme_fetch(const TbmeSrc &t, int a, int b, int c, int d) {
+    if (t.source == CI_TBME_TABLES) {
+        int64_t i = (((int64_t)a * t.S + b) * t.S + c) * t.S + d;
+        return t.dtype == CI_F32 ? (double)((const float *)t.flat)[i]
+                                 : ((const double *)t.flat)[i];
+    }
+    if (t.twom[a] + t.twom[b] != t.twom[c] + t.twom[d]) return 0.0;
+    if (t.channel == 2) {
+        uint32_t P = (uint32_t)(a * t.S + b), Q = (uint32_t)(c * t.S + d);
+        return P <= Q ? tbme_draw(t.seed, 2, P, Q) : tbme_draw(t.seed, 2, Q, P);
+    }
+    if (a == b || c == d) return 0.0;
+    double s = 1.0;
+    if (a > b) { int x = a; a = b; b = x; s = -s; }
+    if (c > d) { int x = c; c = d; d = x; s = -s; }
+    uint32_t P = (uint32_t)(b * (b - 1) / 2 + a), Q = (uint32_t)(d * (d - 1) / 2 + c);
+    return s * (P <= Q ? tbme_draw(t.seed, t.channel, P, Q) : tbme_draw(t.seed, t.channel, Q, P));
+}
+
+// Value of V in the table precision: a float table (or draw) rounds to
+// nearest float when T = float.
+template <class T>
+__device__ __forceinline__ T to_prec(double v, const TbmeSrc &t) {
+    (void)t;
+    return (T)v;
+}
+
+// Compact pair-pair blocks: entry e of group g is row pair iP, column pair
+// iQ with V[row pair][col pair].
+template <class T>
+__global__ void k_stage_compact(TbmeSrc t, int G, const int64_t *grp_off, const int32_t *grp_n,
+                                const int32_t *grp_pairs, const int32_t *pairs, int64_t total,
+                                T *out) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = G - 1;
+        while (lo < hi) {  // last group with grp_off <= e
+            int mid = (lo + hi + 1) >> 1;
+            if (grp_off[mid] <= e) lo = mid; else hi = mid - 1;
+        }
+        int64_t r = e - grp_off[lo];
+        int n = grp_n[lo];
+        int iP = (int)(r / n), iQ = (int)(r % n);
+        int pr = pairs[grp_pairs[lo] + iP], pc = pairs[grp_pairs[lo] + iQ];
+        int c = pr / t.S, d = pr % t.S, a = pc / t.S, b = pc % t.S;
+        out[e] = to_prec<T>(tbme_fetch(t, c, d, a, b), t);
+    }
+}
+
+// U[(c*S+a)*S+k] = V_{ck,ak};  with swap: W[(d*S+b)*S+k] = V_{kd,kb}.
+template <class T>
+__global__ void k_stage_spectator(TbmeSrc t, int swap, T *out) {
+    int64_t total = (int64_t)t.S * t.S * t.S;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int k = (int)(e % t.S);
+        int a = (int)((e / t.S) % t.S);
+        int c = (int)(e / ((int64_t)t.S * t.S));
+        double v = swap ? tbme_fetch(t, k, c, k, a) : tbme_fetch(t, c, k, a, k);
+        out[e] = to_prec<T>(v, t);
+    }
+}
+
+// D[a*S+b] = V_abab
+template <class T>
+__global__ void k_stage_diag(TbmeSrc t, T *out) {
+    int total = t.S * t.S;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+        int a = e / t.S, b = e % t.S;
+        out[e] = to_prec<T>(tbme_fetch(t, a, b, a, b), t);
+    }
+}
+
+// ------------------------------------------------------------------ pair maps
+
+struct PairGroups {
+    std::vector<int64_t> grp_off;   // [G+1] compact offsets
+    std::vector<int32_t> grp_n;     // [G]
+    std::vector<int32_t> grp_pairs; // [G] start in pairs
+    std::vector<int32_t> pairs;     // codes a*S+b
+    std::vector<int32_t> row, col;  // [S*S], -1 where not a pair
+};
+
+static PairGroups make_pairs(const std::vector<int32_t> &twom, bool like) {
+    int S = (int)twom.size();
+    std::map<int, std::vector<int32_t>> by_m;
+    for (int a = 0; a < S; ++a)
+        for (int b = 0; b < S; ++b) {
+            if (like && !(a < b)) continue;
+            by_m[twom[a] + twom[b]].push_back(a * S + b);
+        }
+    PairGroups g;
+    g.row.assign((size_t)S * S, -1);
+    g.col.assign((size_t)S * S, -1);
+    int64_t off = 0;
+    for (auto &kv : by_m) {
+        auto &v = kv.second;
+        g.grp_off.push_back(off);
+        g.grp_n.push_back((int32_t)v.size());
+        g.grp_pairs.push_back((int32_t)g.pairs.size());
+        for (size_t i = 0; i < v.size(); ++i) {
+            g.row[v[i]] = (int32_t)(off + (int64_t)i * (int64_t)v.size());
+            g.col[v[i]] = (int32_t)i;
+            g.pairs.push_back(v[i]);
+        }
+        off += (int64_t)v.size() * (int64_t)v.size();
+    }
+    g.grp_off.push_back(off);
+    return g;
+}
+
+// ------------------------------------------------------------------ create
+
+void problem_create(const ci_problem_desc *d, Problem *p) {
+    if (!d) fail(CI_ERR_INVALID_ARG, "desc is NULL");
+    if (d->n_sp < 1 || d->n_sp > 128) fail(CI_ERR_INVALID_ARG, "n_sp must be 1..128 (got %d)", d->n_sp);
+    if (!d->sp_N || !d->sp_twom || !d->sp_energy)
+        fail(CI_ERR_INVALID_ARG, "sp_N, sp_twom and sp_energy are required");
+    if (d->Z < 0 || d->N < 0 || d->Z > kMaxA || d->N > kMaxA || d->Z > d->n_sp || d->N > d->n_sp)
+        fail(CI_ERR_INVALID_ARG, "Z and N must be 0..min(S,%d)", kMaxA);
+    if (d->nmax < -1) fail(CI_ERR_INVALID_ARG, "nmax must be >= -1");
+    if (d->nmax > 64) fail(CI_ERR_CAPACITY, "nmax above 64 is not supported");
+    if (d->tbme_source != CI_TBME_TABLES && d->tbme_source != CI_TBME_SEED)
+        fail(CI_ERR_INVALID_ARG, "tbme_source must be CI_TBME_TABLES or CI_TBME_SEED");
+    if (d->tbme_source == CI_TBME_TABLES) {
+        if (!d->v_pp || !d->v_nn || !d->v_pn) fail(CI_ERR_INVALID_ARG, "v_pp, v_nn, v_pn are required");
+        if (d->tbme_dtype != CI_F32 && d->tbme_dtype != CI_F64)
+            fail(CI_ERR_INVALID_ARG, "tbme_dtype must be CI_F32 or CI_F64");
+    }
+    p->S = d->n_sp;
+    p->sp_N.assign(d->sp_N, d->sp_N + d->n_sp);
+    p->sp_twom.assign(d->sp_twom, d->sp_twom + d->n_sp);
+    p->sp_energy.assign(d->sp_energy, d->sp_energy + d->n_sp);
+    for (int a = 0; a < p->S; ++a) {
+        if (p->sp_N[a] < 0) fail(CI_ERR_INVALID_ARG, "sp_N[%d] < 0", a);
+        if ((p->sp_twom[a] & 1) == 0) fail(CI_ERR_INVALID_ARG, "sp_twom[%d] must be odd", a);
+        p->K = std::max(p->K, std::abs(p->sp_twom[a]));
+    }
+    p->nds = 2 * p->K + 1;
+    p->Z = d->Z; p->N = d->N; p->nmax = d->nmax; p->twoM = d->twoM;
+    p->tbme_source = d->tbme_source;
+    p->tbme_seed = d->tbme_seed;
+    p->tbme_dtype = d->tbme_dtype;
+
+    cudaStream_t s = 0;
+    if (p->tbme_source == CI_TBME_TABLES) {
+        size_t esz = p->tbme_dtype == CI_F32 ? 4 : 8;
+        size_t bytes = esz * (size_t)p->S * p->S * p->S * p->S;
+        const void *src[3] = {d->v_pp, d->v_nn, d->v_pn};
+        for (int c = 0; c < 3; ++c) {
+            p->flat[c].alloc(bytes);
+            CI_CUDA(cudaMemcpyAsync(p->flat[c].ptr, src[c], bytes, cudaMemcpyDefault, s));
+        }
+    }
+    PairGroups lg = make_pairs(p->sp_twom, true), pg = make_pairs(p->sp_twom, false);
+    p->like_row.upload(lg.row, s); p->like_col.upload(lg.col, s);
+    p->pn_row.upload(pg.row, s); p->pn_col.upload(pg.col, s);
+    p->like_size = lg.grp_off.back();
+    p->pn_size = pg.grp_off.back();
+    p->d_twom.upload(p->sp_twom, s);
+    CI_CUDA(cudaStreamSynchronize(s));
+}
+
+// Stage the tables of precision T (once per precision).
+template <class T>
+void stage_tables(Problem *p, cudaStream_t s) {
+    Tables<T> &t = p->tables<T>();
+    if (t.ready) return;
+    const int S = p->S;
+    PairGroups lg = make_pairs(p->sp_twom, true), pg = make_pairs(p->sp_twom, false);
+    auto upload_groups = [&](const PairGroups &g, DevBuf<int64_t> &off, DevBuf<int32_t> &n,
+                             DevBuf<int32_t> &gp, DevBuf<int32_t> &pairs) {
+        off.upload(g.grp_off, s); n.upload(g.grp_n, s); gp.upload(g.grp_pairs, s); pairs.upload(g.pairs, s);
+    };
+    DevBuf<int64_t> loff, poff;
+    DevBuf<int32_t> ln, lgp, lpairs, pn, pgp, ppairs;
+    upload_groups(lg, loff, ln, lgp, lpairs);
+    upload_groups(pg, poff, pn, pgp, ppairs);
+
+    std::vector<T> eps(p->sp_energy.begin(), p->sp_energy.end());
+    t.eps.upload(eps, s);
+    t.Cpp.alloc(p->like_size); t.Cnn.alloc(p->like_size); t.Cpn.alloc(p->pn_size);
+    size_t S3 = (size_t)S * S * S, S2 = (size_t)S * S;
+    t.Upp.alloc(S3); t.Unn.alloc(S3); t.Upn.alloc(S3); t.Wpn.alloc(S3);
+    t.Dpp.alloc(S2); t.Dnn.alloc(S2); t.Dpn.alloc(S2);
+
+    TbmeSrc src[3];
+    for (int c = 0; c < 3; ++c) {
+        src[c].S = S;
+        src[c].source = p->tbme_source;
+        src[c].dtype = p->tbme_dtype;
+        src[c].flat = p->flat[c].ptr;
+        src[c].seed = p->tbme_seed;
+        src[c].channel = c;
+        src[c].twom = p->d_twom.ptr;
+    }
+    const int thr = 256;
+    int Gl = (int)lg.grp_n.size(), Gp = (int)pg.grp_n.size();
+    if (p->like_size > 0) {
+        k_stage_compact<T><<<grid_for(p->like_size, thr), thr, 0, s>>>(
+            src[0], Gl, loff.ptr, ln.ptr, lgp.ptr, lpairs.ptr, p->like_size, t.Cpp.ptr);
+        k_stage_compact<T><<<grid_for(p->like_size, thr), thr, 0, s>>>(
+            src[1], Gl, loff.ptr, ln.ptr, lgp.ptr, lpairs.ptr, p->like_size, t.Cnn.ptr);
+    }
+    k_stage_compact<T><<<grid_for(p->pn_size, thr), thr, 0, s>>>(
+        src[2], Gp, poff.ptr, pn.ptr, pgp.ptr, ppairs.ptr, p->pn_size, t.Cpn.ptr);
+    k_stage_spectator<T><<<grid_for(S3, thr), thr, 0, s>>>(src[0], 0, t.Upp.ptr);
+    k_stage_spectator<T><<<grid_for(S3, thr), thr, 0, s>>>(src[1], 0, t.Unn.ptr);
+    k_stage_spectator<T><<<grid_for(S3, thr), thr, 0, s>>>(src[2], 0, t.Upn.ptr);
+    k_stage_spectator<T><<<grid_for(S3, thr), thr, 0, s>>>(src[2], 1, t.Wpn.ptr);
+    k_stage_diag<T><<<grid_for(S2, thr), thr, 0, s>>>(src[0], t.Dpp.ptr);
+    k_stage_diag<T><<<grid_for(S2, thr), thr, 0, s>>>(src[1], t.Dnn.ptr);
+    k_stage_diag<T><<<grid_for(S2, thr), thr, 0, s>>>(src[2], t.Dpn.ptr);
+    CI_CHECK_LAUNCH();
+    CI_CUDA(cudaStreamSynchronize(s));  // the group arrays are freed on return
+    t.ready = true;
+}
+
+template void stage_tables<float>(Problem *, cudaStream_t);
+template void stage_tables<double>(Problem *, cudaStream_t);
+
+// ------------------------------------------------------------------ species lists
+
+// Enumerate every A-subset of the s.p. states with excess quanta <= nmax
+// (Sec. 2.1: a determinant is a bit string with A ones), pruning branches
+// whose lightest completion already exceeds the cut.
+static void enumerate_species(const Problem *p, int A, SpeciesList *L) {
+    const int S = p->S;
+    L->A = A;
+    L->W = (S + 63) / 64;
+    // suffix_min[o][r]: smallest sum of r shells among states o..S-1
+    std::vector<std::vector<int>> suffix_min(S + 1, std::vector<int>(A + 1, 1 << 28));
+    for (int o = S; o >= 0; --o) {
+        std::vector<int> v(p->sp_N.begin() + o, p->sp_N.end());
+        std::sort(v.begin(), v.end());
+        int acc = 0;
+        suffix_min[o][0] = 0;
+        for (int r = 1; r <= A && r <= (int)v.size(); ++r) { acc += v[r - 1]; suffix_min[o][r] = acc; }
+    }
+    const int nmin = suffix_min[0][A];
+    const int64_t cap = 1ll << 26;
+    struct Tmp { int twoM, q; uint64_t w[2]; uint8_t occ[kMaxA]; };
+    std::vector<Tmp> out;
+    uint8_t occ[kMaxA];
+    std::function<void(int, int, int, int)> rec = [&](int start, int depth, int Nsum, int msum) {
+        if (depth == A) {
+            Tmp t;
+            t.twoM = msum;
+            t.q = Nsum - nmin;
+            t.w[0] = t.w[1] = 0;
+            for (int k = 0; k < A; ++k) { t.occ[k] = occ[k]; t.w[occ[k] >> 6] |= 1ull << (occ[k] & 63); }
+            out.push_back(t);
+            if ((int64_t)out.size() > cap) fail(CI_ERR_CAPACITY, "species list larger than 2^26 determinants");
+            return;
+        }
+        for (int o = start; o <= S - (A - depth); ++o) {
+            if (p->nmax >= 0) {
+                int lb = Nsum + p->sp_N[o] + suffix_min[o + 1][A - depth - 1];
+                if (lb - nmin > p->nmax) continue;
+            }
+            occ[depth] = (uint8_t)o;
+            rec(o + 1, depth + 1, Nsum + p->sp_N[o], msum + p->sp_twom[o]);
+        }
+    };
+    rec(0, 0, 0, 0);
+    std::sort(out.begin(), out.end(), [](const Tmp &x, const Tmp &y) {
+        if (x.twoM != y.twoM) return x.twoM < y.twoM;
+        if (x.q != y.q) return x.q < y.q;
+        if (x.w[1] != y.w[1]) return x.w[1] < y.w[1];
+        return x.w[0] < y.w[0];
+    });
+    L->n = (int64_t)out.size();
+    L->bits.assign((size_t)L->n * L->W, 0);
+    L->q.resize(L->n); L->twoM.resize(L->n); L->local.resize(L->n);
+    L->occ.assign((size_t)L->n * (A ? A : 1), 0);
+    for (int64_t i = 0; i < L->n; ++i) {
+        for (int w = 0; w < L->W; ++w) L->bits[i * L->W + w] = out[i].w[w];
+        L->q[i] = out[i].q;
+        L->twoM[i] = out[i].twoM;
+        for (int k = 0; k < A; ++k) L->occ[i * A + k] = out[i].occ[k];
+    }
+    // 2M blocks and q prefixes
+    L->nq = p->nmax >= 0 ? p->nmax + 1 : 1;
+    if (L->n == 0) { L->nblk = 0; L->blk_start.assign(1, 0); return; }
+    L->m2min = L->twoM.front();
+    L->nblk = (L->twoM.back() - L->m2min) / 2 + 1;
+    L->blk_start.assign(L->nblk + 1, 0);
+    L->blk_qend.assign((size_t)L->nblk * L->nq, 0);
+    for (int64_t i = 0; i < L->n; ++i) L->blk_start[(L->twoM[i] - L->m2min) / 2 + 1]++;
+    for (int b = 0; b < L->nblk; ++b) L->blk_start[b + 1] += L->blk_start[b];
+    for (int b = 0; b < L->nblk; ++b) {
+        int64_t i = L->blk_start[b];
+        for (int c = 0; c < L->nq; ++c) {
+            if (p->nmax >= 0) { while (i < L->blk_start[b + 1] && L->q[i] <= c) ++i; }
+            else i = L->blk_start[b + 1];
+            L->blk_qend[(size_t)b * L->nq + c] = i;
+        }
+        for (int64_t j = L->blk_start[b]; j < L->blk_start[b + 1]; ++j)
+            L->local[j] = (int32_t)(j - L->blk_start[b]);
+    }
+}
+
+// row -> (p, n): p by binary search over p_row_base, n from p's block
+__global__ void k_row_map(int64_t dim, int64_t nP, const int64_t *p_row_base,
+                          const int64_t *p_nstart, int32_t *row_p, int32_t *row_n) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < dim;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        int64_t lo = 0, hi = nP - 1;
+        while (lo < hi) {  // last p with p_row_base[p] <= r
+            int64_t mid = (lo + hi + 1) >> 1;
+            if (p_row_base[mid] <= r) lo = mid; else hi = mid - 1;
+        }
+        row_p[r] = (int32_t)lo;
+        row_n[r] = (int32_t)(p_nstart[lo] + (r - p_row_base[lo]));
+    }
+}
+
+void enumerate_basis(Problem *p, cudaStream_t s) {
+    if (p->enumerated) return;
+    enumerate_species(p, p->Z, &p->sp[0]);
+    enumerate_species(p, p->N, &p->sp[1]);
+    SpeciesList &P = p->sp[0], &Nn = p->sp[1];
+    p->p_row_base.assign(P.n + 1, 0);
+    std::vector<int64_t> p_nstart(P.n ? P.n : 1, 0);
+    for (int64_t i = 0; i < P.n; ++i) {
+        int b = Nn.block_of(p->twoM - P.twoM[i]);
+        int64_t cnt = 0;
+        if (b >= 0) {
+            p_nstart[i] = Nn.blk_start[b];
+            if (p->nmax >= 0) {
+                int c = p->nmax - P.q[i];
+                if (c >= 0) cnt = Nn.blk_qend[(size_t)b * Nn.nq + std::min(c, Nn.nq - 1)] - Nn.blk_start[b];
+            } else {
+                cnt = Nn.blk_start[b + 1] - Nn.blk_start[b];
+            }
+        }
+        p->p_row_base[i + 1] = p->p_row_base[i] + cnt;
+    }
+    p->dim = P.n ? p->p_row_base[P.n] : 0;
+    if (p->dim > (int64_t)INT32_MAX) fail(CI_ERR_CAPACITY, "basis dimension above 2^31-1");
+    for (int sp = 0; sp < 2; ++sp) {
+        SpeciesList &L = p->sp[sp];
+        L.d_bits.upload(L.bits, s);
+        L.d_q.upload(L.q, s);
+        L.d_twoM.upload(L.twoM, s);
+        L.d_local.upload(L.local, s);
+        L.d_occ.upload(L.occ, s);
+    }
+    p->d_p_row_base.upload(p->p_row_base, s);
+    DevBuf<int64_t> d_nstart;
+    d_nstart.upload(p_nstart, s);
+    p->d_row_p.alloc(p->dim);
+    p->d_row_n.alloc(p->dim);
+    if (p->dim > 0) {
+        k_row_map<<<grid_for(p->dim, 256), 256, 0, s>>>(p->dim, P.n, p->d_p_row_base.ptr, d_nstart.ptr,
+                                                         p->d_row_p.ptr, p->d_row_n.ptr);
+        CI_CHECK_LAUNCH();
+    }
+    CI_CUDA(cudaStreamSynchronize(s));
+    p->enumerated = true;
+}
+
+}  // namespace ci

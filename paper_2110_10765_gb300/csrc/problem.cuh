@@ -1,0 +1,173 @@
+// Internal state of a CI problem: species lists, basis, staged interaction
+// tables, species connectivity and the CSR matrix.
+#pragma once
+
+#include <memory>
+
+#include "common.cuh"
+
+namespace ci {
+
+// ------------------------------------------------------------------ species
+
+// One species determinant list, sorted by (2M, q, value of the bit string),
+// split into blocks of equal 2M (block b has 2M = m2min + 2b).
+struct SpeciesList {
+    int A = 0, W = 1;
+    int64_t n = 0;
+    std::vector<uint64_t> bits;     // [n][W]
+    std::vector<int32_t> q, twoM;   // [n]
+    std::vector<uint8_t> occ;       // [n][A] occupied states, ascending
+    std::vector<int32_t> local;     // [n] index inside its 2M block
+    int m2min = 0, nblk = 0;
+    int nq = 1;                     // stored q caps 0..nq-1 (1 when no Nmax cut)
+    std::vector<int64_t> blk_start; // [nblk+1]
+    std::vector<int64_t> blk_qend;  // [nblk][nq] end of (q' <= q) inside the block
+
+    DevBuf<uint64_t> d_bits;
+    DevBuf<int32_t> d_q, d_twoM, d_local;
+    DevBuf<uint8_t> d_occ;
+
+    int block_of(int twoM_) const {
+        int t = twoM_ - m2min;
+        if (t < 0 || (t & 1)) return -1;
+        t >>= 1;
+        return t < nblk ? t : -1;
+    }
+};
+
+// ------------------------------------------------------------------ tables
+
+// Interaction tables of one precision, staged from the flat TBMEs.
+//   C*  : compact pair-pair blocks, V_cdab = C[row[c*S+d] + col[a*S+b]]
+//   U*  : one-move spectator tables, U[(c*S+a)*S+k] = V_{ck,ak}
+//   Wpn : neutron-move pn spectators, Wpn[(d*S+b)*S+k] = V^pn_{kd,kb}
+//   D*  : pair diagonals, D[a*S+b] = V_abab
+template <class T>
+struct Tables {
+    DevBuf<T> eps;
+    DevBuf<T> Cpp, Cnn, Cpn;
+    DevBuf<T> Upp, Unn, Upn, Wpn;
+    DevBuf<T> Dpp, Dnn, Dpn;
+    bool ready = false;
+};
+
+// One entry of a species connectivity list (row determinant s = bra,
+// partner s' = ket).  info: bits 0-1 difference code (0: d=0, 1: d=2,
+// 2: d=4), bit 2 sign (1: negative), bits 3-9 state a (in s' only), bits
+// 10-16 state c (in s only).  val: d=0 like-particle diagonal energy (one-
+// body + pairs); d=2 unsigned like-particle spectator sum; d=4 signed V.
+template <class T>
+struct ConnEntry {
+    int32_t tgt;
+    int32_t local;
+    uint32_t info;
+    T val;
+};
+
+__host__ __device__ inline int info_dcode(uint32_t i) { return (int)(i & 3u); }
+__host__ __device__ inline int info_neg(uint32_t i) { return (int)((i >> 2) & 1u); }
+__host__ __device__ inline int info_a(uint32_t i) { return (int)((i >> 3) & 127u); }
+__host__ __device__ inline int info_c(uint32_t i) { return (int)((i >> 10) & 127u); }
+__host__ __device__ inline uint32_t make_info(int dcode, int neg, int a, int c) {
+    return (uint32_t)dcode | ((uint32_t)neg << 2) | ((uint32_t)a << 3) | ((uint32_t)c << 10);
+}
+
+template <class T>
+struct ConnList {
+    DevBuf<int64_t> ptr;             // [n+1]
+    DevBuf<ConnEntry<T>> ent;        // [total]
+    int64_t total = 0;
+};
+
+// Which species pairs a list keeps (see ci_species_filter).
+enum ConnMode { CONN_OUTER = 0, CONN_L2 = 1, CONN_L4 = 2 };
+
+template <class T>
+struct Connectivity {
+    ConnList<T> outer;   // protons: d <= 2 (any M) and d = 4 (same M)
+    ConnList<T> l2;      // neutrons: d <= 2 (any M)
+    ConnList<T> l4;      // neutrons: d <= 4, same M
+    DevBuf<int32_t> seg2; // [nN][nds][nq] end of L2 entries with slot<s or (slot==s, q<=c), relative
+    DevBuf<int32_t> seg4; // [nN][nq] end of L4 entries with q <= c, relative
+    bool ready = false;
+};
+
+// ------------------------------------------------------------------ problem
+
+struct Problem {
+    int S = 0;
+    std::vector<int32_t> sp_N, sp_twom;
+    std::vector<double> sp_energy;
+    int Z = 0, N = 0, nmax = -1, twoM = 0;
+    int K = 0;      // max |2m| over the s.p. states
+    int nds = 1;    // 2K+1 slots of 2M change in one move
+
+    // flat TBMEs kept on the device only until the tables are staged
+    int tbme_source = CI_TBME_TABLES;
+    uint64_t tbme_seed = 0;
+    int tbme_dtype = CI_F32;
+    DevBuf<unsigned char> flat[3];   // pp, nn, pn (tbme_dtype elements)
+
+    // pair maps: like pairs a<b and pn pairs, grouped by m_a + m_b
+    DevBuf<int32_t> like_row, like_col, pn_row, pn_col;
+    int64_t like_size = 0, pn_size = 0;   // entries of a compact table
+    DevBuf<int32_t> d_twom;
+
+    Tables<float> t32;
+    Tables<double> t64;
+
+    bool enumerated = false;
+    SpeciesList sp[2];
+    int64_t dim = 0;
+    std::vector<int64_t> p_row_base;   // [nP+1]
+    DevBuf<int64_t> d_p_row_base;
+    DevBuf<int32_t> d_row_p, d_row_n;  // [dim]
+
+    Connectivity<float> c32;
+    Connectivity<double> c64;
+    int conn_prec = -1;                // precision of the last species filter
+
+    DevBuf<int32_t> row_cnt;           // [dim]
+    bool counted = false;
+    int64_t nnz = 0;
+    DevBuf<int64_t> scan_scratch;      // block sums of the exclusive scan
+
+    template <class T> Tables<T> &tables();
+    template <class T> Connectivity<T> &conn();
+};
+
+template <> inline Tables<float> &Problem::tables<float>() { return t32; }
+template <> inline Tables<double> &Problem::tables<double>() { return t64; }
+template <> inline Connectivity<float> &Problem::conn<float>() { return c32; }
+template <> inline Connectivity<double> &Problem::conn<double>() { return c64; }
+
+// ------------------------------------------------------------------ matrix
+
+struct Matrix {
+    int64_t dim = 0, nnz = 0;
+    int vtype = CI_F32;
+    DevBuf<int64_t> row_ptr;
+    DevBuf<int32_t> col;
+    DevBuf<unsigned char> val;       // float, double or bf16 bits
+    DevBuf<float> row_scale;         // BF16 only
+};
+
+// ------------------------------------------------------------------ steps
+
+void problem_create(const ci_problem_desc *d, Problem *p);
+void enumerate_basis(Problem *p, cudaStream_t s);
+template <class T> void stage_tables(Problem *p, cudaStream_t s);
+template <class T> void species_filter(Problem *p, cudaStream_t s);
+void count_rows(Problem *p, int prec, cudaStream_t s);   // prec 0 f32, 1 f64
+void exclusive_scan_i32(const int32_t *counts, int64_t n, int64_t *offsets,
+                        DevBuf<int64_t> &scratch, cudaStream_t s);
+void build_matrix(Problem *p, int vtype, Matrix *m, cudaStream_t s);
+void apply_matrix(const Matrix *m, const void *X, void *Y, int nvec, cudaStream_t s);
+void lowest_eigs(const Matrix *H, const ci_eig_opts *opts, double *evals, double *evecs, ci_eig_info *info,
+                 cudaStream_t s);
+
+}  // namespace ci
+
+struct ci_problem { ci::Problem impl; };
+struct ci_matrix { ci::Matrix impl; };

@@ -1,0 +1,108 @@
+// Exclusive prefix sum (Sec. 2.2, Eq. 1): counts (int32) -> offsets
+// (int64) with the total appended.  Reduce-then-scan in three launches:
+// tile sums, a scan of the tile sums, and a rescan of every tile with its
+// prefix.  Every thread owns kItems consecutive counts; warps combine with
+// shuffles.  No kernel waits on another block, so nothing can spin.
+#include "problem.cuh"
+
+namespace ci {
+
+constexpr int kScanThreads = 512;
+constexpr int kItems = 8;
+constexpr int kTile = kScanThreads * kItems;
+
+__device__ __forceinline__ int64_t warp_incl_scan(int64_t v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int64_t u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+    }
+    return v;
+}
+
+// Exclusive scan of one value per thread across the block; returns the
+// thread's exclusive prefix and writes the block total to *total.
+__device__ int64_t block_excl_scan(int64_t v, int64_t *total) {
+    __shared__ int64_t warp_sums[kScanThreads / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int64_t incl = warp_incl_scan(v);
+    if (lane == 31) warp_sums[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        int64_t w = lane < kScanThreads / 32 ? warp_sums[lane] : 0;
+        int64_t wi = warp_incl_scan(w);
+        if (lane < kScanThreads / 32) warp_sums[lane] = wi - w;
+        if (lane == kScanThreads / 32 - 1) *total = wi;
+    }
+    __syncthreads();
+    int64_t r = warp_sums[wid] + incl - v;
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_tile_sums(const int32_t *x, int64_t n, int64_t *sums) {
+    __shared__ int64_t tot;
+    int64_t base = (int64_t)blockIdx.x * kTile + (int64_t)threadIdx.x * kItems;
+    int64_t v = 0;
+#pragma unroll
+    for (int i = 0; i < kItems; ++i)
+        if (base + i < n) v += x[base + i];
+    block_excl_scan(v, &tot);
+    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+// In-place exclusive scan of nb tile sums by one block (loops for nb > block).
+__global__ void __launch_bounds__(kScanThreads) k_scan_sums(int64_t *sums, int64_t nb) {
+    __shared__ int64_t tot;
+    int64_t carry = 0;
+    for (int64_t b0 = 0; b0 < nb; b0 += kScanThreads) {
+        int64_t i = b0 + threadIdx.x;
+        int64_t v = i < nb ? sums[i] : 0;
+        int64_t e = block_excl_scan(v, &tot);
+        if (i < nb) sums[i] = carry + e;
+        carry += tot;
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_tile_apply(const int32_t *x, int64_t n, const int64_t *sums,
+                                                             int64_t *y) {
+    __shared__ int64_t tot;
+    int64_t base = (int64_t)blockIdx.x * kTile + (int64_t)threadIdx.x * kItems;
+    int64_t v[kItems];
+    int64_t s = 0;
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) {
+        v[i] = base + i < n ? x[base + i] : 0;
+        s += v[i];
+    }
+    int64_t e = block_excl_scan(s, &tot) + sums[blockIdx.x];
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) {
+        if (base + i < n) y[base + i] = e;
+        e += v[i];
+        if (base + i == n - 1) y[n] = e;   // the total
+    }
+}
+
+__global__ void k_zero_total(int64_t *y) { y[0] = 0; }
+
+void exclusive_scan_i32(const int32_t *counts, int64_t n, int64_t *offsets, DevBuf<int64_t> &scratch,
+                        cudaStream_t s) {
+    if (n < 0) fail(CI_ERR_INVALID_ARG, "scan length < 0");
+    if (n == 0) {
+        k_zero_total<<<1, 1, 0, s>>>(offsets);
+        CI_CHECK_LAUNCH();
+        return;
+    }
+    int64_t nb = (n + kTile - 1) / kTile;
+    if (nb > INT32_MAX) fail(CI_ERR_CAPACITY, "scan too long");
+    scratch.ensure((size_t)nb);
+    k_tile_sums<<<(unsigned)nb, kScanThreads, 0, s>>>(counts, n, scratch.ptr);
+    k_scan_sums<<<1, kScanThreads, 0, s>>>(scratch.ptr, nb);
+    k_tile_apply<<<(unsigned)nb, kScanThreads, 0, s>>>(counts, n, scratch.ptr, offsets);
+    CI_CHECK_LAUNCH();
+}
+
+}  // namespace ci

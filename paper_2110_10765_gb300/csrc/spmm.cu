@@ -1,0 +1,114 @@
+// SpMM Y = H X over the CSR matrix (Fig. 2 line 5: FMA of H_ij with the
+// j-th vector element), X and Y row-major [dim][NV].  One warp per row:
+// lanes stride over the row's nonzeros with coalesced col/val loads and one
+// vector load of X's row per nonzero, then a butterfly reduction.
+#include "problem.cuh"
+
+namespace ci {
+
+template <class TX, int NV>
+struct VecLoad {
+    __device__ static void load(const TX *p, TX *x) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) x[i] = p[i];
+    }
+};
+template <>
+struct VecLoad<float, 8> {
+    __device__ static void load(const float *p, float *x) {
+        float4 a = __ldg(reinterpret_cast<const float4 *>(p));
+        float4 b = __ldg(reinterpret_cast<const float4 *>(p) + 1);
+        x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
+        x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+    }
+};
+template <>
+struct VecLoad<float, 4> {
+    __device__ static void load(const float *p, float *x) {
+        float4 a = __ldg(reinterpret_cast<const float4 *>(p));
+        x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
+    }
+};
+template <>
+struct VecLoad<double, 8> {
+    __device__ static void load(const double *p, double *x) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            double2 a = __ldg(reinterpret_cast<const double2 *>(p) + i);
+            x[2 * i] = a.x; x[2 * i + 1] = a.y;
+        }
+    }
+};
+
+template <class TV, class TX, int NV>
+__global__ void __launch_bounds__(256) k_spmm(int64_t dim, const int64_t *__restrict__ rp,
+                                              const int32_t *__restrict__ col, const TV *__restrict__ val,
+                                              const TX *__restrict__ X, TX *__restrict__ Y) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = warp; r < dim; r += nwarps) {
+        TX acc[NV];
+#pragma unroll
+        for (int i = 0; i < NV; ++i) acc[i] = 0;
+        const int64_t e1 = rp[r + 1];
+        for (int64_t e = rp[r] + lane; e < e1; e += 32) {
+            const int c = __ldg(col + e);
+            const TX v = (TX)__ldg(val + e);
+            TX x[NV];
+            VecLoad<TX, NV>::load(X + (int64_t)c * NV, x);
+#pragma unroll
+            for (int i = 0; i < NV; ++i) acc[i] = fma(v, x[i], acc[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], o);
+        }
+        if (lane < NV) {
+            TX y = acc[0];
+#pragma unroll
+            for (int i = 1; i < NV; ++i)
+                if (lane == i) y = acc[i];
+            Y[r * NV + lane] = y;
+        }
+    }
+}
+
+template <class TV, class TX, int NV>
+static void launch(const Matrix *m, const void *X, void *Y, cudaStream_t s) {
+    int grid = grid_for(m->dim * 32, 256, sm_count() * 8);
+    k_spmm<TV, TX, NV><<<grid, 256, 0, s>>>(m->dim, m->row_ptr.ptr, m->col.ptr, (const TV *)m->val.ptr,
+                                            (const TX *)X, (TX *)Y);
+}
+
+template <class TV, class TX>
+static void dispatch(const Matrix *m, const void *X, void *Y, int nvec, cudaStream_t s) {
+    switch (nvec) {
+        case 1: launch<TV, TX, 1>(m, X, Y, s); break;
+        case 2: launch<TV, TX, 2>(m, X, Y, s); break;
+        case 3: launch<TV, TX, 3>(m, X, Y, s); break;
+        case 4: launch<TV, TX, 4>(m, X, Y, s); break;
+        case 5: launch<TV, TX, 5>(m, X, Y, s); break;
+        case 6: launch<TV, TX, 6>(m, X, Y, s); break;
+        case 7: launch<TV, TX, 7>(m, X, Y, s); break;
+        case 8: launch<TV, TX, 8>(m, X, Y, s); break;
+        default: fail(CI_ERR_INVALID_ARG, "nvec must be 1..8 (got %d)", nvec);
+    }
+}
+
+void apply_matrix(const Matrix *m, const void *X, void *Y, int nvec, cudaStream_t s) {
+    if (nvec < 1 || nvec > 8) fail(CI_ERR_INVALID_ARG, "nvec must be 1..8 (got %d)", nvec);
+    if (m->dim == 0) return;
+    if (!X || !Y) fail(CI_ERR_INVALID_ARG, "X and Y must be device pointers");
+    size_t esz = m->vtype == CI_F64 ? 8 : 4;
+    size_t align = (nvec == 8 || nvec == 4) ? 16 : esz;
+    if (((uintptr_t)X % align) != 0 || ((uintptr_t)Y % esz) != 0)
+        fail(CI_ERR_INVALID_ARG, "X must be %zu-byte aligned", align);
+    if (m->vtype == CI_F32) dispatch<float, float>(m, X, Y, nvec, s);
+    else if (m->vtype == CI_F64) dispatch<double, double>(m, X, Y, nvec, s);
+    else fail(CI_ERR_INVALID_ARG, "value type %d not supported by ci_apply_H", m->vtype);
+    CI_CHECK_LAUNCH();
+}
+
+}  // namespace ci

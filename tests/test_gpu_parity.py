@@ -1,0 +1,273 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Bit-exact: species lists, basis, species connectivity, row counts, scan,
+nonzero pattern (column indices).  Values: per element
+|h - h64| <= rel * max(|h64|, sum |terms|) with rel = 1e-6 (FP32) or 1e-12
+(FP64).  Eigenvalues: |l - l64| <= 1e-5 * max(|l64|, 1).
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from helpers import (EIG_REL, REL32, REL64, golden, gpu_problem, inputs, oracle_problem, preset_inputs,
+                     value_bound)
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+SMALL = [
+    # (n_shell, Z, N, nmax) -- ragged sizes, odd A, empty species, Nmax 0
+    (1, 2, 2, -1), (1, 3, 2, -1), (1, 2, 0, -1), (1, 0, 3, -1), (2, 3, 3, 2),
+    (2, 2, 3, 1), (3, 2, 2, 0), (3, 3, 2, 2), (1, 1, 1, -1), (2, 4, 2, 2),
+]
+
+
+def _species_eq(o, g, s):
+    a, b = o.species(s), g.species(s)
+    assert np.array_equal(a["bits"], b["bits"])
+    assert np.array_equal(a["q"], b["q"]) and np.array_equal(a["twoM"], b["twoM"])
+
+
+@pytest.mark.parametrize("case", SMALL + ["c0", "c2_sub"])
+def test_basis_bit_exact(case):
+    inp = preset_inputs(case) if isinstance(case, str) else inputs(*case, seed=3)
+    o, g = oracle_problem(inp), gpu_problem(inp)
+    assert g.enumerate_basis() == o.dim
+    _species_eq(o, g, 0)
+    _species_eq(o, g, 1)
+    p, n = g.basis()
+    assert np.array_equal(p, o.p_idx) and np.array_equal(n, o.n_idx)
+
+
+def _species_pairs(o, s):
+    """Oracle reference of the kept species pairs (difference <= 2, or 4 with equal 2M)."""
+    sp = o.species(s)
+    occ, m = sp["occ"], sp["twoM"]
+    n = len(occ)
+    out = []
+    for i in range(n):
+        row = []
+        for j in range(n):
+            d = o.count_difference(s, i, j)
+            if d <= 2 or (d == 4 and m[i] == m[j]):
+                row.append((j, d))
+        out.append(row)
+    return out
+
+
+@pytest.mark.parametrize("case", [(1, 4, 4, -1), (2, 3, 3, 2), (3, 2, 3, 1)])
+def test_species_connectivity_bit_exact(case):
+    inp = inputs(*case, seed=1)
+    o, g = oracle_problem(inp), gpu_problem(inp)
+    g.species_filter()
+    for s in (0, 1):
+        ptr, idx, d = g.species_conn(s)
+        ref = _species_pairs(o, s)
+        assert len(ptr) == len(ref) + 1
+        for i, row in enumerate(ref):
+            got = list(zip(idx[ptr[i]:ptr[i + 1]].tolist(), d[ptr[i]:ptr[i + 1]].tolist()))
+            assert got == row
+
+
+@pytest.mark.parametrize("case", SMALL + ["c0", "c2_sub"])
+def test_row_counts_bit_exact(case):
+    inp = preset_inputs(case) if isinstance(case, str) else inputs(*case, seed=2)
+    o, g = oracle_problem(inp), gpu_problem(inp)
+    dim = g.enumerate_basis()
+    cnt = torch.zeros(max(dim, 1), dtype=torch.int32, device="cuda")
+    nnz = g.count_nnz(cnt)
+    ref = o.row_counts()
+    assert nnz == int(ref.sum())
+    assert np.array_equal(cnt.cpu().numpy()[:dim], ref)
+
+
+@pytest.mark.parametrize("n", [0, 1, 31, 4095, 4096, 4097, 123457, 3_000_001])
+def test_exclusive_scan_bit_exact(n):
+    import paper_2110_10765_gb300 as ci
+    rng = np.random.default_rng(n)
+    x = rng.integers(0, 2000, n).astype(np.int32)
+    xd = torch.from_numpy(x).cuda() if n else torch.zeros(1, dtype=torch.int32, device="cuda")
+    y = torch.full((n + 1,), -7, dtype=torch.int64, device="cuda")
+    ci.exclusive_scan(xd[:n] if n else xd[:0], y)
+    assert np.array_equal(y.cpu().numpy(), oracle.exclusive_scan(x))
+
+
+def test_exclusive_scan_large_total_int64():
+    import paper_2110_10765_gb300 as ci
+    n = 3_000_000
+    x = np.full(n, 1500, np.int32)  # total 4.5e9 > 2^31
+    y = torch.zeros(n + 1, dtype=torch.int64, device="cuda")
+    ci.exclusive_scan(torch.from_numpy(x).cuda(), y)
+    assert int(y[-1]) == 1500 * n and int(y[n // 2]) == 1500 * (n // 2)
+
+
+def _check_matrix(o, M, rel, rows=None):
+    rp, col, val, _ = M.export()
+    if rows is None:
+        orp, ocol, oval, oab = o.csr()
+        assert np.array_equal(rp, orp)
+        assert np.array_equal(col.astype(np.int64), ocol)
+        err = np.abs(val.astype(np.float64) - oval)
+        assert np.all(err <= value_bound(oval, oab, rel)), err.max()
+        return rp, col, val
+    for i in rows:
+        ocol, oval, oab, _ = o.row(i)
+        s, e = rp[i], rp[i + 1]
+        assert np.array_equal(col[s:e].astype(np.int64), ocol), i
+        err = np.abs(val[s:e].astype(np.float64) - oval)
+        assert np.all(err <= value_bound(oval, oab, rel)), (i, err.max())
+    return rp, col, val
+
+
+@pytest.mark.parametrize("case", SMALL)
+@pytest.mark.parametrize("vtype", ["f32", "f64"])
+def test_build_H_small(case, vtype):
+    inp = inputs(*case, seed=5, dtype=np.float64 if vtype == "f64" else np.float32)
+    o, g = oracle_problem(inp), gpu_problem(inp)
+    M = g.build_H(vtype)
+    assert M.dim == o.dim
+    _check_matrix(o, M, REL64 if vtype == "f64" else REL32)
+
+
+def test_build_H_config0_fp64():
+    inp = preset_inputs("c0")
+    o, g = oracle_problem(inp), gpu_problem(inp)
+    M = g.build_H("f64")
+    assert (M.dim, M.nnz) == (1014, 88462)
+    _check_matrix(o, M, REL64)
+
+
+def test_build_H_nmax2_subspace_fp32():
+    inp = preset_inputs("c2_sub")
+    o, g = oracle_problem(inp), gpu_problem(inp)
+    M = g.build_H("f32")
+    assert M.nnz == golden()["c2_sub"]["nnz"]
+    _check_matrix(o, M, REL32)
+
+
+def test_build_H_config1_full_size_sampled_rows():
+    """Nmax=4, 70 states per species (two-word bit strings), sampled rows."""
+    inp = preset_inputs("c1")
+    o, g = oracle_problem(inp), gpu_problem(inp)
+    M = g.build_H("f32")
+    gd = golden()["c1"]
+    assert (M.dim, M.nnz) == (gd["dim"], gd["nnz"])
+    rng = np.random.default_rng(11)
+    rows = sorted(set(rng.integers(0, M.dim, 150).tolist()) | {0, M.dim - 1})
+    rp, col, val = _check_matrix(o, M, REL32, rows)
+    # structural symmetry and value symmetry on the sampled rows
+    for i in rows[:40]:
+        for j, v in zip(col[rp[i]:rp[i + 1]].tolist(), val[rp[i]:rp[i + 1]].tolist()):
+            seg = col[rp[j]:rp[j + 1]]
+            k = np.searchsorted(seg, i)
+            assert k < len(seg) and seg[k] == i
+            assert abs(val[rp[j] + k] - v) <= 1e-5 * max(abs(v), 1.0)
+
+
+def test_seeded_tables_match_synth_tables():
+    """The device TBME generator reproduces synth's tables bit for bit."""
+    inp = inputs(2, 3, 2, 2, seed=77)
+    g_tab = gpu_problem(inp)
+    g_seed = gpu_problem(inp, seed=77)
+    A = g_tab.build_H("f32").export()
+    B = g_seed.build_H("f32").export()
+    assert np.array_equal(A[0], B[0]) and np.array_equal(A[1], B[1]) and np.array_equal(A[2], B[2])
+
+
+def _rand_block(dim, nvec, dtype, seed=0):
+    return np.random.default_rng(seed).standard_normal((dim, nvec)).astype(dtype)
+
+
+@pytest.mark.parametrize("nvec", [1, 3, 8])
+def test_apply_H_small_full(nvec):
+    inp = inputs(2, 3, 3, 2, seed=4)
+    o, g = oracle_problem(inp), gpu_problem(inp)
+    M = g.build_H("f32")
+    rp, cols, vals, ab = o.csr()
+    X = _rand_block(o.dim, nvec, np.float32)
+    Y = torch.empty((o.dim, nvec), dtype=torch.float32, device="cuda")
+    M.apply_H(torch.from_numpy(X).cuda(), Y)
+    torch.cuda.synchronize()
+    ref = oracle.spmm(rp, cols, vals, X.astype(np.float64))
+    # FP32 accumulation: bound by sum |H_ij X_j| * 1e-6 per row
+    bound = 1e-6 * oracle.spmm(rp, cols, np.abs(vals), np.abs(X.astype(np.float64))) + 1e-30
+    assert np.all(np.abs(Y.cpu().numpy() - ref) <= bound)
+
+
+def test_apply_H_config0_fp64():
+    inp = preset_inputs("c0")
+    o, g = oracle_problem(inp), gpu_problem(inp)
+    M = g.build_H("f64")
+    rp, cols, vals, ab = o.csr()
+    X = _rand_block(o.dim, 8, np.float64, 1)
+    Y = torch.empty((o.dim, 8), dtype=torch.float64, device="cuda")
+    M.apply_H(torch.from_numpy(X).cuda(), Y)
+    ref = oracle.spmm(rp, cols, vals, X)
+    bound = 1e-12 * oracle.spmm(rp, cols, np.abs(vals), np.abs(X)) + 1e-300
+    assert np.all(np.abs(Y.cpu().numpy() - ref) <= bound)
+
+
+def test_apply_H_config1_sampled_rows():
+    inp = preset_inputs("c1")
+    o, g = oracle_problem(inp), gpu_problem(inp)
+    M = g.build_H("f32")
+    X = _rand_block(M.dim, 8, np.float32, 2)
+    Y = torch.empty((M.dim, 8), dtype=torch.float32, device="cuda")
+    M.apply_H(torch.from_numpy(X).cuda(), Y)
+    Yh = Y.cpu().numpy()
+    X64 = X.astype(np.float64)
+    for i in np.random.default_rng(3).integers(0, M.dim, 60):
+        c, v, ab, _ = o.row(int(i))
+        ref = v @ X64[c]
+        bound = 1e-6 * (np.abs(v) @ np.abs(X64[c]))
+        assert np.all(np.abs(Yh[i] - ref) <= bound + 1e-30)
+
+
+def test_lowest_eigs_config0_fp64():
+    inp = preset_inputs("c0")
+    g = gpu_problem(inp)
+    M = g.build_H("f64")
+    ev, info = M.lowest_eigs(k=5)
+    ref = np.array(golden()["c0"]["lowest"])
+    assert np.all(np.abs(ev - ref) <= 1e-9 * np.maximum(np.abs(ref), 1))
+
+
+def test_lowest_eigs_degenerate_closed_form():
+    """Zero interaction: lowest five levels are all 320 MeV (51-fold)."""
+    inp = inputs(1, 4, 4, -1, zero=True, dtype=np.float64)
+    M = gpu_problem(inp).build_H("f64")
+    ev, info = M.lowest_eigs(k=5)
+    assert np.allclose(ev, 320.0, rtol=0, atol=1e-8)
+
+
+def test_lowest_eigs_nmax2_subspace_fp32():
+    inp = preset_inputs("c2_sub")
+    M = gpu_problem(inp).build_H("f32")
+    evecs = torch.zeros((M.dim, 10), dtype=torch.float64, device="cuda")
+    ev, info = M.lowest_eigs(k=10, evecs=evecs)
+    ref = np.array(golden()["c2_sub"]["lowest"])
+    assert np.all(np.abs(ev - ref) <= EIG_REL * np.maximum(np.abs(ref), 1)), ev - ref
+    V = evecs.cpu().numpy()
+    assert np.allclose(V.T @ V, np.eye(10), atol=1e-6)
+
+
+def test_lowest_eigs_config1_fp32():
+    inp = preset_inputs("c1")
+    M = gpu_problem(inp).build_H("f32")
+    ev, info = M.lowest_eigs(k=5)
+    ref = np.array(golden()["c1"]["lowest"])
+    assert np.all(np.abs(ev - ref) <= EIG_REL * np.maximum(np.abs(ref), 1)), ev - ref
+    assert max(info["residual"]) <= 1e-4 * info["hnorm_est"]
+
+
+@pytest.mark.parametrize("case", [(1, 2, 2, -1), (2, 2, 1, 1), (1, 1, 1, -1)])
+def test_lowest_eigs_small_dense_path(case):
+    inp = inputs(*case, seed=9, dtype=np.float64)
+    o = oracle_problem(inp)
+    M = gpu_problem(inp).build_H("f64")
+    k = min(3, o.dim)
+    ev, info = M.lowest_eigs(k=k, max_basis=32, block=4) if o.dim >= 3 else M.lowest_eigs(k=1, block=1,
+                                                                                              max_basis=16)
+    ref = oracle.lowest_dense(oracle.dense_from_csr(*o.csr()[:3], o.dim), len(ev))
+    assert np.allclose(ev, ref, atol=1e-9)
