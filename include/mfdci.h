@@ -237,6 +237,23 @@ typedef struct {
 ci_status ci_lowest_eigs(const ci_matrix *m, const ci_eig_opts *opts, double *evals,
                          double *evecs, ci_eig_info *info, void *stream);
 
+/* ---------------------------------------------------------------- tracing */
+
+/* Kernel tracing.  While on, every kernel the library launches is
+ * bracketed by two CUDA events on its launch stream (a small overhead per
+ * launch).  No paper counterpart beyond timing regions (Listing 10). */
+typedef struct {
+    char name[48];       /* kernel name                                  */
+    int64_t launches;    /* launches recorded since the last reset       */
+    double total_ms;     /* sum of their event-measured durations (ms)   */
+} ci_trace_entry;
+
+ci_status ci_trace_enable(int32_t on);
+/* Synchronise the recorded events and copy up to cap entries (sorted by
+ * name) to out; *n receives the number of kernel names.  reset != 0 clears
+ * the statistics after reading. */
+ci_status ci_trace_read(ci_trace_entry *out, int32_t cap, int32_t *n, int32_t reset);
+
 #ifdef __cplusplus
 }
 #endif

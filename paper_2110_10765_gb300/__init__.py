@@ -18,7 +18,7 @@ from . import _lib
 from ._lib import (CIError, CI_F32, CI_F64, CI_BF16_ROWSCALE, CI_TBME_TABLES,
                    CI_TBME_SEED, check, lib)
 
-__all__ = ["Problem", "Matrix", "exclusive_scan", "CIError", "CI_F32", "CI_F64",
+__all__ = ["Problem", "Matrix", "exclusive_scan", "trace_enable", "trace_read", "CIError", "CI_F32", "CI_F64",
            "CI_BF16_ROWSCALE", "VTYPES", "lib", "current_stream"]
 
 VTYPES = {"f32": CI_F32, "f64": CI_F64, "bf16": CI_BF16_ROWSCALE}
@@ -215,6 +215,20 @@ class Matrix:
                "basis_size": info.basis_size, "hnorm_est": info.hnorm_est,
                "residual": list(info.residual)[:k], "seconds": info.seconds, "status": st}
         return ev, out
+
+
+def trace_enable(on=True):
+    """Bracket every library kernel launch with CUDA events (ci_trace_enable)."""
+    check(lib().ci_trace_enable(1 if on else 0), "ci_trace_enable")
+
+
+def trace_read(reset=True):
+    """{kernel name: (launches, total ms)} since the last reset (ci_trace_read)."""
+    n = C.c_int32()
+    check(lib().ci_trace_read(None, 0, C.byref(n), 0), "ci_trace_read")
+    buf = (_lib.TraceEntry * max(n.value, 1))()
+    check(lib().ci_trace_read(buf, n.value, C.byref(n), 1 if reset else 0), "ci_trace_read")
+    return {buf[i].name.decode(): (buf[i].launches, buf[i].total_ms) for i in range(n.value)}
 
 
 def exclusive_scan(counts, offsets, stream=None):

@@ -43,6 +43,10 @@ class EigInfo(C.Structure):
                 ("residual", C.c_double * 32), ("seconds", C.c_double)]
 
 
+class TraceEntry(C.Structure):
+    _fields_ = [("name", C.c_char * 48), ("launches", C.c_int64), ("total_ms", C.c_double)]
+
+
 class CIError(RuntimeError):
     def __init__(self, status, name, msg):
         super().__init__("%s: %s" % (name, msg))
@@ -71,6 +75,8 @@ _SIGS = {
     "ci_matrix_export": (C.c_int, [_P, _P, _P, _P, _P, _P]),
     "ci_apply_H": (C.c_int, [_P, _P, _P, C.c_int32, _P]),
     "ci_lowest_eigs": (C.c_int, [_P, C.POINTER(EigOpts), _P, _P, C.POINTER(EigInfo), _P]),
+    "ci_trace_enable": (C.c_int, [C.c_int32]),
+    "ci_trace_read": (C.c_int, [C.POINTER(TraceEntry), C.c_int32, C.POINTER(C.c_int32), C.c_int32]),
 }
 
 

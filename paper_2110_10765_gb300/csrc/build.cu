@@ -222,7 +222,7 @@ static void count_rows_t(Problem *p, cudaStream_t s) {
     p->row_cnt.alloc(p->dim);
     if (p->dim > 0) {
         RowArgs<T> a = row_args<T>(p);
-        k_count_rows<T><<<row_grid(p->dim), 256, 0, s>>>(a);
+        launch("k_count_rows", k_count_rows<T>, row_grid(p->dim), 256, 0, s, a);
         CI_CHECK_LAUNCH();
     }
     p->conn_prec = sizeof(T) == 4 ? 0 : 1;
@@ -255,11 +255,11 @@ void build_matrix(Problem *p, int vtype, Matrix *m, cudaStream_t s) {
     if (prec == 0) {
         RowArgs<float> a = row_args<float>(p);
         a.row_ptr = m->row_ptr.ptr; a.col = m->col.ptr; a.val = (float *)m->val.ptr;
-        k_fill_rows<float><<<row_grid(p->dim), 256, 0, s>>>(a);
+        launch("k_fill_rows", k_fill_rows<float>, row_grid(p->dim), 256, 0, s, a);
     } else {
         RowArgs<double> a = row_args<double>(p);
         a.row_ptr = m->row_ptr.ptr; a.col = m->col.ptr; a.val = (double *)m->val.ptr;
-        k_fill_rows<double><<<row_grid(p->dim), 256, 0, s>>>(a);
+        launch("k_fill_rows", k_fill_rows<double>, row_grid(p->dim), 256, 0, s, a);
     }
     CI_CHECK_LAUNCH();
 }

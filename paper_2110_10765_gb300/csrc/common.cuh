@@ -136,3 +136,29 @@ __host__ __device__ inline uint64_t below_mask_word(int o, int word) {
 }
 
 }  // namespace ci
+
+namespace ci {
+
+// ------------------------------------------------------------------ tracing
+
+// When tracing is on (ci_trace_enable), every kernel launch of the library
+// is bracketed by two CUDA events on the launch stream; ci_trace_read sums
+// their elapsed times per kernel name.
+bool trace_on();
+void trace_begin(const char *name, cudaStream_t s, void **token);
+void trace_end(void *token, cudaStream_t s);
+
+template <class K, class... Args>
+inline void launch(const char *name, K kernel, dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                   Args... args) {
+    void *tok = nullptr;
+    if (trace_on()) trace_begin(name, s, &tok);
+    kernel<<<grid, block, smem, s>>>(args...);
+    cudaError_t e = cudaGetLastError();
+    if (tok) trace_end(tok, s);
+    if (e != cudaSuccess)
+        fail(e == cudaErrorMemoryAllocation ? CI_ERR_OOM : CI_ERR_CUDA, "launch of %s failed: %s", name,
+             cudaGetErrorString(e));
+}
+
+}  // namespace ci

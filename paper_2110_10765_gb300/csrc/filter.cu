@@ -205,16 +205,16 @@ static void build_list(Problem *p, int species, int mode, ConnList<T> &L, cudaSt
     }
     const int thr = 256;
     int grid = grid_for(sp.n * 32, thr, sm_count() * 8);
-    if (sp.W == 1) k_filter<T, 1><<<grid, thr, 0, s>>>(a, 0);
-    else k_filter<T, 2><<<grid, thr, 0, s>>>(a, 0);
+    if (sp.W == 1) launch("k_filter", k_filter<T, 1>, grid, thr, 0, s, a, 0);
+    else launch("k_filter", k_filter<T, 2>, grid, thr, 0, s, a, 0);
     CI_CHECK_LAUNCH();
     exclusive_scan_i32(cnt.ptr, sp.n, L.ptr.ptr, p->scan_scratch, s);
     CI_CUDA(cudaMemcpyAsync(&L.total, L.ptr.ptr + sp.n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     CI_CUDA(cudaStreamSynchronize(s));
     L.ent.alloc(L.total);
     a.ptr = L.ptr.ptr; a.ent = L.ent.ptr;
-    if (sp.W == 1) k_filter<T, 1><<<grid, thr, 0, s>>>(a, 1);
-    else k_filter<T, 2><<<grid, thr, 0, s>>>(a, 1);
+    if (sp.W == 1) launch("k_filter", k_filter<T, 1>, grid, thr, 0, s, a, 1);
+    else launch("k_filter", k_filter<T, 2>, grid, thr, 0, s, a, 1);
     CI_CHECK_LAUNCH();
 }
 
@@ -232,11 +232,11 @@ void species_filter(Problem *p, cudaStream_t s) {
     c.seg4.alloc((size_t)Nn.n * Nn.nq);
     if (Nn.n > 0) {
         const bool f = sizeof(T) == 4;
-        k_seg2<<<grid_for(Nn.n * p->nds * Nn.nq, 256), 256, 0, s>>>(
+        launch("k_seg2", k_seg2, grid_for(Nn.n * p->nds * Nn.nq, 256), 256, 0, s, 
             Nn.n, p->nds, Nn.nq, p->K, cut, c.l2.ptr.ptr,
             f ? (const ConnEntry<float> *)c.l2.ent.ptr : nullptr,
             f ? nullptr : (const ConnEntry<double> *)c.l2.ent.ptr, Nn.d_twoM.ptr, Nn.d_q.ptr, c.seg2.ptr);
-        k_seg4<<<grid_for(Nn.n * Nn.nq, 256), 256, 0, s>>>(
+        launch("k_seg4", k_seg4, grid_for(Nn.n * Nn.nq, 256), 256, 0, s, 
             Nn.n, Nn.nq, cut, c.l4.ptr.ptr, f ? (const ConnEntry<float> *)c.l4.ent.ptr : nullptr,
             f ? nullptr : (const ConnEntry<double> *)c.l4.ent.ptr, Nn.d_q.ptr, c.seg4.ptr);
         CI_CHECK_LAUNCH();

@@ -157,8 +157,8 @@ struct Solver {
     // host != null, copied to host.
     void tn(const double *A, int lda, int na, const double *B, int ldb, int nb, double *Cout,
             std::vector<double> *host) {
-        k_tn_partial<<<nblk, kTnThreads, 0, s>>>(dim, A, lda, na, B, ldb, nb, part.ptr, rows_per_blk);
-        k_reduce_partial<<<grid_for(na * nb, 128, 64), 128, 0, s>>>(part.ptr, nblk, na * nb, Cout);
+        launch("k_tn_partial", k_tn_partial, nblk, kTnThreads, 0, s, dim, A, lda, na, B, ldb, nb, part.ptr, rows_per_blk);
+        launch("k_reduce_partial", k_reduce_partial, grid_for(na * nb, 128, 64), 128, 0, s, part.ptr, nblk, na * nb, Cout);
         CI_CHECK_LAUNCH();
         if (host) {
             host->resize((size_t)na * nb);
@@ -169,7 +169,7 @@ struct Solver {
 
     void nn(const double *A, int lda, int na, const double *C, int nb, double *Wout, int ldw, double alpha,
             double beta) {
-        k_nn_update<<<grid(dim * nb), 256, 0, s>>>(dim, A, lda, na, C, nb, Wout, ldw, alpha, beta);
+        launch("k_nn_update", k_nn_update, grid(dim * nb), 256, 0, s, dim, A, lda, na, C, nb, Wout, ldw, alpha, beta);
         CI_CHECK_LAUNCH();
     }
 
@@ -180,12 +180,12 @@ struct Solver {
     // Wout [dim][nb] (contiguous) = H V, V with leading dimension ldv.
     void apply(const double *V, int ldv, int nb, double *Wout) {
         if (f64) {
-            k_copy_cols<<<grid(dim * nb), 256, 0, s>>>(dim, nb, V, ldv, X64.ptr, nb);
+            launch("k_copy_cols", k_copy_cols, grid(dim * nb), 256, 0, s, dim, nb, V, ldv, X64.ptr, nb);
             apply_matrix(H, X64.ptr, Wout, nb, s);
         } else {
-            k_cvt_to_f32<<<grid(dim * nb), 256, 0, s>>>(dim, nb, V, ldv, X32.ptr);
+            launch("k_cvt_to_f32", k_cvt_to_f32, grid(dim * nb), 256, 0, s, dim, nb, V, ldv, X32.ptr);
             apply_matrix(H, X32.ptr, Y32.ptr, nb, s);
-            k_cvt_to_f64<<<grid(dim * nb), 256, 0, s>>>(dim, nb, Y32.ptr, Wout, nb);
+            launch("k_cvt_to_f64", k_cvt_to_f64, grid(dim * nb), 256, 0, s, dim, nb, Y32.ptr, Wout, nb);
         }
         CI_CHECK_LAUNCH();
     }
@@ -234,7 +234,7 @@ struct Solver {
             // random completion of columns r..b-1
             double *Vr = tmp.ptr;
             int nr = b - r;
-            k_random_cols<<<grid(dim * nr), 256, 0, s>>>(dim, nr, seed, Vr, nr);
+            launch("k_random_cols", k_random_cols, grid(dim * nr), 256, 0, s, dim, nr, seed, Vr, nr);
             CI_CHECK_LAUNCH();
             for (int pass = 0; pass < 2; ++pass) {
                 if (m > 0) {
@@ -246,7 +246,7 @@ struct Solver {
                     nn(V, mmax, r, Cdev.ptr, nr, Vr, nr, -1.0, 1.0);
                 }
             }
-            k_copy_cols<<<grid(dim * nr), 256, 0, s>>>(dim, nr, Vr, nr, V + r, mmax);
+            launch("k_copy_cols", k_copy_cols, grid(dim * nr), 256, 0, s, dim, nr, Vr, nr, V + r, mmax);
             CI_CHECK_LAUNCH();
         }
         // second pass: V <- V G2^{-1/2}, R <- G2^{1/2} R
@@ -266,7 +266,7 @@ struct Solver {
             }
         upload(Mi, Mdev.ptr);
         nn(V, mmax, b, Mdev.ptr, b, tmp.ptr, b, 1.0, 0.0);
-        k_copy_cols<<<grid(dim * b), 256, 0, s>>>(dim, b, tmp.ptr, b, V, mmax);
+        launch("k_copy_cols", k_copy_cols, grid(dim * b), 256, 0, s, dim, b, tmp.ptr, b, V, mmax);
         CI_CHECK_LAUNCH();
         std::vector<double> R2((size_t)b * b, 0.0);
         for (int a = 0; a < b; ++a)
@@ -395,7 +395,7 @@ void lowest_eigs(const Matrix *H, const ci_eig_opts *opts_in, double *evals, dou
     std::vector<double> T((size_t)mmax * mmax, 0.0);
     std::vector<double> R, coef;
     // start block
-    k_random_cols<<<sv.grid(dim * b), 256, 0, s>>>(dim, b, o.seed, sv.W.ptr, b);
+    launch("k_random_cols", k_random_cols, sv.grid(dim * b), 256, 0, s, dim, b, o.seed, sv.W.ptr, b);
     CI_CHECK_LAUNCH();
     sv.block_qr(sv.W.ptr, 0, o.seed ^ 0x5bd1e995ull, R);
     int m_cur = b, j0 = 0;
@@ -455,8 +455,8 @@ void lowest_eigs(const Matrix *H, const ci_eig_opts *opts_in, double *evals, dou
                 sv.nn(sv.Q.ptr, mmax, m_act, sv.Mdev.ptr, nc, sv.tmp.ptr + c0, keep, 1.0, 0.0);
             }
             // new block Q[:, m_act:m_act+b] -> Q[:, keep:keep+b]; Ritz vectors -> Q[:, 0:keep]
-            k_copy_cols<<<sv.grid(dim * b), 256, 0, s>>>(dim, b, sv.Q.ptr + m_act, mmax, sv.Q.ptr + keep, mmax);
-            k_copy_cols<<<sv.grid(dim * keep), 256, 0, s>>>(dim, keep, sv.tmp.ptr, keep, sv.Q.ptr, mmax);
+            launch("k_copy_cols", k_copy_cols, sv.grid(dim * b), 256, 0, s, dim, b, sv.Q.ptr + m_act, mmax, sv.Q.ptr + keep, mmax);
+            launch("k_copy_cols", k_copy_cols, sv.grid(dim * keep), 256, 0, s, dim, keep, sv.tmp.ptr, keep, sv.Q.ptr, mmax);
             CI_CHECK_LAUNCH();
             std::fill(T.begin(), T.end(), 0.0);
             for (int i = 0; i < keep; ++i) T[(size_t)i * mmax + i] = last.theta[i];
@@ -492,7 +492,7 @@ void lowest_eigs(const Matrix *H, const ci_eig_opts *opts_in, double *evals, dou
         std::vector<double> th(last.theta.begin() + c0, last.theta.begin() + c0 + nc);
         sv.upload(th, sv.theta_dev.ptr);
         double *Rr = sv.Q.ptr;  // basis no longer needed: scratch [dim][nc]
-        k_residual<double><<<sv.grid(dim * nc), 256, 0, s>>>(dim, nc, sv.W.ptr, X + c0, k, sv.theta_dev.ptr, Rr);
+        launch("k_residual", k_residual<double>, sv.grid(dim * nc), 256, 0, s, dim, nc, sv.W.ptr, X + c0, k, sv.theta_dev.ptr, Rr);
         CI_CHECK_LAUNCH();
         std::vector<double> G;
         sv.tn(Rr, nc, nc, Rr, nc, nc, sv.Cdev.ptr, &G);

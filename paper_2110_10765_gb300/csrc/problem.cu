@@ -282,20 +282,20 @@ void stage_tables(Problem *p, cudaStream_t s) {
     const int thr = 256;
     int Gl = (int)lg.grp_n.size(), Gp = (int)pg.grp_n.size();
     if (p->like_size > 0) {
-        k_stage_compact<T><<<grid_for(p->like_size, thr), thr, 0, s>>>(
+        launch("k_stage_compact", k_stage_compact<T>, grid_for(p->like_size, thr), thr, 0, s, 
             src[0], Gl, loff.ptr, ln.ptr, lgp.ptr, lpairs.ptr, p->like_size, t.Cpp.ptr);
-        k_stage_compact<T><<<grid_for(p->like_size, thr), thr, 0, s>>>(
+        launch("k_stage_compact", k_stage_compact<T>, grid_for(p->like_size, thr), thr, 0, s, 
             src[1], Gl, loff.ptr, ln.ptr, lgp.ptr, lpairs.ptr, p->like_size, t.Cnn.ptr);
     }
-    k_stage_compact<T><<<grid_for(p->pn_size, thr), thr, 0, s>>>(
+    launch("k_stage_compact", k_stage_compact<T>, grid_for(p->pn_size, thr), thr, 0, s, 
         src[2], Gp, poff.ptr, pn.ptr, pgp.ptr, ppairs.ptr, p->pn_size, t.Cpn.ptr);
-    k_stage_spectator<T><<<grid_for(S3, thr), thr, 0, s>>>(src[0], 0, t.Upp.ptr);
-    k_stage_spectator<T><<<grid_for(S3, thr), thr, 0, s>>>(src[1], 0, t.Unn.ptr);
-    k_stage_spectator<T><<<grid_for(S3, thr), thr, 0, s>>>(src[2], 0, t.Upn.ptr);
-    k_stage_spectator<T><<<grid_for(S3, thr), thr, 0, s>>>(src[2], 1, t.Wpn.ptr);
-    k_stage_diag<T><<<grid_for(S2, thr), thr, 0, s>>>(src[0], t.Dpp.ptr);
-    k_stage_diag<T><<<grid_for(S2, thr), thr, 0, s>>>(src[1], t.Dnn.ptr);
-    k_stage_diag<T><<<grid_for(S2, thr), thr, 0, s>>>(src[2], t.Dpn.ptr);
+    launch("k_stage_spectator", k_stage_spectator<T>, grid_for(S3, thr), thr, 0, s, src[0], 0, t.Upp.ptr);
+    launch("k_stage_spectator", k_stage_spectator<T>, grid_for(S3, thr), thr, 0, s, src[1], 0, t.Unn.ptr);
+    launch("k_stage_spectator", k_stage_spectator<T>, grid_for(S3, thr), thr, 0, s, src[2], 0, t.Upn.ptr);
+    launch("k_stage_spectator", k_stage_spectator<T>, grid_for(S3, thr), thr, 0, s, src[2], 1, t.Wpn.ptr);
+    launch("k_stage_diag", k_stage_diag<T>, grid_for(S2, thr), thr, 0, s, src[0], t.Dpp.ptr);
+    launch("k_stage_diag", k_stage_diag<T>, grid_for(S2, thr), thr, 0, s, src[1], t.Dnn.ptr);
+    launch("k_stage_diag", k_stage_diag<T>, grid_for(S2, thr), thr, 0, s, src[2], t.Dpn.ptr);
     CI_CHECK_LAUNCH();
     CI_CUDA(cudaStreamSynchronize(s));  // the group arrays are freed on return
     t.ready = true;
@@ -437,7 +437,7 @@ void enumerate_basis(Problem *p, cudaStream_t s) {
     p->d_row_p.alloc(p->dim);
     p->d_row_n.alloc(p->dim);
     if (p->dim > 0) {
-        k_row_map<<<grid_for(p->dim, 256), 256, 0, s>>>(p->dim, P.n, p->d_p_row_base.ptr, d_nstart.ptr,
+        launch("k_row_map", k_row_map, grid_for(p->dim, 256), 256, 0, s, p->dim, P.n, p->d_p_row_base.ptr, d_nstart.ptr,
                                                          p->d_row_p.ptr, p->d_row_n.ptr);
         CI_CHECK_LAUNCH();
     }

@@ -92,16 +92,16 @@ void exclusive_scan_i32(const int32_t *counts, int64_t n, int64_t *offsets, DevB
                         cudaStream_t s) {
     if (n < 0) fail(CI_ERR_INVALID_ARG, "scan length < 0");
     if (n == 0) {
-        k_zero_total<<<1, 1, 0, s>>>(offsets);
+        launch("k_zero_total", k_zero_total, 1, 1, 0, s, offsets);
         CI_CHECK_LAUNCH();
         return;
     }
     int64_t nb = (n + kTile - 1) / kTile;
     if (nb > INT32_MAX) fail(CI_ERR_CAPACITY, "scan too long");
     scratch.ensure((size_t)nb);
-    k_tile_sums<<<(unsigned)nb, kScanThreads, 0, s>>>(counts, n, scratch.ptr);
-    k_scan_sums<<<1, kScanThreads, 0, s>>>(scratch.ptr, nb);
-    k_tile_apply<<<(unsigned)nb, kScanThreads, 0, s>>>(counts, n, scratch.ptr, offsets);
+    launch("k_tile_sums", k_tile_sums, (unsigned)nb, kScanThreads, 0, s, counts, n, scratch.ptr);
+    launch("k_scan_sums", k_scan_sums, 1, kScanThreads, 0, s, scratch.ptr, nb);
+    launch("k_tile_apply", k_tile_apply, (unsigned)nb, kScanThreads, 0, s, counts, n, scratch.ptr, offsets);
     CI_CHECK_LAUNCH();
 }
 

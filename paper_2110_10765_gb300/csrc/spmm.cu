@@ -76,23 +76,23 @@ __global__ void __launch_bounds__(256) k_spmm(int64_t dim, const int64_t *__rest
 }
 
 template <class TV, class TX, int NV>
-static void launch(const Matrix *m, const void *X, void *Y, cudaStream_t s) {
+static void launch_spmm(const Matrix *m, const void *X, void *Y, cudaStream_t s) {
     int grid = grid_for(m->dim * 32, 256, sm_count() * 8);
-    k_spmm<TV, TX, NV><<<grid, 256, 0, s>>>(m->dim, m->row_ptr.ptr, m->col.ptr, (const TV *)m->val.ptr,
-                                            (const TX *)X, (TX *)Y);
+    launch("k_spmm", k_spmm<TV, TX, NV>, grid, 256, 0, s, m->dim, m->row_ptr.ptr, m->col.ptr,
+           (const TV *)m->val.ptr, (const TX *)X, (TX *)Y);
 }
 
 template <class TV, class TX>
 static void dispatch(const Matrix *m, const void *X, void *Y, int nvec, cudaStream_t s) {
     switch (nvec) {
-        case 1: launch<TV, TX, 1>(m, X, Y, s); break;
-        case 2: launch<TV, TX, 2>(m, X, Y, s); break;
-        case 3: launch<TV, TX, 3>(m, X, Y, s); break;
-        case 4: launch<TV, TX, 4>(m, X, Y, s); break;
-        case 5: launch<TV, TX, 5>(m, X, Y, s); break;
-        case 6: launch<TV, TX, 6>(m, X, Y, s); break;
-        case 7: launch<TV, TX, 7>(m, X, Y, s); break;
-        case 8: launch<TV, TX, 8>(m, X, Y, s); break;
+        case 1: launch_spmm<TV, TX, 1>(m, X, Y, s); break;
+        case 2: launch_spmm<TV, TX, 2>(m, X, Y, s); break;
+        case 3: launch_spmm<TV, TX, 3>(m, X, Y, s); break;
+        case 4: launch_spmm<TV, TX, 4>(m, X, Y, s); break;
+        case 5: launch_spmm<TV, TX, 5>(m, X, Y, s); break;
+        case 6: launch_spmm<TV, TX, 6>(m, X, Y, s); break;
+        case 7: launch_spmm<TV, TX, 7>(m, X, Y, s); break;
+        case 8: launch_spmm<TV, TX, 8>(m, X, Y, s); break;
         default: fail(CI_ERR_INVALID_ARG, "nvec must be 1..8 (got %d)", nvec);
     }
 }
