@@ -215,7 +215,8 @@ typedef struct {
     int32_t max_iter;     /* block steps in total                       [2000] */
     double tol;           /* converged when ||H x - theta x|| <= tol*||H||[1e-8] */
     uint64_t seed;        /* seed of the start block                      [1]  */
-    int32_t reorth_passes;/* full Gram-Schmidt passes per step, 1..2      [2]  */
+    int32_t reorth_passes;/* full Gram-Schmidt passes per step after the
+                             projection on the two newest blocks, 1..2    [1]  */
     int32_t check_every;  /* block steps between convergence checks       [2]  */
 } ci_eig_opts;
 
@@ -230,7 +231,9 @@ typedef struct {
 } ci_eig_info;
 
 /* Fig. 1 line 15 (Sec. 2): lowest k eigenvalues of H by block Lanczos with
- * full FP64 reorthogonalisation and thick restart.  SpMM in the matrix's
+ * full FP64 reorthogonalisation (classical Gram-Schmidt against the two
+ * newest blocks, then reorth_passes passes over the whole basis) and thick
+ * restart.  SpMM in the matrix's
  * precision, everything else in FP64.  evals: host [k], ascending.  evecs:
  * nullable device double [dim][k], unit norm.  info: nullable.  Returns
  * CI_ERR_NOT_CONVERGED (with the best estimates written) if max_iter is hit. */

@@ -22,8 +22,7 @@ struct RowArgs {
     const int64_t *o_ptr, *l2_ptr, *l4_ptr;
     const ConnEntry<T> *o_ent, *l2_ent, *l4_ent;
     const int32_t *seg2, *seg4;
-    const T *Upn, *Wpn, *Dpn, *Cpn;
-    const int32_t *pn_row, *pn_col;
+    const T *Upn, *Wpn, *Dpn, *Tpn;
     int32_t *row_cnt;          // count pass
     const int64_t *row_ptr;    // fill pass
     int32_t *col;
@@ -138,6 +137,7 @@ __global__ void __launch_bounds__(256) k_fill_rows(RowArgs<T> a) {
                 }
                 const int k = t - __shfl_sync(0xffffffffu, excl, j);
                 const int pt = __shfl_sync(0xffffffffu, ep.tgt, j);
+                const int ptb = __shfl_sync(0xffffffffu, ep.local, j);
                 const uint32_t pinfo = __shfl_sync(0xffffffffu, ep.info, j);
                 const T pval = __shfl_sync(0xffffffffu, ep.val, j);
                 const int jkind = __shfl_sync(0xffffffffu, kind, j);
@@ -157,9 +157,8 @@ __global__ void __launch_bounds__(256) k_fill_rows(RowArgs<T> a) {
                             const T *u = a.Upn + ((int64_t)cp * S + ap) * S;
                             T h = pval + sum_over_bits<T>(u, nb0, nb1);
                             v = info_neg(pinfo) ? -h : h;
-                        } else {                          // (2,2): V^pn_{c d, a b}
-                            const int an = info_a(en.info), cn = info_c(en.info);
-                            T w = a.Cpn[a.pn_row[cp * S + cn] + a.pn_col[ap * S + an]];
+                        } else {                          // (2,2): V^pn_{c_p c_n, a_p a_n}
+                            T w = a.Tpn[ptb + info_tcol(en.info)];
                             v = (info_neg(pinfo) ^ info_neg(en.info)) ? -w : w;
                         }
                     } else {                        // p' = p
@@ -208,8 +207,7 @@ static RowArgs<T> row_args(Problem *p) {
     a.o_ptr = c.outer.ptr.ptr; a.l2_ptr = c.l2.ptr.ptr; a.l4_ptr = c.l4.ptr.ptr;
     a.o_ent = c.outer.ent.ptr; a.l2_ent = c.l2.ent.ptr; a.l4_ent = c.l4.ent.ptr;
     a.seg2 = c.seg2.ptr; a.seg4 = c.seg4.ptr;
-    a.Upn = t.Upn.ptr; a.Wpn = t.Wpn.ptr; a.Dpn = t.Dpn.ptr; a.Cpn = t.Cpn.ptr;
-    a.pn_row = p->pn_row.ptr; a.pn_col = p->pn_col.ptr;
+    a.Upn = t.Upn.ptr; a.Wpn = t.Wpn.ptr; a.Dpn = t.Dpn.ptr; a.Tpn = t.Tpn.ptr;
     a.row_cnt = p->row_cnt.ptr; a.row_ptr = nullptr; a.col = nullptr; a.val = nullptr;
     return a;
 }

@@ -17,6 +17,8 @@ struct FilterArgs {
     const uint8_t *occ;        // [n][A]
     const T *eps, *U, *D, *C;  // like-particle tables of this species
     const int32_t *pair_row, *pair_col;
+    const int32_t *tr_base;    // outer list: row offset of a proton move in the pn table
+    const int32_t *tr_idx;     // neutron lists: column index of a neutron move
     int32_t *count;            // pass 0
     const int64_t *ptr;        // pass 1
     ConnEntry<T> *ent;         // pass 1
@@ -74,6 +76,8 @@ __device__ ConnEntry<T> make_entry(const FilterArgs<T> &a, int64_t s, int64_t t,
         for (int i = 0; i < a.A; ++i)
             if (o[i] != ao) h += u[o[i]];
         e.info = make_info(1, par & 1, ao, co);
+        if (a.mode == CONN_OUTER) e.local = a.tr_base[co * S + ao];
+        else e.info |= (uint32_t)a.tr_idx[co * S + ao] << 17;
         e.val = h;
         return e;
     }
@@ -97,42 +101,80 @@ __device__ ConnEntry<T> make_entry(const FilterArgs<T> &a, int64_t s, int64_t t,
     return e;
 }
 
-// One warp per row determinant s; lanes sweep the partners t in order.
-template <class T, int W>
+// Each warp owns RW row determinants; the block's warps sweep the partner
+// list in tiles of kTile determinants staged in shared memory (bits and 2M),
+// so the list is read once per block.  Lanes take one partner each and a
+// warp ballot per row keeps the partners in ascending order.
+constexpr int kTile = 512;
+
+template <class T, int W, int RW>
 __global__ void __launch_bounds__(256) k_filter(FilterArgs<T> a, int pass) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t s = warp; s < a.n; s += nwarps) {
-        uint64_t bs[kMaxWords] = {0, 0};
-        for (int w = 0; w < W; ++w) bs[w] = a.bits[s * W + w];
-        const int ms = a.twoM[s];
-        int64_t out = pass ? a.ptr[s] : 0;
-        int cnt = 0;
-        for (int64_t base = 0; base < a.n; base += 32) {
-            int64_t t = base + lane;
-            bool keep = false;
-            int d = 0;
-            uint64_t bt[kMaxWords] = {0, 0};
-            if (t < a.n) {
-                for (int w = 0; w < W; ++w) {
-                    bt[w] = a.bits[t * W + w];
-                    d += __popcll(bs[w] ^ bt[w]);
-                }
-                bool sameM = a.twoM[t] == ms;
+    __shared__ uint64_t sbits[kTile * W];
+    __shared__ int32_t sm2[kTile];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t row0 = ((int64_t)blockIdx.x * 8 + wid) * RW;
+    uint64_t bs[RW][kMaxWords];
+    int ms[RW];
+    int64_t out[RW];
+    int cnt[RW];
+#pragma unroll
+    for (int i = 0; i < RW; ++i) {
+        const int64_t s = row0 + i;
+        const bool ok = s < a.n;
+#pragma unroll
+        for (int w = 0; w < kMaxWords; ++w) bs[i][w] = (ok && w < W) ? a.bits[s * W + w] : 0ull;
+        ms[i] = ok ? a.twoM[s] : 0;
+        out[i] = (ok && pass) ? a.ptr[s] : 0;
+        cnt[i] = 0;
+    }
+    for (int64_t t0 = 0; t0 < a.n; t0 += kTile) {
+        const int nt = (int)min((int64_t)kTile, a.n - t0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < nt * W; e += blockDim.x) sbits[e] = a.bits[t0 * W + e];
+        for (int e = threadIdx.x; e < nt; e += blockDim.x) sm2[e] = a.twoM[t0 + e];
+        __syncthreads();
+        for (int c0 = 0; c0 < nt; c0 += 32) {
+            const int tl = c0 + lane;
+            const bool tv = tl < nt;
+            uint64_t bt[kMaxWords] = {0ull, 0ull};
+#pragma unroll
+            for (int w = 0; w < W; ++w) bt[w] = tv ? sbits[tl * W + w] : 0ull;
+            const int mt = tv ? sm2[tl] : 0;
+#pragma unroll
+            for (int i = 0; i < RW; ++i) {
+                int d = 0;
+#pragma unroll
+                for (int w = 0; w < W; ++w) d += __popcll(bs[i][w] ^ bt[w]);
+                const bool sameM = mt == ms[i];
+                bool keep;
                 if (a.mode == CONN_OUTER) keep = d <= 2 || (d == 4 && sameM);
                 else if (a.mode == CONN_L2) keep = d <= 2;
                 else keep = d <= 4 && sameM;
+                keep = keep && tv && (row0 + i < a.n);
+                const unsigned bal = __ballot_sync(0xffffffffu, keep);
+                if (pass && keep) {
+                    const int rank = __popc(bal & ((1u << lane) - 1u));
+                    a.ent[out[i] + rank] = make_entry<T>(a, row0 + i, t0 + tl, bs[i], bt, d);
+                }
+                out[i] += __popc(bal);
+                cnt[i] += __popc(bal);
             }
-            unsigned bal = __ballot_sync(0xffffffffu, keep);
-            if (pass && keep) {
-                int rank = __popc(bal & ((1u << lane) - 1u));
-                a.ent[out + rank] = make_entry<T>(a, s, t, bs, bt, d);
-            }
-            out += __popc(bal);
-            cnt += __popc(bal);
         }
-        if (!pass && lane == 0) a.count[s] = cnt;
+    }
+    if (!pass && lane == 0) {
+#pragma unroll
+        for (int i = 0; i < RW; ++i)
+            if (row0 + i < a.n) a.count[row0 + i] = cnt[i];
+    }
+}
+
+template <class T, int W>
+static void launch_filter(const FilterArgs<T> &a, int pass, cudaStream_t s) {
+    // rows per warp: 4 when that still gives every SM a few blocks
+    if (a.n >= (int64_t)sm_count() * 4 * 32) {
+        launch("k_filter", k_filter<T, W, 4>, (unsigned)((a.n + 31) / 32), 256, 0, s, a, pass);
+    } else {
+        launch("k_filter", k_filter<T, W, 1>, (unsigned)((a.n + 7) / 8), 256, 0, s, a, pass);
     }
 }
 
@@ -194,6 +236,7 @@ static void build_list(Problem *p, int species, int mode, ConnList<T> &L, cudaSt
     a.D = species == 0 ? t.Dpp.ptr : t.Dnn.ptr;
     a.C = species == 0 ? t.Cpp.ptr : t.Cnn.ptr;
     a.pair_row = p->like_row.ptr; a.pair_col = p->like_col.ptr;
+    a.tr_base = p->tr_base.ptr; a.tr_idx = p->tr_idx.ptr;
     DevBuf<int32_t> cnt(sp.n);
     a.count = cnt.ptr; a.ptr = nullptr; a.ent = nullptr;
     L.ptr.alloc(sp.n + 1);
@@ -203,18 +246,16 @@ static void build_list(Problem *p, int species, int mode, ConnList<T> &L, cudaSt
         L.ent.alloc(1);
         return;
     }
-    const int thr = 256;
-    int grid = grid_for(sp.n * 32, thr, sm_count() * 8);
-    if (sp.W == 1) launch("k_filter", k_filter<T, 1>, grid, thr, 0, s, a, 0);
-    else launch("k_filter", k_filter<T, 2>, grid, thr, 0, s, a, 0);
+    if (sp.W == 1) launch_filter<T, 1>(a, 0, s);
+    else launch_filter<T, 2>(a, 0, s);
     CI_CHECK_LAUNCH();
     exclusive_scan_i32(cnt.ptr, sp.n, L.ptr.ptr, p->scan_scratch, s);
     CI_CUDA(cudaMemcpyAsync(&L.total, L.ptr.ptr + sp.n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     CI_CUDA(cudaStreamSynchronize(s));
     L.ent.alloc(L.total);
     a.ptr = L.ptr.ptr; a.ent = L.ent.ptr;
-    if (sp.W == 1) launch("k_filter", k_filter<T, 1>, grid, thr, 0, s, a, 1);
-    else launch("k_filter", k_filter<T, 2>, grid, thr, 0, s, a, 1);
+    if (sp.W == 1) launch_filter<T, 1>(a, 1, s);
+    else launch_filter<T, 2>(a, 1, s);
     CI_CHECK_LAUNCH();
 }
 

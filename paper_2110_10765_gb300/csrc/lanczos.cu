@@ -18,40 +18,74 @@ namespace ci {
 constexpr int kTnThreads = 256;   // 8 warps: warp v owns column v of B
 constexpr int kMaxNa = 256;       // columns of A in one product
 
-// part[blk][u][v] = sum_{i in rows of blk} A[i][u] B[i][v], u < na, v < nb <= 8
+constexpr int kTR = 32;           // rows of A and B staged per tile
+
+// part[blk][u][v] = sum over the block's rows i of A[i][u] B[i][v]
+// (u < na <= 256, v < nb <= 8).  Tiles of kTR rows of A and B are staged
+// in shared memory with coalesced loads; thread t owns outputs t + 256 j.
 __global__ void __launch_bounds__(kTnThreads) k_tn_partial(int64_t dim, const double *__restrict__ A, int lda, int na,
                                                            const double *__restrict__ B, int ldb, int nb,
                                                            double *__restrict__ part, int64_t rows_per_blk) {
-    const int v = threadIdx.x >> 5, u0 = threadIdx.x & 31;
-    double acc[kMaxNa / 32];
+    extern __shared__ double sm[];
+    double *As = sm;             // [kTR][na]
+    double *Bs = sm + kTR * na;  // [kTR][nb]
+    const int nout = na * nb;
+    double acc[kMaxNa * 8 / kTnThreads];
 #pragma unroll
-    for (int j = 0; j < kMaxNa / 32; ++j) acc[j] = 0.0;
+    for (int j = 0; j < kMaxNa * 8 / kTnThreads; ++j) acc[j] = 0.0;
     const int64_t r0 = blockIdx.x * rows_per_blk;
     const int64_t r1 = min(dim, r0 + rows_per_blk);
-    if (v < nb) {
-        for (int64_t i = r0; i < r1; ++i) {
-            const double bv = B[i * ldb + v];
-            const double *Ai = A + i * lda;
+    for (int64_t t0 = r0; t0 < r1; t0 += kTR) {
+        const int rows = (int)min((int64_t)kTR, r1 - t0);
+#pragma unroll 4
+        for (int e = threadIdx.x; e < rows * na; e += kTnThreads) {
+            const int r = e / na, u = e - r * na;
+            As[e] = A[(t0 + r) * lda + u];
+        }
+        for (int e = threadIdx.x; e < rows * nb; e += kTnThreads) {
+            const int r = e / nb, v = e - r * nb;
+            Bs[e] = B[(t0 + r) * ldb + v];
+        }
+        __syncthreads();
 #pragma unroll
-            for (int j = 0; j < kMaxNa / 32; ++j) {
-                const int u = u0 + 32 * j;
-                if (u < na) acc[j] = fma(Ai[u], bv, acc[j]);
+        for (int j = 0; j < kMaxNa * 8 / kTnThreads; ++j) {
+            const int o = threadIdx.x + j * kTnThreads;
+            if (o < nout) {
+                const int u = o / nb, v = o - u * nb;
+                double s = acc[j];
+                for (int r = 0; r < rows; ++r) s = fma(As[r * na + u], Bs[r * nb + v], s);
+                acc[j] = s;
             }
         }
+        __syncthreads();
+    }
 #pragma unroll
-        for (int j = 0; j < kMaxNa / 32; ++j) {
-            const int u = u0 + 32 * j;
-            if (u < na) part[((int64_t)blockIdx.x * na + u) * nb + v] = acc[j];
-        }
+    for (int j = 0; j < kMaxNa * 8 / kTnThreads; ++j) {
+        const int o = threadIdx.x + j * kTnThreads;
+        if (o < nout) part[(int64_t)blockIdx.x * nout + o] = acc[j];
     }
 }
 
-// out[e] = sum_blk part[blk][e] in block order (deterministic)
-__global__ void k_reduce_partial(const double *__restrict__ part, int nblk, int n, double *__restrict__ out) {
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
-        double s = 0.0;
-        for (int b = 0; b < nblk; ++b) s += part[(int64_t)b * n + e];
-        out[e] = s;
+// out[o] = sum_blk part[blk][o]: 32 outputs per block, 8 warps each sum a
+// fixed stride of blocks, then warp 0 adds the 8 partials in order
+// (deterministic).
+__global__ void __launch_bounds__(256) k_reduce_partial(const double *__restrict__ part, int nblk, int n,
+                                                        double *__restrict__ out) {
+    __shared__ double red[8][33];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int o = blockIdx.x * 32 + lane;
+    double s = 0.0;
+    if (o < n) {
+#pragma unroll 4
+        for (int b = w; b < nblk; b += 8) s += part[(int64_t)b * n + o];
+    }
+    red[w][lane] = s;
+    __syncthreads();
+    if (w == 0 && o < n) {
+        double t = 0.0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) t += red[i][lane];
+        out[o] = t;
     }
 }
 
@@ -129,7 +163,7 @@ struct Solver {
     bool f64;
     int nblk;
     int64_t rows_per_blk;
-    DevBuf<double> Q, W, tmp, part, Cdev, Mdev, theta_dev;
+    DevBuf<double> Q, W, tmp, part, Cdev, Mdev, theta_dev, Cacc;
     DevBuf<float> X32, Y32;
     DevBuf<double> X64;
     double hnorm = 0.0;
@@ -137,7 +171,13 @@ struct Solver {
     Solver(const Matrix *H_, cudaStream_t s_, int b_, int k_, int mmax_)
         : H(H_), s(s_), dim(H_->dim), b(b_), k(k_), mmax(mmax_), f64(H_->vtype == CI_F64) {
         int sms = sm_count();
-        nblk = (int)std::min<int64_t>((int64_t)sms * 4, (dim + 63) / 64);
+        static bool attr = false;
+        if (!attr) {
+            CI_CUDA(cudaFuncSetAttribute(k_tn_partial, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(sizeof(double) * kTR * (kMaxNa + 8))));
+            attr = true;
+        }
+        nblk = (int)std::min<int64_t>((int64_t)sms * 2, (dim + 63) / 64);
         if (nblk < 1) nblk = 1;
         rows_per_blk = (dim + nblk - 1) / nblk;
         Q.alloc((size_t)dim * mmax);
@@ -157,8 +197,10 @@ struct Solver {
     // host != null, copied to host.
     void tn(const double *A, int lda, int na, const double *B, int ldb, int nb, double *Cout,
             std::vector<double> *host) {
-        launch("k_tn_partial", k_tn_partial, nblk, kTnThreads, 0, s, dim, A, lda, na, B, ldb, nb, part.ptr, rows_per_blk);
-        launch("k_reduce_partial", k_reduce_partial, grid_for(na * nb, 128, 64), 128, 0, s, part.ptr, nblk, na * nb, Cout);
+        const size_t smem = sizeof(double) * kTR * (na + nb);
+        launch("k_tn_partial", k_tn_partial, nblk, kTnThreads, smem, s, dim, A, lda, na, B, ldb, nb, part.ptr,
+               rows_per_blk);
+        launch("k_reduce_partial", k_reduce_partial, (na * nb + 31) / 32, 256, 0, s, part.ptr, nblk, na * nb, Cout);
         CI_CHECK_LAUNCH();
         if (host) {
             host->resize((size_t)na * nb);
@@ -192,16 +234,34 @@ struct Solver {
 
     // Project the block Wb [dim][nb] (ld nb) against Q[:, 0:m], `passes`
     // times; returns the summed coefficients (m x nb, host).
-    void project(double *Wb, int nb, int m, int passes, std::vector<double> *coef) {
+    // Orthogonalise Wb [dim][nb] (ld nb) against Q[:, 0:m]: first against
+    // the columns [lo, m) (the newest blocks, which carry the large
+    // three-term components), then `passes` full classical Gram-Schmidt
+    // passes against all m columns.  coef (m x nb, host) receives the sum
+    // of all projection coefficients, i.e. Q^T (H V_j).  One host sync.
+    void project(double *Wb, int nb, int m, int lo, int passes, std::vector<double> *coef) {
         if (coef) coef->assign((size_t)m * nb, 0.0);
         if (m == 0) return;
-        std::vector<double> c;
-        for (int p = 0; p < passes; ++p) {
-            tn(Q.ptr, mmax, m, Wb, nb, nb, Cdev.ptr, coef ? &c : nullptr);
-            nn(Q.ptr, mmax, m, Cdev.ptr, nb, Wb, nb, -1.0, 1.0);
-            if (coef)
-                for (size_t e = 0; e < c.size(); ++e) (*coef)[e] += c[e];
+        const int nl = m - lo;
+        Cacc.ensure((size_t)(passes + 1) * kMaxNa * 8);
+        double *cl = Cacc.ptr;
+        if (nl > 0) {
+            tn(Q.ptr + lo, mmax, nl, Wb, nb, nb, cl, nullptr);
+            nn(Q.ptr + lo, mmax, nl, cl, nb, Wb, nb, -1.0, 1.0);
         }
+        for (int p = 0; p < passes; ++p) {
+            double *cp = Cacc.ptr + (size_t)(p + 1) * kMaxNa * 8;
+            tn(Q.ptr, mmax, m, Wb, nb, nb, cp, nullptr);
+            nn(Q.ptr, mmax, m, cp, nb, Wb, nb, -1.0, 1.0);
+        }
+        if (!coef) return;
+        std::vector<double> h((size_t)(passes + 1) * kMaxNa * 8);
+        CI_CUDA(cudaMemcpyAsync(h.data(), Cacc.ptr, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s));
+        CI_CUDA(cudaStreamSynchronize(s));
+        for (int i = 0; i < nl; ++i)
+            for (int v = 0; v < nb; ++v) (*coef)[(size_t)(lo + i) * nb + v] += h[(size_t)i * nb + v];
+        for (int p = 0; p < passes; ++p)
+            for (size_t e = 0; e < (size_t)m * nb; ++e) (*coef)[e] += h[(size_t)(p + 1) * kMaxNa * 8 + e];
     }
 
     // Orthonormalise Wb [dim][b] (already orthogonal to Q[:, 0:m]) into
@@ -317,7 +377,7 @@ void lowest_eigs(const Matrix *H, const ci_eig_opts *opts_in, double *evals, dou
     if (o.max_iter == 0) o.max_iter = 2000;
     if (o.tol == 0.0) o.tol = H->vtype == CI_F64 ? 1e-10 : 1e-7;
     if (o.seed == 0) o.seed = 1;
-    if (o.reorth_passes == 0) o.reorth_passes = 2;
+    if (o.reorth_passes == 0) o.reorth_passes = 1;
     if (o.check_every == 0) o.check_every = 2;
     if (o.k < 1 || o.k > 32) fail(CI_ERR_INVALID_ARG, "k must be 1..32");
     if (o.block < 1 || o.block > 8) fail(CI_ERR_INVALID_ARG, "block must be 1..8");
@@ -407,7 +467,7 @@ void lowest_eigs(const Matrix *H, const ci_eig_opts *opts_in, double *evals, dou
     while (true) {
         // W = H V_j, orthogonalised against the whole basis
         sv.apply(sv.Q.ptr + j0, mmax, b, sv.W.ptr);
-        sv.project(sv.W.ptr, b, m_cur, o.reorth_passes, &coef);
+        sv.project(sv.W.ptr, b, m_cur, std::max(0, j0 - b), o.reorth_passes, &coef);
         for (int i = 0; i < j0; ++i)
             for (int v = 0; v < b; ++v) {
                 T[(size_t)i * mmax + j0 + v] = coef[(size_t)i * b + v];

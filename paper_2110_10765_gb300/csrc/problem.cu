@@ -110,12 +110,15 @@ __device__ __forceinline__ T to_prec(double v, const TbmeSrc &t) {
     return (T)v;
 }
 
-// Compact pair-pair blocks: entry e of group g is row pair iP, column pair
-// iQ with V[row pair][col pair].
+// Compact blocks: entry e of group g is (row item i, column item j) of the
+// group's row and column lists; items are codes x*S+y.
+//   mode 0 (like pairs): row (c,d), column (a,b) -> V_{cd,ab}
+//   mode 1 (pn moves):   row (c,a) proton move, column (c',a') neutron move
+//                        -> V^pn_{c c', a a'}
 template <class T>
-__global__ void k_stage_compact(TbmeSrc t, int G, const int64_t *grp_off, const int32_t *grp_n,
-                                const int32_t *grp_pairs, const int32_t *pairs, int64_t total,
-                                T *out) {
+__global__ void k_stage_compact(TbmeSrc t, int mode, int G, const int64_t *grp_off, const int32_t *grp_ncol,
+                                const int32_t *grp_rows, const int32_t *grp_cols, const int32_t *items,
+                                int64_t total, T *out) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
         int lo = 0, hi = G - 1;
@@ -124,11 +127,12 @@ __global__ void k_stage_compact(TbmeSrc t, int G, const int64_t *grp_off, const 
             if (grp_off[mid] <= e) lo = mid; else hi = mid - 1;
         }
         int64_t r = e - grp_off[lo];
-        int n = grp_n[lo];
-        int iP = (int)(r / n), iQ = (int)(r % n);
-        int pr = pairs[grp_pairs[lo] + iP], pc = pairs[grp_pairs[lo] + iQ];
-        int c = pr / t.S, d = pr % t.S, a = pc / t.S, b = pc % t.S;
-        out[e] = to_prec<T>(tbme_fetch(t, c, d, a, b), t);
+        int n = grp_ncol[lo];
+        int i = (int)(r / n), j = (int)(r % n);
+        int pr = items[grp_rows[lo] + i], pc = items[grp_cols[lo] + j];
+        int x1 = pr / t.S, y1 = pr % t.S, x2 = pc / t.S, y2 = pc % t.S;
+        double v = mode == 0 ? tbme_fetch(t, x1, y1, x2, y2) : tbme_fetch(t, x1, x2, y1, y2);
+        out[e] = to_prec<T>(v, t);
     }
 }
 
@@ -158,22 +162,23 @@ __global__ void k_stage_diag(TbmeSrc t, T *out) {
 
 // ------------------------------------------------------------------ pair maps
 
+// Groups of a compact table: group g has rows items[grp_rows[g] ..] and
+// columns items[grp_cols[g] ..], stored row-major from grp_off[g].
 struct PairGroups {
     std::vector<int64_t> grp_off;   // [G+1] compact offsets
-    std::vector<int32_t> grp_n;     // [G]
-    std::vector<int32_t> grp_pairs; // [G] start in pairs
-    std::vector<int32_t> pairs;     // codes a*S+b
-    std::vector<int32_t> row, col;  // [S*S], -1 where not a pair
+    std::vector<int32_t> grp_ncol;  // [G]
+    std::vector<int32_t> grp_rows;  // [G] start of the row items
+    std::vector<int32_t> grp_cols;  // [G] start of the column items
+    std::vector<int32_t> items;     // codes x*S+y
+    std::vector<int32_t> row, col;  // [S*S]: row offset / column index, -1 if none
 };
 
-static PairGroups make_pairs(const std::vector<int32_t> &twom, bool like) {
+// like pairs a<b grouped by m_a + m_b (rows = columns = the group's pairs)
+static PairGroups make_like_pairs(const std::vector<int32_t> &twom) {
     int S = (int)twom.size();
     std::map<int, std::vector<int32_t>> by_m;
     for (int a = 0; a < S; ++a)
-        for (int b = 0; b < S; ++b) {
-            if (like && !(a < b)) continue;
-            by_m[twom[a] + twom[b]].push_back(a * S + b);
-        }
+        for (int b = a + 1; b < S; ++b) by_m[twom[a] + twom[b]].push_back(a * S + b);
     PairGroups g;
     g.row.assign((size_t)S * S, -1);
     g.col.assign((size_t)S * S, -1);
@@ -181,14 +186,52 @@ static PairGroups make_pairs(const std::vector<int32_t> &twom, bool like) {
     for (auto &kv : by_m) {
         auto &v = kv.second;
         g.grp_off.push_back(off);
-        g.grp_n.push_back((int32_t)v.size());
-        g.grp_pairs.push_back((int32_t)g.pairs.size());
+        g.grp_ncol.push_back((int32_t)v.size());
+        g.grp_rows.push_back((int32_t)g.items.size());
+        g.grp_cols.push_back((int32_t)g.items.size());
         for (size_t i = 0; i < v.size(); ++i) {
             g.row[v[i]] = (int32_t)(off + (int64_t)i * (int64_t)v.size());
             g.col[v[i]] = (int32_t)i;
-            g.pairs.push_back(v[i]);
+            g.items.push_back(v[i]);
         }
         off += (int64_t)v.size() * (int64_t)v.size();
+    }
+    g.grp_off.push_back(off);
+    return g;
+}
+
+// one-particle moves a -> c (c != a) grouped by D = 2m_c - 2m_a; the block
+// of D has the proton moves of D as rows and the neutron moves of -D as
+// columns (total M is conserved).  row[c*S+a] = offset of the move's row,
+// col[c*S+a] = index of the move in its own group (its column index).
+static PairGroups make_transitions(const std::vector<int32_t> &twom) {
+    int S = (int)twom.size();
+    std::map<int, std::vector<int32_t>> by_d;
+    for (int c = 0; c < S; ++c)
+        for (int a = 0; a < S; ++a)
+            if (c != a) by_d[twom[c] - twom[a]].push_back(c * S + a);
+    PairGroups g;
+    g.row.assign((size_t)S * S, -1);
+    g.col.assign((size_t)S * S, -1);
+    std::map<int, int32_t> start;
+    for (auto &kv : by_d) {
+        start[kv.first] = (int32_t)g.items.size();
+        for (size_t i = 0; i < kv.second.size(); ++i) {
+            g.col[kv.second[i]] = (int32_t)i;
+            g.items.push_back(kv.second[i]);
+        }
+    }
+    int64_t off = 0;
+    for (auto &kv : by_d) {
+        auto it = by_d.find(-kv.first);
+        if (it == by_d.end()) continue;
+        int32_t nr = (int32_t)kv.second.size(), nc = (int32_t)it->second.size();
+        g.grp_off.push_back(off);
+        g.grp_ncol.push_back(nc);
+        g.grp_rows.push_back(start[kv.first]);
+        g.grp_cols.push_back(start[-kv.first]);
+        for (int32_t i = 0; i < nr; ++i) g.row[kv.second[i]] = (int32_t)(off + (int64_t)i * nc);
+        off += (int64_t)nr * nc;
     }
     g.grp_off.push_back(off);
     return g;
@@ -237,11 +280,11 @@ void problem_create(const ci_problem_desc *d, Problem *p) {
             CI_CUDA(cudaMemcpyAsync(p->flat[c].ptr, src[c], bytes, cudaMemcpyDefault, s));
         }
     }
-    PairGroups lg = make_pairs(p->sp_twom, true), pg = make_pairs(p->sp_twom, false);
+    PairGroups lg = make_like_pairs(p->sp_twom), tg = make_transitions(p->sp_twom);
     p->like_row.upload(lg.row, s); p->like_col.upload(lg.col, s);
-    p->pn_row.upload(pg.row, s); p->pn_col.upload(pg.col, s);
+    p->tr_base.upload(tg.row, s); p->tr_idx.upload(tg.col, s);
     p->like_size = lg.grp_off.back();
-    p->pn_size = pg.grp_off.back();
+    p->tr_size = tg.grp_off.back();
     p->d_twom.upload(p->sp_twom, s);
     CI_CUDA(cudaStreamSynchronize(s));
 }
@@ -252,19 +295,20 @@ void stage_tables(Problem *p, cudaStream_t s) {
     Tables<T> &t = p->tables<T>();
     if (t.ready) return;
     const int S = p->S;
-    PairGroups lg = make_pairs(p->sp_twom, true), pg = make_pairs(p->sp_twom, false);
-    auto upload_groups = [&](const PairGroups &g, DevBuf<int64_t> &off, DevBuf<int32_t> &n,
-                             DevBuf<int32_t> &gp, DevBuf<int32_t> &pairs) {
-        off.upload(g.grp_off, s); n.upload(g.grp_n, s); gp.upload(g.grp_pairs, s); pairs.upload(g.pairs, s);
+    PairGroups lg = make_like_pairs(p->sp_twom), tg = make_transitions(p->sp_twom);
+    auto upload_groups = [&](const PairGroups &g, DevBuf<int64_t> &off, DevBuf<int32_t> &nc, DevBuf<int32_t> &gr,
+                             DevBuf<int32_t> &gc, DevBuf<int32_t> &items) {
+        off.upload(g.grp_off, s); nc.upload(g.grp_ncol, s); gr.upload(g.grp_rows, s);
+        gc.upload(g.grp_cols, s); items.upload(g.items, s);
     };
-    DevBuf<int64_t> loff, poff;
-    DevBuf<int32_t> ln, lgp, lpairs, pn, pgp, ppairs;
-    upload_groups(lg, loff, ln, lgp, lpairs);
-    upload_groups(pg, poff, pn, pgp, ppairs);
+    DevBuf<int64_t> loff, toff;
+    DevBuf<int32_t> lnc, lgr, lgc, litems, tnc, tgr, tgc, titems;
+    upload_groups(lg, loff, lnc, lgr, lgc, litems);
+    upload_groups(tg, toff, tnc, tgr, tgc, titems);
 
     std::vector<T> eps(p->sp_energy.begin(), p->sp_energy.end());
     t.eps.upload(eps, s);
-    t.Cpp.alloc(p->like_size); t.Cnn.alloc(p->like_size); t.Cpn.alloc(p->pn_size);
+    t.Cpp.alloc(p->like_size); t.Cnn.alloc(p->like_size); t.Tpn.alloc(p->tr_size);
     size_t S3 = (size_t)S * S * S, S2 = (size_t)S * S;
     t.Upp.alloc(S3); t.Unn.alloc(S3); t.Upn.alloc(S3); t.Wpn.alloc(S3);
     t.Dpp.alloc(S2); t.Dnn.alloc(S2); t.Dpn.alloc(S2);
@@ -280,15 +324,16 @@ void stage_tables(Problem *p, cudaStream_t s) {
         src[c].twom = p->d_twom.ptr;
     }
     const int thr = 256;
-    int Gl = (int)lg.grp_n.size(), Gp = (int)pg.grp_n.size();
+    int Gl = (int)lg.grp_ncol.size(), Gt = (int)tg.grp_ncol.size();
     if (p->like_size > 0) {
-        launch("k_stage_compact", k_stage_compact<T>, grid_for(p->like_size, thr), thr, 0, s, 
-            src[0], Gl, loff.ptr, ln.ptr, lgp.ptr, lpairs.ptr, p->like_size, t.Cpp.ptr);
-        launch("k_stage_compact", k_stage_compact<T>, grid_for(p->like_size, thr), thr, 0, s, 
-            src[1], Gl, loff.ptr, ln.ptr, lgp.ptr, lpairs.ptr, p->like_size, t.Cnn.ptr);
+        launch("k_stage_compact", k_stage_compact<T>, grid_for(p->like_size, thr), thr, 0, s, src[0], 0, Gl,
+               loff.ptr, lnc.ptr, lgr.ptr, lgc.ptr, litems.ptr, p->like_size, t.Cpp.ptr);
+        launch("k_stage_compact", k_stage_compact<T>, grid_for(p->like_size, thr), thr, 0, s, src[1], 0, Gl,
+               loff.ptr, lnc.ptr, lgr.ptr, lgc.ptr, litems.ptr, p->like_size, t.Cnn.ptr);
     }
-    launch("k_stage_compact", k_stage_compact<T>, grid_for(p->pn_size, thr), thr, 0, s, 
-        src[2], Gp, poff.ptr, pn.ptr, pgp.ptr, ppairs.ptr, p->pn_size, t.Cpn.ptr);
+    if (p->tr_size > 0)
+        launch("k_stage_compact", k_stage_compact<T>, grid_for(p->tr_size, thr), thr, 0, s, src[2], 1, Gt,
+               toff.ptr, tnc.ptr, tgr.ptr, tgc.ptr, titems.ptr, p->tr_size, t.Tpn.ptr);
     launch("k_stage_spectator", k_stage_spectator<T>, grid_for(S3, thr), thr, 0, s, src[0], 0, t.Upp.ptr);
     launch("k_stage_spectator", k_stage_spectator<T>, grid_for(S3, thr), thr, 0, s, src[1], 0, t.Unn.ptr);
     launch("k_stage_spectator", k_stage_spectator<T>, grid_for(S3, thr), thr, 0, s, src[2], 0, t.Upn.ptr);

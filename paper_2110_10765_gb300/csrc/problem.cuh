@@ -39,14 +39,18 @@ struct SpeciesList {
 // ------------------------------------------------------------------ tables
 
 // Interaction tables of one precision, staged from the flat TBMEs.
-//   C*  : compact pair-pair blocks, V_cdab = C[row[c*S+d] + col[a*S+b]]
+//   C*  : compact like-pair blocks, V_cdab = C[row[c*S+d] + col[a*S+b]] (c<d, a<b)
+//   Tpn : proton-transition x neutron-transition blocks,
+//         V^pn_{c c', a a'} = Tpn[tr_base[c*S+a] + tr_idx[c'*S+a']]
+//         (rows: proton moves a -> c, columns: neutron moves a' -> c', grouped
+//         by the change of 2m, which the two moves must cancel)
 //   U*  : one-move spectator tables, U[(c*S+a)*S+k] = V_{ck,ak}
 //   Wpn : neutron-move pn spectators, Wpn[(d*S+b)*S+k] = V^pn_{kd,kb}
 //   D*  : pair diagonals, D[a*S+b] = V_abab
 template <class T>
 struct Tables {
     DevBuf<T> eps;
-    DevBuf<T> Cpp, Cnn, Cpn;
+    DevBuf<T> Cpp, Cnn, Tpn;
     DevBuf<T> Upp, Unn, Upn, Wpn;
     DevBuf<T> Dpp, Dnn, Dpn;
     bool ready = false;
@@ -55,8 +59,12 @@ struct Tables {
 // One entry of a species connectivity list (row determinant s = bra,
 // partner s' = ket).  info: bits 0-1 difference code (0: d=0, 1: d=2,
 // 2: d=4), bit 2 sign (1: negative), bits 3-9 state a (in s' only), bits
-// 10-16 state c (in s only).  val: d=0 like-particle diagonal energy (one-
-// body + pairs); d=2 unsigned like-particle spectator sum; d=4 signed V.
+// 10-16 state c (in s only), bits 17-31 for d=2 entries of the neutron
+// lists: the column index of the move a -> c in the pn transition table.
+// local: neutron lists, index of s' inside its 2M block; proton list, for
+// d=2 entries the row offset tr_base of the move a -> c in that table.
+// val: d=0 like-particle diagonal energy (one-body + pairs); d=2 unsigned
+// like-particle spectator sum; d=4 signed V.
 template <class T>
 struct ConnEntry {
     int32_t tgt;
@@ -69,6 +77,7 @@ __host__ __device__ inline int info_dcode(uint32_t i) { return (int)(i & 3u); }
 __host__ __device__ inline int info_neg(uint32_t i) { return (int)((i >> 2) & 1u); }
 __host__ __device__ inline int info_a(uint32_t i) { return (int)((i >> 3) & 127u); }
 __host__ __device__ inline int info_c(uint32_t i) { return (int)((i >> 10) & 127u); }
+__host__ __device__ inline int info_tcol(uint32_t i) { return (int)(i >> 17); }
 __host__ __device__ inline uint32_t make_info(int dcode, int neg, int a, int c) {
     return (uint32_t)dcode | ((uint32_t)neg << 2) | ((uint32_t)a << 3) | ((uint32_t)c << 10);
 }
@@ -109,9 +118,11 @@ struct Problem {
     int tbme_dtype = CI_F32;
     DevBuf<unsigned char> flat[3];   // pp, nn, pn (tbme_dtype elements)
 
-    // pair maps: like pairs a<b and pn pairs, grouped by m_a + m_b
-    DevBuf<int32_t> like_row, like_col, pn_row, pn_col;
-    int64_t like_size = 0, pn_size = 0;   // entries of a compact table
+    // like pairs a<b grouped by m_a + m_b; one-particle moves a -> c grouped
+    // by 2m_c - 2m_a (tr_base: row offset as a proton move, tr_idx: column
+    // index as a neutron move)
+    DevBuf<int32_t> like_row, like_col, tr_base, tr_idx;
+    int64_t like_size = 0, tr_size = 0;   // entries of the compact tables
     DevBuf<int32_t> d_twom;
 
     Tables<float> t32;

@@ -44,6 +44,7 @@ template <class TV, class TX, int NV>
 __global__ void __launch_bounds__(256) k_spmm(int64_t dim, const int64_t *__restrict__ rp,
                                               const int32_t *__restrict__ col, const TV *__restrict__ val,
                                               const TX *__restrict__ X, TX *__restrict__ Y) {
+    constexpr int U = 4;  // nonzeros in flight per lane
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -52,9 +53,26 @@ __global__ void __launch_bounds__(256) k_spmm(int64_t dim, const int64_t *__rest
 #pragma unroll
         for (int i = 0; i < NV; ++i) acc[i] = 0;
         const int64_t e1 = rp[r + 1];
-        for (int64_t e = rp[r] + lane; e < e1; e += 32) {
-            const int c = __ldg(col + e);
-            const TX v = (TX)__ldg(val + e);
+        int64_t e = rp[r] + lane;
+        for (; e + 32 * (U - 1) < e1; e += 32 * U) {
+            int c[U];
+            TX v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {  // col/val stream once: evict-first loads
+                c[u] = __ldcs(col + e + 32 * u);
+                v[u] = (TX)__ldcs(val + e + 32 * u);
+            }
+            TX x[U][NV];
+#pragma unroll
+            for (int u = 0; u < U; ++u) VecLoad<TX, NV>::load(X + (int64_t)c[u] * NV, x[u]);
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int i = 0; i < NV; ++i) acc[i] = fma(v[u], x[u][i], acc[i]);
+        }
+        for (; e < e1; e += 32) {
+            const int c = __ldcs(col + e);
+            const TX v = (TX)__ldcs(val + e);
             TX x[NV];
             VecLoad<TX, NV>::load(X + (int64_t)c * NV, x);
 #pragma unroll
@@ -75,9 +93,72 @@ __global__ void __launch_bounds__(256) k_spmm(int64_t dim, const int64_t *__rest
     }
 }
 
+// Eight-vector float SpMM with two lanes per nonzero: lane pair (2j, 2j+1)
+// shares nonzero e and each lane gathers one 16-byte half of X's row, so a
+// warp instruction touches 16 rows of X (one sector each) instead of
+// issuing two loads per row.  Lanes accumulate their four components over
+// the row's nonzeros j, j+16, ... in ascending order, then reduce over the
+// 16 lanes of the same parity.
+template <class TV>
+__global__ void __launch_bounds__(256) k_spmm8_half(int64_t dim, const int64_t *__restrict__ rp,
+                                                    const int32_t *__restrict__ col, const TV *__restrict__ val,
+                                                    const float *__restrict__ X, float *__restrict__ Y) {
+    constexpr int U = 4;  // nonzeros in flight per lane pair
+    const int lane = threadIdx.x & 31, half = lane & 1, pair = lane >> 1;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const float4 *X4 = reinterpret_cast<const float4 *>(X);
+    for (int64_t r = warp; r < dim; r += nwarps) {
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        const int64_t e1 = rp[r + 1];
+        int64_t e = rp[r] + pair;
+        for (; e + 16 * (U - 1) < e1; e += 16 * U) {
+            int c[U];
+            float v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                c[u] = __ldcs(col + e + 16 * u);
+                v[u] = (float)__ldcs(val + e + 16 * u);
+            }
+            float4 x[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) x[u] = __ldg(X4 + (int64_t)c[u] * 2 + half);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                a0 = fmaf(v[u], x[u].x, a0);
+                a1 = fmaf(v[u], x[u].y, a1);
+                a2 = fmaf(v[u], x[u].z, a2);
+                a3 = fmaf(v[u], x[u].w, a3);
+            }
+        }
+        for (; e < e1; e += 16) {
+            const int c = __ldcs(col + e);
+            const float v = (float)__ldcs(val + e);
+            const float4 x = __ldg(X4 + (int64_t)c * 2 + half);
+            a0 = fmaf(v, x.x, a0);
+            a1 = fmaf(v, x.y, a1);
+            a2 = fmaf(v, x.z, a2);
+            a3 = fmaf(v, x.w, a3);
+        }
+#pragma unroll
+        for (int o = 16; o > 1; o >>= 1) {
+            a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+            a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+            a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+            a3 += __shfl_xor_sync(0xffffffffu, a3, o);
+        }
+        if (lane < 2) reinterpret_cast<float4 *>(Y)[r * 2 + half] = make_float4(a0, a1, a2, a3);
+    }
+}
+
 template <class TV, class TX, int NV>
 static void launch_spmm(const Matrix *m, const void *X, void *Y, cudaStream_t s) {
     int grid = grid_for(m->dim * 32, 256, sm_count() * 8);
+    if (NV == 8 && sizeof(TX) == 4) {
+        launch("k_spmm", k_spmm8_half<TV>, grid, 256, 0, s, m->dim, m->row_ptr.ptr, m->col.ptr,
+               (const TV *)m->val.ptr, (const float *)X, (float *)Y);
+        return;
+    }
     launch("k_spmm", k_spmm<TV, TX, NV>, grid, 256, 0, s, m->dim, m->row_ptr.ptr, m->col.ptr,
            (const TV *)m->val.ptr, (const TX *)X, (TX *)Y);
 }
@@ -103,8 +184,8 @@ void apply_matrix(const Matrix *m, const void *X, void *Y, int nvec, cudaStream_
     if (!X || !Y) fail(CI_ERR_INVALID_ARG, "X and Y must be device pointers");
     size_t esz = m->vtype == CI_F64 ? 8 : 4;
     size_t align = (nvec == 8 || nvec == 4) ? 16 : esz;
-    if (((uintptr_t)X % align) != 0 || ((uintptr_t)Y % esz) != 0)
-        fail(CI_ERR_INVALID_ARG, "X must be %zu-byte aligned", align);
+    if (((uintptr_t)X % align) != 0 || ((uintptr_t)Y % align) != 0)
+        fail(CI_ERR_INVALID_ARG, "X and Y must be %zu-byte aligned", align);
     if (m->vtype == CI_F32) dispatch<float, float>(m, X, Y, nvec, s);
     else if (m->vtype == CI_F64) dispatch<double, double>(m, X, Y, nvec, s);
     else fail(CI_ERR_INVALID_ARG, "value type %d not supported by ci_apply_H", m->vtype);
