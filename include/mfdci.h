@@ -184,6 +184,19 @@ ci_status ci_count_nnz(ci_problem *p, int64_t *nnz, int32_t *row_cnt, void *stre
  * Uses a library-owned scratch buffer, grown on demand. */
 ci_status ci_exclusive_scan(const int32_t *counts, int64_t n, int64_t *offsets, void *stream);
 
+/* The same exclusive scan without any device allocation, for callers that
+ * cannot allocate: code whose device memory is owned by another caching
+ * allocator or a fixed reservation, and latency-critical threads on which
+ * cudaMalloc / cudaFree would stall by synchronising the device.  The
+ * paper has no counterpart.  Its tile sums live in one static device array
+ * (512 KB, held by every GPU that loads the library until the process
+ * exits), so n is limited to 2^28 counts; larger n returns CI_ERR_CAPACITY.
+ * The first call on a device looks up the array's device address (make it
+ * before any stream capture).  All calls share the array: calls that
+ * overlap on the GPU (other streams, other threads) race and must be
+ * serialised by the caller.  Outputs are identical to ci_exclusive_scan. */
+ci_status ci_exclusive_scan_noalloc(const int32_t *counts, int64_t n, int64_t *offsets, void *stream);
+
 /* Fig. 1 lines 9-14 (Sec. 2.3, Listing 7): build H in CSR form on the
  * device.  Row i holds every column j with at most 4 differing s.p. states
  * (stored even when its value is 0), columns ascending.  H_ij = <Phi_i|H|Phi_j>

@@ -3,6 +3,8 @@
 // tile sums, a scan of the tile sums, and a rescan of every tile with its
 // prefix.  Every thread owns kItems consecutive counts; warps combine with
 // shuffles.  No kernel waits on another block, so nothing can spin.
+#include <mutex>
+
 #include "problem.cuh"
 
 namespace ci {
@@ -106,3 +108,65 @@ void exclusive_scan_i32(const int32_t *counts, int64_t n, int64_t *offsets, DevB
 }
 
 }  // namespace ci
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the exclusive scan.
+//
+// For callers that must not allocate device memory: code running under a
+// caching allocator that already owns the device's memory budget (a
+// framework pool, a serving process with a fixed reservation), and code on
+// a latency-critical thread where cudaMalloc / cudaFree would stall it by
+// synchronising the device.  The tile sums live in one file-scope device
+// array instead of a library-owned buffer; the caller still passes counts
+// and offsets.
+namespace ci {
+
+constexpr int64_t kNoAllocMaxTiles = 65536;  // n <= 65536 * 4096 = 2^28 counts
+static __device__ __align__(256) int64_t g_scan_tiles[kNoAllocMaxTiles];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+int64_t *g_noalloc_ptr[kMaxDevices];  // device address of g_scan_tiles per device ordinal
+}  // namespace
+
+// Device address of g_scan_tiles on the current device (looked up once per
+// device; the host-side name is only a stand-in for the device symbol).
+static int64_t *noalloc_scratch() {
+    int dev = 0;
+    CI_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) fail(CI_ERR_CAPACITY, "device ordinal %d above %d", dev, kMaxDevices);
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        CI_CUDA(cudaGetSymbolAddress(&p, g_scan_tiles));
+        g_noalloc_ptr[dev] = (int64_t *)p;
+    }
+    return g_noalloc_ptr[dev];
+}
+
+}  // namespace ci
+
+extern "C" ci_status ci_exclusive_scan_noalloc(const int32_t *counts, int64_t n, int64_t *offsets,
+                                               void *stream) {
+    return ci::guard([&] {
+        using namespace ci;
+        if (n < 0) fail(CI_ERR_INVALID_ARG, "n < 0");
+        if (!offsets || (n > 0 && !counts)) fail(CI_ERR_INVALID_ARG, "counts/offsets are NULL");
+        const int64_t nb = (n + kTile - 1) / kTile;
+        if (nb > kNoAllocMaxTiles)
+            fail(CI_ERR_CAPACITY, "ci_exclusive_scan_noalloc: n = %lld exceeds the maximum %lld counts",
+                 (long long)n, (long long)(kNoAllocMaxTiles * kTile));
+        cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+        int64_t *tiles = noalloc_scratch();
+        if (n == 0) {
+            launch("k_zero_total", k_zero_total, 1, 1, 0, s, offsets);
+            return;
+        }
+        // every tile sum is written by k_tile_sums before it is read
+        launch("k_tile_sums", k_tile_sums, (unsigned)nb, kScanThreads, 0, s, counts, n, tiles);
+        launch("k_scan_sums", k_scan_sums, 1, kScanThreads, 0, s, tiles, nb);
+        launch("k_tile_apply", k_tile_apply, (unsigned)nb, kScanThreads, 0, s, counts, n, (const int64_t *)tiles,
+               offsets);
+    });
+}
