@@ -253,6 +253,34 @@ typedef struct {
 ci_status ci_lowest_eigs(const ci_matrix *m, const ci_eig_opts *opts, double *evals,
                          double *evecs, ci_eig_info *info, void *stream);
 
+/* ---------------------------------------------------------------- batched solves */
+
+/* Many independent problems built and solved together (Fig. 1 lines 1-15
+ * for each): every build step runs as one launch over all problems (the
+ * matrices form one block-diagonal CSR, FP32 values), and the solve is a
+ * block Lanczos whose per-problem control (basis size, thick restart,
+ * FP64 Ritz solve by Jacobi, convergence) runs in kernels, so one step of
+ * every unfinished problem is a CUDA graph replay.
+ *
+ * probs: n problem handles (borrowed; they must outlive the batch).
+ * k: per-problem eigenpair counts (1..16), or NULL to use opts->k.
+ * opts: block must be 0 or 8; max_basis (default 64) a multiple of 8 in
+ * 32..96 with 2(k+8) <= max_basis; tol default 1e-7 (relative to ||H||);
+ * max_iter default 400 steps; check_every default 4 steps.
+ * Problems need dimension > max_basis + 16. */
+ci_status ci_batch_create(ci_problem *const *probs, int32_t n, const int32_t *k, const ci_eig_opts *opts,
+                          ci_batch **out);
+/* Build every H and solve.  Synchronous. */
+ci_status ci_batch_run(ci_batch *b, void *stream);
+/* Eigenvalues of problem i (host [k], ascending) and, in info, the steps
+ * taken and the FP64 residuals ||H x - theta x|| (H applied in FP32).
+ * Returns CI_ERR_NOT_CONVERGED (with the values written) if the problem
+ * stopped at max_iter. */
+ci_status ci_batch_result(const ci_batch *b, int32_t i, double *evals, ci_eig_info *info);
+/* Wall time of the build and of the solve, engine steps, total nonzeros. */
+ci_status ci_batch_stats(const ci_batch *b, double *build_s, double *solve_s, int32_t *steps, int64_t *nnz);
+void ci_batch_destroy(ci_batch *b);
+
 /* ---------------------------------------------------------------- tracing */
 
 /* Kernel tracing.  While on, every kernel the library launches is

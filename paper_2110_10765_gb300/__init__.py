@@ -18,7 +18,7 @@ from . import _lib
 from ._lib import (CIError, CI_F32, CI_F64, CI_BF16_ROWSCALE, CI_TBME_TABLES,
                    CI_TBME_SEED, check, lib)
 
-__all__ = ["Problem", "Matrix", "exclusive_scan", "trace_enable", "trace_read", "CIError", "CI_F32", "CI_F64",
+__all__ = ["Problem", "Matrix", "Batch", "exclusive_scan", "trace_enable", "trace_read", "CIError", "CI_F32", "CI_F64",
            "CI_BF16_ROWSCALE", "VTYPES", "lib", "current_stream"]
 
 VTYPES = {"f32": CI_F32, "f64": CI_F64, "bf16": CI_BF16_ROWSCALE}
@@ -215,6 +215,51 @@ class Matrix:
                "basis_size": info.basis_size, "hnorm_est": info.hnorm_est,
                "residual": list(info.residual)[:k], "seconds": info.seconds, "status": st}
         return ev, out
+
+
+class Batch:
+    """Many problems built and solved together (``ci_batch_*``).
+
+    problems: list of ``Problem`` (kept alive by this object); k: int or a
+    list of per-problem eigenpair counts.
+    """
+
+    def __init__(self, problems, k=5, max_basis=64, tol=1e-7, max_iter=400, check_every=4, seed=1):
+        self.problems = list(problems)
+        n = len(self.problems)
+        ks = [int(k)] * n if np.isscalar(k) else [int(x) for x in k]
+        self._k = ks
+        arr = (C.c_void_p * n)(*[p._h.value for p in self.problems])
+        karr = (C.c_int32 * n)(*ks)
+        o = _lib.EigOpts(0, 8, max_basis, max_iter, tol, seed, 0, check_every)
+        h = C.c_void_p()
+        check(lib().ci_batch_create(C.cast(arr, C.POINTER(C.c_void_p)), n, C.cast(karr, C.c_void_p), C.byref(o),
+                                    C.byref(h)), "ci_batch_create")
+        self._h = h
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().ci_batch_destroy(h)
+            self._h = None
+
+    def run(self, stream=None):
+        check(lib().ci_batch_run(self._h, _stream(stream)), "ci_batch_run")
+
+    def result(self, i, allow_unconverged=False):
+        k = self._k[i]
+        ev = np.zeros(k)
+        info = _lib.EigInfo()
+        st = lib().ci_batch_result(self._h, i, _ptr(ev), C.byref(info))
+        if not (allow_unconverged and st == _lib.CI_ERR_NOT_CONVERGED):
+            check(st, "ci_batch_result")
+        return ev, {"iterations": info.iterations, "converged": info.converged,
+                    "residual": list(info.residual)[:k], "status": st}
+
+    def stats(self):
+        b, s, st, nnz = C.c_double(), C.c_double(), C.c_int32(), C.c_int64()
+        check(lib().ci_batch_stats(self._h, C.byref(b), C.byref(s), C.byref(st), C.byref(nnz)), "ci_batch_stats")
+        return {"build_s": b.value, "solve_s": s.value, "steps": st.value, "nnz": nnz.value}
 
 
 def trace_enable(on=True):

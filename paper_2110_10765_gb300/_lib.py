@@ -76,6 +76,11 @@ _SIGS = {
     "ci_matrix_export": (C.c_int, [_P, _P, _P, _P, _P, _P]),
     "ci_apply_H": (C.c_int, [_P, _P, _P, C.c_int32, _P]),
     "ci_lowest_eigs": (C.c_int, [_P, C.POINTER(EigOpts), _P, _P, C.POINTER(EigInfo), _P]),
+    "ci_batch_create": (C.c_int, [C.POINTER(_P), C.c_int32, _P, C.POINTER(EigOpts), C.POINTER(_P)]),
+    "ci_batch_run": (C.c_int, [_P, _P]),
+    "ci_batch_result": (C.c_int, [_P, C.c_int32, _P, C.POINTER(EigInfo)]),
+    "ci_batch_stats": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int32), _I64P]),
+    "ci_batch_destroy": (None, [_P]),
     "ci_trace_enable": (C.c_int, [C.c_int32]),
     "ci_trace_read": (C.c_int, [C.POINTER(TraceEntry), C.c_int32, C.POINTER(C.c_int32), C.c_int32]),
 }

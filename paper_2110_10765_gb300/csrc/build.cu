@@ -72,12 +72,26 @@ __device__ __forceinline__ int warp_incl_scan_i32(int v) {
     return v;
 }
 
+// problem of global row gr in a group (row_off: [G+1])
+__device__ __forceinline__ int group_of(const int64_t *row_off, int G, int64_t gr) {
+    int lo = 0, hi = G - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (row_off[mid] <= gr) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
 template <class T>
-__global__ void __launch_bounds__(256) k_count_rows(RowArgs<T> a) {
+__global__ void __launch_bounds__(256) k_count_rows(const RowArgs<T> *args, const int64_t *row_off, int G) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t r = warp; r < a.dim; r += nwarps) {
+    const int64_t rows = row_off[G];
+    for (int64_t gr = warp; gr < rows; gr += nwarps) {
+        const int g = group_of(row_off, G, gr);
+        const RowArgs<T> &a = args[g];
+        const int64_t r = gr - row_off[g];
         const int p = a.row_p[r], n = a.row_n[r];
         const int64_t e0 = a.o_ptr[p], e1 = a.o_ptr[p + 1];
         int cnt = 0;
@@ -102,12 +116,16 @@ __device__ __forceinline__ T sum_over_bits(const T *tab, uint64_t w0, uint64_t w
 }
 
 template <class T>
-__global__ void __launch_bounds__(256) k_fill_rows(RowArgs<T> a) {
+__global__ void __launch_bounds__(256) k_fill_rows(const RowArgs<T> *args, const int64_t *row_off, int G) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int S = a.S;
-    for (int64_t r = warp; r < a.dim; r += nwarps) {
+    const int64_t rows = row_off[G];
+    for (int64_t gr = warp; gr < rows; gr += nwarps) {
+        const int g = group_of(row_off, G, gr);
+        const RowArgs<T> &a = args[g];
+        const int S = a.S;
+        const int64_t r = gr - row_off[g];
         const int p = a.row_p[r], n = a.row_n[r];
         const uint64_t pb0 = a.p_bits[(int64_t)p * a.W], pb1 = a.W > 1 ? a.p_bits[(int64_t)p * a.W + 1] : 0;
         const uint64_t nb0 = a.n_bits[(int64_t)n * a.W], nb1 = a.W > 1 ? a.n_bits[(int64_t)n * a.W + 1] : 0;
@@ -198,68 +216,108 @@ static RowArgs<T> row_args(Problem *p) {
     Connectivity<T> &c = p->conn<T>();
     Tables<T> &t = p->tables<T>();
     SpeciesList &P = p->sp[0], &Nn = p->sp[1];
-    RowArgs<T> a;
+    RowArgs<T> a{};
     a.dim = p->dim; a.S = p->S; a.W = P.W; a.nq = Nn.nq; a.nds = p->nds; a.K = p->K;
     a.nmax = p->nmax; a.twoM = p->twoM;
     a.row_p = p->d_row_p.ptr; a.row_n = p->d_row_n.ptr; a.p_row_base = p->d_p_row_base.ptr;
     a.p_q = P.d_q.ptr; a.p_twoM = P.d_twoM.ptr; a.n_q = Nn.d_q.ptr; a.n_twoM = Nn.d_twoM.ptr;
     a.n_local = Nn.d_local.ptr; a.p_bits = P.d_bits.ptr; a.n_bits = Nn.d_bits.ptr;
-    a.o_ptr = c.outer.ptr.ptr; a.l2_ptr = c.l2.ptr.ptr; a.l4_ptr = c.l4.ptr.ptr;
-    a.o_ent = c.outer.ent.ptr; a.l2_ent = c.l2.ent.ptr; a.l4_ent = c.l4.ent.ptr;
+    a.o_ptr = c.outer.ptr; a.l2_ptr = c.l2.ptr; a.l4_ptr = c.l4.ptr;
+    a.o_ent = c.outer.ent; a.l2_ent = c.l2.ent; a.l4_ent = c.l4.ent;
     a.seg2 = c.seg2.ptr; a.seg4 = c.seg4.ptr;
     a.Upn = t.Upn.ptr; a.Wpn = t.Wpn.ptr; a.Dpn = t.Dpn.ptr; a.Tpn = t.Tpn.ptr;
-    a.row_cnt = p->row_cnt.ptr; a.row_ptr = nullptr; a.col = nullptr; a.val = nullptr;
     return a;
 }
 
-static int row_grid(int64_t dim) { return grid_for(dim * 32, 256, sm_count() * 8); }
+static int row_grid(int64_t rows) { return grid_for(rows * 32, 256, sm_count() * 8); }
 
 template <class T>
-static void count_rows_t(Problem *p, cudaStream_t s) {
-    species_filter<T>(p, s);
-    p->row_cnt.alloc(p->dim);
-    if (p->dim > 0) {
-        RowArgs<T> a = row_args<T>(p);
-        launch("k_count_rows", k_count_rows<T>, row_grid(p->dim), 256, 0, s, a);
-        CI_CHECK_LAUNCH();
-    }
-    p->conn_prec = sizeof(T) == 4 ? 0 : 1;
-    p->counted = true;
+static void upload_args(const std::vector<RowArgs<T>> &args, const std::vector<int64_t> &row_off,
+                        DevBuf<unsigned char> &dargs, DevBuf<int64_t> &doff, cudaStream_t s) {
+    dargs.alloc(sizeof(RowArgs<T>) * args.size());
+    doff.alloc(row_off.size());
+    CI_CUDA(cudaMemcpyAsync(dargs.ptr, args.data(), sizeof(RowArgs<T>) * args.size(), cudaMemcpyHostToDevice, s));
+    CI_CUDA(cudaMemcpyAsync(doff.ptr, row_off.data(), sizeof(int64_t) * row_off.size(), cudaMemcpyHostToDevice, s));
 }
 
-void count_rows(Problem *p, int prec, cudaStream_t s) {
-    if (p->counted && p->conn_prec == prec) return;
-    if (prec == 0) count_rows_t<float>(p, s);
-    else count_rows_t<double>(p, s);
+template <class T>
+static void count_group_t(const std::vector<Problem *> &ps, GroupCSR *g, cudaStream_t s) {
+    species_filter_group<T>(ps, s);
+    g->prec = sizeof(T) == 4 ? 0 : 1;
+    g->row_off.assign(1, 0);
+    std::vector<RowArgs<T>> args;
+    for (Problem *p : ps) {
+        g->row_off.push_back(g->row_off.back() + p->dim);
+        args.push_back(row_args<T>(p));
+    }
+    const int64_t rows = g->row_off.back();
+    g->row_cnt.alloc(rows);
+    for (size_t i = 0; i < ps.size(); ++i) args[i].row_cnt = g->row_cnt.ptr + g->row_off[i];
+    if (rows > 0) {
+        DevBuf<unsigned char> dargs;
+        DevBuf<int64_t> doff;
+        upload_args<T>(args, g->row_off, dargs, doff, s);
+        launch("k_count_rows", k_count_rows<T>, row_grid(rows), 256, 0, s, (const RowArgs<T> *)dargs.ptr,
+               (const int64_t *)doff.ptr, (int)ps.size());
+        CI_CUDA(cudaStreamSynchronize(s));
+    }
+}
+
+void count_group(const std::vector<Problem *> &ps, int prec, GroupCSR *g, cudaStream_t s) {
+    if (prec == 0) count_group_t<float>(ps, g, s);
+    else count_group_t<double>(ps, g, s);
+    // offsets of every row (Eq. 1) and the total per problem
+    const int64_t rows = g->row_off.back();
+    g->row_ptr.alloc(rows + 1);
+    exclusive_scan_i32(g->row_cnt.ptr, rows, g->row_ptr.ptr, ps[0]->scan_scratch, s);
+    std::vector<int64_t> ends(ps.size() + 1);
+    for (size_t i = 0; i <= ps.size(); ++i)
+        CI_CUDA(cudaMemcpyAsync(&ends[i], g->row_ptr.ptr + g->row_off[i], sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CI_CUDA(cudaStreamSynchronize(s));
+    g->nnz = ends[ps.size()];
+    g->nnz_of.resize(ps.size());
+    for (size_t i = 0; i < ps.size(); ++i) g->nnz_of[i] = ends[i + 1] - ends[i];
+}
+
+template <class T>
+static void fill_group_t(const std::vector<Problem *> &ps, GroupCSR *g, cudaStream_t s) {
+    std::vector<RowArgs<T>> args;
+    for (size_t i = 0; i < ps.size(); ++i) {
+        args.push_back(row_args<T>(ps[i]));
+        args.back().row_ptr = g->row_ptr.ptr + g->row_off[i];
+        args.back().col = g->col.ptr;
+        args.back().val = (T *)g->val.ptr;
+    }
+    const int64_t rows = g->row_off.back();
+    if (rows == 0) return;
+    DevBuf<unsigned char> dargs;
+    DevBuf<int64_t> doff;
+    upload_args<T>(args, g->row_off, dargs, doff, s);
+    launch("k_fill_rows", k_fill_rows<T>, row_grid(rows), 256, 0, s, (const RowArgs<T> *)dargs.ptr,
+           (const int64_t *)doff.ptr, (int)ps.size());
+    CI_CUDA(cudaStreamSynchronize(s));  // the argument arrays are freed on return
+}
+
+// Fig. 1 lines 9-14 for a counted group: allocate and fill col / val.
+void fill_group(const std::vector<Problem *> &ps, GroupCSR *g, cudaStream_t s) {
+    g->col.alloc(g->nnz);
+    g->val.alloc(g->nnz * (g->prec ? sizeof(double) : sizeof(float)));
+    if (g->prec == 0) fill_group_t<float>(ps, g, s);
+    else fill_group_t<double>(ps, g, s);
 }
 
 void build_matrix(Problem *p, int vtype, Matrix *m, cudaStream_t s) {
     if (vtype != CI_F32 && vtype != CI_F64)
         fail(CI_ERR_INVALID_ARG, "value type %d is not supported by ci_build_H", vtype);
-    const int prec = vtype == CI_F64 ? 1 : 0;
-    enumerate_basis(p, s);
-    count_rows(p, prec, s);
+    GroupCSR g;
+    count_group({p}, vtype == CI_F64 ? 1 : 0, &g, s);
+    fill_group({p}, &g, s);
     m->dim = p->dim;
     m->vtype = vtype;
-    m->row_ptr.alloc(p->dim + 1);
-    exclusive_scan_i32(p->row_cnt.ptr, p->dim, m->row_ptr.ptr, p->scan_scratch, s);
-    CI_CUDA(cudaMemcpyAsync(&m->nnz, m->row_ptr.ptr + p->dim, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    CI_CUDA(cudaStreamSynchronize(s));
-    p->nnz = m->nnz;
-    m->col.alloc(m->nnz);
-    const size_t esz = prec ? sizeof(double) : sizeof(float);
-    m->val.alloc(m->nnz * esz);
-    if (p->dim == 0) return;
-    if (prec == 0) {
-        RowArgs<float> a = row_args<float>(p);
-        a.row_ptr = m->row_ptr.ptr; a.col = m->col.ptr; a.val = (float *)m->val.ptr;
-        launch("k_fill_rows", k_fill_rows<float>, row_grid(p->dim), 256, 0, s, a);
-    } else {
-        RowArgs<double> a = row_args<double>(p);
-        a.row_ptr = m->row_ptr.ptr; a.col = m->col.ptr; a.val = (double *)m->val.ptr;
-        launch("k_fill_rows", k_fill_rows<double>, row_grid(p->dim), 256, 0, s, a);
-    }
-    CI_CHECK_LAUNCH();
+    m->nnz = g.nnz;
+    m->row_ptr = std::move(g.row_ptr);
+    m->col = std::move(g.col);
+    m->val = std::move(g.val);
 }
 
 }  // namespace ci

@@ -25,12 +25,14 @@ static void export_conn(const Problem &P, int species, int64_t *ptr, int32_t *id
         if (total) *total = L.total;
         int64_t n = P.sp[0].n;
         std::vector<int64_t> hp(n + 1);
-        CI_CUDA(cudaMemcpy(hp.data(), L.ptr.ptr, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost));
+        CI_CUDA(cudaMemcpy(hp.data(), L.ptr, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost));
+        for (auto &x : hp) x -= L.first;
         if (ptr) std::memcpy(ptr, hp.data(), hp.size() * sizeof(int64_t));
         if (!idx && !d) return;
         if (cap < L.total) fail(CI_ERR_CAPACITY, "cap below the entry count");
         std::vector<ConnEntry<T>> he(L.total);
-        if (L.total) CI_CUDA(cudaMemcpy(he.data(), L.ent.ptr, L.total * sizeof(ConnEntry<T>), cudaMemcpyDeviceToHost));
+        if (L.total)
+            CI_CUDA(cudaMemcpy(he.data(), L.ent + L.first, L.total * sizeof(ConnEntry<T>), cudaMemcpyDeviceToHost));
         for (int64_t i = 0; i < L.total; ++i) {
             if (idx) idx[i] = he[i].tgt;
             if (d) d[i] = (int8_t)(2 * info_dcode(he[i].info));
@@ -39,11 +41,15 @@ static void export_conn(const Problem &P, int species, int64_t *ptr, int32_t *id
     }
     int64_t n = P.sp[1].n;
     std::vector<int64_t> p2(n + 1), p4(n + 1);
-    CI_CUDA(cudaMemcpy(p2.data(), c.l2.ptr.ptr, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost));
-    CI_CUDA(cudaMemcpy(p4.data(), c.l4.ptr.ptr, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost));
+    CI_CUDA(cudaMemcpy(p2.data(), c.l2.ptr, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost));
+    CI_CUDA(cudaMemcpy(p4.data(), c.l4.ptr, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost));
+    for (auto &x : p2) x -= c.l2.first;
+    for (auto &x : p4) x -= c.l4.first;
     std::vector<ConnEntry<T>> e2(c.l2.total), e4(c.l4.total);
-    if (c.l2.total) CI_CUDA(cudaMemcpy(e2.data(), c.l2.ent.ptr, c.l2.total * sizeof(ConnEntry<T>), cudaMemcpyDeviceToHost));
-    if (c.l4.total) CI_CUDA(cudaMemcpy(e4.data(), c.l4.ent.ptr, c.l4.total * sizeof(ConnEntry<T>), cudaMemcpyDeviceToHost));
+    if (c.l2.total)
+        CI_CUDA(cudaMemcpy(e2.data(), c.l2.ent + c.l2.first, c.l2.total * sizeof(ConnEntry<T>), cudaMemcpyDeviceToHost));
+    if (c.l4.total)
+        CI_CUDA(cudaMemcpy(e4.data(), c.l4.ent + c.l4.first, c.l4.total * sizeof(ConnEntry<T>), cudaMemcpyDeviceToHost));
     std::vector<int64_t> hp(n + 1, 0);
     std::vector<int32_t> hi;
     std::vector<int8_t> hd;
@@ -174,14 +180,11 @@ ci_status ci_count_nnz(ci_problem *p, int64_t *nnz, int32_t *row_cnt, void *stre
         cudaStream_t s = as_stream(stream);
         Problem &P = p->impl;
         enumerate_basis(&P, s);
-        count_rows(&P, P.conn_prec >= 0 ? P.conn_prec : 0, s);
-        DevBuf<int64_t> off(P.dim + 1);
-        exclusive_scan_i32(P.row_cnt.ptr, P.dim, off.ptr, P.scan_scratch, s);
-        int64_t total = 0;
-        CI_CUDA(cudaMemcpyAsync(&total, off.ptr + P.dim, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-        if (row_cnt) copy_out(row_cnt, P.row_cnt.ptr, P.dim * sizeof(int32_t), s);
+        GroupCSR g;
+        count_group({&P}, P.c64.ready && !P.c32.ready ? 1 : 0, &g, s);
+        if (row_cnt) copy_out(row_cnt, g.row_cnt.ptr, P.dim * sizeof(int32_t), s);
         CI_CUDA(cudaStreamSynchronize(s));
-        if (nnz) *nnz = total;
+        if (nnz) *nnz = g.nnz;
     });
 }
 

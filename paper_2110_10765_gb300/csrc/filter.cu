@@ -108,11 +108,18 @@ __device__ ConnEntry<T> make_entry(const FilterArgs<T> &a, int64_t s, int64_t t,
 constexpr int kTile = 512;
 
 template <class T, int W, int RW>
-__global__ void __launch_bounds__(256) k_filter(FilterArgs<T> a, int pass) {
+__global__ void __launch_bounds__(256) k_filter(const FilterArgs<T> *jobs, const int64_t *job_blk, int njobs,
+                                                int pass) {
     __shared__ uint64_t sbits[kTile * W];
     __shared__ int32_t sm2[kTile];
+    int lo = 0, hi = njobs - 1;  // the job (one list of one problem) of this block
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (job_blk[mid] <= (int64_t)blockIdx.x) lo = mid; else hi = mid - 1;
+    }
+    const FilterArgs<T> &a = jobs[lo];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int64_t row0 = ((int64_t)blockIdx.x * 8 + wid) * RW;
+    const int64_t row0 = (((int64_t)blockIdx.x - job_blk[lo]) * 8 + wid) * RW;
     uint64_t bs[RW][kMaxWords];
     int ms[RW];
     int64_t out[RW];
@@ -168,67 +175,102 @@ __global__ void __launch_bounds__(256) k_filter(FilterArgs<T> a, int pass) {
     }
 }
 
-template <class T, int W>
-static void launch_filter(const FilterArgs<T> &a, int pass, cudaStream_t s) {
-    // rows per warp: 4 when that still gives every SM a few blocks
-    if (a.n >= (int64_t)sm_count() * 4 * 32) {
-        launch("k_filter", k_filter<T, W, 4>, (unsigned)((a.n + 31) / 32), 256, 0, s, a, pass);
-    } else {
-        launch("k_filter", k_filter<T, W, 1>, (unsigned)((a.n + 7) / 8), 256, 0, s, a, pass);
-    }
+// Launch pass 0 (counts) or 1 (entries) for jobs sharing W, RW rows per warp.
+template <class T, int W, int RW>
+static void launch_filter(const std::vector<FilterArgs<T>> &jobs, int pass, cudaStream_t s) {
+    if (jobs.empty()) return;
+    std::vector<int64_t> blk(1, 0);
+    for (auto &j : jobs) blk.push_back(blk.back() + (j.n + 8 * RW - 1) / (8 * RW));
+    if (blk.back() == 0) return;
+    if (blk.back() > INT32_MAX) fail(CI_ERR_CAPACITY, "species filter grid too large");
+    DevBuf<FilterArgs<T>> dj(jobs.size());
+    DevBuf<int64_t> db(blk.size());
+    CI_CUDA(cudaMemcpyAsync(dj.ptr, jobs.data(), sizeof(FilterArgs<T>) * jobs.size(), cudaMemcpyHostToDevice, s));
+    CI_CUDA(cudaMemcpyAsync(db.ptr, blk.data(), sizeof(int64_t) * blk.size(), cudaMemcpyHostToDevice, s));
+    launch("k_filter", k_filter<T, W, RW>, (unsigned)blk.back(), 256, 0, s, (const FilterArgs<T> *)dj.ptr,
+           (const int64_t *)db.ptr, (int)jobs.size(), pass);
+    CI_CUDA(cudaStreamSynchronize(s));  // the job arrays are freed on return
 }
 
-// seg2[n][ds][c]: end (relative to ptr[n]) of the L2 entries whose key
-// (2M, q) is <= (2M_n + 2(ds-K), c); with no Nmax cut the q part is ignored.
-__global__ void k_seg2(int64_t n, int nds, int nq, int K, int cut, const int64_t *ptr,
-                       const ConnEntry<float> *ent_f, const ConnEntry<double> *ent_d,
-                       const int32_t *twoM, const int32_t *q, int32_t *seg) {
-    int64_t total = n * nds * nq;
+template <class T>
+static void filter_pass(const std::vector<FilterArgs<T>> &jobs, int pass, cudaStream_t s) {
+    // rows per warp: 4 only when that still leaves every SM 16 blocks of
+    // 8 warps (the sweep is latency bound, so more warps beat more reuse)
+    std::vector<FilterArgs<T>> j1, j2;
+    int64_t rows = 0;
+    for (auto &j : jobs) {
+        (j.W == 1 ? j1 : j2).push_back(j);
+        rows += j.n;
+    }
+    const bool wide = rows >= (int64_t)sm_count() * 16 * 32;
+    if (wide) { launch_filter<T, 1, 4>(j1, pass, s); launch_filter<T, 2, 4>(j2, pass, s); }
+    else { launch_filter<T, 1, 1>(j1, pass, s); launch_filter<T, 2, 1>(j2, pass, s); }
+}
+
+// Segment tables of one problem's neutron lists.
+//   seg2[n][ds][c]: end (relative to ptr[n]) of the L2 entries whose key
+//   (2M, q) is <= (2M_n + 2(ds-K), c); with no Nmax cut the q part is ignored.
+//   seg4[n][c]: end (relative) of the L4 entries with q <= c (all same 2M).
+template <class T>
+struct SegJob {
+    int64_t n;
+    int nds, nq, K, cut;
+    const int64_t *p2, *p4;
+    const ConnEntry<T> *e2, *e4;
+    const int32_t *twoM, *q;
+    int32_t *seg2, *seg4;
+};
+
+template <class T>
+__global__ void k_seg(const SegJob<T> *jobs, const int64_t *job_off, int njobs) {
+    const int64_t total = job_off[njobs];
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
-        int c = (int)(e % nq);
-        int ds = (int)((e / nq) % nds);
-        int64_t s = e / ((int64_t)nq * nds);
-        int mt = twoM[s] + 2 * (ds - K);
-        int64_t lo = ptr[s], hi = ptr[s + 1];  // first entry with key > (mt, c)
-        while (lo < hi) {
-            int64_t mid = (lo + hi) >> 1;
-            int tg = ent_f ? ent_f[mid].tgt : ent_d[mid].tgt;
-            int mm = twoM[tg];
-            bool le = mm < mt || (mm == mt && (!cut || q[tg] <= c));
-            if (le) lo = mid + 1; else hi = mid;
+        int jl = 0, jh = njobs - 1;
+        while (jl < jh) {
+            int mid = (jl + jh + 1) >> 1;
+            if (job_off[mid] <= e) jl = mid; else jh = mid - 1;
         }
-        seg[e] = (int32_t)(lo - ptr[s]);
-    }
-}
-
-// seg4[n][c]: end (relative) of the L4 entries with q <= c (all same 2M).
-__global__ void k_seg4(int64_t n, int nq, int cut, const int64_t *ptr, const ConnEntry<float> *ent_f,
-                       const ConnEntry<double> *ent_d, const int32_t *q, int32_t *seg) {
-    int64_t total = n * nq;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        int c = (int)(e % nq);
-        int64_t s = e / nq;
-        int64_t lo = ptr[s], hi = ptr[s + 1];
-        if (cut) {
+        const SegJob<T> &j = jobs[jl];
+        int64_t r = e - job_off[jl];
+        const int64_t n2 = j.n * j.nds * j.nq;
+        if (r < n2) {
+            const int c = (int)(r % j.nq);
+            const int ds = (int)((r / j.nq) % j.nds);
+            const int64_t s = r / ((int64_t)j.nq * j.nds);
+            const int mt = j.twoM[s] + 2 * (ds - j.K);
+            int64_t lo = j.p2[s], hi = j.p2[s + 1];  // first entry with key > (mt, c)
             while (lo < hi) {
-                int64_t mid = (lo + hi) >> 1;
-                int tg = ent_f ? ent_f[mid].tgt : ent_d[mid].tgt;
-                if (q[tg] <= c) lo = mid + 1; else hi = mid;
+                const int64_t mid = (lo + hi) >> 1;
+                const int tg = j.e2[mid].tgt;
+                const int mm = j.twoM[tg];
+                const bool le = mm < mt || (mm == mt && (!j.cut || j.q[tg] <= c));
+                if (le) lo = mid + 1; else hi = mid;
             }
+            j.seg2[r] = (int32_t)(lo - j.p2[s]);
         } else {
-            lo = hi;
+            r -= n2;
+            const int c = (int)(r % j.nq);
+            const int64_t s = r / j.nq;
+            int64_t lo = j.p4[s], hi = j.p4[s + 1];
+            if (j.cut) {
+                while (lo < hi) {
+                    const int64_t mid = (lo + hi) >> 1;
+                    if (j.q[j.e4[mid].tgt] <= c) lo = mid + 1; else hi = mid;
+                }
+            } else {
+                lo = hi;
+            }
+            j.seg4[r] = (int32_t)(lo - j.p4[s]);
         }
-        seg[e] = (int32_t)(lo - ptr[s]);
     }
 }
 
 template <class T>
-static void build_list(Problem *p, int species, int mode, ConnList<T> &L, cudaStream_t s) {
+static FilterArgs<T> filter_job(Problem *p, int species, int mode) {
     SpeciesList &sp = p->sp[species];
     Tables<T> &t = p->tables<T>();
-    FilterArgs<T> a;
+    FilterArgs<T> a{};
     a.n = sp.n; a.A = sp.A; a.S = p->S; a.W = sp.W; a.mode = mode;
     a.bits = sp.d_bits.ptr; a.twoM = sp.d_twoM.ptr; a.local = sp.d_local.ptr; a.occ = sp.d_occ.ptr;
     a.eps = t.eps.ptr;
@@ -237,56 +279,87 @@ static void build_list(Problem *p, int species, int mode, ConnList<T> &L, cudaSt
     a.C = species == 0 ? t.Cpp.ptr : t.Cnn.ptr;
     a.pair_row = p->like_row.ptr; a.pair_col = p->like_col.ptr;
     a.tr_base = p->tr_base.ptr; a.tr_idx = p->tr_idx.ptr;
-    DevBuf<int32_t> cnt(sp.n);
-    a.count = cnt.ptr; a.ptr = nullptr; a.ent = nullptr;
-    L.ptr.alloc(sp.n + 1);
-    if (sp.n == 0) {
-        CI_CUDA(cudaMemsetAsync(L.ptr.ptr, 0, sizeof(int64_t), s));
-        L.total = 0;
-        L.ent.alloc(1);
-        return;
-    }
-    if (sp.W == 1) launch_filter<T, 1>(a, 0, s);
-    else launch_filter<T, 2>(a, 0, s);
-    CI_CHECK_LAUNCH();
-    exclusive_scan_i32(cnt.ptr, sp.n, L.ptr.ptr, p->scan_scratch, s);
-    CI_CUDA(cudaMemcpyAsync(&L.total, L.ptr.ptr + sp.n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    CI_CUDA(cudaStreamSynchronize(s));
-    L.ent.alloc(L.total);
-    a.ptr = L.ptr.ptr; a.ent = L.ent.ptr;
-    if (sp.W == 1) launch_filter<T, 1>(a, 1, s);
-    else launch_filter<T, 2>(a, 1, s);
-    CI_CHECK_LAUNCH();
+    return a;
 }
 
+// Species connectivity of every problem of ps (Fig. 1 lines 2-5): count
+// pass, one scan over all lists, one allocation, fill pass, segment tables.
 template <class T>
-void species_filter(Problem *p, cudaStream_t s) {
-    Connectivity<T> &c = p->conn<T>();
-    if (c.ready) return;
-    stage_tables<T>(p, s);
-    build_list<T>(p, 0, CONN_OUTER, c.outer, s);
-    build_list<T>(p, 1, CONN_L2, c.l2, s);
-    build_list<T>(p, 1, CONN_L4, c.l4, s);
-    SpeciesList &Nn = p->sp[1];
-    const int cut = p->nmax >= 0;
-    c.seg2.alloc((size_t)Nn.n * p->nds * Nn.nq);
-    c.seg4.alloc((size_t)Nn.n * Nn.nq);
-    if (Nn.n > 0) {
-        const bool f = sizeof(T) == 4;
-        launch("k_seg2", k_seg2, grid_for(Nn.n * p->nds * Nn.nq, 256), 256, 0, s, 
-            Nn.n, p->nds, Nn.nq, p->K, cut, c.l2.ptr.ptr,
-            f ? (const ConnEntry<float> *)c.l2.ent.ptr : nullptr,
-            f ? nullptr : (const ConnEntry<double> *)c.l2.ent.ptr, Nn.d_twoM.ptr, Nn.d_q.ptr, c.seg2.ptr);
-        launch("k_seg4", k_seg4, grid_for(Nn.n * Nn.nq, 256), 256, 0, s, 
-            Nn.n, Nn.nq, cut, c.l4.ptr.ptr, f ? (const ConnEntry<float> *)c.l4.ent.ptr : nullptr,
-            f ? nullptr : (const ConnEntry<double> *)c.l4.ent.ptr, Nn.d_q.ptr, c.seg4.ptr);
-        CI_CHECK_LAUNCH();
+void species_filter_group(const std::vector<Problem *> &ps_in, cudaStream_t s) {
+    std::vector<Problem *> ps;
+    for (Problem *p : ps_in)
+        if (!p->conn<T>().ready) ps.push_back(p);
+    if (ps.empty()) return;
+    for (Problem *p : ps) enumerate_basis(p, s);
+    stage_tables_group<T>(ps, s);
+    // jobs: 3 lists per problem, their counts side by side in one array
+    std::vector<FilterArgs<T>> jobs;
+    std::vector<ConnList<T> *> lists;
+    std::vector<int64_t> cnt_off(1, 0);
+    for (Problem *p : ps) {
+        Connectivity<T> &c = p->conn<T>();
+        const int modes[3] = {CONN_OUTER, CONN_L2, CONN_L4};
+        ConnList<T> *ls[3] = {&c.outer, &c.l2, &c.l4};
+        for (int i = 0; i < 3; ++i) {
+            jobs.push_back(filter_job<T>(p, i == 0 ? 0 : 1, modes[i]));
+            lists.push_back(ls[i]);
+            cnt_off.push_back(cnt_off.back() + jobs.back().n);
+        }
     }
+    const int64_t ncnt = cnt_off.back();
+    DevBuf<int32_t> cnt((size_t)ncnt);
+    auto offs = std::make_shared<DevBuf<int64_t>>((size_t)ncnt + 1);
+    for (size_t i = 0; i < jobs.size(); ++i) jobs[i].count = cnt.ptr + cnt_off[i];
+    filter_pass<T>(jobs, 0, s);
+    exclusive_scan_i32(cnt.ptr, ncnt, offs->ptr, ps[0]->scan_scratch, s);
+    std::vector<int64_t> hoff((size_t)ncnt + 1);
+    CI_CUDA(cudaMemcpyAsync(hoff.data(), offs->ptr, sizeof(int64_t) * (ncnt + 1), cudaMemcpyDeviceToHost, s));
     CI_CUDA(cudaStreamSynchronize(s));
-    c.ready = true;
+    auto ents = std::make_shared<DevBuf<ConnEntry<T>>>((size_t)hoff[ncnt]);
+    for (size_t i = 0; i < jobs.size(); ++i) {
+        ConnList<T> &L = *lists[i];
+        L.ptr_buf = offs;
+        L.ent_buf = ents;
+        L.ptr = offs->ptr + cnt_off[i];
+        L.ent = ents->ptr;
+        L.n = jobs[i].n;
+        L.first = hoff[cnt_off[i]];
+        L.total = hoff[cnt_off[i + 1]] - hoff[cnt_off[i]];
+        jobs[i].ptr = L.ptr;
+        jobs[i].ent = L.ent;
+    }
+    filter_pass<T>(jobs, 1, s);
+    // segment tables of the neutron lists
+    std::vector<SegJob<T>> sj;
+    std::vector<int64_t> soff(1, 0);
+    for (Problem *p : ps) {
+        Connectivity<T> &c = p->conn<T>();
+        SpeciesList &Nn = p->sp[1];
+        c.seg2.alloc((size_t)Nn.n * p->nds * Nn.nq);
+        c.seg4.alloc((size_t)Nn.n * Nn.nq);
+        SegJob<T> j{};
+        j.n = Nn.n; j.nds = p->nds; j.nq = Nn.nq; j.K = p->K; j.cut = p->nmax >= 0;
+        j.p2 = c.l2.ptr; j.p4 = c.l4.ptr; j.e2 = c.l2.ent; j.e4 = c.l4.ent;
+        j.twoM = Nn.d_twoM.ptr; j.q = Nn.d_q.ptr; j.seg2 = c.seg2.ptr; j.seg4 = c.seg4.ptr;
+        const int64_t w = Nn.n * p->nds * Nn.nq + Nn.n * Nn.nq;
+        if (w == 0) continue;
+        sj.push_back(j);
+        soff.push_back(soff.back() + w);
+    }
+    if (!sj.empty()) {
+        DevBuf<SegJob<T>> dsj(sj.size());
+        DevBuf<int64_t> dso(soff.size());
+        CI_CUDA(cudaMemcpyAsync(dsj.ptr, sj.data(), sizeof(SegJob<T>) * sj.size(), cudaMemcpyHostToDevice, s));
+        CI_CUDA(cudaMemcpyAsync(dso.ptr, soff.data(), sizeof(int64_t) * soff.size(), cudaMemcpyHostToDevice, s));
+        launch("k_seg", k_seg<T>, grid_for(soff.back(), 256, sm_count() * 16), 256, 0, s, (const SegJob<T> *)dsj.ptr,
+               (const int64_t *)dso.ptr, (int)sj.size());
+        CI_CUDA(cudaStreamSynchronize(s));
+    }
+    for (Problem *p : ps) p->conn<T>().ready = true;
 }
 
-template void species_filter<float>(Problem *, cudaStream_t);
-template void species_filter<double>(Problem *, cudaStream_t);
+template void species_filter_group<float>(const std::vector<Problem *> &, cudaStream_t);
+template void species_filter_group<double>(const std::vector<Problem *> &, cudaStream_t);
+
 
 }  // namespace ci

@@ -110,53 +110,66 @@ __device__ __forceinline__ T to_prec(double v, const TbmeSrc &t) {
     return (T)v;
 }
 
-// Compact blocks: entry e of group g is (row item i, column item j) of the
-// group's row and column lists; items are codes x*S+y.
-//   mode 0 (like pairs): row (c,d), column (a,b) -> V_{cd,ab}
-//   mode 1 (pn moves):   row (c,a) proton move, column (c',a') neutron move
-//                        -> V^pn_{c c', a a'}
+// One staging job fills one table of one problem.
+//   kind 0, compact blocks: entry e of group g is (row item i, column item j)
+//     of the group's lists (items are codes x*S+y); mode 0 (like pairs): row
+//     (c,d), column (a,b) -> V_{cd,ab}; mode 1 (pn moves): row (c,a) proton
+//     move, column (c',a') neutron move -> V^pn_{c c', a a'}
+//   kind 1, spectators: U[(c*S+a)*S+k] = V_{ck,ak}; mode 1: W[(d*S+b)*S+k] = V_{kd,kb}
+//   kind 2, pair diagonals: D[a*S+b] = V_abab
+//   kind 3, one-body energies: eps[a] (from eps64)
 template <class T>
-__global__ void k_stage_compact(TbmeSrc t, int mode, int G, const int64_t *grp_off, const int32_t *grp_ncol,
-                                const int32_t *grp_rows, const int32_t *grp_cols, const int32_t *items,
-                                int64_t total, T *out) {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        int lo = 0, hi = G - 1;
-        while (lo < hi) {  // last group with grp_off <= e
-            int mid = (lo + hi + 1) >> 1;
-            if (grp_off[mid] <= e) lo = mid; else hi = mid - 1;
-        }
-        int64_t r = e - grp_off[lo];
-        int n = grp_ncol[lo];
-        int i = (int)(r / n), j = (int)(r % n);
-        int pr = items[grp_rows[lo] + i], pc = items[grp_cols[lo] + j];
-        int x1 = pr / t.S, y1 = pr % t.S, x2 = pc / t.S, y2 = pc % t.S;
-        double v = mode == 0 ? tbme_fetch(t, x1, y1, x2, y2) : tbme_fetch(t, x1, x2, y1, y2);
-        out[e] = to_prec<T>(v, t);
-    }
-}
+struct StageJob {
+    TbmeSrc src;
+    int kind, mode, G;
+    const int64_t *goff;
+    const int32_t *gncol, *grows, *gcols, *items;
+    const double *eps64;
+    int64_t total;
+    T *out;
+};
 
-// U[(c*S+a)*S+k] = V_{ck,ak};  with swap: W[(d*S+b)*S+k] = V_{kd,kb}.
 template <class T>
-__global__ void k_stage_spectator(TbmeSrc t, int swap, T *out) {
-    int64_t total = (int64_t)t.S * t.S * t.S;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
+__device__ void stage_one(const StageJob<T> &j, int64_t e) {
+    const TbmeSrc &t = j.src;
+    if (j.kind == 0) {
+        int lo = 0, hi = j.G - 1;
+        while (lo < hi) {  // last group with goff <= e
+            int mid = (lo + hi + 1) >> 1;
+            if (j.goff[mid] <= e) lo = mid; else hi = mid - 1;
+        }
+        int64_t r = e - j.goff[lo];
+        int n = j.gncol[lo];
+        int i = (int)(r / n), k = (int)(r % n);
+        int pr = j.items[j.grows[lo] + i], pc = j.items[j.gcols[lo] + k];
+        int x1 = pr / t.S, y1 = pr % t.S, x2 = pc / t.S, y2 = pc % t.S;
+        double v = j.mode == 0 ? tbme_fetch(t, x1, y1, x2, y2) : tbme_fetch(t, x1, x2, y1, y2);
+        j.out[e] = to_prec<T>(v, t);
+    } else if (j.kind == 1) {
         int k = (int)(e % t.S);
         int a = (int)((e / t.S) % t.S);
         int c = (int)(e / ((int64_t)t.S * t.S));
-        double v = swap ? tbme_fetch(t, k, c, k, a) : tbme_fetch(t, c, k, a, k);
-        out[e] = to_prec<T>(v, t);
+        double v = j.mode ? tbme_fetch(t, k, c, k, a) : tbme_fetch(t, c, k, a, k);
+        j.out[e] = to_prec<T>(v, t);
+    } else if (j.kind == 2) {
+        int a = (int)(e / t.S), b = (int)(e % t.S);
+        j.out[e] = to_prec<T>(tbme_fetch(t, a, b, a, b), t);
+    } else {
+        j.out[e] = (T)j.eps64[e];
     }
 }
 
-// D[a*S+b] = V_abab
 template <class T>
-__global__ void k_stage_diag(TbmeSrc t, T *out) {
-    int total = t.S * t.S;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
-        int a = e / t.S, b = e % t.S;
-        out[e] = to_prec<T>(tbme_fetch(t, a, b, a, b), t);
+__global__ void k_stage(const StageJob<T> *jobs, const int64_t *job_off, int njobs) {
+    const int64_t total = job_off[njobs];
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = njobs - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (job_off[mid] <= e) lo = mid; else hi = mid - 1;
+        }
+        stage_one<T>(jobs[lo], e - job_off[lo]);
     }
 }
 
@@ -285,69 +298,84 @@ void problem_create(const ci_problem_desc *d, Problem *p) {
     p->tr_base.upload(tg.row, s); p->tr_idx.upload(tg.col, s);
     p->like_size = lg.grp_off.back();
     p->tr_size = tg.grp_off.back();
+    p->like_G = (int)lg.grp_ncol.size();
+    p->tr_G = (int)tg.grp_ncol.size();
+    p->lg_off.upload(lg.grp_off, s); p->lg_ncol.upload(lg.grp_ncol, s); p->lg_rows.upload(lg.grp_rows, s);
+    p->lg_cols.upload(lg.grp_cols, s); p->lg_items.upload(lg.items, s);
+    p->tg_off.upload(tg.grp_off, s); p->tg_ncol.upload(tg.grp_ncol, s); p->tg_rows.upload(tg.grp_rows, s);
+    p->tg_cols.upload(tg.grp_cols, s); p->tg_items.upload(tg.items, s);
     p->d_twom.upload(p->sp_twom, s);
+    p->d_eps.upload(p->sp_energy, s);
     CI_CUDA(cudaStreamSynchronize(s));
 }
 
-// Stage the tables of precision T (once per precision).
+// Stage the tables of precision T of every problem in ps that lacks them,
+// in one launch.
 template <class T>
-void stage_tables(Problem *p, cudaStream_t s) {
-    Tables<T> &t = p->tables<T>();
-    if (t.ready) return;
-    const int S = p->S;
-    PairGroups lg = make_like_pairs(p->sp_twom), tg = make_transitions(p->sp_twom);
-    auto upload_groups = [&](const PairGroups &g, DevBuf<int64_t> &off, DevBuf<int32_t> &nc, DevBuf<int32_t> &gr,
-                             DevBuf<int32_t> &gc, DevBuf<int32_t> &items) {
-        off.upload(g.grp_off, s); nc.upload(g.grp_ncol, s); gr.upload(g.grp_rows, s);
-        gc.upload(g.grp_cols, s); items.upload(g.items, s);
+void stage_tables_group(const std::vector<Problem *> &ps, cudaStream_t s) {
+    std::vector<StageJob<T>> jobs;
+    std::vector<int64_t> off(1, 0);
+    auto add = [&](const StageJob<T> &j) {
+        if (j.total <= 0) return;
+        jobs.push_back(j);
+        off.push_back(off.back() + j.total);
     };
-    DevBuf<int64_t> loff, toff;
-    DevBuf<int32_t> lnc, lgr, lgc, litems, tnc, tgr, tgc, titems;
-    upload_groups(lg, loff, lnc, lgr, lgc, litems);
-    upload_groups(tg, toff, tnc, tgr, tgc, titems);
-
-    std::vector<T> eps(p->sp_energy.begin(), p->sp_energy.end());
-    t.eps.upload(eps, s);
-    t.Cpp.alloc(p->like_size); t.Cnn.alloc(p->like_size); t.Tpn.alloc(p->tr_size);
-    size_t S3 = (size_t)S * S * S, S2 = (size_t)S * S;
-    t.Upp.alloc(S3); t.Unn.alloc(S3); t.Upn.alloc(S3); t.Wpn.alloc(S3);
-    t.Dpp.alloc(S2); t.Dnn.alloc(S2); t.Dpn.alloc(S2);
-
-    TbmeSrc src[3];
-    for (int c = 0; c < 3; ++c) {
-        src[c].S = S;
-        src[c].source = p->tbme_source;
-        src[c].dtype = p->tbme_dtype;
-        src[c].flat = p->flat[c].ptr;
-        src[c].seed = p->tbme_seed;
-        src[c].channel = c;
-        src[c].twom = p->d_twom.ptr;
+    std::vector<Problem *> todo;
+    for (Problem *p : ps) {
+        Tables<T> &t = p->tables<T>();
+        if (t.ready) continue;
+        todo.push_back(p);
+        const int S = p->S;
+        const int64_t S3 = (int64_t)S * S * S, S2 = (int64_t)S * S;
+        t.eps.alloc(S);
+        t.Cpp.alloc(p->like_size); t.Cnn.alloc(p->like_size); t.Tpn.alloc(p->tr_size);
+        t.Upp.alloc(S3); t.Unn.alloc(S3); t.Upn.alloc(S3); t.Wpn.alloc(S3);
+        t.Dpp.alloc(S2); t.Dnn.alloc(S2); t.Dpn.alloc(S2);
+        TbmeSrc src[3];
+        for (int c = 0; c < 3; ++c) {
+            src[c].S = S;
+            src[c].source = p->tbme_source;
+            src[c].dtype = p->tbme_dtype;
+            src[c].flat = p->flat[c].ptr;
+            src[c].seed = p->tbme_seed;
+            src[c].channel = c;
+            src[c].twom = p->d_twom.ptr;
+        }
+        StageJob<T> j{};
+        j.kind = 0; j.mode = 0; j.G = p->like_G; j.goff = p->lg_off.ptr; j.gncol = p->lg_ncol.ptr;
+        j.grows = p->lg_rows.ptr; j.gcols = p->lg_cols.ptr; j.items = p->lg_items.ptr; j.total = p->like_size;
+        j.src = src[0]; j.out = t.Cpp.ptr; add(j);
+        j.src = src[1]; j.out = t.Cnn.ptr; add(j);
+        j.mode = 1; j.G = p->tr_G; j.goff = p->tg_off.ptr; j.gncol = p->tg_ncol.ptr; j.grows = p->tg_rows.ptr;
+        j.gcols = p->tg_cols.ptr; j.items = p->tg_items.ptr; j.total = p->tr_size; j.src = src[2]; j.out = t.Tpn.ptr;
+        add(j);
+        StageJob<T> k{};
+        k.kind = 1; k.total = S3;
+        k.src = src[0]; k.mode = 0; k.out = t.Upp.ptr; add(k);
+        k.src = src[1]; k.out = t.Unn.ptr; add(k);
+        k.src = src[2]; k.out = t.Upn.ptr; add(k);
+        k.mode = 1; k.out = t.Wpn.ptr; add(k);
+        StageJob<T> d{};
+        d.kind = 2; d.total = S2;
+        d.src = src[0]; d.out = t.Dpp.ptr; add(d);
+        d.src = src[1]; d.out = t.Dnn.ptr; add(d);
+        d.src = src[2]; d.out = t.Dpn.ptr; add(d);
+        StageJob<T> e{};
+        e.kind = 3; e.total = S; e.src = src[0]; e.eps64 = p->d_eps.ptr; e.out = t.eps.ptr; add(e);
     }
-    const int thr = 256;
-    int Gl = (int)lg.grp_ncol.size(), Gt = (int)tg.grp_ncol.size();
-    if (p->like_size > 0) {
-        launch("k_stage_compact", k_stage_compact<T>, grid_for(p->like_size, thr), thr, 0, s, src[0], 0, Gl,
-               loff.ptr, lnc.ptr, lgr.ptr, lgc.ptr, litems.ptr, p->like_size, t.Cpp.ptr);
-        launch("k_stage_compact", k_stage_compact<T>, grid_for(p->like_size, thr), thr, 0, s, src[1], 0, Gl,
-               loff.ptr, lnc.ptr, lgr.ptr, lgc.ptr, litems.ptr, p->like_size, t.Cnn.ptr);
-    }
-    if (p->tr_size > 0)
-        launch("k_stage_compact", k_stage_compact<T>, grid_for(p->tr_size, thr), thr, 0, s, src[2], 1, Gt,
-               toff.ptr, tnc.ptr, tgr.ptr, tgc.ptr, titems.ptr, p->tr_size, t.Tpn.ptr);
-    launch("k_stage_spectator", k_stage_spectator<T>, grid_for(S3, thr), thr, 0, s, src[0], 0, t.Upp.ptr);
-    launch("k_stage_spectator", k_stage_spectator<T>, grid_for(S3, thr), thr, 0, s, src[1], 0, t.Unn.ptr);
-    launch("k_stage_spectator", k_stage_spectator<T>, grid_for(S3, thr), thr, 0, s, src[2], 0, t.Upn.ptr);
-    launch("k_stage_spectator", k_stage_spectator<T>, grid_for(S3, thr), thr, 0, s, src[2], 1, t.Wpn.ptr);
-    launch("k_stage_diag", k_stage_diag<T>, grid_for(S2, thr), thr, 0, s, src[0], t.Dpp.ptr);
-    launch("k_stage_diag", k_stage_diag<T>, grid_for(S2, thr), thr, 0, s, src[1], t.Dnn.ptr);
-    launch("k_stage_diag", k_stage_diag<T>, grid_for(S2, thr), thr, 0, s, src[2], t.Dpn.ptr);
-    CI_CHECK_LAUNCH();
-    CI_CUDA(cudaStreamSynchronize(s));  // the group arrays are freed on return
-    t.ready = true;
+    if (jobs.empty()) return;
+    DevBuf<StageJob<T>> djobs((size_t)jobs.size());
+    DevBuf<int64_t> doff(off.size());
+    CI_CUDA(cudaMemcpyAsync(djobs.ptr, jobs.data(), sizeof(StageJob<T>) * jobs.size(), cudaMemcpyHostToDevice, s));
+    CI_CUDA(cudaMemcpyAsync(doff.ptr, off.data(), sizeof(int64_t) * off.size(), cudaMemcpyHostToDevice, s));
+    launch("k_stage", k_stage<T>, grid_for(off.back(), 256, sm_count() * 16), 256, 0, s, (const StageJob<T> *)djobs.ptr,
+           (const int64_t *)doff.ptr, (int)jobs.size());
+    CI_CUDA(cudaStreamSynchronize(s));  // the job arrays are freed on return
+    for (Problem *p : todo) p->tables<T>().ready = true;
 }
 
-template void stage_tables<float>(Problem *, cudaStream_t);
-template void stage_tables<double>(Problem *, cudaStream_t);
+template void stage_tables_group<float>(const std::vector<Problem *> &, cudaStream_t);
+template void stage_tables_group<double>(const std::vector<Problem *> &, cudaStream_t);
 
 // ------------------------------------------------------------------ species lists
 
@@ -477,16 +505,14 @@ void enumerate_basis(Problem *p, cudaStream_t s) {
         L.d_occ.upload(L.occ, s);
     }
     p->d_p_row_base.upload(p->p_row_base, s);
-    DevBuf<int64_t> d_nstart;
-    d_nstart.upload(p_nstart, s);
+    p->d_p_nstart.upload(p_nstart, s);
     p->d_row_p.alloc(p->dim);
     p->d_row_n.alloc(p->dim);
     if (p->dim > 0) {
-        launch("k_row_map", k_row_map, grid_for(p->dim, 256), 256, 0, s, p->dim, P.n, p->d_p_row_base.ptr, d_nstart.ptr,
+        launch("k_row_map", k_row_map, grid_for(p->dim, 256), 256, 0, s, p->dim, P.n, p->d_p_row_base.ptr, p->d_p_nstart.ptr,
                                                          p->d_row_p.ptr, p->d_row_n.ptr);
         CI_CHECK_LAUNCH();
     }
-    CI_CUDA(cudaStreamSynchronize(s));
     p->enumerated = true;
 }
 

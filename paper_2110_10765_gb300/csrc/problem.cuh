@@ -82,11 +82,18 @@ __host__ __device__ inline uint32_t make_info(int dcode, int neg, int a, int c) 
     return (uint32_t)dcode | ((uint32_t)neg << 2) | ((uint32_t)a << 3) | ((uint32_t)c << 10);
 }
 
+// A species list inside a group allocation: ptr [n+1] holds absolute
+// positions into ent (the buffers are shared by every list built in the
+// same batched launch).
 template <class T>
 struct ConnList {
-    DevBuf<int64_t> ptr;             // [n+1]
-    DevBuf<ConnEntry<T>> ent;        // [total]
-    int64_t total = 0;
+    std::shared_ptr<DevBuf<int64_t>> ptr_buf;
+    std::shared_ptr<DevBuf<ConnEntry<T>>> ent_buf;
+    const int64_t *ptr = nullptr;
+    ConnEntry<T> *ent = nullptr;
+    int64_t n = 0;      // determinants (rows of the list)
+    int64_t first = 0;  // ptr[0]
+    int64_t total = 0;  // ptr[n] - ptr[0]
 };
 
 // Which species pairs a list keeps (see ci_species_filter).
@@ -123,7 +130,12 @@ struct Problem {
     // index as a neutron move)
     DevBuf<int32_t> like_row, like_col, tr_base, tr_idx;
     int64_t like_size = 0, tr_size = 0;   // entries of the compact tables
+    // group layouts of the compact tables (kept for staging)
+    int like_G = 0, tr_G = 0;
+    DevBuf<int64_t> lg_off, tg_off;
+    DevBuf<int32_t> lg_ncol, lg_rows, lg_cols, lg_items, tg_ncol, tg_rows, tg_cols, tg_items;
     DevBuf<int32_t> d_twom;
+    DevBuf<double> d_eps;
 
     Tables<float> t32;
     Tables<double> t64;
@@ -132,16 +144,13 @@ struct Problem {
     SpeciesList sp[2];
     int64_t dim = 0;
     std::vector<int64_t> p_row_base;   // [nP+1]
-    DevBuf<int64_t> d_p_row_base;
+    DevBuf<int64_t> d_p_row_base, d_p_nstart;
     DevBuf<int32_t> d_row_p, d_row_n;  // [dim]
 
     Connectivity<float> c32;
     Connectivity<double> c64;
     int conn_prec = -1;                // precision of the last species filter
 
-    DevBuf<int32_t> row_cnt;           // [dim]
-    bool counted = false;
-    int64_t nnz = 0;
     DevBuf<int64_t> scan_scratch;      // block sums of the exclusive scan
 
     template <class T> Tables<T> &tables();
@@ -166,11 +175,28 @@ struct Matrix {
 
 // ------------------------------------------------------------------ steps
 
+// Rows of a group of problems built together (one launch per step for the
+// whole group): problem g owns rows [row_off[g], row_off[g+1]) of the
+// group's counts, offsets, col and val.
+struct GroupCSR {
+    std::vector<int64_t> row_off;    // [G+1]
+    DevBuf<int32_t> row_cnt;         // [rows]
+    DevBuf<int64_t> row_ptr;         // [rows+1] absolute positions
+    DevBuf<int32_t> col;             // [nnz] problem-local columns
+    DevBuf<unsigned char> val;       // [nnz] float or double
+    int64_t nnz = 0;
+    int prec = 0;                    // 0 float, 1 double
+    std::vector<int64_t> nnz_of;     // [G]
+};
+
 void problem_create(const ci_problem_desc *d, Problem *p);
 void enumerate_basis(Problem *p, cudaStream_t s);
-template <class T> void stage_tables(Problem *p, cudaStream_t s);
-template <class T> void species_filter(Problem *p, cudaStream_t s);
-void count_rows(Problem *p, int prec, cudaStream_t s);   // prec 0 f32, 1 f64
+template <class T> void stage_tables_group(const std::vector<Problem *> &ps, cudaStream_t s);
+template <class T> void species_filter_group(const std::vector<Problem *> &ps, cudaStream_t s);
+template <class T> void species_filter(Problem *p, cudaStream_t s) { species_filter_group<T>({p}, s); }
+// count (and optionally fill) the rows of every problem of ps in one launch each
+void count_group(const std::vector<Problem *> &ps, int prec, GroupCSR *g, cudaStream_t s);
+void fill_group(const std::vector<Problem *> &ps, GroupCSR *g, cudaStream_t s);
 void exclusive_scan_i32(const int32_t *counts, int64_t n, int64_t *offsets,
                         DevBuf<int64_t> &scratch, cudaStream_t s);
 void build_matrix(Problem *p, int vtype, Matrix *m, cudaStream_t s);

@@ -1,0 +1,84 @@
+"""Batched solves (many problems in one build and one device-driven block
+Lanczos) against the FP64 oracle and against the single-problem solver;
+a problem's result is the same alone and in a mix."""
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from helpers import EIG_REL, gpu_problem, inputs, oracle_problem
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+# (shells, Z, N, nmax, seed): dims between ~100 and a few thousand
+MIX = [(2, 2, 3, 2, 11), (2, 3, 3, 2, 12), (3, 2, 2, 3, 13), (2, 2, 2, 4, 14), (3, 3, 2, 2, 15),
+       (2, 4, 2, 2, 16), (2, 3, 2, 3, 17)]
+
+
+def _seeded(case):
+    n_shell, Z, N, nmax, seed = case
+    sp = synth.ho_sp_table(n_shell)
+    eps = synth.sp_energies(sp, 20.0)
+    import paper_2110_10765_gb300 as ci
+    return ci.Problem(sp, Z, N, nmax, (Z + N) % 2, eps, seed=seed)
+
+
+def _oracle_lowest(case, k):
+    n_shell, Z, N, nmax, seed = case
+    inp = inputs(n_shell, Z, N, nmax, seed=seed, dtype=np.float32)
+    o = oracle_problem(inp)
+    rp, c, v, _ = o.csr(with_absums=False)
+    if o.dim <= 3000:
+        return o.dim, oracle.lowest_dense(oracle.dense_from_csr(rp, c, v, o.dim), k)
+    return o.dim, oracle.lowest_sparse(rp, c, v, o.dim, k)
+
+
+def test_batch_matches_oracle():
+    import paper_2110_10765_gb300 as ci
+    probs = [_seeded(c) for c in MIX]
+    ks = [5, 3, 8, 5, 1, 6, 4]
+    b = ci.Batch(probs, k=ks)
+    b.run()
+    for i, c in enumerate(MIX):
+        dim, ref = _oracle_lowest(c, ks[i])
+        ev, info = b.result(i)
+        assert np.all(np.abs(ev - ref) <= EIG_REL * np.maximum(np.abs(ref), 1)), (c, ev - ref)
+        assert max(info["residual"]) <= 1e-4 * max(abs(ref[-1]), 1.0)
+    st = b.stats()
+    assert st["nnz"] > 0 and st["steps"] > 0
+
+
+def test_batch_same_alone_and_in_mix():
+    import paper_2110_10765_gb300 as ci
+    alone = ci.Batch([_seeded(MIX[1])], k=[4])
+    alone.run()
+    mix = ci.Batch([_seeded(c) for c in MIX], k=[4] * len(MIX))
+    mix.run()
+    a, _ = alone.result(0)
+    m, _ = mix.result(1)
+    assert np.array_equal(a, m)
+
+
+def test_batch_matches_single_problem_solver():
+    import paper_2110_10765_gb300 as ci
+    c = MIX[3]
+    b = ci.Batch([_seeded(c)], k=[5])
+    b.run()
+    ev_b, _ = b.result(0)
+    ev_s, _ = _seeded(c).build_H("f32").lowest_eigs(k=5)
+    assert np.allclose(ev_b, ev_s, rtol=1e-6, atol=0)
+
+
+def test_batch_zero_interaction_degenerate():
+    """V = 0: the lowest levels are sums of eps, with multiplicity."""
+    import paper_2110_10765_gb300 as ci
+    inp = inputs(2, 2, 2, 3, zero=True, dtype=np.float32)
+    p = gpu_problem(inp)
+    b = ci.Batch([p], k=[6])
+    b.run()
+    ev, _ = b.result(0)
+    o = oracle_problem(inp)
+    ref = oracle.lowest_dense(oracle.dense_from_csr(*o.csr()[:3], o.dim), 6)
+    assert np.allclose(ev, ref, atol=1e-4)
