@@ -281,6 +281,57 @@ ci_status ci_batch_result(const ci_batch *b, int32_t i, double *evals, ci_eig_in
 ci_status ci_batch_stats(const ci_batch *b, double *build_s, double *solve_s, int32_t *steps, int64_t *nnz);
 void ci_batch_destroy(ci_batch *b);
 
+/* ---------------------------------------------------------------- serving */
+
+/* A solve queue with continuous batching.  A worker thread owns the GPU:
+ * between two steps of the batched block Lanczos (see ci_batch_create) it
+ * returns finished problems and admits waiting ones, first come first
+ * served, into free slots while their device memory (CSR, Krylov basis,
+ * connectivity lists, tables) fits mem_budget.  Admitted problems are built
+ * together and join the running ones at the next step, so requests that
+ * arrive while others run overlap with them; each keeps H and its Krylov
+ * vectors on the device until it finishes.  A problem's result does not
+ * depend on what else runs beside it (per-problem start block and
+ * reductions).  The paper has no counterpart. */
+typedef struct {
+    size_t mem_budget;    /* device bytes the queue may hold; 0 = 70 % of free memory */
+    int32_t max_slots;    /* problems running at once, 1..4096                  [256] */
+    int32_t max_basis;    /* Krylov vectors per problem (multiple of 8, 32..96)  [64] */
+    int32_t max_iter;     /* block steps per problem                             [400] */
+    int32_t max_tiles;    /* 256-row tiles over all running problems           [65536] */
+    double tol;           /* residual tolerance relative to ||H||              [1e-7] */
+} ci_queue_desc;
+
+typedef struct {
+    ci_problem_desc desc; /* copied at submission (tables too) */
+    int32_t k;            /* eigenpairs, 1..16 with 2(k+8) <= max_basis */
+} ci_request;
+
+typedef struct {
+    int32_t status;       /* CI_OK, CI_NOT_READY, or the request's error */
+    int32_t k;
+    int32_t iterations;
+    int64_t dim, nnz;
+    double evals[16];     /* ascending */
+    double residual[16];  /* ||H x - theta x||, FP64 */
+    double t_submit, t_admit, t_done;  /* seconds on the queue's steady clock */
+    double latency_s;     /* t_done - t_submit */
+} ci_result;
+
+ci_status ci_queue_create(const ci_queue_desc *desc, ci_queue **out);
+/* Queue a request; returns at once with a ticket. */
+ci_status ci_submit(ci_queue *q, const ci_request *req, uint64_t *ticket);
+/* CI_NOT_READY while the request waits or runs; then its final status
+ * (CI_OK, CI_ERR_NOT_CONVERGED, CI_ERR_CAPACITY, CI_ERR_CANCELLED, ...),
+ * with res filled either way. */
+ci_status ci_poll(ci_queue *q, uint64_t ticket, ci_result *res);
+/* Cancel a waiting or running request (it finishes as CI_ERR_CANCELLED). */
+ci_status ci_cancel(ci_queue *q, uint64_t ticket);
+ci_status ci_queue_stats(ci_queue *q, int64_t *submitted, int64_t *admitted, int64_t *completed, int64_t *steps,
+                         size_t *mem_used);
+/* Cancels what is left, waits for the worker and frees everything. */
+void ci_queue_destroy(ci_queue *q);
+
 /* ---------------------------------------------------------------- tracing */
 
 /* Kernel tracing.  While on, every kernel the library launches is

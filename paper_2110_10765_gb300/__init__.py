@@ -18,7 +18,7 @@ from . import _lib
 from ._lib import (CIError, CI_F32, CI_F64, CI_BF16_ROWSCALE, CI_TBME_TABLES,
                    CI_TBME_SEED, check, lib)
 
-__all__ = ["Problem", "Matrix", "Batch", "exclusive_scan", "trace_enable", "trace_read", "CIError", "CI_F32", "CI_F64",
+__all__ = ["Problem", "Matrix", "Batch", "Queue", "exclusive_scan", "trace_enable", "trace_read", "CIError", "CI_F32", "CI_F64",
            "CI_BF16_ROWSCALE", "VTYPES", "lib", "current_stream"]
 
 VTYPES = {"f32": CI_F32, "f64": CI_F64, "bf16": CI_BF16_ROWSCALE}
@@ -260,6 +260,75 @@ class Batch:
         b, s, st, nnz = C.c_double(), C.c_double(), C.c_int32(), C.c_int64()
         check(lib().ci_batch_stats(self._h, C.byref(b), C.byref(s), C.byref(st), C.byref(nnz)), "ci_batch_stats")
         return {"build_s": b.value, "solve_s": s.value, "steps": st.value, "nnz": nnz.value}
+
+
+def _desc(sp, Z, N, nmax, twoM, eps, keep, tables=None, seed=None):
+    """Fill a ProblemDesc; arrays it points to are appended to keep."""
+    spN = np.ascontiguousarray(sp["N"], dtype=np.int32)
+    spm = np.ascontiguousarray(sp["twom"], dtype=np.int32)
+    e = np.ascontiguousarray(eps, dtype=np.float64)
+    keep += [spN, spm, e]
+    d = _lib.ProblemDesc()
+    d.n_sp = len(spN)
+    d.sp_N = spN.ctypes.data_as(C.POINTER(C.c_int32))
+    d.sp_twom = spm.ctypes.data_as(C.POINTER(C.c_int32))
+    d.sp_energy = e.ctypes.data_as(C.POINTER(C.c_double))
+    d.Z, d.N, d.nmax, d.twoM = int(Z), int(N), int(nmax), int(twoM)
+    if tables is not None:
+        arrs = [np.ascontiguousarray(tables[k]) for k in ("pp", "nn", "pn")]
+        keep += arrs
+        d.tbme_source = CI_TBME_TABLES
+        d.tbme_dtype = CI_F32 if arrs[0].dtype == np.float32 else CI_F64
+        d.v_pp, d.v_nn, d.v_pn = [_ptr(a) for a in arrs]
+    else:
+        d.tbme_source = CI_TBME_SEED
+        d.tbme_dtype = CI_F32
+        d.tbme_seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+    return d
+
+
+class Queue:
+    """Solve queue with continuous batching (``ci_queue_*``)."""
+
+    def __init__(self, mem_budget=0, max_slots=256, max_basis=64, max_iter=400, tol=1e-7, max_tiles=0):
+        d = _lib.QueueDesc(int(mem_budget), max_slots, max_basis, max_iter, max_tiles, tol)
+        h = C.c_void_p()
+        check(lib().ci_queue_create(C.byref(d), C.byref(h)), "ci_queue_create")
+        self._h = h
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().ci_queue_destroy(h)
+            self._h = None
+
+    __del__ = close
+
+    def submit(self, sp, Z, N, nmax, twoM, eps, k, seed=None, tables=None):
+        keep = []
+        r = _lib.Request(_desc(sp, Z, N, nmax, twoM, eps, keep, tables, seed), int(k))
+        t = C.c_uint64()
+        check(lib().ci_submit(self._h, C.byref(r), C.byref(t)), "ci_submit")
+        return t.value
+
+    def poll(self, ticket):
+        """(status, result dict); status 6 (CI_NOT_READY) while running."""
+        r = _lib.Result()
+        st = lib().ci_poll(self._h, ticket, C.byref(r))
+        res = {"status": r.status, "k": r.k, "iterations": r.iterations, "dim": r.dim, "nnz": r.nnz,
+               "evals": np.array(r.evals[: r.k]), "residual": np.array(r.residual[: r.k]),
+               "t_submit": r.t_submit, "t_admit": r.t_admit, "t_done": r.t_done, "latency_s": r.latency_s}
+        return st, res
+
+    def cancel(self, ticket):
+        check(lib().ci_cancel(self._h, ticket), "ci_cancel")
+
+    def stats(self):
+        a, b, c, d, m = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64(), C.c_size_t()
+        check(lib().ci_queue_stats(self._h, C.byref(a), C.byref(b), C.byref(c), C.byref(d), C.byref(m)),
+              "ci_queue_stats")
+        return {"submitted": a.value, "admitted": b.value, "completed": c.value, "steps": d.value,
+                "mem_used": m.value}
 
 
 def trace_enable(on=True):

@@ -43,6 +43,22 @@ class EigInfo(C.Structure):
                 ("residual", C.c_double * 32), ("seconds", C.c_double)]
 
 
+class QueueDesc(C.Structure):
+    _fields_ = [("mem_budget", C.c_size_t), ("max_slots", C.c_int32), ("max_basis", C.c_int32),
+                ("max_iter", C.c_int32), ("max_tiles", C.c_int32), ("tol", C.c_double)]
+
+
+class Request(C.Structure):
+    _fields_ = [("desc", ProblemDesc), ("k", C.c_int32)]
+
+
+class Result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("k", C.c_int32), ("iterations", C.c_int32), ("dim", C.c_int64),
+                ("nnz", C.c_int64), ("evals", C.c_double * 16), ("residual", C.c_double * 16),
+                ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double),
+                ("latency_s", C.c_double)]
+
+
 class TraceEntry(C.Structure):
     _fields_ = [("name", C.c_char * 48), ("launches", C.c_int64), ("total_ms", C.c_double)]
 
@@ -81,6 +97,12 @@ _SIGS = {
     "ci_batch_result": (C.c_int, [_P, C.c_int32, _P, C.POINTER(EigInfo)]),
     "ci_batch_stats": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int32), _I64P]),
     "ci_batch_destroy": (None, [_P]),
+    "ci_queue_create": (C.c_int, [C.POINTER(QueueDesc), C.POINTER(_P)]),
+    "ci_submit": (C.c_int, [_P, C.POINTER(Request), C.POINTER(C.c_uint64)]),
+    "ci_poll": (C.c_int, [_P, C.c_uint64, C.POINTER(Result)]),
+    "ci_cancel": (C.c_int, [_P, C.c_uint64]),
+    "ci_queue_stats": (C.c_int, [_P, _I64P, _I64P, _I64P, _I64P, C.POINTER(C.c_size_t)]),
+    "ci_queue_destroy": (None, [_P]),
     "ci_trace_enable": (C.c_int, [C.c_int32]),
     "ci_trace_read": (C.c_int, [C.POINTER(TraceEntry), C.c_int32, C.POINTER(C.c_int32), C.c_int32]),
 }

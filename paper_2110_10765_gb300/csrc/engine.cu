@@ -746,6 +746,7 @@ void engine_create(Engine *e, int max_slots, int max_tiles, int MB, cudaStream_t
     n.evals.alloc((size_t)max_slots * EKMAX);
     n.tres.alloc((size_t)max_slots * EKMAX);
     e->host_slots.assign(max_slots, SlotDev{});
+    e->fresh.assign(max_slots, 0);
     CI_CUDA(cudaMemsetAsync(e->slots.ptr, 0, sizeof(SlotDev) * max_slots, e->stream));
     CI_CUDA(cudaMemsetAsync(e->ntiles.ptr, 0, sizeof(int32_t), e->stream));
     CI_CUDA(cudaMallocHost(&e->pinned_counter, sizeof(int32_t) * 4));
@@ -763,10 +764,12 @@ void engine_set_slot(Engine *e, int i, const SlotDev &d) {
     x.flags = 0;
     x.m_cur = 0; x.j0 = 0; x.m_act = 0; x.it = 0; x.restarts = 0; x.rank = EB; x.hnorm = 0.0;
     e->host_slots[i] = x;
+    e->fresh[i] = 1;
 }
 
 void engine_free_slot(Engine *e, int i) {
     e->host_slots[i] = SlotDev{};
+    e->fresh[i] = 0;
 }
 
 void engine_retile(Engine *e) {
@@ -780,7 +783,8 @@ void engine_retile(Engine *e) {
         SlotDev &h = e->host_slots[i];
         if (h.dim == 0 || h.Q == nullptr) { h = SlotDev{}; continue; }
         // slots admitted earlier keep the control state the kernels evolved
-        if (h.state != S_INIT && cur[i].Q == h.Q) h = cur[i];
+        if (!e->fresh[i] && cur[i].Q == h.Q) h = cur[i];
+        e->fresh[i] = 0;
         h.tile0 = (int32_t)tl.size();
         for (int64_t r = 0; r < h.dim; r += ETILE) tl.push_back(Tile{i, (int32_t)std::min<int64_t>(ETILE, h.dim - r), r});
         h.tile1 = (int32_t)tl.size();

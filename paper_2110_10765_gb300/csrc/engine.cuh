@@ -61,6 +61,7 @@ struct Engine {
     DevBuf<double> part;          // [max_tiles][MB*EB]
     EngineDense dn;
     std::vector<SlotDev> host_slots;
+    std::vector<char> fresh;      // slots set since the last retile
     std::vector<Tile> host_tiles;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
