@@ -308,7 +308,9 @@ def run_ours(args):
         rec["e2e"] = {"value": nnz * args.steps * world / e2e_s, "unit": "nnz/s", "h2d_bytes_per_step": int(h2d),
                       "d2h_bytes_per_step": int(8 * p.k + 8), "ms_per_step": e2e_s / args.steps * 1e3}
     if not args.no_batch:
-        rec["batch"] = run_batch_leg(args)
+        rec["batch"], pool = run_batch_leg(args)
+        if not args.no_serve:
+            rec["serve"] = run_serve_leg(rec["batch"]["solves_per_s"], pool)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rec["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     if world > 1:
@@ -386,7 +388,53 @@ def run_batch_leg(args):
             "fp64_single": {"sample": len(sample), "rows_fraction": frac, "seconds": t_single,
                             "solves_per_s": single_rate,
                             "max_rel_diff_vs_batch": max_rel},
-            "k": 5, "precision": "batch: FP32 H + FP64 Lanczos; single: FP64 H + FP64 Lanczos"}
+            "k": 5, "precision": "batch: FP32 H + FP64 Lanczos; single: FP64 H + FP64 Lanczos"}, \
+        [c for c, _, _ in items]
+
+
+def run_serve_leg(capacity, pool, n_requests=400, seed=4):
+    """Poisson arrivals at 80 % of the batched capacity, drawn from the batched
+    mix plus 5 % requests of the benchmark size (4p+4n, N<=4, Nmax=4), each
+    with its own TBME seed and 1..10 wanted eigenvalues."""
+    import numpy as np
+
+    import synth
+    import paper_2110_10765_gb300 as ci
+    rate = 0.8 * capacity
+    reqs = synth.serve_requests(rate, n_requests, seed=seed, small_pool=pool)
+    sps = {n: synth.ho_sp_table(n) for n in (3, 4)}
+    epss = {n: synth.sp_energies(sps[n], 20.0) for n in (3, 4)}
+    q = ci.Queue(mem_budget=96 << 30, max_slots=256)
+    t0 = time.perf_counter()
+    tickets = []
+    for r in reqs:
+        dt = t0 + r["t_arrival"] - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        n = r["n_shell_max"]
+        tickets.append(q.submit(sps[n], r["Z"], r["N"], r["nmax"], (r["Z"] + r["N"]) % 2, epss[n], r["k"],
+                                seed=r["seed"]))
+    results = {}
+    while len(results) < len(tickets):
+        for t in tickets:
+            if t not in results:
+                st, res = q.poll(t)
+                if st != 6:
+                    results[t] = (st, res)
+        time.sleep(0.001)
+    stats = q.stats()
+    q.close()
+    ok = [res for st, res in results.values() if st == 0]
+    lat = np.array([res["latency_s"] for res in ok]) * 1e3
+    span = max(res["t_done"] for _, res in results.values()) - min(res["t_submit"] for _, res in results.values())
+    big = [res["latency_s"] * 1e3 for res in ok if res["dim"] > 100000]
+    return {"requests": len(reqs), "completed_ok": len(ok), "failed": len(reqs) - len(ok),
+            "offered_rate_per_s": rate, "solves_per_s": len(ok) / span, "span_s": span,
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "mean": float(lat.mean()), "max": float(lat.max())},
+            "big_requests": len(big), "big_latency_ms_p50": float(np.median(big)) if big else None,
+            "engine_steps": stats["steps"],
+            "mix": "batched mix (Z,N in 2..6, Nmax 0..4, shells N<=3) + 5% 4p4n N<=4 Nmax=4; k in 1..10"}
 
 
 # ---------------------------------------------------------------- the oracle

@@ -375,20 +375,63 @@ __device__ void jacobi_small(double *A, int n, double *w, double *U) {
             }
 }
 
-// qr1: eigen-decomposition of G = W^T W, rank by threshold, M = U_k L_k^-1/2
-// (columns of the kept directions, largest first), R = L_k^1/2 U_k^T.
-// qr2: G2 = V^T V, M = G2^-1/2, R <- G2^1/2 R.
+// Cholesky factor of a symmetric 8 x 8 matrix (lower, row-major).  Returns
+// false when a pivot falls below rel * the matching diagonal entry (the
+// block is too ill-conditioned for a Cholesky QR).
+__device__ bool chol8(const double *G, double *L, double rel) {
+    for (int i = 0; i < EB * EB; ++i) L[i] = 0.0;
+    for (int j = 0; j < EB; ++j) {
+        double d = G[j * EB + j];
+        for (int k = 0; k < j; ++k) d -= L[j * EB + k] * L[j * EB + k];
+        if (!(d > rel * G[j * EB + j]) || !(d > 0.0)) return false;
+        const double ljj = sqrt(d);
+        L[j * EB + j] = ljj;
+        for (int i = j + 1; i < EB; ++i) {
+            double x = G[i * EB + j];
+            for (int k = 0; k < j; ++k) x -= L[i * EB + k] * L[j * EB + k];
+            L[i * EB + j] = x / ljj;
+        }
+    }
+    return true;
+}
+
+// Inverse of the upper triangular R = L^T: M = R^-1 (upper), row-major.
+__device__ void inv_upper_from_lower(const double *L, double *M) {
+    for (int i = 0; i < EB * EB; ++i) M[i] = 0.0;
+    for (int j = EB - 1; j >= 0; --j) {  // column j of R^-1 by back substitution
+        M[j * EB + j] = 1.0 / L[j * EB + j];
+        for (int i = j - 1; i >= 0; --i) {
+            double x = 0.0;
+            for (int k = i + 1; k <= j; ++k) x += L[k * EB + i] * M[k * EB + j];  // R[i][k] = L[k][i]
+            M[i * EB + j] = -x / L[i * EB + i];
+        }
+    }
+}
+
+// qr1: W = V R.  Cholesky QR (G = W^T W = R^T R, M = R^-1, rank 8) when the
+// Gram matrix is well conditioned; otherwise the eigen-decomposition of G
+// decides the rank: M = U_k L_k^-1/2 on the kept directions (largest first),
+// R = L_k^1/2 U_k^T, and the remaining columns are completed at random.
+// qr2: G2 = V^T V ~ I, Cholesky G2 = R2^T R2, M = R2^-1, R <- R2 R.
 __global__ void k_e_small(SlotDev *slots, int nslots, int phase, int which, DensePtrs d) {
     const int si = blockIdx.x * blockDim.x + threadIdx.x;
     if (si >= nslots) return;
     SlotDev &s = slots[si];
     if (!eligible(s, phase)) return;
-    double A[EB * EB], U[EB * EB], w[EB];
+    double A[EB * EB], L[EB * EB];
     const double *G = d.G + (int64_t)si * EB * EB;
     for (int i = 0; i < EB * EB; ++i) A[i] = 0.5 * (G[i] + G[(i % EB) * EB + i / EB]);
-    jacobi_small(A, EB, w, U);
     double *M = d.M + (int64_t)si * EB * EB, *R = d.R + (int64_t)si * EB * EB;
     if (which == 1) {
+        if (chol8(A, L, 1e-12)) {
+            inv_upper_from_lower(L, M);
+            for (int r = 0; r < EB; ++r)
+                for (int c = 0; c < EB; ++c) R[r * EB + c] = c >= r ? L[c * EB + r] : 0.0;
+            s.rank = EB;
+            return;
+        }
+        double U[EB * EB], w[EB];
+        jacobi_small(A, EB, w, U);
         const double lmax = fmax(w[EB - 1], 0.0);
         const double scale = fmax(s.hnorm, sqrt(lmax));
         const double thr = 1e-20 * scale * scale + 1e-300;
@@ -405,23 +448,18 @@ __global__ void k_e_small(SlotDev *slots, int nslots, int phase, int which, Dens
         }
         s.rank = r;
     } else {
-        double Ms[EB * EB], R2[EB * EB];
-        for (int a = 0; a < EB; ++a)
-            for (int c = 0; c < EB; ++c) {
-                double x = 0.0, y = 0.0;
-                for (int i = 0; i < EB; ++i) {
-                    const double wi = fmax(w[i], 1e-300);
-                    x += U[a * EB + i] * U[c * EB + i] / sqrt(wi);
-                    y += U[a * EB + i] * U[c * EB + i] * sqrt(wi);
-                }
-                M[a * EB + c] = x;
-                Ms[a * EB + c] = y;
-            }
-        for (int a = 0; a < EB; ++a)
+        // V^T V is the identity up to rounding (and to the completed columns
+        // scale), so its Cholesky factor exists
+        if (!chol8(A, L, 1e-30)) {
+            for (int i = 0; i < EB * EB; ++i) L[i] = (i / EB == i % EB) ? sqrt(fmax(A[i], 1e-300)) : 0.0;
+        }
+        inv_upper_from_lower(L, M);
+        double R2[EB * EB];
+        for (int r = 0; r < EB; ++r)
             for (int c = 0; c < EB; ++c) {
                 double x = 0.0;
-                for (int i = 0; i < EB; ++i) x += Ms[a * EB + i] * R[i * EB + c];
-                R2[a * EB + c] = x;
+                for (int k = r; k < EB; ++k) x += L[k * EB + r] * R[k * EB + c];  // R2 = L^T R
+                R2[r * EB + c] = x;
             }
         for (int i = 0; i < EB * EB; ++i) R[i] = R2[i];
     }
