@@ -224,7 +224,7 @@ ci_status ci_apply_H(const ci_matrix *m, const void *X, void *Y, int32_t nvec, v
 typedef struct {
     int32_t k;            /* eigenpairs wanted, 1..32                      [5]  */
     int32_t block;        /* block size b, 1..8                            [8]  */
-    int32_t max_basis;    /* Krylov vectors kept before a thick restart  [128] */
+    int32_t max_basis;    /* Krylov vectors kept before a thick restart   [64] */
     int32_t max_iter;     /* block steps in total                       [2000] */
     double tol;           /* converged when ||H x - theta x|| <= tol*||H||[1e-8] */
     uint64_t seed;        /* seed of the start block                      [1]  */

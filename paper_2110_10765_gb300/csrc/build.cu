@@ -36,15 +36,15 @@ template <class T>
 __device__ __forceinline__ void partner_segment(const RowArgs<T> &a, int p, int n, const ConnEntry<T> &e,
                                                 int &kind, int &beg, int &len) {
     const int dc = info_dcode(e.info);
-    const int pp = e.tgt;
+    const int qp = info_q(e.info);   // q of the proton partner
     kind = 0; beg = 0; len = 0;
     if (dc == 2) {  // four states moved among protons: the neutrons stay put
-        if (a.nmax < 0 || a.p_q[pp] + a.n_q[n] <= a.nmax) len = 1;
+        if (a.nmax < 0 || qp + a.n_q[n] <= a.nmax) len = 1;
         return;
     }
     int c = 0;
     if (a.nmax >= 0) {
-        c = a.nmax - a.p_q[pp];
+        c = a.nmax - qp;
         if (c < 0) return;
         if (c > a.nq - 1) c = a.nq - 1;
     }
@@ -54,7 +54,8 @@ __device__ __forceinline__ void partner_segment(const RowArgs<T> &a, int p, int 
         return;
     }
     kind = 1;       // one proton moved: neutron partners at most one move away
-    int ds = ((a.twoM - a.p_twoM[pp]) - a.n_twoM[n]) / 2 + a.K;
+    // target 2M of n' is twoM - 2M(p') = 2M(n) - (2M(p') - 2M(p))
+    const int ds = a.K - info_dslot(e.info);
     if (ds < 0 || ds >= a.nds) return;
     const int32_t *sg = a.seg2 + (int64_t)n * a.nds * a.nq;
     beg = ds == 0 ? 0 : sg[(ds - 1) * a.nq + (a.nq - 1)];
@@ -115,6 +116,13 @@ __device__ __forceinline__ T sum_over_bits(const T *tab, uint64_t w0, uint64_t w
     return s;
 }
 
+// Fill one row per warp.  The proton partners are taken 32 at a time; a
+// warp scan of their segment lengths gives every partner its output slot,
+// then three phases write the elements without sorting:
+//   0. four protons moved: one element (n' = n) per partner, by its lane;
+//   1. one proton moved: the segments of L2(n) are expanded with the warp's
+//      lanes balanced over the elements (a search over segment starts);
+//   2. p' = p: the warp walks the row's L4(n) segment contiguously.
 template <class T>
 __global__ void __launch_bounds__(256) k_fill_rows(const RowArgs<T> *args, const int64_t *row_off, int G) {
     const int lane = threadIdx.x & 31;
@@ -143,67 +151,80 @@ __global__ void __launch_bounds__(256) k_fill_rows(const RowArgs<T> *args, const
                 ep.tgt = 0; ep.local = 0; ep.info = 0; ep.val = 0;
             }
             const int incl = warp_incl_scan_i32(len);
-            const int excl = incl - len;
             const int total = __shfl_sync(0xffffffffu, incl, 31);
-            for (int t0 = 0; t0 < total; t0 += 32) {
+            const int64_t pos = out + (incl - len);
+            const int colbase = ep.tgt;   // first basis row of the proton partner
+            // 0. four protons moved: the neutrons stay, one element
+            if (kind == 0 && len == 1) {
+                a.col[pos] = colbase + n_local;
+                a.val[pos] = ep.val;
+            }
+            // 1. one proton moved (a -> c): L2(n)[beg, beg+len)
+            const int len1 = kind == 1 ? len : 0;
+            const int incl1 = warp_incl_scan_i32(len1);
+            const int excl1 = incl1 - len1;
+            const int total1 = __shfl_sync(0xffffffffu, incl1, 31);
+            for (int t0 = 0; t0 < total1; t0 += 32) {
                 const int t = t0 + lane;
-                int j = 0;  // last lane whose segment starts at or before t
+                int j = 0;  // last lane whose kind-1 segment starts at or before t
 #pragma unroll
                 for (int step = 16; step > 0; step >>= 1) {
-                    int v = __shfl_sync(0xffffffffu, excl, j + step);
+                    const int v = __shfl_sync(0xffffffffu, excl1, j + step);
                     if (v <= t) j += step;
                 }
-                const int k = t - __shfl_sync(0xffffffffu, excl, j);
-                const int pt = __shfl_sync(0xffffffffu, ep.tgt, j);
-                const int ptb = __shfl_sync(0xffffffffu, ep.local, j);
+                const int k = t - __shfl_sync(0xffffffffu, excl1, j);
+                const int64_t jpos = __shfl_sync(0xffffffffu, pos, j);
+                const int jcol = __shfl_sync(0xffffffffu, colbase, j);
+                const int jtb = __shfl_sync(0xffffffffu, ep.local, j);
                 const uint32_t pinfo = __shfl_sync(0xffffffffu, ep.info, j);
                 const T pval = __shfl_sync(0xffffffffu, ep.val, j);
-                const int jkind = __shfl_sync(0xffffffffu, kind, j);
                 const int jbeg = __shfl_sync(0xffffffffu, beg, j);
-                if (t < total) {
-                    const int64_t colbase = a.p_row_base[pt];
-                    int colv;
+                if (t < total1) {
+                    const ConnEntry<T> en = a.l2_ent[l2b + jbeg + k];
                     T v;
-                    if (jkind == 0) {               // (4,0): n' = n
-                        colv = (int)colbase + n_local;
-                        v = pval;
-                    } else if (jkind == 1) {        // one proton move (a -> c)
-                        const ConnEntry<T> en = a.l2_ent[l2b + jbeg + k];
-                        colv = (int)colbase + en.local;
-                        const int ap = info_a(pinfo), cp = info_c(pinfo);
-                        if (info_dcode(en.info) == 0) {   // (2,0): neutrons are spectators
-                            const T *u = a.Upn + ((int64_t)cp * S + ap) * S;
-                            T h = pval + sum_over_bits<T>(u, nb0, nb1);
-                            v = info_neg(pinfo) ? -h : h;
-                        } else {                          // (2,2): V^pn_{c_p c_n, a_p a_n}
-                            T w = a.Tpn[ptb + info_tcol(en.info)];
-                            v = (info_neg(pinfo) ^ info_neg(en.info)) ? -w : w;
-                        }
-                    } else {                        // p' = p
-                        const ConnEntry<T> en = a.l4_ent[l4b + k];
-                        colv = (int)colbase + en.local;
-                        const int dn = info_dcode(en.info);
-                        if (dn == 0) {                    // diagonal
-                            T h = pval + en.val;
-                            uint64_t x0 = pb0, x1 = pb1;
-                            while (x0 | x1) {
-                                int kp;
-                                if (x0) { kp = __ffsll((long long)x0) - 1; x0 &= x0 - 1; }
-                                else { kp = 64 + __ffsll((long long)x1) - 1; x1 &= x1 - 1; }
-                                h += sum_over_bits<T>(a.Dpn + (int64_t)kp * S, nb0, nb1);
-                            }
-                            v = h;
-                        } else if (dn == 1) {             // (0,2): protons are spectators
-                            const int an = info_a(en.info), cn = info_c(en.info);
-                            const T *w = a.Wpn + ((int64_t)cn * S + an) * S;
-                            T h = en.val + sum_over_bits<T>(w, pb0, pb1);
-                            v = info_neg(en.info) ? -h : h;
-                        } else {                          // (0,4)
-                            v = en.val;
-                        }
+                    if (info_dcode(en.info) != 0) {   // (2,2): V^pn_{c_p c_n, a_p a_n}
+                        const T w = a.Tpn[jtb + info_tcol(en.info)];
+                        v = (info_neg(pinfo) ^ info_neg(en.info)) ? -w : w;
+                    } else {                          // (2,0): neutrons are spectators
+                        const T *u = a.Upn + ((int64_t)info_c(pinfo) * S + info_a(pinfo)) * S;
+                        const T h = pval + sum_over_bits<T>(u, nb0, nb1);
+                        v = info_neg(pinfo) ? -h : h;
                     }
-                    a.col[out + t] = colv;
-                    a.val[out + t] = v;
+                    a.col[jpos + k] = jcol + en.local;
+                    a.val[jpos + k] = v;
+                }
+            }
+            // 2. p' = p: every same-2M neutron partner of n, L4(n)[0, len)
+            const unsigned b2 = __ballot_sync(0xffffffffu, kind == 2 && len > 0);
+            if (b2) {
+                const int src = __ffs(b2) - 1;
+                const int len2 = __shfl_sync(0xffffffffu, len, src);
+                const int64_t pos2 = __shfl_sync(0xffffffffu, pos, src);
+                const int col2 = __shfl_sync(0xffffffffu, colbase, src);
+                const T pval2 = __shfl_sync(0xffffffffu, ep.val, src);
+                for (int k = lane; k < len2; k += 32) {
+                    const ConnEntry<T> en = a.l4_ent[l4b + k];
+                    const int dn = info_dcode(en.info);
+                    T v;
+                    if (dn == 2) {                    // (0,4)
+                        v = en.val;
+                    } else if (dn == 1) {             // (0,2): protons are spectators
+                        const T *w = a.Wpn + ((int64_t)info_c(en.info) * S + info_a(en.info)) * S;
+                        const T h = en.val + sum_over_bits<T>(w, pb0, pb1);
+                        v = info_neg(en.info) ? -h : h;
+                    } else {                          // diagonal
+                        T h = pval2 + en.val;
+                        uint64_t x0 = pb0, x1 = pb1;
+                        while (x0 | x1) {
+                            int kp;
+                            if (x0) { kp = __ffsll((long long)x0) - 1; x0 &= x0 - 1; }
+                            else { kp = 64 + __ffsll((long long)x1) - 1; x1 &= x1 - 1; }
+                            h += sum_over_bits<T>(a.Dpn + (int64_t)kp * S, nb0, nb1);
+                        }
+                        v = h;
+                    }
+                    a.col[pos2 + k] = col2 + en.local;
+                    a.val[pos2 + k] = v;
                 }
             }
             out += total;

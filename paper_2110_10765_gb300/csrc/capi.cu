@@ -31,10 +31,13 @@ static void export_conn(const Problem &P, int species, int64_t *ptr, int32_t *id
         if (!idx && !d) return;
         if (cap < L.total) fail(CI_ERR_CAPACITY, "cap below the entry count");
         std::vector<ConnEntry<T>> he(L.total);
-        if (L.total)
+        std::vector<int32_t> ht(L.total);
+        if (L.total) {
             CI_CUDA(cudaMemcpy(he.data(), L.ent + L.first, L.total * sizeof(ConnEntry<T>), cudaMemcpyDeviceToHost));
+            CI_CUDA(cudaMemcpy(ht.data(), L.tgt + L.first, L.total * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        }
         for (int64_t i = 0; i < L.total; ++i) {
-            if (idx) idx[i] = he[i].tgt;
+            if (idx) idx[i] = ht[i];
             if (d) d[i] = (int8_t)(2 * info_dcode(he[i].info));
         }
         return;

@@ -19,9 +19,12 @@ struct FilterArgs {
     const int32_t *pair_row, *pair_col;
     const int32_t *tr_base;    // outer list: row offset of a proton move in the pn table
     const int32_t *tr_idx;     // neutron lists: column index of a neutron move
+    const int32_t *q;          // [n] excess quanta
+    const int64_t *p_row_base; // proton list: first basis row of every determinant
     int32_t *count;            // pass 0
     const int64_t *ptr;        // pass 1
     ConnEntry<T> *ent;         // pass 1
+    int32_t *tgt;              // pass 1: partner index of every entry
 };
 
 __device__ __forceinline__ int lowest_state(const uint64_t *x, int W) {
@@ -40,8 +43,8 @@ __device__ __forceinline__ void flip(uint64_t *K, int o) { K[o >> 6] ^= 1ull << 
 
 // Entry for row determinant s (bra) and partner t (ket).
 template <class T>
-__device__ ConnEntry<T> make_entry(const FilterArgs<T> &a, int64_t s, int64_t t, const uint64_t *bs,
-                                   const uint64_t *bt, int d) {
+__device__ __forceinline__ ConnEntry<T> make_entry_core(const FilterArgs<T> &a, int64_t s, int64_t t, const uint64_t *bs,
+                                                        const uint64_t *bt, int d) {
     ConnEntry<T> e;
     e.tgt = (int32_t)t;
     e.local = a.local[t];
@@ -101,6 +104,20 @@ __device__ ConnEntry<T> make_entry(const FilterArgs<T> &a, int64_t s, int64_t t,
     return e;
 }
 
+// Entry of row s, partner t; the proton list carries what the row kernels
+// need about t (first basis row, q, change of 2M) instead of t itself.
+template <class T>
+__device__ __forceinline__ ConnEntry<T> make_entry(const FilterArgs<T> &a, int64_t s, int64_t t, const uint64_t *bs,
+                                                   const uint64_t *bt, int d) {
+    ConnEntry<T> e = make_entry_core<T>(a, s, t, bs, bt, d);
+    if (a.mode == CONN_OUTER) {
+        e.tgt = (int32_t)a.p_row_base[t];
+        const int dslot = (a.twoM[t] - a.twoM[s]) / 2;
+        e.info = (e.info & 0x1FFFFu) | ((uint32_t)a.q[t] << 17) | ((uint32_t)(dslot + 64) << 25);
+    }
+    return e;
+}
+
 // Each warp owns RW row determinants; the block's warps sweep the partner
 // list in tiles of kTile determinants staged in shared memory (bits and 2M),
 // so the list is read once per block.  Lanes take one partner each and a
@@ -117,7 +134,7 @@ __global__ void __launch_bounds__(256) k_filter(const FilterArgs<T> *jobs, const
         int mid = (lo + hi + 1) >> 1;
         if (job_blk[mid] <= (int64_t)blockIdx.x) lo = mid; else hi = mid - 1;
     }
-    const FilterArgs<T> &a = jobs[lo];
+    const FilterArgs<T> a = jobs[lo];  // by value: stores to ent cannot alias it
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t row0 = (((int64_t)blockIdx.x - job_blk[lo]) * 8 + wid) * RW;
     uint64_t bs[RW][kMaxWords];
@@ -162,6 +179,7 @@ __global__ void __launch_bounds__(256) k_filter(const FilterArgs<T> *jobs, const
                 if (pass && keep) {
                     const int rank = __popc(bal & ((1u << lane) - 1u));
                     a.ent[out[i] + rank] = make_entry<T>(a, row0 + i, t0 + tl, bs[i], bt, d);
+                    a.tgt[out[i] + rank] = (int32_t)(t0 + tl);
                 }
                 out[i] += __popc(bal);
                 cnt[i] += __popc(bal);
@@ -273,6 +291,8 @@ static FilterArgs<T> filter_job(Problem *p, int species, int mode) {
     FilterArgs<T> a{};
     a.n = sp.n; a.A = sp.A; a.S = p->S; a.W = sp.W; a.mode = mode;
     a.bits = sp.d_bits.ptr; a.twoM = sp.d_twoM.ptr; a.local = sp.d_local.ptr; a.occ = sp.d_occ.ptr;
+    a.q = sp.d_q.ptr;
+    a.p_row_base = species == 0 ? p->d_p_row_base.ptr : nullptr;
     a.eps = t.eps.ptr;
     a.U = species == 0 ? t.Upp.ptr : t.Unn.ptr;
     a.D = species == 0 ? t.Dpp.ptr : t.Dnn.ptr;
@@ -316,10 +336,13 @@ void species_filter_group(const std::vector<Problem *> &ps_in, cudaStream_t s) {
     CI_CUDA(cudaMemcpyAsync(hoff.data(), offs->ptr, sizeof(int64_t) * (ncnt + 1), cudaMemcpyDeviceToHost, s));
     CI_CUDA(cudaStreamSynchronize(s));
     auto ents = std::make_shared<DevBuf<ConnEntry<T>>>((size_t)hoff[ncnt]);
+    auto tgts = std::make_shared<DevBuf<int32_t>>((size_t)hoff[ncnt]);
     for (size_t i = 0; i < jobs.size(); ++i) {
         ConnList<T> &L = *lists[i];
         L.ptr_buf = offs;
         L.ent_buf = ents;
+        L.tgt_buf = tgts;
+        L.tgt = tgts->ptr;
         L.ptr = offs->ptr + cnt_off[i];
         L.ent = ents->ptr;
         L.n = jobs[i].n;
@@ -327,6 +350,7 @@ void species_filter_group(const std::vector<Problem *> &ps_in, cudaStream_t s) {
         L.total = hoff[cnt_off[i + 1]] - hoff[cnt_off[i]];
         jobs[i].ptr = L.ptr;
         jobs[i].ent = L.ent;
+        jobs[i].tgt = tgts->ptr;
     }
     filter_pass<T>(jobs, 1, s);
     // segment tables of the neutron lists

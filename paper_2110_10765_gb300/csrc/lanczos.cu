@@ -373,7 +373,7 @@ void lowest_eigs(const Matrix *H, const ci_eig_opts *opts_in, double *evals, dou
     ci_eig_opts o = opts_in ? *opts_in : ci_eig_opts{};
     if (o.k == 0) o.k = 5;
     if (o.block == 0) o.block = 8;
-    if (o.max_basis == 0) o.max_basis = 128;
+    if (o.max_basis == 0) o.max_basis = 64;
     if (o.max_iter == 0) o.max_iter = 2000;
     if (o.tol == 0.0) o.tol = H->vtype == CI_F64 ? 1e-10 : 1e-7;
     if (o.seed == 0) o.seed = 1;

@@ -277,6 +277,7 @@ void problem_create(const ci_problem_desc *d, Problem *p) {
         if ((p->sp_twom[a] & 1) == 0) fail(CI_ERR_INVALID_ARG, "sp_twom[%d] must be odd", a);
         p->K = std::max(p->K, std::abs(p->sp_twom[a]));
     }
+    if (p->K > 63) fail(CI_ERR_CAPACITY, "|2m| above 63 is not supported");
     p->nds = 2 * p->K + 1;
     p->Z = d->Z; p->N = d->N; p->nmax = d->nmax; p->twoM = d->twoM;
     p->tbme_source = d->tbme_source;

@@ -59,8 +59,11 @@ struct Tables {
 // One entry of a species connectivity list (row determinant s = bra,
 // partner s' = ket).  info: bits 0-1 difference code (0: d=0, 1: d=2,
 // 2: d=4), bit 2 sign (1: negative), bits 3-9 state a (in s' only), bits
-// 10-16 state c (in s only), bits 17-31 for d=2 entries of the neutron
-// lists: the column index of the move a -> c in the pn transition table.
+// 10-16 state c (in s only).  Neutron lists: bits 17-31 of d=2 entries hold
+// the column index of the move a -> c in the pn transition table.  Proton
+// list: bits 17-24 hold q(s'), bits 25-31 (2M(s') - 2M(s))/2 + 64.
+// tgt: neutron lists, the partner s'; proton list, the first basis row of
+// s' (p_row_base[s']), the partner index itself being kept in ConnList::tgt.
 // local: neutron lists, index of s' inside its 2M block; proton list, for
 // d=2 entries the row offset tr_base of the move a -> c in that table.
 // val: d=0 like-particle diagonal energy (one-body + pairs); d=2 unsigned
@@ -78,6 +81,8 @@ __host__ __device__ inline int info_neg(uint32_t i) { return (int)((i >> 2) & 1u
 __host__ __device__ inline int info_a(uint32_t i) { return (int)((i >> 3) & 127u); }
 __host__ __device__ inline int info_c(uint32_t i) { return (int)((i >> 10) & 127u); }
 __host__ __device__ inline int info_tcol(uint32_t i) { return (int)(i >> 17); }
+__host__ __device__ inline int info_q(uint32_t i) { return (int)((i >> 17) & 255u); }
+__host__ __device__ inline int info_dslot(uint32_t i) { return (int)(i >> 25) - 64; }
 __host__ __device__ inline uint32_t make_info(int dcode, int neg, int a, int c) {
     return (uint32_t)dcode | ((uint32_t)neg << 2) | ((uint32_t)a << 3) | ((uint32_t)c << 10);
 }
@@ -89,8 +94,10 @@ template <class T>
 struct ConnList {
     std::shared_ptr<DevBuf<int64_t>> ptr_buf;
     std::shared_ptr<DevBuf<ConnEntry<T>>> ent_buf;
+    std::shared_ptr<DevBuf<int32_t>> tgt_buf;
     const int64_t *ptr = nullptr;
     ConnEntry<T> *ent = nullptr;
+    const int32_t *tgt = nullptr;   // partner index per entry (absolute positions, as ent)
     int64_t n = 0;      // determinants (rows of the list)
     int64_t first = 0;  // ptr[0]
     int64_t total = 0;  // ptr[n] - ptr[0]
