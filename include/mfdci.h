@@ -226,7 +226,9 @@ typedef struct {
     int32_t block;        /* block size b, 1..8                            [8]  */
     int32_t max_basis;    /* Krylov vectors kept before a thick restart   [64] */
     int32_t max_iter;     /* block steps in total                       [2000] */
-    double tol;           /* converged when ||H x - theta x|| <= tol*||H||[1e-8] */
+    double tol;           /* converged when the Ritz residual estimate is
+                             <= tol*||H|| [1e-6 for FP32 H, 1e-10 for FP64 H];
+                             the eigenvalue error is then ~ residual^2/gap */
     uint64_t seed;        /* seed of the start block                      [1]  */
     int32_t reorth_passes;/* full Gram-Schmidt passes per step after the
                              projection on the two newest blocks, 1..2    [1]  */

@@ -126,6 +126,7 @@ ci_status ci_batch_run(ci_batch *b, void *stream) {
     return guard([&] {
         if (!b) fail(CI_ERR_INVALID_ARG, "batch is NULL");
         if (b->impl.ran) fail(CI_ERR_STATE, "batch already ran");
+        StreamScope scope(reinterpret_cast<cudaStream_t>(stream));
         batch_run(&b->impl, reinterpret_cast<cudaStream_t>(stream));
     });
 }
@@ -165,6 +166,10 @@ ci_status ci_batch_stats(const ci_batch *b, double *build_s, double *solve_s, in
     });
 }
 
-void ci_batch_destroy(ci_batch *b) { delete b; }
+void ci_batch_destroy(ci_batch *b) {
+    if (!b) return;
+    HandleRelease hr;
+    delete b;
+}
 
 }  // extern "C"

@@ -280,7 +280,6 @@ static void count_group_t(const std::vector<Problem *> &ps, GroupCSR *g, cudaStr
         upload_args<T>(args, g->row_off, dargs, doff, s);
         launch("k_count_rows", k_count_rows<T>, row_grid(rows), 256, 0, s, (const RowArgs<T> *)dargs.ptr,
                (const int64_t *)doff.ptr, (int)ps.size());
-        CI_CUDA(cudaStreamSynchronize(s));
     }
 }
 
@@ -291,10 +290,7 @@ void count_group(const std::vector<Problem *> &ps, int prec, GroupCSR *g, cudaSt
     const int64_t rows = g->row_off.back();
     g->row_ptr.alloc(rows + 1);
     exclusive_scan_i32(g->row_cnt.ptr, rows, g->row_ptr.ptr, ps[0]->scan_scratch, s);
-    std::vector<int64_t> ends(ps.size() + 1);
-    for (size_t i = 0; i <= ps.size(); ++i)
-        CI_CUDA(cudaMemcpyAsync(&ends[i], g->row_ptr.ptr + g->row_off[i], sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    CI_CUDA(cudaStreamSynchronize(s));
+    const std::vector<int64_t> ends = gather_i64(g->row_ptr.ptr, g->row_off, s);
     g->nnz = ends[ps.size()];
     g->nnz_of.resize(ps.size());
     for (size_t i = 0; i < ps.size(); ++i) g->nnz_of[i] = ends[i + 1] - ends[i];
@@ -316,7 +312,6 @@ static void fill_group_t(const std::vector<Problem *> &ps, GroupCSR *g, cudaStre
     upload_args<T>(args, g->row_off, dargs, doff, s);
     launch("k_fill_rows", k_fill_rows<T>, row_grid(rows), 256, 0, s, (const RowArgs<T> *)dargs.ptr,
            (const int64_t *)doff.ptr, (int)ps.size());
-    CI_CUDA(cudaStreamSynchronize(s));  // the argument arrays are freed on return
 }
 
 // Fig. 1 lines 9-14 for a counted group: allocate and fill col / val.

@@ -115,10 +115,15 @@ ci_status ci_problem_create(const ci_problem_desc *desc, ci_problem **out) {
     });
 }
 
-void ci_problem_destroy(ci_problem *p) { delete p; }
+void ci_problem_destroy(ci_problem *p) {
+    if (!p) return;
+    HandleRelease hr;
+    delete p;
+}
 
 ci_status ci_enumerate_basis(ci_problem *p, int64_t *dim, void *stream) {
     return guard([&] {
+        StreamScope scope(as_stream(stream));
         if (!p) fail(CI_ERR_INVALID_ARG, "problem is NULL");
         enumerate_basis(&p->impl, as_stream(stream));
         if (dim) *dim = p->impl.dim;
@@ -160,6 +165,7 @@ ci_status ci_get_basis(const ci_problem *p, int32_t *p_idx, int32_t *n_idx, int6
 
 ci_status ci_species_filter(ci_problem *p, void *stream) {
     return guard([&] {
+        StreamScope scope(as_stream(stream));
         if (!p) fail(CI_ERR_INVALID_ARG, "problem is NULL");
         enumerate_basis(&p->impl, as_stream(stream));
         species_filter<float>(&p->impl, as_stream(stream));
@@ -179,6 +185,7 @@ ci_status ci_get_species_conn(const ci_problem *p, int32_t species, int64_t *ptr
 
 ci_status ci_count_nnz(ci_problem *p, int64_t *nnz, int32_t *row_cnt, void *stream) {
     return guard([&] {
+        StreamScope scope(as_stream(stream));
         if (!p) fail(CI_ERR_INVALID_ARG, "problem is NULL");
         cudaStream_t s = as_stream(stream);
         Problem &P = p->impl;
@@ -193,6 +200,7 @@ ci_status ci_count_nnz(ci_problem *p, int64_t *nnz, int32_t *row_cnt, void *stre
 
 ci_status ci_exclusive_scan(const int32_t *counts, int64_t n, int64_t *offsets, void *stream) {
     return guard([&] {
+        StreamScope scope(as_stream(stream));
         if (n < 0) fail(CI_ERR_INVALID_ARG, "n < 0");
         if (!offsets || (n > 0 && !counts)) fail(CI_ERR_INVALID_ARG, "counts/offsets are NULL");
         static DevBuf<int64_t> scratch;   // library-owned, grown on demand
@@ -205,6 +213,7 @@ ci_status ci_exclusive_scan(const int32_t *counts, int64_t n, int64_t *offsets, 
 
 ci_status ci_build_H(ci_problem *p, int32_t vtype, ci_matrix **out, void *stream) {
     return guard([&] {
+        StreamScope scope(as_stream(stream));
         if (!p || !out) fail(CI_ERR_INVALID_ARG, "problem or out is NULL");
         *out = nullptr;
         std::unique_ptr<ci_matrix> m(new ci_matrix());
@@ -214,7 +223,11 @@ ci_status ci_build_H(ci_problem *p, int32_t vtype, ci_matrix **out, void *stream
     });
 }
 
-void ci_matrix_destroy(ci_matrix *m) { delete m; }
+void ci_matrix_destroy(ci_matrix *m) {
+    if (!m) return;
+    HandleRelease hr;
+    delete m;
+}
 
 ci_status ci_matrix_info(const ci_matrix *m, int64_t *dim, int64_t *nnz, int32_t *vtype) {
     return guard([&] {
@@ -228,6 +241,7 @@ ci_status ci_matrix_info(const ci_matrix *m, int64_t *dim, int64_t *nnz, int32_t
 ci_status ci_matrix_export(const ci_matrix *m, int64_t *row_ptr, int32_t *col, void *val, float *row_scale,
                            void *stream) {
     return guard([&] {
+        StreamScope scope(as_stream(stream));
         if (!m) fail(CI_ERR_INVALID_ARG, "matrix is NULL");
         const Matrix &M = m->impl;
         cudaStream_t s = as_stream(stream);
@@ -242,6 +256,7 @@ ci_status ci_matrix_export(const ci_matrix *m, int64_t *row_ptr, int32_t *col, v
 
 ci_status ci_apply_H(const ci_matrix *m, const void *X, void *Y, int32_t nvec, void *stream) {
     return guard([&] {
+        StreamScope scope(as_stream(stream));
         if (!m) fail(CI_ERR_INVALID_ARG, "matrix is NULL");
         apply_matrix(&m->impl, X, Y, nvec, as_stream(stream));
     });

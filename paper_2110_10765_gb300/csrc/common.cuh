@@ -60,30 +60,60 @@ ci_status guard(F &&f) {
 
 // ------------------------------------------------------------------ memory
 
-// Owning device buffer (cudaMalloc / cudaFree).
+// Device memory comes from one stream-ordered pool per device
+// (cudaMallocFromPoolAsync / cudaFreeAsync).  A buffer is allocated on the
+// stream current on the calling thread and released on that same stream,
+// so a temporary needs no synchronisation before it is dropped and freed
+// blocks are reused without a round trip to the driver.  Every ABI call
+// that takes a stream makes it current (StreamScope) for its duration;
+// without one the legacy default stream is current.
+cudaStream_t current_stream();
+struct StreamScope {
+    cudaStream_t prev;
+    explicit StreamScope(cudaStream_t s);
+    ~StreamScope();
+    StreamScope(const StreamScope &) = delete;
+    StreamScope &operator=(const StreamScope &) = delete;
+};
+void *pool_alloc(size_t bytes, cudaStream_t s);
+void pool_free(void *p, cudaStream_t s);
+// Handle destruction: waits for the device, then releases every buffer on
+// the legacy default stream while it is alive (the stream a buffer was
+// allocated on may no longer exist).
+struct HandleRelease {
+    bool prev;
+    HandleRelease();
+    ~HandleRelease();
+    HandleRelease(const HandleRelease &) = delete;
+    HandleRelease &operator=(const HandleRelease &) = delete;
+};
+
+// Owning device buffer from the pool.
 template <class T>
 struct DevBuf {
     T *ptr = nullptr;
     size_t n = 0;
+    cudaStream_t st = nullptr;   // stream of the allocation and of the release
     DevBuf() = default;
     explicit DevBuf(size_t count) { alloc(count); }
     DevBuf(const DevBuf &) = delete;
     DevBuf &operator=(const DevBuf &) = delete;
-    DevBuf(DevBuf &&o) noexcept : ptr(o.ptr), n(o.n) { o.ptr = nullptr; o.n = 0; }
+    DevBuf(DevBuf &&o) noexcept : ptr(o.ptr), n(o.n), st(o.st) { o.ptr = nullptr; o.n = 0; }
     DevBuf &operator=(DevBuf &&o) noexcept {
-        if (this != &o) { release(); ptr = o.ptr; n = o.n; o.ptr = nullptr; o.n = 0; }
+        if (this != &o) { release(); ptr = o.ptr; n = o.n; st = o.st; o.ptr = nullptr; o.n = 0; }
         return *this;
     }
     ~DevBuf() { release(); }
     void alloc(size_t count) {
         release();
         if (count == 0) count = 1;  // keep a valid pointer for empty arrays
-        CI_CUDA(cudaMalloc(&ptr, count * sizeof(T)));
+        st = current_stream();
+        ptr = static_cast<T *>(pool_alloc(count * sizeof(T), st));
         n = count;
     }
     void ensure(size_t count) { if (n < count || ptr == nullptr) alloc(count); }
     void release() {
-        if (ptr) cudaFree(ptr);
+        if (ptr) pool_free(ptr, st);
         ptr = nullptr;
         n = 0;
     }

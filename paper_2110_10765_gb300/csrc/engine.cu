@@ -740,9 +740,14 @@ static DensePtrs dense_ptrs(Engine *e) {
 }
 
 Engine::~Engine() {
+    HandleRelease hr;
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     if (pinned_counter) cudaFreeHost(pinned_counter);
+    slots.release(); tiles.release(); ntiles.release(); counters.release(); part.release();
+    for (DevBuf<double> *b : {&dn.T, &dn.S, &dn.theta, &dn.Cl, &dn.Cf, &dn.Cr, &dn.G, &dn.M, &dn.R, &dn.res,
+                              &dn.evals, &dn.tres})
+        b->release();
     if (stream) cudaStreamDestroy(stream);
 }
 
@@ -764,7 +769,16 @@ void engine_create(Engine *e, int max_slots, int max_tiles, int MB, cudaStream_t
     e->max_slots = max_slots;
     e->max_tiles = max_tiles;
     CI_CUDA(cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking));
-    (void)s;
+    // the engine stream starts after the caller's work (its buffers, built
+    // matrices) and owns the engine's own buffers
+    {
+        cudaEvent_t ev;
+        CI_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        CI_CUDA(cudaEventRecord(ev, s));
+        CI_CUDA(cudaStreamWaitEvent(e->stream, ev, 0));
+        CI_CUDA(cudaEventDestroy(ev));
+    }
+    StreamScope scope(e->stream);
     e->slots.alloc(max_slots);
     e->tiles.alloc(max_tiles);
     e->ntiles.alloc(1);

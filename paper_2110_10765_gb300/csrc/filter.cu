@@ -207,7 +207,6 @@ static void launch_filter(const std::vector<FilterArgs<T>> &jobs, int pass, cuda
     CI_CUDA(cudaMemcpyAsync(db.ptr, blk.data(), sizeof(int64_t) * blk.size(), cudaMemcpyHostToDevice, s));
     launch("k_filter", k_filter<T, W, RW>, (unsigned)blk.back(), 256, 0, s, (const FilterArgs<T> *)dj.ptr,
            (const int64_t *)db.ptr, (int)jobs.size(), pass);
-    CI_CUDA(cudaStreamSynchronize(s));  // the job arrays are freed on return
 }
 
 template <class T>
@@ -332,11 +331,10 @@ void species_filter_group(const std::vector<Problem *> &ps_in, cudaStream_t s) {
     for (size_t i = 0; i < jobs.size(); ++i) jobs[i].count = cnt.ptr + cnt_off[i];
     filter_pass<T>(jobs, 0, s);
     exclusive_scan_i32(cnt.ptr, ncnt, offs->ptr, ps[0]->scan_scratch, s);
-    std::vector<int64_t> hoff((size_t)ncnt + 1);
-    CI_CUDA(cudaMemcpyAsync(hoff.data(), offs->ptr, sizeof(int64_t) * (ncnt + 1), cudaMemcpyDeviceToHost, s));
-    CI_CUDA(cudaStreamSynchronize(s));
-    auto ents = std::make_shared<DevBuf<ConnEntry<T>>>((size_t)hoff[ncnt]);
-    auto tgts = std::make_shared<DevBuf<int32_t>>((size_t)hoff[ncnt]);
+    // list boundaries: hb[i] = offs[cnt_off[i]]
+    std::vector<int64_t> hb = gather_i64(offs->ptr, cnt_off, s);
+    auto ents = std::make_shared<DevBuf<ConnEntry<T>>>((size_t)hb.back());
+    auto tgts = std::make_shared<DevBuf<int32_t>>((size_t)hb.back());
     for (size_t i = 0; i < jobs.size(); ++i) {
         ConnList<T> &L = *lists[i];
         L.ptr_buf = offs;
@@ -346,8 +344,8 @@ void species_filter_group(const std::vector<Problem *> &ps_in, cudaStream_t s) {
         L.ptr = offs->ptr + cnt_off[i];
         L.ent = ents->ptr;
         L.n = jobs[i].n;
-        L.first = hoff[cnt_off[i]];
-        L.total = hoff[cnt_off[i + 1]] - hoff[cnt_off[i]];
+        L.first = hb[i];
+        L.total = hb[i + 1] - hb[i];
         jobs[i].ptr = L.ptr;
         jobs[i].ent = L.ent;
         jobs[i].tgt = tgts->ptr;
@@ -377,7 +375,6 @@ void species_filter_group(const std::vector<Problem *> &ps_in, cudaStream_t s) {
         CI_CUDA(cudaMemcpyAsync(dso.ptr, soff.data(), sizeof(int64_t) * soff.size(), cudaMemcpyHostToDevice, s));
         launch("k_seg", k_seg<T>, grid_for(soff.back(), 256, sm_count() * 16), 256, 0, s, (const SegJob<T> *)dsj.ptr,
                (const int64_t *)dso.ptr, (int)sj.size());
-        CI_CUDA(cudaStreamSynchronize(s));
     }
     for (Problem *p : ps) p->conn<T>().ready = true;
 }

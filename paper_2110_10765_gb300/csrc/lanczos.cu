@@ -375,7 +375,7 @@ void lowest_eigs(const Matrix *H, const ci_eig_opts *opts_in, double *evals, dou
     if (o.block == 0) o.block = 8;
     if (o.max_basis == 0) o.max_basis = 64;
     if (o.max_iter == 0) o.max_iter = 2000;
-    if (o.tol == 0.0) o.tol = H->vtype == CI_F64 ? 1e-10 : 1e-7;
+    if (o.tol == 0.0) o.tol = H->vtype == CI_F64 ? 1e-10 : 1e-6;
     if (o.seed == 0) o.seed = 1;
     if (o.reorth_passes == 0) o.reorth_passes = 1;
     if (o.check_every == 0) o.check_every = 2;
@@ -578,6 +578,7 @@ extern "C" ci_status ci_lowest_eigs(const ci_matrix *m, const ci_eig_opts *opts,
                                     ci_eig_info *info, void *stream) {
     return ci::guard([&] {
         if (!m) ci::fail(CI_ERR_INVALID_ARG, "matrix is NULL");
+        ci::StreamScope scope(reinterpret_cast<cudaStream_t>(stream));
         ci::lowest_eigs(&m->impl, opts, evals, evecs, info, reinterpret_cast<cudaStream_t>(stream));
     });
 }

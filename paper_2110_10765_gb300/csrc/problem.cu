@@ -284,7 +284,7 @@ void problem_create(const ci_problem_desc *d, Problem *p) {
     p->tbme_seed = d->tbme_seed;
     p->tbme_dtype = d->tbme_dtype;
 
-    cudaStream_t s = 0;
+    cudaStream_t s = current_stream();
     if (p->tbme_source == CI_TBME_TABLES) {
         size_t esz = p->tbme_dtype == CI_F32 ? 4 : 8;
         size_t bytes = esz * (size_t)p->S * p->S * p->S * p->S;
@@ -371,7 +371,6 @@ void stage_tables_group(const std::vector<Problem *> &ps, cudaStream_t s) {
     CI_CUDA(cudaMemcpyAsync(doff.ptr, off.data(), sizeof(int64_t) * off.size(), cudaMemcpyHostToDevice, s));
     launch("k_stage", k_stage<T>, grid_for(off.back(), 256, sm_count() * 16), 256, 0, s, (const StageJob<T> *)djobs.ptr,
            (const int64_t *)doff.ptr, (int)jobs.size());
-    CI_CUDA(cudaStreamSynchronize(s));  // the job arrays are freed on return
     for (Problem *p : todo) p->tables<T>().ready = true;
 }
 
@@ -399,29 +398,36 @@ static void enumerate_species(const Problem *p, int A, SpeciesList *L) {
     const int nmin = suffix_min[0][A];
     const int64_t cap = 1ll << 26;
     struct Tmp { int twoM, q; uint64_t w[2]; uint8_t occ[kMaxA]; };
-    std::vector<Tmp> out;
-    uint8_t occ[kMaxA];
-    std::function<void(int, int, int, int)> rec = [&](int start, int depth, int Nsum, int msum) {
-        if (depth == A) {
-            Tmp t;
-            t.twoM = msum;
-            t.q = Nsum - nmin;
-            t.w[0] = t.w[1] = 0;
-            for (int k = 0; k < A; ++k) { t.occ[k] = occ[k]; t.w[occ[k] >> 6] |= 1ull << (occ[k] & 63); }
-            out.push_back(t);
-            if ((int64_t)out.size() > cap) fail(CI_ERR_CAPACITY, "species list larger than 2^26 determinants");
-            return;
-        }
-        for (int o = start; o <= S - (A - depth); ++o) {
-            if (p->nmax >= 0) {
-                int lb = Nsum + p->sp_N[o] + suffix_min[o + 1][A - depth - 1];
-                if (lb - nmin > p->nmax) continue;
+    struct Walk {
+        const Problem *p;
+        const std::vector<std::vector<int>> &suffix_min;
+        int S, A, nmin;
+        int64_t cap;
+        std::vector<Tmp> out;
+        uint8_t occ[kMaxA];
+        void rec(int start, int depth, int Nsum, int msum) {
+            if (depth == A) {
+                Tmp t;
+                t.twoM = msum;
+                t.q = Nsum - nmin;
+                t.w[0] = t.w[1] = 0;
+                for (int k = 0; k < A; ++k) { t.occ[k] = occ[k]; t.w[occ[k] >> 6] |= 1ull << (occ[k] & 63); }
+                out.push_back(t);
+                if ((int64_t)out.size() > cap) fail(CI_ERR_CAPACITY, "species list larger than 2^26 determinants");
+                return;
             }
-            occ[depth] = (uint8_t)o;
-            rec(o + 1, depth + 1, Nsum + p->sp_N[o], msum + p->sp_twom[o]);
+            for (int o = start; o <= S - (A - depth); ++o) {
+                if (p->nmax >= 0) {
+                    int lb = Nsum + p->sp_N[o] + suffix_min[o + 1][A - depth - 1];
+                    if (lb - nmin > p->nmax) continue;
+                }
+                occ[depth] = (uint8_t)o;
+                rec(o + 1, depth + 1, Nsum + p->sp_N[o], msum + p->sp_twom[o]);
+            }
         }
-    };
-    rec(0, 0, 0, 0);
+    } walk{p, suffix_min, S, A, nmin, cap, {}, {}};
+    walk.rec(0, 0, 0, 0);
+    std::vector<Tmp> &out = walk.out;
     std::sort(out.begin(), out.end(), [](const Tmp &x, const Tmp &y) {
         if (x.twoM != y.twoM) return x.twoM < y.twoM;
         if (x.q != y.q) return x.q < y.q;
@@ -477,7 +483,14 @@ __global__ void k_row_map(int64_t dim, int64_t nP, const int64_t *p_row_base,
 void enumerate_basis(Problem *p, cudaStream_t s) {
     if (p->enumerated) return;
     enumerate_species(p, p->Z, &p->sp[0]);
-    enumerate_species(p, p->N, &p->sp[1]);
+    if (p->N == p->Z) {  // both species draw from the same s.p. table
+        SpeciesList &a = p->sp[0], &b = p->sp[1];
+        b.A = a.A; b.W = a.W; b.n = a.n; b.bits = a.bits; b.q = a.q; b.twoM = a.twoM; b.occ = a.occ;
+        b.local = a.local; b.m2min = a.m2min; b.nblk = a.nblk; b.nq = a.nq; b.blk_start = a.blk_start;
+        b.blk_qend = a.blk_qend;
+    } else {
+        enumerate_species(p, p->N, &p->sp[1]);
+    }
     SpeciesList &P = p->sp[0], &Nn = p->sp[1];
     p->p_row_base.assign(P.n + 1, 0);
     std::vector<int64_t> p_nstart(P.n ? P.n : 1, 0);

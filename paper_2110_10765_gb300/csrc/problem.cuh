@@ -206,6 +206,8 @@ void count_group(const std::vector<Problem *> &ps, int prec, GroupCSR *g, cudaSt
 void fill_group(const std::vector<Problem *> &ps, GroupCSR *g, cudaStream_t s);
 void exclusive_scan_i32(const int32_t *counts, int64_t n, int64_t *offsets,
                         DevBuf<int64_t> &scratch, cudaStream_t s);
+// src[idx[i]] for every i, copied to the host (synchronises s)
+std::vector<int64_t> gather_i64(const int64_t *src, const std::vector<int64_t> &idx, cudaStream_t s);
 void build_matrix(Problem *p, int vtype, Matrix *m, cudaStream_t s);
 void apply_matrix(const Matrix *m, const void *X, void *Y, int nvec, cudaStream_t s);
 void lowest_eigs(const Matrix *H, const ci_eig_opts *opts, double *evals, double *evecs, ci_eig_info *info,

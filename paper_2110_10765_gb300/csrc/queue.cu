@@ -234,6 +234,7 @@ void Queue::admit() {
 void Queue::run() {
     try {
         CI_CUDA(cudaSetDevice(device));
+        StreamScope scope(eng.stream);  // requests live on the engine stream
         int64_t since = 0;
         while (true) {
             {
@@ -410,6 +411,7 @@ void ci_queue_destroy(ci_queue *q) {
         q->impl.cv.notify_all();
     }
     if (q->impl.worker.joinable()) q->impl.worker.join();
+    HandleRelease hr;
     delete q;
 }
 

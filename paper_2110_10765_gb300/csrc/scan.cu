@@ -107,6 +107,28 @@ void exclusive_scan_i32(const int32_t *counts, int64_t n, int64_t *offsets, DevB
     CI_CHECK_LAUNCH();
 }
 
+__global__ void k_gather_i64(const int64_t *src, const int64_t *idx, int64_t n, int64_t *out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = src[idx[i]];
+}
+
+std::vector<int64_t> gather_i64(const int64_t *src, const std::vector<int64_t> &idx, cudaStream_t s) {
+    const int64_t n = (int64_t)idx.size();
+    std::vector<int64_t> out((size_t)n);
+    if (n == 0) return out;
+    if (n <= 2) {
+        for (int64_t i = 0; i < n; ++i)
+            CI_CUDA(cudaMemcpyAsync(&out[i], src + idx[i], sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    } else {
+        DevBuf<int64_t> di((size_t)n), dout((size_t)n);
+        CI_CUDA(cudaMemcpyAsync(di.ptr, idx.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, s));
+        launch("k_gather_i64", k_gather_i64, grid_for(n, 256), 256, 0, s, src, (const int64_t *)di.ptr, n, dout.ptr);
+        CI_CUDA(cudaMemcpyAsync(out.data(), dout.ptr, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, s));
+    }
+    CI_CUDA(cudaStreamSynchronize(s));
+    return out;
+}
+
 }  // namespace ci
 
 // ---------------------------------------------------------------------------
