@@ -6,24 +6,31 @@
 
 namespace ci {
 
+// One sweep of a species list against itself.  It serves every list of
+// that species (mode bits 1 << CONN_*): the XOR + popcount of a pair is
+// taken once and each list applies its own keep rule.  Both species share
+// the sweep when they are the same list (Z = N over one s.p. table).
 template <class T>
 struct FilterArgs {
     int64_t n;
     int A, S, W;
-    int mode;                  // ConnMode
+    int modes;                 // lists filled by this sweep
     const uint64_t *bits;      // [n][W]
     const int32_t *twoM;       // [n]
     const int32_t *local;      // [n]
     const uint8_t *occ;        // [n][A]
-    const T *eps, *U, *D, *C;  // like-particle tables of this species
-    const int32_t *pair_row, *pair_col;
-    const int32_t *tr_base;    // outer list: row offset of a proton move in the pn table
-    const int32_t *tr_idx;     // neutron lists: column index of a neutron move
     const int32_t *q;          // [n] excess quanta
+    const int64_t *blk_start;  // [nblk+1] 2M blocks of the sorted list
+    int m2min, nblk, K;        // lowest 2M, blocks, largest |2m| of a state
+    const T *eps;
+    const T *U[2], *D[2], *C[2];   // like-particle tables: [0] protons, [1] neutrons
+    const int32_t *pair_row, *pair_col;
+    const int32_t *tr_base;    // proton list: row offset of a proton move in the pn table
+    const int32_t *tr_idx;     // neutron lists: column index of a neutron move
     const int64_t *p_row_base; // proton list: first basis row of every determinant
-    int32_t *count;            // pass 0
-    const int64_t *ptr;        // pass 1
-    ConnEntry<T> *ent;         // pass 1
+    int32_t *count[3];         // pass 0, per list
+    const int64_t *ptr[3];     // pass 1, per list
+    ConnEntry<T> *ent;         // pass 1 (shared entry array)
     int32_t *tgt;              // pass 1: partner index of every entry
 };
 
@@ -41,10 +48,13 @@ __device__ __forceinline__ int count_below(const uint64_t *K, int W, int o) {
 
 __device__ __forceinline__ void flip(uint64_t *K, int o) { K[o >> 6] ^= 1ull << (o & 63); }
 
-// Entry for row determinant s (bra) and partner t (ket).
+// Entry for row determinant s (bra) and partner t (ket) of one list: the
+// like-particle Slater-Condon part with the species' tables (sp 0 protons,
+// 1 neutrons) and what the row kernels need about the move.
 template <class T>
-__device__ __forceinline__ ConnEntry<T> make_entry_core(const FilterArgs<T> &a, int64_t s, int64_t t, const uint64_t *bs,
-                                                        const uint64_t *bt, int d) {
+__device__ __forceinline__ ConnEntry<T> make_entry(const FilterArgs<T> &a, int mode, int64_t s, int64_t t,
+                                                   const uint64_t *bs, const uint64_t *bt, int d) {
+    const int sp = mode == CONN_OUTER ? 0 : 1;
     ConnEntry<T> e;
     e.tgt = (int32_t)t;
     e.local = a.local[t];
@@ -52,65 +62,59 @@ __device__ __forceinline__ ConnEntry<T> make_entry_core(const FilterArgs<T> &a, 
     if (d == 0) {
         // like-particle diagonal: one-body energies + every occupied pair
         const uint8_t *o = a.occ + s * a.A;
+        const T *D = a.D[sp];
         T v = 0;
         for (int i = 0; i < a.A; ++i) v += a.eps[o[i]];
         for (int i = 0; i < a.A; ++i)
-            for (int j = i + 1; j < a.A; ++j) v += a.D[o[i] * S + o[j]];
+            for (int j = i + 1; j < a.A; ++j) v += D[o[i] * S + o[j]];
         e.info = make_info(0, 0, 0, 0);
         e.val = v;
-        return e;
+    } else {
+        uint64_t xa[kMaxWords], xc[kMaxWords], K[kMaxWords];
+        for (int w = 0; w < kMaxWords; ++w) {
+            uint64_t x = w < W ? (bs[w] ^ bt[w]) : 0ull;
+            xa[w] = w < W ? (x & bt[w]) : 0ull;   // in the ket only: annihilated
+            xc[w] = w < W ? (x & bs[w]) : 0ull;   // in the bra only: created
+            K[w] = w < W ? bt[w] : 0ull;
+        }
+        if (d == 2) {
+            int ao = lowest_state(xa, W), co = lowest_state(xc, W);
+            int par = count_below(K, W, ao);       // a_a on the ket
+            flip(K, ao);
+            par += count_below(K, W, co);          // then a+_c
+            // spectators: the ket's other particles
+            const uint8_t *o = a.occ + t * a.A;
+            T h = 0;
+            const T *u = a.U[sp] + ((int64_t)co * S + ao) * S;
+            for (int i = 0; i < a.A; ++i)
+                if (o[i] != ao) h += u[o[i]];
+            e.info = make_info(1, par & 1, ao, co);
+            if (mode == CONN_OUTER) e.local = a.tr_base[co * S + ao];
+            else e.info |= (uint32_t)a.tr_idx[co * S + ao] << 17;
+            e.val = h;
+        } else {
+            // d == 4: (a<b) -> (c<d), operator a+_c a+_d a_b a_a on the ket
+            int a1 = lowest_state(xa, W);
+            flip(xa, a1);
+            int b1 = lowest_state(xa, W);
+            int c1 = lowest_state(xc, W);
+            flip(xc, c1);
+            int d1 = lowest_state(xc, W);
+            int par = count_below(K, W, a1);
+            flip(K, a1);
+            par += count_below(K, W, b1);
+            flip(K, b1);
+            par += count_below(K, W, d1);
+            flip(K, d1);
+            par += count_below(K, W, c1);
+            T v = a.C[sp][a.pair_row[c1 * S + d1] + a.pair_col[a1 * S + b1]];
+            e.info = make_info(2, 0, a1, c1);
+            e.val = (par & 1) ? -v : v;
+        }
     }
-    uint64_t xa[kMaxWords], xc[kMaxWords], K[kMaxWords];
-    for (int w = 0; w < kMaxWords; ++w) {
-        uint64_t x = w < W ? (bs[w] ^ bt[w]) : 0ull;
-        xa[w] = w < W ? (x & bt[w]) : 0ull;   // in the ket only: annihilated
-        xc[w] = w < W ? (x & bs[w]) : 0ull;   // in the bra only: created
-        K[w] = w < W ? bt[w] : 0ull;
-    }
-    if (d == 2) {
-        int ao = lowest_state(xa, W), co = lowest_state(xc, W);
-        int par = count_below(K, W, ao);       // a_a on the ket
-        flip(K, ao);
-        par += count_below(K, W, co);          // then a+_c
-        // spectators: the ket's other particles
-        const uint8_t *o = a.occ + t * a.A;
-        T h = 0;
-        const T *u = a.U + ((int64_t)co * S + ao) * S;
-        for (int i = 0; i < a.A; ++i)
-            if (o[i] != ao) h += u[o[i]];
-        e.info = make_info(1, par & 1, ao, co);
-        if (a.mode == CONN_OUTER) e.local = a.tr_base[co * S + ao];
-        else e.info |= (uint32_t)a.tr_idx[co * S + ao] << 17;
-        e.val = h;
-        return e;
-    }
-    // d == 4: (a<b) -> (c<d), operator a+_c a+_d a_b a_a on the ket
-    int a1 = lowest_state(xa, W);
-    flip(xa, a1);
-    int b1 = lowest_state(xa, W);
-    int c1 = lowest_state(xc, W);
-    flip(xc, c1);
-    int d1 = lowest_state(xc, W);
-    int par = count_below(K, W, a1);
-    flip(K, a1);
-    par += count_below(K, W, b1);
-    flip(K, b1);
-    par += count_below(K, W, d1);
-    flip(K, d1);
-    par += count_below(K, W, c1);
-    T v = a.C[a.pair_row[c1 * S + d1] + a.pair_col[a1 * S + b1]];
-    e.info = make_info(2, 0, a1, c1);
-    e.val = (par & 1) ? -v : v;
-    return e;
-}
-
-// Entry of row s, partner t; the proton list carries what the row kernels
-// need about t (first basis row, q, change of 2M) instead of t itself.
-template <class T>
-__device__ __forceinline__ ConnEntry<T> make_entry(const FilterArgs<T> &a, int64_t s, int64_t t, const uint64_t *bs,
-                                                   const uint64_t *bt, int d) {
-    ConnEntry<T> e = make_entry_core<T>(a, s, t, bs, bt, d);
-    if (a.mode == CONN_OUTER) {
+    if (mode == CONN_OUTER) {
+        // the proton list carries what the row kernels need about t (first
+        // basis row, q, change of 2M) instead of t itself
         e.tgt = (int32_t)a.p_row_base[t];
         const int dslot = (a.twoM[t] - a.twoM[s]) / 2;
         e.info = (e.info & 0x1FFFFu) | ((uint32_t)a.q[t] << 17) | ((uint32_t)(dslot + 64) << 25);
@@ -119,28 +123,36 @@ __device__ __forceinline__ ConnEntry<T> make_entry(const FilterArgs<T> &a, int64
 }
 
 // Each warp owns RW row determinants; the block's warps sweep the partner
-// list in tiles of kTile determinants staged in shared memory (bits and 2M),
-// so the list is read once per block.  Lanes take one partner each and a
-// warp ballot per row keeps the partners in ascending order.
+// window in tiles of kTile determinants staged in shared memory (bits and
+// 2M), so the window is read once per block.  Pass 0 counts the partners
+// of every row and list; pass 1 writes their indices (the entries are
+// evaluated afterwards by k_entries, one warp per row and list).  The window holds every
+// determinant whose 2M is within 2K of a row's 2M (a single move changes
+// 2M by at most 2K; a double move is kept only at equal 2M), and only the
+// row's own 2M block when the sweep fills the L4 list alone.  Lanes take
+// one partner each and a warp ballot per row and list keeps the partners
+// in ascending order.
 constexpr int kTile = 512;
 
-template <class T, int W, int RW>
-__global__ void __launch_bounds__(256) k_filter(const FilterArgs<T> *jobs, const int64_t *job_blk, int njobs,
-                                                int pass) {
+template <class T, int W, int RW, int PASS>
+__global__ void __launch_bounds__(256) k_filter(const FilterArgs<T> *jobs, const int64_t *job_blk, int njobs) {
+    constexpr bool pass = PASS != 0;
     __shared__ uint64_t sbits[kTile * W];
     __shared__ int32_t sm2[kTile];
-    int lo = 0, hi = njobs - 1;  // the job (one list of one problem) of this block
+    int lo = 0, hi = njobs - 1;  // the job (one species list of one problem) of this block
     while (lo < hi) {
         int mid = (lo + hi + 1) >> 1;
         if (job_blk[mid] <= (int64_t)blockIdx.x) lo = mid; else hi = mid - 1;
     }
     const FilterArgs<T> a = jobs[lo];  // by value: stores to ent cannot alias it
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int64_t row0 = (((int64_t)blockIdx.x - job_blk[lo]) * 8 + wid) * RW;
+    const int64_t blk_row0 = ((int64_t)blockIdx.x - job_blk[lo]) * 8 * RW;
+    const int64_t row0 = blk_row0 + (int64_t)wid * RW;
+    const bool mO = a.modes & (1 << CONN_OUTER), m2 = a.modes & (1 << CONN_L2), m4 = a.modes & (1 << CONN_L4);
     uint64_t bs[RW][kMaxWords];
     int ms[RW];
-    int64_t out[RW];
-    int cnt[RW];
+    int64_t out[RW][3];
+    int cnt[RW][3];
 #pragma unroll
     for (int i = 0; i < RW; ++i) {
         const int64_t s = row0 + i;
@@ -148,11 +160,20 @@ __global__ void __launch_bounds__(256) k_filter(const FilterArgs<T> *jobs, const
 #pragma unroll
         for (int w = 0; w < kMaxWords; ++w) bs[i][w] = (ok && w < W) ? a.bits[s * W + w] : 0ull;
         ms[i] = ok ? a.twoM[s] : 0;
-        out[i] = (ok && pass) ? a.ptr[s] : 0;
-        cnt[i] = 0;
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+            out[i][m] = (ok && pass && (a.modes >> m & 1)) ? a.ptr[m][s] : 0;
+            cnt[i][m] = 0;
+        }
     }
-    for (int64_t t0 = 0; t0 < a.n; t0 += kTile) {
-        const int nt = (int)min((int64_t)kTile, a.n - t0);
+    // partner window of the block's rows (rows are sorted by 2M)
+    const int64_t last = min(a.n - 1, blk_row0 + 8 * RW - 1);
+    const int b0 = (a.twoM[blk_row0] - a.m2min) / 2, b1 = (a.twoM[last] - a.m2min) / 2;
+    const int reach = (mO || m2) ? a.K : 0;
+    const int64_t t_lo = a.blk_start[max(b0 - reach, 0)];
+    const int64_t t_hi = a.blk_start[min(b1 + reach + 1, a.nblk)];
+    for (int64_t t0 = t_lo; t0 < t_hi; t0 += kTile) {
+        const int nt = (int)min((int64_t)kTile, t_hi - t0);
         __syncthreads();
         for (int e = threadIdx.x; e < nt * W; e += blockDim.x) sbits[e] = a.bits[t0 * W + e];
         for (int e = threadIdx.x; e < nt; e += blockDim.x) sm2[e] = a.twoM[t0 + e];
@@ -170,26 +191,30 @@ __global__ void __launch_bounds__(256) k_filter(const FilterArgs<T> *jobs, const
 #pragma unroll
                 for (int w = 0; w < W; ++w) d += __popcll(bs[i][w] ^ bt[w]);
                 const bool sameM = mt == ms[i];
-                bool keep;
-                if (a.mode == CONN_OUTER) keep = d <= 2 || (d == 4 && sameM);
-                else if (a.mode == CONN_L2) keep = d <= 2;
-                else keep = d <= 4 && sameM;
-                keep = keep && tv && (row0 + i < a.n);
-                const unsigned bal = __ballot_sync(0xffffffffu, keep);
-                if (pass && keep) {
-                    const int rank = __popc(bal & ((1u << lane) - 1u));
-                    a.ent[out[i] + rank] = make_entry<T>(a, row0 + i, t0 + tl, bs[i], bt, d);
-                    a.tgt[out[i] + rank] = (int32_t)(t0 + tl);
+                const bool valid = tv && (row0 + i < a.n);
+                const bool keep[3] = {mO && valid && (d <= 2 || (d == 4 && sameM)), m2 && valid && d <= 2,
+                                      m4 && valid && d <= 4 && sameM};
+#pragma unroll
+                for (int m = 0; m < 3; ++m) {
+                    if (!(a.modes >> m & 1)) continue;   // uniform over the block
+                    const unsigned bal = __ballot_sync(0xffffffffu, keep[m]);
+                    if (pass && keep[m]) {
+                        const int rank = __popc(bal & ((1u << lane) - 1u));
+                        a.tgt[out[i][m] + rank] = (int32_t)(t0 + tl);
+                    }
+                    out[i][m] += __popc(bal);
+                    cnt[i][m] += __popc(bal);
                 }
-                out[i] += __popc(bal);
-                cnt[i] += __popc(bal);
             }
         }
     }
     if (!pass && lane == 0) {
 #pragma unroll
         for (int i = 0; i < RW; ++i)
-            if (row0 + i < a.n) a.count[row0 + i] = cnt[i];
+            if (row0 + i < a.n)
+#pragma unroll
+                for (int m = 0; m < 3; ++m)
+                    if (a.modes >> m & 1) a.count[m][row0 + i] = cnt[i][m];
     }
 }
 
@@ -205,22 +230,74 @@ static void launch_filter(const std::vector<FilterArgs<T>> &jobs, int pass, cuda
     DevBuf<int64_t> db(blk.size());
     CI_CUDA(cudaMemcpyAsync(dj.ptr, jobs.data(), sizeof(FilterArgs<T>) * jobs.size(), cudaMemcpyHostToDevice, s));
     CI_CUDA(cudaMemcpyAsync(db.ptr, blk.data(), sizeof(int64_t) * blk.size(), cudaMemcpyHostToDevice, s));
-    launch("k_filter", k_filter<T, W, RW>, (unsigned)blk.back(), 256, 0, s, (const FilterArgs<T> *)dj.ptr,
-           (const int64_t *)db.ptr, (int)jobs.size(), pass);
+    if (pass) launch("k_filter", k_filter<T, W, RW, 1>, (unsigned)blk.back(), 256, 0, s,
+                     (const FilterArgs<T> *)dj.ptr, (const int64_t *)db.ptr, (int)jobs.size());
+    else launch("k_filter_count", k_filter<T, W, RW, 0>, (unsigned)blk.back(), 256, 0, s,
+                (const FilterArgs<T> *)dj.ptr, (const int64_t *)db.ptr, (int)jobs.size());
+}
+
+// Slater-Condon entries of every stored pair (s, tgt[e]) of the lists:
+// one warp per row of a list, lanes over its entries.
+template <class T, int W>
+__global__ void __launch_bounds__(256) k_entries(const FilterArgs<T> *jobs, const int64_t *job_row, int njobs) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t rows = job_row[njobs];
+    for (int64_t gr = warp; gr < rows; gr += nwarps) {
+        int lo = 0, hi = njobs - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (job_row[mid] <= gr) lo = mid; else hi = mid - 1;
+        }
+        const FilterArgs<T> &a = jobs[lo];
+        const int mode = __ffs(a.modes) - 1;
+        const int64_t s = gr - job_row[lo];
+        uint64_t bs[kMaxWords] = {0ull, 0ull};
+#pragma unroll
+        for (int w = 0; w < W; ++w) bs[w] = a.bits[s * W + w];
+        const int64_t e1 = a.ptr[mode][s + 1];
+        for (int64_t e = a.ptr[mode][s] + lane; e < e1; e += 32) {
+            const int64_t t = a.tgt[e];
+            uint64_t bt[kMaxWords] = {0ull, 0ull};
+            int d = 0;
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                bt[w] = a.bits[t * W + w];
+                d += __popcll(bs[w] ^ bt[w]);
+            }
+            a.ent[e] = make_entry<T>(a, mode, s, t, bs, bt, d);
+        }
+    }
+}
+
+template <class T, int W>
+static void launch_entries(const std::vector<FilterArgs<T>> &jobs, cudaStream_t s) {
+    if (jobs.empty()) return;
+    std::vector<int64_t> off(1, 0);
+    for (auto &j : jobs) off.push_back(off.back() + j.n);
+    if (off.back() == 0) return;
+    DevBuf<FilterArgs<T>> dj(jobs.size());
+    DevBuf<int64_t> doff(off.size());
+    CI_CUDA(cudaMemcpyAsync(dj.ptr, jobs.data(), sizeof(FilterArgs<T>) * jobs.size(), cudaMemcpyHostToDevice, s));
+    CI_CUDA(cudaMemcpyAsync(doff.ptr, off.data(), sizeof(int64_t) * off.size(), cudaMemcpyHostToDevice, s));
+    launch("k_entries", k_entries<T, W>, grid_for(off.back() * 32, 256, sm_count() * 8), 256, 0, s,
+           (const FilterArgs<T> *)dj.ptr, (const int64_t *)doff.ptr, (int)jobs.size());
 }
 
 template <class T>
 static void filter_pass(const std::vector<FilterArgs<T>> &jobs, int pass, cudaStream_t s) {
-    // rows per warp: 4 only when that still leaves every SM 16 blocks of
+    // rows per warp: 2 only when that still leaves every SM 16 blocks of
     // 8 warps (the sweep is latency bound, so more warps beat more reuse)
     std::vector<FilterArgs<T>> j1, j2;
     int64_t rows = 0;
     for (auto &j : jobs) {
+        if (j.n == 0) continue;
         (j.W == 1 ? j1 : j2).push_back(j);
         rows += j.n;
     }
-    const bool wide = rows >= (int64_t)sm_count() * 16 * 32;
-    if (wide) { launch_filter<T, 1, 4>(j1, pass, s); launch_filter<T, 2, 4>(j2, pass, s); }
+    const bool wide = rows >= (int64_t)sm_count() * 16 * 16;
+    if (wide) { launch_filter<T, 1, 2>(j1, pass, s); launch_filter<T, 2, 2>(j2, pass, s); }
     else { launch_filter<T, 1, 1>(j1, pass, s); launch_filter<T, 2, 1>(j2, pass, s); }
 }
 
@@ -284,18 +361,18 @@ __global__ void k_seg(const SegJob<T> *jobs, const int64_t *job_off, int njobs) 
 }
 
 template <class T>
-static FilterArgs<T> filter_job(Problem *p, int species, int mode) {
+static FilterArgs<T> filter_job(Problem *p, int species, int modes) {
     SpeciesList &sp = p->sp[species];
     Tables<T> &t = p->tables<T>();
     FilterArgs<T> a{};
-    a.n = sp.n; a.A = sp.A; a.S = p->S; a.W = sp.W; a.mode = mode;
+    a.n = sp.n; a.A = sp.A; a.S = p->S; a.W = sp.W; a.modes = modes;
     a.bits = sp.d_bits.ptr; a.twoM = sp.d_twoM.ptr; a.local = sp.d_local.ptr; a.occ = sp.d_occ.ptr;
     a.q = sp.d_q.ptr;
-    a.p_row_base = species == 0 ? p->d_p_row_base.ptr : nullptr;
+    a.blk_start = sp.d_blk_start.ptr; a.m2min = sp.m2min; a.nblk = sp.nblk; a.K = p->K;
+    a.p_row_base = p->d_p_row_base.ptr;
     a.eps = t.eps.ptr;
-    a.U = species == 0 ? t.Upp.ptr : t.Unn.ptr;
-    a.D = species == 0 ? t.Dpp.ptr : t.Dnn.ptr;
-    a.C = species == 0 ? t.Cpp.ptr : t.Cnn.ptr;
+    a.U[0] = t.Upp.ptr; a.D[0] = t.Dpp.ptr; a.C[0] = t.Cpp.ptr;
+    a.U[1] = t.Unn.ptr; a.D[1] = t.Dnn.ptr; a.C[1] = t.Cnn.ptr;
     a.pair_row = p->like_row.ptr; a.pair_col = p->like_col.ptr;
     a.tr_base = p->tr_base.ptr; a.tr_idx = p->tr_idx.ptr;
     return a;
@@ -311,31 +388,37 @@ void species_filter_group(const std::vector<Problem *> &ps_in, cudaStream_t s) {
     if (ps.empty()) return;
     for (Problem *p : ps) enumerate_basis(p, s);
     stage_tables_group<T>(ps, s);
-    // jobs: 3 lists per problem, their counts side by side in one array
+    // three lists per problem, their counts side by side in one array; one
+    // sweep per species list (one per problem when the species coincide)
     std::vector<FilterArgs<T>> jobs;
     std::vector<ConnList<T> *> lists;
+    std::vector<int> list_job, list_mode;
     std::vector<int64_t> cnt_off(1, 0);
     for (Problem *p : ps) {
         Connectivity<T> &c = p->conn<T>();
-        const int modes[3] = {CONN_OUTER, CONN_L2, CONN_L4};
+        const bool same = p->Z == p->N;
+        const int first = (int)jobs.size();
+        jobs.push_back(filter_job<T>(p, 0, same ? 7 : 1 << CONN_OUTER));
+        if (!same) jobs.push_back(filter_job<T>(p, 1, (1 << CONN_L2) | (1 << CONN_L4)));
         ConnList<T> *ls[3] = {&c.outer, &c.l2, &c.l4};
-        for (int i = 0; i < 3; ++i) {
-            jobs.push_back(filter_job<T>(p, i == 0 ? 0 : 1, modes[i]));
-            lists.push_back(ls[i]);
-            cnt_off.push_back(cnt_off.back() + jobs.back().n);
+        for (int m = 0; m < 3; ++m) {
+            lists.push_back(ls[m]);
+            list_job.push_back(m == 0 || same ? first : first + 1);
+            list_mode.push_back(m);
+            cnt_off.push_back(cnt_off.back() + (m == 0 ? p->sp[0].n : p->sp[1].n));
         }
     }
     const int64_t ncnt = cnt_off.back();
     DevBuf<int32_t> cnt((size_t)ncnt);
     auto offs = std::make_shared<DevBuf<int64_t>>((size_t)ncnt + 1);
-    for (size_t i = 0; i < jobs.size(); ++i) jobs[i].count = cnt.ptr + cnt_off[i];
+    for (size_t i = 0; i < lists.size(); ++i) jobs[list_job[i]].count[list_mode[i]] = cnt.ptr + cnt_off[i];
     filter_pass<T>(jobs, 0, s);
     exclusive_scan_i32(cnt.ptr, ncnt, offs->ptr, ps[0]->scan_scratch, s);
     // list boundaries: hb[i] = offs[cnt_off[i]]
     std::vector<int64_t> hb = gather_i64(offs->ptr, cnt_off, s);
     auto ents = std::make_shared<DevBuf<ConnEntry<T>>>((size_t)hb.back());
     auto tgts = std::make_shared<DevBuf<int32_t>>((size_t)hb.back());
-    for (size_t i = 0; i < jobs.size(); ++i) {
+    for (size_t i = 0; i < lists.size(); ++i) {
         ConnList<T> &L = *lists[i];
         L.ptr_buf = offs;
         L.ent_buf = ents;
@@ -343,14 +426,24 @@ void species_filter_group(const std::vector<Problem *> &ps_in, cudaStream_t s) {
         L.tgt = tgts->ptr;
         L.ptr = offs->ptr + cnt_off[i];
         L.ent = ents->ptr;
-        L.n = jobs[i].n;
+        L.n = cnt_off[i + 1] - cnt_off[i];
         L.first = hb[i];
         L.total = hb[i + 1] - hb[i];
-        jobs[i].ptr = L.ptr;
-        jobs[i].ent = L.ent;
-        jobs[i].tgt = tgts->ptr;
+        FilterArgs<T> &j = jobs[list_job[i]];
+        j.ptr[list_mode[i]] = L.ptr;
+        j.ent = L.ent;
+        j.tgt = tgts->ptr;
     }
     filter_pass<T>(jobs, 1, s);
+    std::vector<FilterArgs<T>> ej1, ej2;
+    for (size_t i = 0; i < lists.size(); ++i) {
+        FilterArgs<T> j = jobs[list_job[i]];
+        j.modes = 1 << list_mode[i];
+        j.n = lists[i]->n;
+        (j.W == 1 ? ej1 : ej2).push_back(j);
+    }
+    launch_entries<T, 1>(ej1, s);
+    launch_entries<T, 2>(ej2, s);
     // segment tables of the neutron lists
     std::vector<SegJob<T>> sj;
     std::vector<int64_t> soff(1, 0);

@@ -517,6 +517,7 @@ void enumerate_basis(Problem *p, cudaStream_t s) {
         L.d_twoM.upload(L.twoM, s);
         L.d_local.upload(L.local, s);
         L.d_occ.upload(L.occ, s);
+        L.d_blk_start.upload(L.blk_start, s);
     }
     p->d_p_row_base.upload(p->p_row_base, s);
     p->d_p_nstart.upload(p_nstart, s);

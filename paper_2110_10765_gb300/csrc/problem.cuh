@@ -25,6 +25,7 @@ struct SpeciesList {
     std::vector<int64_t> blk_qend;  // [nblk][nq] end of (q' <= q) inside the block
 
     DevBuf<uint64_t> d_bits;
+    DevBuf<int64_t> d_blk_start;
     DevBuf<int32_t> d_q, d_twoM, d_local;
     DevBuf<uint8_t> d_occ;
 
