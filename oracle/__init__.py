@@ -10,16 +10,17 @@ than itself):
 
 * ``ci_oracle.c`` (plain C, FP64): species determinant lists, product basis,
   difference counts, Slater-Condon matrix elements, rows / CSR of H, FP64
-  SpMM and the exclusive scan of Eq. 1;
+  SpMM, the exclusive scan of Eq. 1 and the per-state counts of the count
+  benchmark (Sec. 3.1);
 * ``brute.py`` (pure Python): H built by applying every second-quantised
   operator term to every basis state, for tiny spaces;
 * ``eig.py``: lowest eigenvalues by LAPACK (dense) or ARPACK (sparse), the
   plain definition of "lowest k eigenvalues".
 """
 
-from .core import OracleProblem, build_library, exclusive_scan, spmm
+from .core import OracleProblem, build_library, count_pairs, exclusive_scan, spmm
 from .eig import lowest_dense, lowest_sparse, dense_from_csr
 from . import brute
 
-__all__ = ["OracleProblem", "build_library", "exclusive_scan", "spmm",
+__all__ = ["OracleProblem", "build_library", "count_pairs", "exclusive_scan", "spmm",
            "lowest_dense", "lowest_sparse", "dense_from_csr", "brute"]

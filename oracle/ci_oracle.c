@@ -17,7 +17,10 @@
  *     Sec. 2.1), with the fermion phase found by applying the creation and
  *     annihilation operators one at a time to the ket's occupation list;
  *   - rows of H in ascending column order, visiting every column j as in the
- *     dense count of Listing 2, and the full CSR matrix.
+ *     dense count of Listing 2, and the full CSR matrix;
+ *   - the count benchmark of Sec. 3.1 (Listing 2 over independent random
+ *     states in MBS form): per state, the number of states that differ from
+ *     it in at most max_diff single-particle states.
  *
  * Hamiltonian:  H = sum_a eps_a a+_a a_a   (both species)
  *                 + 1/4 sum V^pp_abcd a+_a a+_b a_d a_c   (same for nn)
@@ -484,4 +487,34 @@ void orc_exclusive_scan(const int64_t *x, int64_t n, int64_t *y)
 {
     y[0] = 0;
     for (int64_t i = 0; i < n; ++i) y[i + 1] = y[i] + x[i];
+}
+
+/* Count benchmark (Sec. 3.1, Listing 2).  mbs holds n states of N
+ * particles, each the ascending list of its occupied s.p. states.  For each
+ * of the nrows states rows[r], out[r] = the number of states j (all n,
+ * j = rows[r] included) whose occupations differ from it in at most
+ * max_diff s.p. states, both sides counted (Sec. 2.1).  The difference of
+ * two states is found by walking both sorted lists, as in Listing 1. */
+static int diff_u16(const uint16_t *a, const uint16_t *b, int N)
+{
+    int i = 0, j = 0, d = 0;
+    while (i < N && j < N) {
+        if (a[i] < b[j]) { ++d; ++i; }
+        else if (a[i] > b[j]) { ++d; ++j; }
+        else { ++i; ++j; }
+    }
+    return d + (N - i) + (N - j);
+}
+
+void orc_count_pairs(const uint16_t *mbs, int64_t n, int N, int max_diff, const int64_t *rows, int64_t nrows,
+                     int64_t *out)
+{
+    #pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t r = 0; r < nrows; ++r) {
+        const uint16_t *a = mbs + rows[r] * N;
+        int64_t c = 0;
+        for (int64_t j = 0; j < n; ++j)
+            if (diff_u16(a, mbs + j * N, N) <= max_diff) ++c;
+        out[r] = c;
+    }
 }

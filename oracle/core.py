@@ -71,6 +71,8 @@ def _load():
             lib.orc_fill.argtypes = [P(_BasisView)] + [C.c_void_p] * 4
             lib.orc_spmm.argtypes = [C.c_int64] + [C.c_void_p] * 5 + [C.c_int]
             lib.orc_exclusive_scan.argtypes = [C.c_void_p, C.c_int64, C.c_void_p]
+            lib.orc_count_pairs.argtypes = [C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_void_p, C.c_int64,
+                                            C.c_void_p]
             _lib = lib
     return _lib
 
@@ -198,6 +200,19 @@ class OracleProblem:
         occ = self.species(s)["occ"]
         x = np.ascontiguousarray(occ[a]); y = np.ascontiguousarray(occ[b])
         return self.lib.orc_count_difference(_ptr(x), _ptr(y), occ.shape[1])
+
+
+def count_pairs(mbs, rows=None, max_diff=4):
+    """Count benchmark of Sec. 3.1 (Listing 2): for each state i in rows (all
+    states by default) the number of states j of mbs [n][N] (uint16,
+    ascending) that differ from it in at most max_diff s.p. states."""
+    lib = _load()
+    mbs = np.ascontiguousarray(mbs, dtype=np.uint16)
+    n, N = mbs.shape
+    rows = np.arange(n, dtype=np.int64) if rows is None else np.ascontiguousarray(rows, dtype=np.int64)
+    out = np.zeros(len(rows), np.int64)
+    lib.orc_count_pairs(_ptr(mbs), n, N, max_diff, _ptr(rows), len(rows), _ptr(out))
+    return out
 
 
 def exclusive_scan(x):

@@ -9,7 +9,8 @@ This module holds inputs only, none of the configuration-interaction method:
   generator so that any implementation of the same published recipe gets the
   same bits;
 * the workload presets (the shapes and sizes of the benchmark problems) and
-  the random draws of the batched and served problem mixes.
+  the random draws of the batched and served problem mixes;
+* the random states of the paper's nonzero-count benchmark (``e1``).
 
 Every function is deterministic in its seed.  Nothing here depends on numpy's
 own random streams.
@@ -20,10 +21,12 @@ from .tbme import (CH_PP, CH_NN, CH_PN, splitmix64_mix, tbme_gaussian,
                    tbme_tables, tbme_tables_zero)
 from .workloads import (PRESETS, Preset, preset, batch_candidates,
                         serve_requests)
+from .e1 import E1_RATIO, e1_states
 
 __all__ = [
     "ho_sp_table", "sp_energies",
     "CH_PP", "CH_NN", "CH_PN", "splitmix64_mix", "tbme_gaussian",
     "tbme_tables", "tbme_tables_zero",
     "PRESETS", "Preset", "preset", "batch_candidates", "serve_requests",
+    "E1_RATIO", "e1_states",
 ]

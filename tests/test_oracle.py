@@ -351,3 +351,40 @@ def test_sparse_lowest_matches_dense():
     X = np.random.default_rng(2).standard_normal((o.dim, 4))
     rq = np.einsum("ij,ij->j", X, H @ X) / np.einsum("ij,ij->j", X, X)
     assert np.all(rq >= wd[0] - 1e-9)
+
+
+# ---- count benchmark (Sec. 3.1, Listing 2) -------------------------------------
+
+def _all_subsets(S, N):
+    import itertools
+    return np.array(list(itertools.combinations(range(S), N)), np.uint16)
+
+
+@pytest.mark.parametrize("S,N,max_diff,expect", [
+    (10, 4, 4, 1 + 4 * 6 + 6 * 15),             # k <= 2 moved particles: sum C(N,k) C(S-N,k)
+    (10, 4, 6, 1 + 4 * 6 + 6 * 15 + 4 * 20),
+    (10, 4, 0, 1),
+    (9, 3, 4, 1 + 3 * 6 + 3 * 15)])
+def test_count_pairs_closed_form_all_subsets(S, N, max_diff, expect):
+    """Over every N-subset of S states, each state has sum_k C(N,k) C(S-N,k)
+    partners with at most k moved particles (2k differing states)."""
+    mbs = _all_subsets(S, N)
+    c = oracle.count_pairs(mbs, max_diff=max_diff)
+    assert np.all(c == expect)
+
+
+def test_count_pairs_brute_force_sets():
+    import synth
+    mbs = synth.e1_states(300, N=8, S=128, r=0.9, seed=5)   # denser than the benchmark
+    sets = [set(x.tolist()) for x in mbs]
+    ref = np.array([sum(len(a ^ b) <= 4 for b in sets) for a in sets])
+    assert ref.sum() > 2 * len(sets)          # the case has off-diagonal pairs
+    assert np.array_equal(oracle.count_pairs(mbs), ref)
+    rows = np.array([7, 0, 299, 7])
+    assert np.array_equal(oracle.count_pairs(mbs, rows=rows), ref[rows])
+
+
+def test_count_pairs_duplicates_and_singletons():
+    mbs = np.array([[0, 1, 2, 3], [0, 1, 2, 3], [0, 1, 2, 4], [10, 11, 12, 13]], np.uint16)
+    assert oracle.count_pairs(mbs).tolist() == [3, 3, 3, 1]
+    assert oracle.count_pairs(mbs[:0]).tolist() == []
