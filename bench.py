@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--batch-n", type=int, default=256)
     ap.add_argument("--fp64-sample", type=int, default=12, help="problems solved one by one in FP64")
+    ap.add_argument("--no-count", action="store_true", help="skip the count-benchmark leg")
+    ap.add_argument("--count-n", type=int, default=131072, help="states of the count benchmark")
     return ap.parse_args()
 
 
@@ -307,6 +309,8 @@ def run_ours(args):
         h2d = sum(v.numel() * v.element_size() for v in host.values()) + 3 * 4 * len(sp["N"]) + 8 * len(sp["N"])
         rec["e2e"] = {"value": nnz * args.steps * world / e2e_s, "unit": "nnz/s", "h2d_bytes_per_step": int(h2d),
                       "d2h_bytes_per_step": int(8 * p.k + 8), "ms_per_step": e2e_s / args.steps * 1e3}
+    if not args.no_count:
+        rec["count"] = run_count_leg(args.count_n, clock_mhz=(clk or {}).get("sm_mhz"))
     if not args.no_batch:
         rec["batch"], pool = run_batch_leg(args)
         if not args.no_serve:
@@ -319,6 +323,54 @@ def run_ours(args):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(rec))
+
+
+# ---------------------------------------------------------------- count benchmark
+
+# 32-bit population counts per clock per SM (CUDA arithmetic-throughput
+# table) and the GB300's SM count: the ALU roofline of the count kernels,
+# whose pairs cost two 32-bit popcounts (64-bit prefilter) or four (128 bits).
+POPC_PER_CLK_SM = 16
+SMS = 152
+
+
+def run_count_leg(n, N=8, S=128, reps=5, clock_mhz=None):
+    """The paper's nonzero-count benchmark (Sec. 3.1, Figs. 3-4): n random
+    8-particle states over 128 s.p. states biased to low states; rate =
+    n^2 / time for the three forms of the pair test."""
+    import numpy as np
+    import torch
+
+    import synth
+    import paper_2110_10765_gb300 as ci
+    mbs = synth.e1_states(n, N=N, S=S, seed=1)
+    d = torch.from_numpy(mbs.view(np.int16)).cuda()
+    stream = torch.cuda.current_stream()
+    out = {"n": n, "N": N, "S": S, "bias_ratio": synth.E1_RATIO, "variants": {}}
+    for v in ("hybrid", "bits", "mbs"):
+        r = reps if v != "mbs" else 2
+        total = ci.count_pairs(d, S, v)
+        ms = []
+        for _ in range(r):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            total = ci.count_pairs(d, S, v)
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        t = statistics.median(ms)
+        out["variants"][v] = {"ms": t, "pairs_per_s": n * n / (t * 1e-3), "total": total}
+    tot = out["variants"]["hybrid"]["total"]
+    out["density_offdiag"] = (tot - n) / (n * n - n)
+    out["forms_agree"] = len({x["total"] for x in out["variants"].values()}) == 1
+    f = (clock_mhz or 2070.0) * 1e6
+    peak = POPC_PER_CLK_SM * SMS * f / 2          # hybrid: two 32-bit popcounts per pair
+    ach = out["variants"]["hybrid"]["pairs_per_s"]
+    out["roofline"] = {"kernel": "k_count_hybrid", "bound": "alu", "achieved": ach, "peak": peak,
+                       "unit": "pairs/s", "frac": ach / peak,
+                       "peak_basis": "%d popc/clk/SM x %d SMs x %.0f MHz / 2 popc per pair" % (
+                           POPC_PER_CLK_SM, SMS, f / 1e6)}
+    return out
 
 
 # ---------------------------------------------------------------- batched solves

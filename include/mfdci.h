@@ -178,6 +178,31 @@ ci_status ci_get_species_conn(const ci_problem *p, int32_t species, int64_t *ptr
  * total; row_cnt (nullable, host or device, int32 [dim]) the per-row counts. */
 ci_status ci_count_nnz(ci_problem *p, int64_t *nnz, int32_t *row_cnt, void *stream);
 
+/* ---- Nonzero-count benchmark (Sec. 3.1, Listings 1-2, Figs. 3-4) ------- */
+
+/* Forms of the pair test of ci_count_pairs; all give the same counts. */
+typedef enum {
+    CI_COUNT_HYBRID = 0,  /* popcount over the lowest 64 s.p. states, then the
+                             MBS comparison for pairs that pass (Listing 2) */
+    CI_COUNT_MBS = 1,     /* MBS comparison for every pair (no prefilter) */
+    CI_COUNT_BITS = 2     /* full bit representation, popcount only; S <= 128 */
+} ci_count_variant;
+
+/* For n independent N-particle states, the number of states j (all n,
+ * j = i included) whose occupations differ from state i in at most
+ * max_diff single-particle states, both sides counted (Sec. 2.1: 2d = 4 for
+ * a two-body operator, 6 for three-body).
+ *   mbs         device, uint16 [n][N]: each state's occupied s.p. indices,
+ *               strictly ascending, all < S (the MBS form of Sec. 2.1).
+ *               Other inputs give unspecified counts but no fault.
+ *   N           1..32; S: N..65535 (<= 128 for CI_COUNT_BITS).
+ *   total       host int64: sum of the counts (the stream is synchronised).
+ *   row_counts  device int64 [n] or NULL: the per-state counts.
+ * Errors: CI_ERR_INVALID_ARG for bad sizes, host pointers or an unknown
+ * variant; CI_ERR_CAPACITY when the launch grid would be too large. */
+ci_status ci_count_pairs(const uint16_t *mbs, int64_t n, int32_t N, int32_t S, int32_t variant,
+                         int32_t max_diff, int64_t *total, int64_t *row_counts, void *stream);
+
 /* Eq. 1 / Alg. 1 (Sec. 2.2): exclusive prefix sum of n int32 counts into
  * n+1 int64 offsets, offsets[0] = 0 and offsets[n] = total.  counts and
  * offsets are device pointers; n >= 0 (n = 0 writes offsets[0] = 0).

@@ -18,7 +18,7 @@ from . import _lib
 from ._lib import (CIError, CI_F32, CI_F64, CI_BF16_ROWSCALE, CI_TBME_TABLES,
                    CI_TBME_SEED, check, lib)
 
-__all__ = ["Problem", "Matrix", "Batch", "Queue", "exclusive_scan", "trace_enable", "trace_read", "CIError", "CI_F32", "CI_F64",
+__all__ = ["Problem", "Matrix", "Batch", "Queue", "exclusive_scan", "count_pairs", "COUNT_VARIANTS", "trace_enable", "trace_read", "CIError", "CI_F32", "CI_F64",
            "CI_BF16_ROWSCALE", "VTYPES", "lib", "current_stream"]
 
 VTYPES = {"f32": CI_F32, "f64": CI_F64, "bf16": CI_BF16_ROWSCALE}
@@ -343,6 +343,23 @@ def trace_read(reset=True):
     buf = (_lib.TraceEntry * max(n.value, 1))()
     check(lib().ci_trace_read(buf, n.value, C.byref(n), 1 if reset else 0), "ci_trace_read")
     return {buf[i].name.decode(): (buf[i].launches, buf[i].total_ms) for i in range(n.value)}
+
+
+COUNT_VARIANTS = {"hybrid": 0, "mbs": 1, "bits": 2}
+
+
+def count_pairs(mbs, S, variant="hybrid", max_diff=4, row_counts=None, stream=None):
+    """Count benchmark of Sec. 3.1 (Listing 2) on the device.
+
+    mbs: device uint16-compatible tensor [n, N] (torch.int16 / uint16 bits),
+    each row the ascending occupied s.p. states of one state.  Returns the
+    total number of pairs within max_diff differing states; row_counts
+    (device int64 [n]) receives the per-state counts."""
+    n, N = (int(mbs.shape[0]), int(mbs.shape[1])) if mbs.dim() == 2 else (0, 1)
+    total = C.c_int64()
+    check(lib().ci_count_pairs(_ptr(mbs), n, N, int(S), COUNT_VARIANTS.get(variant, variant), int(max_diff),
+                               C.byref(total), _ptr(row_counts), _stream(stream)), "ci_count_pairs")
+    return total.value
 
 
 def exclusive_scan(counts, offsets, stream=None):

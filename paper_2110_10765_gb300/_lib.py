@@ -86,6 +86,8 @@ _SIGS = {
     "ci_count_nnz": (C.c_int, [_P, _I64P, _P, _P]),
     "ci_exclusive_scan": (C.c_int, [_P, C.c_int64, _P, _P]),
     "ci_exclusive_scan_noalloc": (C.c_int, [_P, C.c_int64, _P, _P]),
+    "ci_count_pairs": (C.c_int, [_P, C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                                 C.POINTER(C.c_int64), _P, _P]),
     "ci_build_H": (C.c_int, [_P, C.c_int32, C.POINTER(_P), _P]),
     "ci_matrix_destroy": (None, [_P]),
     "ci_matrix_info": (C.c_int, [_P, _I64P, _I64P, C.POINTER(C.c_int32)]),
