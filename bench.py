@@ -63,6 +63,23 @@ def dist_info():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
+def max_over_ranks(x, world, device=None):
+    """The largest value of x over all ranks (all_reduce MAX); x for one rank.
+    Ranks are independent replicas: this is the only exchange of a run."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, max_ms):
+    """Units processed by all ranks per second of the slowest rank's time."""
+    return units_per_rank * world / (max_ms * 1e-3)
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -218,11 +235,7 @@ def run_ours(args):
     build_ms = [ev_s[i].elapsed_time(ev_b[i]) for i in range(args.steps)]
     solve_ms = [ev_b[i].elapsed_time(ev_e[i]) for i in range(args.steps)]
     total_ms = sum(step_ms)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, world, dev)
 
     # ---- standalone SpMM (Y = H X, 8 vectors): fraction of the HBM roofline
     prob = ci.Problem(sp, p.Z, p.N, p.nmax, p.twoM, eps, tables=dtab)
@@ -275,7 +288,7 @@ def run_ours(args):
                    "parallelism": "replicas" if world > 1 else "single GPU"},
     }
     per_rank_nnz = nnz * args.steps
-    rec["value"] = per_rank_nnz * world / (total_ms * 1e-3)
+    rec["value"] = whole_job_rate(per_rank_nnz, world, total_ms)
     rec["ms_per_step"] = total_ms / args.steps
     rec["phases_ms"] = {"build_median": statistics.median(build_ms), "solve_median": statistics.median(solve_ms),
                         "step_median": statistics.median(step_ms), "wall_total_s": t_wall}
@@ -314,7 +327,7 @@ def run_ours(args):
     if not args.no_batch:
         rec["batch"], pool = run_batch_leg(args)
         if not args.no_serve:
-            rec["serve"] = run_serve_leg(rec["batch"]["solves_per_s"], pool)
+            rec["serve"] = run_serve_leg(pool)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rec["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     if world > 1:
@@ -444,16 +457,11 @@ def run_batch_leg(args):
         [c for c, _, _ in items]
 
 
-def run_serve_leg(capacity, pool, n_requests=400, seed=4):
-    """Poisson arrivals at 80 % of the batched capacity, drawn from the batched
-    mix plus 5 % requests of the benchmark size (4p+4n, N<=4, Nmax=4), each
-    with its own TBME seed and 1..10 wanted eigenvalues."""
-    import numpy as np
-
+def _serve(reqs, paced):
+    """Submit reqs to a fresh queue (at their arrival times when paced, all
+    at once otherwise) and wait for every result."""
     import synth
     import paper_2110_10765_gb300 as ci
-    rate = 0.8 * capacity
-    reqs = synth.serve_requests(rate, n_requests, seed=seed, small_pool=pool)
     sps = {n: synth.ho_sp_table(n) for n in (3, 4)}
     epss = {n: synth.sp_energies(sps[n], 20.0) for n in (3, 4)}
     q = ci.Queue(mem_budget=96 << 30, max_slots=256)
@@ -461,7 +469,7 @@ def run_serve_leg(capacity, pool, n_requests=400, seed=4):
     tickets = []
     for r in reqs:
         dt = t0 + r["t_arrival"] - time.perf_counter()
-        if dt > 0:
+        if paced and dt > 0:
             time.sleep(dt)
         n = r["n_shell_max"]
         tickets.append(q.submit(sps[n], r["Z"], r["N"], r["nmax"], (r["Z"] + r["N"]) % 2, epss[n], r["k"],
@@ -477,10 +485,29 @@ def run_serve_leg(capacity, pool, n_requests=400, seed=4):
     stats = q.stats()
     q.close()
     ok = [res for st, res in results.values() if st == 0]
-    lat = np.array([res["latency_s"] for res in ok]) * 1e3
     span = max(res["t_done"] for _, res in results.values()) - min(res["t_submit"] for _, res in results.values())
+    return ok, span, stats
+
+
+def run_serve_leg(pool, n_requests=400, n_capacity=300, seed=4):
+    """Continuous-batching solve queue.  Its capacity is measured first
+    (n_capacity requests submitted at once, completions per second); then
+    Poisson arrivals at 80 % of that rate, drawn from the batched mix plus
+    5 % requests of the benchmark size (4p+4n, N<=4, Nmax=4), each with its
+    own TBME seed and 1..10 wanted eigenvalues."""
+    import numpy as np
+
+    import synth
+    cap_reqs = synth.serve_requests(1.0, n_capacity, seed=seed + 100, small_pool=pool)
+    ok_c, span_c, _ = _serve(cap_reqs, paced=False)
+    capacity = len(ok_c) / span_c
+    rate = 0.8 * capacity
+    reqs = synth.serve_requests(rate, n_requests, seed=seed, small_pool=pool)
+    ok, span, stats = _serve(reqs, paced=True)
+    lat = np.array([res["latency_s"] for res in ok]) * 1e3
     big = [res["latency_s"] * 1e3 for res in ok if res["dim"] > 100000]
     return {"requests": len(reqs), "completed_ok": len(ok), "failed": len(reqs) - len(ok),
+            "capacity_per_s": capacity, "capacity_requests": n_capacity,
             "offered_rate_per_s": rate, "solves_per_s": len(ok) / span, "span_s": span,
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                            "mean": float(lat.mean()), "max": float(lat.max())},

@@ -1,12 +1,18 @@
 // Count -> scan -> fill of the Hamiltonian rows (Fig. 1 lines 6-14,
 // Sec. 2.2-2.3).  One warp owns one row (p, n).  The row's partners are
-// the proton connectivity list of p (ascending p') crossed with segments of
-// the neutron lists of n: for p' two states away, the L2(n) entries in the
-// 2M block that pairs with p' and within the Nmax cut; for p' = p, the
-// L4(n) entries; for p' four states away, n itself.  Columns therefore come
-// out ascending without sorting, and every lane writes its own slot of a
-// coalesced run (the deterministic counterpart of Listing 7's atomic
-// capture).
+// the proton partners p' of p (ascending) crossed with segments of the
+// neutron lists of n: for p' two states away (list O2), the L2(n) entries
+// in the 2M block that pairs with p' and within the Nmax cut; for p' = p,
+// the L4(n) entries; for p' four states away (list O4, same 2M), n itself.
+// Only partners that can still meet a neutron partner under the cut are
+// visited: per 2M slot of O2 the q-prefix up to Nmax - (smallest q of the
+// matching L2 slot), and the q-prefix of O4 up to Nmax - q(n).  The O4
+// partners interleave with the same-2M slot of O2 by column.  Columns
+// therefore come out ascending without sorting, and every lane writes its
+// own slot of a coalesced run (the deterministic counterpart of Listing 7's
+// atomic capture).
+#include <climits>
+
 #include "problem.cuh"
 
 namespace ci {
@@ -19,9 +25,10 @@ struct RowArgs {
     const int64_t *p_row_base;
     const int32_t *p_q, *p_twoM, *n_q, *n_twoM, *n_local;
     const uint64_t *p_bits, *n_bits;
-    const int64_t *o_ptr, *l2_ptr, *l4_ptr;
-    const ConnEntry<T> *o_ent, *l2_ent, *l4_ent;
-    const int32_t *seg2, *seg4;
+    const int64_t *o_ptr, *o4_ptr, *l2_ptr, *l4_ptr;
+    const ConnEntry<T> *o_ent, *o4_ent, *l2_ent, *l4_ent;
+    const int32_t *o_xr;       // cross ranks of the same-2M proton entries (O2 <-> O4)
+    const int32_t *seg2, *seg4, *qmin2, *oseg2, *oseg4;
     const T *Upn, *Wpn, *Dpn, *Tpn;
     int32_t *row_cnt;          // count pass
     const int64_t *row_ptr;    // fill pass
@@ -83,6 +90,60 @@ __device__ __forceinline__ int group_of(const int64_t *row_off, int G, int64_t g
     return lo;
 }
 
+// Admissible O2 partners of row (p, n) in 2M slots [g_lo, g_hi), ascending,
+// 32 at a time: body(e, valid) with e the lane's entry of the O2 list.
+// Warp-uniform calls.
+template <class T, class F>
+__device__ __forceinline__ void for_o2(const RowArgs<T> &a, int p, int n, int g_lo, int g_hi, F &&body) {
+    const int lane = threadIdx.x & 31;
+    const int64_t e0 = a.o_ptr[p];
+    const int32_t *os = a.oseg2 + (int64_t)p * a.nds * a.nq;
+    const int32_t *qm = a.qmin2 + (int64_t)n * a.nds;
+    for (int g0 = g_lo; g0 < g_hi; g0 += 32) {
+        const int g = g0 + lane;
+        int gb = 0, gl = 0;
+        if (g < g_hi) {
+            gb = g == 0 ? 0 : os[(g - 1) * a.nq + a.nq - 1];
+            int ge;
+            if (a.nmax < 0) {
+                ge = os[g * a.nq + a.nq - 1];
+            } else {
+                // partners p' of slot g meet the L2(n) slot 2K - g; they need
+                // q(p') <= Nmax - (smallest q there)
+                int c = a.nmax - qm[2 * a.K - g];
+                if (c > a.nq - 1) c = a.nq - 1;
+                ge = c < 0 ? gb : os[g * a.nq + c];
+            }
+            gl = ge > gb ? ge - gb : 0;
+        }
+        const int incl = warp_incl_scan_i32(gl);
+        const int excl = incl - gl;
+        const int tot = __shfl_sync(0xffffffffu, incl, 31);
+        for (int t0 = 0; t0 < tot; t0 += 32) {
+            const int t = t0 + lane;
+            int j = 0;  // last slot starting at or before t
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const int v = __shfl_sync(0xffffffffu, excl, j + step);
+                if (v <= t) j += step;
+            }
+            const int64_t e = e0 + __shfl_sync(0xffffffffu, gb, j) + (t - __shfl_sync(0xffffffffu, excl, j));
+            body(e, t < tot);
+        }
+    }
+}
+
+// Admissible O4 partners of row (p, n): the q-prefix up to Nmax - q(n).
+template <class T>
+__device__ __forceinline__ int o4_count(const RowArgs<T> &a, int p, int n) {
+    const int64_t b = a.o4_ptr[p];
+    if (a.nmax < 0) return (int)(a.o4_ptr[p + 1] - b);
+    int c = a.nmax - a.n_q[n];
+    if (c < 0) return 0;
+    if (c > a.nq - 1) c = a.nq - 1;
+    return a.oseg4[(int64_t)p * a.nq + c];
+}
+
 template <class T>
 __global__ void __launch_bounds__(256) k_count_rows(const RowArgs<T> *args, const int64_t *row_off, int G) {
     const int lane = threadIdx.x & 31;
@@ -94,16 +155,17 @@ __global__ void __launch_bounds__(256) k_count_rows(const RowArgs<T> *args, cons
         const RowArgs<T> &a = args[g];
         const int64_t r = gr - row_off[g];
         const int p = a.row_p[r], n = a.row_n[r];
-        const int64_t e0 = a.o_ptr[p], e1 = a.o_ptr[p + 1];
         int cnt = 0;
-        for (int64_t e = e0 + lane; e < e1; e += 32) {
-            int kind, beg, len;
-            partner_segment<T>(a, p, n, a.o_ent[e], kind, beg, len);
-            cnt += len;
-        }
+        for_o2<T>(a, p, n, 0, a.nds, [&](int64_t e, bool ok) {
+            if (ok) {
+                int kind, beg, len;
+                partner_segment<T>(a, p, n, a.o_ent[e], kind, beg, len);
+                cnt += len;
+            }
+        });
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-        if (lane == 0) a.row_cnt[r] = cnt;
+        if (lane == 0) a.row_cnt[r] = cnt + o4_count<T>(a, p, n);
     }
 }
 
@@ -116,13 +178,139 @@ __device__ __forceinline__ T sum_over_bits(const T *tab, uint64_t w0, uint64_t w
     return s;
 }
 
-// Fill one row per warp.  The proton partners are taken 32 at a time; a
-// warp scan of their segment lengths gives every partner its output slot,
-// then three phases write the elements without sorting:
-//   0. four protons moved: one element (n' = n) per partner, by its lane;
+// Row context of the fill.
+struct RowCtx {
+    int p, n, n_local;
+    int64_t l2b, l4b;
+    uint64_t pb0, pb1, nb0, nb1;
+};
+
+// One chunk of up to 32 O2 partners (one per lane: entry ep, segment kind,
+// beg, len; extra = elements of other partners placed before this one's
+// segment).  The lane's segment goes to out + (exclusive scan of len) +
+// extra, written in three phases without sorting:
+//   0. four protons moved: one element (n' = n), by its lane;
 //   1. one proton moved: the segments of L2(n) are expanded with the warp's
 //      lanes balanced over the elements (a search over segment starts);
 //   2. p' = p: the warp walks the row's L4(n) segment contiguously.
+// Returns the chunk's element count.
+template <class T>
+__device__ __forceinline__ int fill_chunk(const RowArgs<T> &a, const RowCtx &x, const ConnEntry<T> &ep, int kind,
+                                          int beg, int len, int extra, int64_t out) {
+    const int lane = threadIdx.x & 31;
+    const int S = a.S;
+    const int incl = warp_incl_scan_i32(len);
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    const int64_t pos = out + (incl - len) + extra;
+    const int colbase = ep.tgt;   // first basis row of the proton partner
+    // 0. four protons moved: the neutrons stay, one element
+    if (kind == 0 && len == 1) {
+        a.col[pos] = colbase + x.n_local;
+        a.val[pos] = ep.val;
+    }
+    // 1. one proton moved (a -> c): L2(n)[beg, beg+len)
+    const int len1 = kind == 1 ? len : 0;
+    const int incl1 = warp_incl_scan_i32(len1);
+    const int excl1 = incl1 - len1;
+    const int total1 = __shfl_sync(0xffffffffu, incl1, 31);
+    // two elements per lane and pass: both dependent load chains (entry,
+    // then table) are in flight together
+    for (int t0 = 0; t0 < total1; t0 += 64) {
+        int jj[2], kk[2];
+        ConnEntry<T> en[2];
+        bool live[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int t = t0 + 32 * h + lane;
+            int j = 0;  // last lane whose kind-1 segment starts at or before t
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const int v = __shfl_sync(0xffffffffu, excl1, j + step);
+                if (v <= t) j += step;
+            }
+            jj[h] = j;
+            kk[h] = t - __shfl_sync(0xffffffffu, excl1, j);
+            live[h] = t < total1;
+            const int jbeg = __shfl_sync(0xffffffffu, beg, j);
+            if (live[h]) en[h] = a.l2_ent[x.l2b + jbeg + kk[h]];
+        }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int j = jj[h];
+            const int64_t jpos = __shfl_sync(0xffffffffu, pos, j);
+            const int jcol = __shfl_sync(0xffffffffu, colbase, j);
+            const int jtb = __shfl_sync(0xffffffffu, ep.local, j);
+            const uint32_t pinfo = __shfl_sync(0xffffffffu, ep.info, j);
+            const T pval = __shfl_sync(0xffffffffu, ep.val, j);
+            if (live[h]) {
+                T v;
+                if (info_dcode(en[h].info) != 0) {   // (2,2): V^pn_{c_p c_n, a_p a_n}
+                    const T w = a.Tpn[jtb + info_tcol(en[h].info)];
+                    v = (info_neg(pinfo) ^ info_neg(en[h].info)) ? -w : w;
+                } else {                             // (2,0): neutrons are spectators
+                    const T *u = a.Upn + ((int64_t)info_c(pinfo) * S + info_a(pinfo)) * S;
+                    const T hv = pval + sum_over_bits<T>(u, x.nb0, x.nb1);
+                    v = info_neg(pinfo) ? -hv : hv;
+                }
+                a.col[jpos + kk[h]] = jcol + en[h].local;
+                a.val[jpos + kk[h]] = v;
+            }
+        }
+    }
+    // 2. p' = p: every same-2M neutron partner of n, L4(n)[0, len)
+    const unsigned b2 = __ballot_sync(0xffffffffu, kind == 2 && len > 0);
+    if (b2) {
+        const int src = __ffs(b2) - 1;
+        const int len2 = __shfl_sync(0xffffffffu, len, src);
+        const int64_t pos2 = __shfl_sync(0xffffffffu, pos, src);
+        const int col2 = __shfl_sync(0xffffffffu, colbase, src);
+        const T pval2 = __shfl_sync(0xffffffffu, ep.val, src);
+        for (int k = lane; k < len2; k += 32) {
+            const ConnEntry<T> en = a.l4_ent[x.l4b + k];
+            const int dn = info_dcode(en.info);
+            T v;
+            if (dn == 2) {                    // (0,4)
+                v = en.val;
+            } else if (dn == 1) {             // (0,2): protons are spectators
+                const T *w = a.Wpn + ((int64_t)info_c(en.info) * S + info_a(en.info)) * S;
+                const T h = en.val + sum_over_bits<T>(w, x.pb0, x.pb1);
+                v = info_neg(en.info) ? -h : h;
+            } else {                          // diagonal
+                T h = pval2 + en.val;
+                uint64_t x0 = x.pb0, x1 = x.pb1;
+                while (x0 | x1) {
+                    int kp;
+                    if (x0) { kp = __ffsll((long long)x0) - 1; x0 &= x0 - 1; }
+                    else { kp = 64 + __ffsll((long long)x1) - 1; x1 &= x1 - 1; }
+                    h += sum_over_bits<T>(a.Dpn + (int64_t)kp * S, x.nb0, x.nb1);
+                }
+                v = h;
+            }
+            a.col[pos2 + k] = col2 + en.local;
+            a.val[pos2 + k] = v;
+        }
+    }
+    return total;
+}
+
+template <class T>
+__device__ __forceinline__ void load_partner(const RowArgs<T> &a, const RowCtx &x, int64_t e, bool ok,
+                                             ConnEntry<T> &ep, int &kind, int &beg, int &len) {
+    if (ok) {
+        ep = a.o_ent[e];
+        partner_segment<T>(a, x.p, x.n, ep, kind, beg, len);
+    } else {
+        ep.tgt = 0; ep.local = 0; ep.info = 0; ep.val = 0;
+        kind = 0; beg = 0; len = 0;
+    }
+}
+
+// Fill one row per warp.  One pass over the admissible O2 partners places
+// their segments: a partner of 2M slot 0 is preceded by the admissible O4
+// partners with a smaller index (its cross rank, capped at their number
+// m4), a partner of a higher slot by all m4 of them.  Then the O4 partners
+// (one element each) go between, after as many slot-0 O2 elements as their
+// own cross rank says.
 template <class T>
 __global__ void __launch_bounds__(256) k_fill_rows(const RowArgs<T> *args, const int64_t *row_off, int G) {
     const int lane = threadIdx.x & 31;
@@ -132,102 +320,72 @@ __global__ void __launch_bounds__(256) k_fill_rows(const RowArgs<T> *args, const
     for (int64_t gr = warp; gr < rows; gr += nwarps) {
         const int g = group_of(row_off, G, gr);
         const RowArgs<T> &a = args[g];
-        const int S = a.S;
         const int64_t r = gr - row_off[g];
-        const int p = a.row_p[r], n = a.row_n[r];
-        const uint64_t pb0 = a.p_bits[(int64_t)p * a.W], pb1 = a.W > 1 ? a.p_bits[(int64_t)p * a.W + 1] : 0;
-        const uint64_t nb0 = a.n_bits[(int64_t)n * a.W], nb1 = a.W > 1 ? a.n_bits[(int64_t)n * a.W + 1] : 0;
-        const int n_local = a.n_local[n];
-        const int64_t l2b = a.l2_ptr[n], l4b = a.l4_ptr[n];
-        const int64_t e0 = a.o_ptr[p], e1 = a.o_ptr[p + 1];
-        int64_t out = a.row_ptr[r];
-        for (int64_t c0 = e0; c0 < e1; c0 += 32) {
+        RowCtx x;
+        x.p = a.row_p[r];
+        x.n = a.row_n[r];
+        const int p = x.p, n = x.n;
+        x.pb0 = a.p_bits[(int64_t)p * a.W]; x.pb1 = a.W > 1 ? a.p_bits[(int64_t)p * a.W + 1] : 0;
+        x.nb0 = a.n_bits[(int64_t)n * a.W]; x.nb1 = a.W > 1 ? a.n_bits[(int64_t)n * a.W + 1] : 0;
+        x.n_local = a.n_local[n];
+        x.l2b = a.l2_ptr[n];
+        x.l4b = a.l4_ptr[n];
+        const int m4 = o4_count<T>(a, p, n);
+        const int64_t row0 = a.row_ptr[r];
+        int64_t out = row0;       // O2 elements placed so far (O4 ones not counted)
+        int below = 0;            // O2 elements of the slots below p's own
+        int m2 = 0;               // admissible O2 partners of p's own slot
+        for_o2<T>(a, p, n, 0, a.nds, [&](int64_t e, bool ok) {
             ConnEntry<T> ep;
-            int kind = 0, beg = 0, len = 0;
-            if (c0 + lane < e1) {
-                ep = a.o_ent[c0 + lane];
-                partner_segment<T>(a, p, n, ep, kind, beg, len);
-            } else {
-                ep.tgt = 0; ep.local = 0; ep.info = 0; ep.val = 0;
-            }
-            const int incl = warp_incl_scan_i32(len);
-            const int total = __shfl_sync(0xffffffffu, incl, 31);
-            const int64_t pos = out + (incl - len);
-            const int colbase = ep.tgt;   // first basis row of the proton partner
-            // 0. four protons moved: the neutrons stay, one element
-            if (kind == 0 && len == 1) {
-                a.col[pos] = colbase + n_local;
-                a.val[pos] = ep.val;
-            }
-            // 1. one proton moved (a -> c): L2(n)[beg, beg+len)
-            const int len1 = kind == 1 ? len : 0;
-            const int incl1 = warp_incl_scan_i32(len1);
-            const int excl1 = incl1 - len1;
-            const int total1 = __shfl_sync(0xffffffffu, incl1, 31);
-            for (int t0 = 0; t0 < total1; t0 += 32) {
-                const int t = t0 + lane;
-                int j = 0;  // last lane whose kind-1 segment starts at or before t
+            int kind, beg, len;
+            load_partner<T>(a, x, e, ok, ep, kind, beg, len);
+            const int ds = ok ? info_dslot(ep.info) : -1;
+            const int extra = ds > 0 ? m4 : (ds == 0 ? min(a.o_xr[e], m4) : 0);
+            unsigned lo_mask = __ballot_sync(0xffffffffu, ok && ds < 0);
+            int bl = (lo_mask >> lane) & 1 ? len : 0;
 #pragma unroll
-                for (int step = 16; step > 0; step >>= 1) {
-                    const int v = __shfl_sync(0xffffffffu, excl1, j + step);
-                    if (v <= t) j += step;
+            for (int o = 16; o > 0; o >>= 1) bl += __shfl_xor_sync(0xffffffffu, bl, o);
+            below += bl;
+            m2 += __popc(__ballot_sync(0xffffffffu, ok && ds == 0));
+            out += fill_chunk<T>(a, x, ep, kind, beg, len, extra, out);
+        });
+        if (m4 > 0) {
+            // slot-0 O2 partners: the admissible ones are the first m2 of the
+            // slot; the slot starts at entry s0
+            const int64_t s0 = a.o_ptr[p] + (a.K == 0 ? 0 : a.oseg2[((int64_t)p * a.nds + a.K - 1) * a.nq + a.nq - 1]);
+            const int64_t o4b = a.o4_ptr[p];
+            for (int k0 = 0; k0 < m4; k0 += 32) {
+                const int k = k0 + lane;
+                const bool ok = k < m4;
+                ConnEntry<T> e4;
+                int lim = 0;          // slot-0 O2 partners before this O4 partner
+                if (ok) {
+                    e4 = a.o4_ent[o4b + k];
+                    lim = min(a.o_xr[o4b + k], m2);
+                } else {
+                    e4.tgt = 0; e4.local = 0; e4.info = 0; e4.val = 0;
                 }
-                const int k = t - __shfl_sync(0xffffffffu, excl1, j);
-                const int64_t jpos = __shfl_sync(0xffffffffu, pos, j);
-                const int jcol = __shfl_sync(0xffffffffu, colbase, j);
-                const int jtb = __shfl_sync(0xffffffffu, ep.local, j);
-                const uint32_t pinfo = __shfl_sync(0xffffffffu, ep.info, j);
-                const T pval = __shfl_sync(0xffffffffu, ep.val, j);
-                const int jbeg = __shfl_sync(0xffffffffu, beg, j);
-                if (t < total1) {
-                    const ConnEntry<T> en = a.l2_ent[l2b + jbeg + k];
-                    T v;
-                    if (info_dcode(en.info) != 0) {   // (2,2): V^pn_{c_p c_n, a_p a_n}
-                        const T w = a.Tpn[jtb + info_tcol(en.info)];
-                        v = (info_neg(pinfo) ^ info_neg(en.info)) ? -w : w;
-                    } else {                          // (2,0): neutrons are spectators
-                        const T *u = a.Upn + ((int64_t)info_c(pinfo) * S + info_a(pinfo)) * S;
-                        const T h = pval + sum_over_bits<T>(u, nb0, nb1);
-                        v = info_neg(pinfo) ? -h : h;
+                int lensum = 0;
+                for (int i0 = 0; i0 < m2; i0 += 32) {
+                    const int i = i0 + lane;
+                    int len = 0;
+                    if (i < m2) {
+                        ConnEntry<T> ep = a.o_ent[s0 + i];
+                        int kind, beg;
+                        partner_segment<T>(a, p, n, ep, kind, beg, len);
                     }
-                    a.col[jpos + k] = jcol + en.local;
-                    a.val[jpos + k] = v;
+                    const int incl = warp_incl_scan_i32(len);
+                    const int tot = __shfl_sync(0xffffffffu, incl, 31);
+                    const int idx = min(max(lim - i0, 0), 32);   // this chunk's partners before k
+                    const int part = __shfl_sync(0xffffffffu, incl, idx > 0 ? idx - 1 : 0);
+                    lensum += idx >= 32 ? tot : (idx > 0 ? part : 0);
+                }
+                if (ok) {
+                    const int64_t pos = row0 + below + k + lensum;
+                    a.col[pos] = e4.tgt + x.n_local;
+                    a.val[pos] = e4.val;
                 }
             }
-            // 2. p' = p: every same-2M neutron partner of n, L4(n)[0, len)
-            const unsigned b2 = __ballot_sync(0xffffffffu, kind == 2 && len > 0);
-            if (b2) {
-                const int src = __ffs(b2) - 1;
-                const int len2 = __shfl_sync(0xffffffffu, len, src);
-                const int64_t pos2 = __shfl_sync(0xffffffffu, pos, src);
-                const int col2 = __shfl_sync(0xffffffffu, colbase, src);
-                const T pval2 = __shfl_sync(0xffffffffu, ep.val, src);
-                for (int k = lane; k < len2; k += 32) {
-                    const ConnEntry<T> en = a.l4_ent[l4b + k];
-                    const int dn = info_dcode(en.info);
-                    T v;
-                    if (dn == 2) {                    // (0,4)
-                        v = en.val;
-                    } else if (dn == 1) {             // (0,2): protons are spectators
-                        const T *w = a.Wpn + ((int64_t)info_c(en.info) * S + info_a(en.info)) * S;
-                        const T h = en.val + sum_over_bits<T>(w, pb0, pb1);
-                        v = info_neg(en.info) ? -h : h;
-                    } else {                          // diagonal
-                        T h = pval2 + en.val;
-                        uint64_t x0 = pb0, x1 = pb1;
-                        while (x0 | x1) {
-                            int kp;
-                            if (x0) { kp = __ffsll((long long)x0) - 1; x0 &= x0 - 1; }
-                            else { kp = 64 + __ffsll((long long)x1) - 1; x1 &= x1 - 1; }
-                            h += sum_over_bits<T>(a.Dpn + (int64_t)kp * S, nb0, nb1);
-                        }
-                        v = h;
-                    }
-                    a.col[pos2 + k] = col2 + en.local;
-                    a.val[pos2 + k] = v;
-                }
-            }
-            out += total;
         }
     }
 }
@@ -243,9 +401,10 @@ static RowArgs<T> row_args(Problem *p) {
     a.row_p = p->d_row_p.ptr; a.row_n = p->d_row_n.ptr; a.p_row_base = p->d_p_row_base.ptr;
     a.p_q = P.d_q.ptr; a.p_twoM = P.d_twoM.ptr; a.n_q = Nn.d_q.ptr; a.n_twoM = Nn.d_twoM.ptr;
     a.n_local = Nn.d_local.ptr; a.p_bits = P.d_bits.ptr; a.n_bits = Nn.d_bits.ptr;
-    a.o_ptr = c.outer.ptr; a.l2_ptr = c.l2.ptr; a.l4_ptr = c.l4.ptr;
-    a.o_ent = c.outer.ent; a.l2_ent = c.l2.ent; a.l4_ent = c.l4.ent;
-    a.seg2 = c.seg2.ptr; a.seg4 = c.seg4.ptr;
+    a.o_ptr = c.outer.ptr; a.o4_ptr = c.outer4.ptr; a.l2_ptr = c.l2.ptr; a.l4_ptr = c.l4.ptr;
+    a.o_ent = c.outer.ent; a.o4_ent = c.outer4.ent; a.l2_ent = c.l2.ent; a.l4_ent = c.l4.ent;
+    a.o_xr = c.outer.xr;
+    a.seg2 = c.seg2.ptr; a.seg4 = c.seg4.ptr; a.qmin2 = c.qmin2.ptr; a.oseg2 = c.oseg2.ptr; a.oseg4 = c.oseg4.ptr;
     a.Upn = t.Upn.ptr; a.Wpn = t.Wpn.ptr; a.Dpn = t.Dpn.ptr; a.Tpn = t.Tpn.ptr;
     return a;
 }

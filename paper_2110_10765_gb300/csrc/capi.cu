@@ -21,24 +21,42 @@ static void export_conn(const Problem &P, int species, int64_t *ptr, int32_t *id
     // species 0: the proton list; species 1: the union of the neutron lists
     // L2 and L4 (the neutron pairs kept), merged per row in ascending order.
     if (species == 0) {
-        const ConnList<T> &L = c.outer;
-        if (total) *total = L.total;
-        int64_t n = P.sp[0].n;
-        std::vector<int64_t> hp(n + 1);
-        CI_CUDA(cudaMemcpy(hp.data(), L.ptr, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost));
-        for (auto &x : hp) x -= L.first;
-        if (ptr) std::memcpy(ptr, hp.data(), hp.size() * sizeof(int64_t));
+        // O2 (d <= 2) and O4 (d = 4, same 2M) merged per row by partner index
+        const ConnList<T> &A = c.outer, &B = c.outer4;
+        const int64_t n = P.sp[0].n;
+        std::vector<int64_t> pa(n + 1), pb(n + 1);
+        CI_CUDA(cudaMemcpy(pa.data(), A.ptr, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost));
+        CI_CUDA(cudaMemcpy(pb.data(), B.ptr, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost));
+        for (auto &x : pa) x -= A.first;
+        for (auto &x : pb) x -= B.first;
+        const int64_t tot = A.total + B.total;
+        if (total) *total = tot;
+        if (ptr)
+            for (int64_t i = 0; i <= n; ++i) ptr[i] = pa[i] + pb[i];
         if (!idx && !d) return;
-        if (cap < L.total) fail(CI_ERR_CAPACITY, "cap below the entry count");
-        std::vector<ConnEntry<T>> he(L.total);
-        std::vector<int32_t> ht(L.total);
-        if (L.total) {
-            CI_CUDA(cudaMemcpy(he.data(), L.ent + L.first, L.total * sizeof(ConnEntry<T>), cudaMemcpyDeviceToHost));
-            CI_CUDA(cudaMemcpy(ht.data(), L.tgt + L.first, L.total * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        if (cap < tot) fail(CI_ERR_CAPACITY, "cap below the entry count");
+        std::vector<ConnEntry<T>> ea(A.total), eb(B.total);
+        std::vector<int32_t> ta(A.total), tb(B.total);
+        if (A.total) {
+            CI_CUDA(cudaMemcpy(ea.data(), A.ent + A.first, A.total * sizeof(ConnEntry<T>), cudaMemcpyDeviceToHost));
+            CI_CUDA(cudaMemcpy(ta.data(), A.tgt + A.first, A.total * sizeof(int32_t), cudaMemcpyDeviceToHost));
         }
-        for (int64_t i = 0; i < L.total; ++i) {
-            if (idx) idx[i] = ht[i];
-            if (d) d[i] = (int8_t)(2 * info_dcode(he[i].info));
+        if (B.total) {
+            CI_CUDA(cudaMemcpy(eb.data(), B.ent + B.first, B.total * sizeof(ConnEntry<T>), cudaMemcpyDeviceToHost));
+            CI_CUDA(cudaMemcpy(tb.data(), B.tgt + B.first, B.total * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        }
+        int64_t o = 0;
+        for (int64_t s = 0; s < n; ++s) {
+            int64_t i = pa[s], j = pb[s];
+            while (i < pa[s + 1] || j < pb[s + 1]) {
+                const bool takeA = j >= pb[s + 1] || (i < pa[s + 1] && ta[i] < tb[j]);
+                const int32_t t = takeA ? ta[i] : tb[j];
+                const int dc = info_dcode(takeA ? ea[i].info : eb[j].info);
+                if (idx) idx[o] = t;
+                if (d) d[o] = (int8_t)(2 * dc);
+                ++o;
+                if (takeA) ++i; else ++j;
+            }
         }
         return;
     }

@@ -28,8 +28,8 @@ struct FilterArgs {
     const int32_t *tr_base;    // proton list: row offset of a proton move in the pn table
     const int32_t *tr_idx;     // neutron lists: column index of a neutron move
     const int64_t *p_row_base; // proton list: first basis row of every determinant
-    int32_t *count[3];         // pass 0, per list
-    const int64_t *ptr[3];     // pass 1, per list
+    int32_t *count[kModes];    // pass 0, per list
+    const int64_t *ptr[kModes];   // pass 1, per list
     ConnEntry<T> *ent;         // pass 1 (shared entry array)
     int32_t *tgt;              // pass 1: partner index of every entry
 };
@@ -54,7 +54,8 @@ __device__ __forceinline__ void flip(uint64_t *K, int o) { K[o >> 6] ^= 1ull << 
 template <class T>
 __device__ __forceinline__ ConnEntry<T> make_entry(const FilterArgs<T> &a, int mode, int64_t s, int64_t t,
                                                    const uint64_t *bs, const uint64_t *bt, int d) {
-    const int sp = mode == CONN_OUTER ? 0 : 1;
+    const bool proton = mode == CONN_OUTER || mode == CONN_O4;
+    const int sp = proton ? 0 : 1;
     ConnEntry<T> e;
     e.tgt = (int32_t)t;
     e.local = a.local[t];
@@ -89,7 +90,7 @@ __device__ __forceinline__ ConnEntry<T> make_entry(const FilterArgs<T> &a, int m
             for (int i = 0; i < a.A; ++i)
                 if (o[i] != ao) h += u[o[i]];
             e.info = make_info(1, par & 1, ao, co);
-            if (mode == CONN_OUTER) e.local = a.tr_base[co * S + ao];
+            if (proton) e.local = a.tr_base[co * S + ao];
             else e.info |= (uint32_t)a.tr_idx[co * S + ao] << 17;
             e.val = h;
         } else {
@@ -112,8 +113,8 @@ __device__ __forceinline__ ConnEntry<T> make_entry(const FilterArgs<T> &a, int m
             e.val = (par & 1) ? -v : v;
         }
     }
-    if (mode == CONN_OUTER) {
-        // the proton list carries what the row kernels need about t (first
+    if (proton) {
+        // the proton lists carry what the row kernels need about t (first
         // basis row, q, change of 2M) instead of t itself
         e.tgt = (int32_t)a.p_row_base[t];
         const int dslot = (a.twoM[t] - a.twoM[s]) / 2;
@@ -129,7 +130,7 @@ __device__ __forceinline__ ConnEntry<T> make_entry(const FilterArgs<T> &a, int m
 // evaluated afterwards by k_entries, one warp per row and list).  The window holds every
 // determinant whose 2M is within 2K of a row's 2M (a single move changes
 // 2M by at most 2K; a double move is kept only at equal 2M), and only the
-// row's own 2M block when the sweep fills the L4 list alone.  Lanes take
+// row's own 2M block when the sweep fills same-2M lists only.  Lanes take
 // one partner each and a warp ballot per row and list keeps the partners
 // in ascending order.
 constexpr int kTile = 512;
@@ -148,11 +149,12 @@ __global__ void __launch_bounds__(256) k_filter(const FilterArgs<T> *jobs, const
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t blk_row0 = ((int64_t)blockIdx.x - job_blk[lo]) * 8 * RW;
     const int64_t row0 = blk_row0 + (int64_t)wid * RW;
-    const bool mO = a.modes & (1 << CONN_OUTER), m2 = a.modes & (1 << CONN_L2), m4 = a.modes & (1 << CONN_L4);
+    const bool mO = a.modes & (1 << CONN_OUTER), m2 = a.modes & (1 << CONN_L2), m4 = a.modes & (1 << CONN_L4),
+               mO4 = a.modes & (1 << CONN_O4);
     uint64_t bs[RW][kMaxWords];
     int ms[RW];
-    int64_t out[RW][3];
-    int cnt[RW][3];
+    int64_t out[RW][kModes];
+    int cnt[RW][kModes];
 #pragma unroll
     for (int i = 0; i < RW; ++i) {
         const int64_t s = row0 + i;
@@ -161,7 +163,7 @@ __global__ void __launch_bounds__(256) k_filter(const FilterArgs<T> *jobs, const
         for (int w = 0; w < kMaxWords; ++w) bs[i][w] = (ok && w < W) ? a.bits[s * W + w] : 0ull;
         ms[i] = ok ? a.twoM[s] : 0;
 #pragma unroll
-        for (int m = 0; m < 3; ++m) {
+        for (int m = 0; m < kModes; ++m) {
             out[i][m] = (ok && pass && (a.modes >> m & 1)) ? a.ptr[m][s] : 0;
             cnt[i][m] = 0;
         }
@@ -170,6 +172,7 @@ __global__ void __launch_bounds__(256) k_filter(const FilterArgs<T> *jobs, const
     const int64_t last = min(a.n - 1, blk_row0 + 8 * RW - 1);
     const int b0 = (a.twoM[blk_row0] - a.m2min) / 2, b1 = (a.twoM[last] - a.m2min) / 2;
     const int reach = (mO || m2) ? a.K : 0;
+    (void)mO4;
     const int64_t t_lo = a.blk_start[max(b0 - reach, 0)];
     const int64_t t_hi = a.blk_start[min(b1 + reach + 1, a.nblk)];
     for (int64_t t0 = t_lo; t0 < t_hi; t0 += kTile) {
@@ -192,10 +195,10 @@ __global__ void __launch_bounds__(256) k_filter(const FilterArgs<T> *jobs, const
                 for (int w = 0; w < W; ++w) d += __popcll(bs[i][w] ^ bt[w]);
                 const bool sameM = mt == ms[i];
                 const bool valid = tv && (row0 + i < a.n);
-                const bool keep[3] = {mO && valid && (d <= 2 || (d == 4 && sameM)), m2 && valid && d <= 2,
-                                      m4 && valid && d <= 4 && sameM};
+                const bool keep[kModes] = {mO && valid && d <= 2, m2 && valid && d <= 2,
+                                           m4 && valid && d <= 4 && sameM, mO4 && valid && d == 4 && sameM};
 #pragma unroll
-                for (int m = 0; m < 3; ++m) {
+                for (int m = 0; m < kModes; ++m) {
                     if (!(a.modes >> m & 1)) continue;   // uniform over the block
                     const unsigned bal = __ballot_sync(0xffffffffu, keep[m]);
                     if (pass && keep[m]) {
@@ -213,7 +216,7 @@ __global__ void __launch_bounds__(256) k_filter(const FilterArgs<T> *jobs, const
         for (int i = 0; i < RW; ++i)
             if (row0 + i < a.n)
 #pragma unroll
-                for (int m = 0; m < 3; ++m)
+                for (int m = 0; m < kModes; ++m)
                     if (a.modes >> m & 1) a.count[m][row0 + i] = cnt[i][m];
     }
 }
@@ -301,19 +304,40 @@ static void filter_pass(const std::vector<FilterArgs<T>> &jobs, int pass, cudaSt
     else { launch_filter<T, 1, 1>(j1, pass, s); launch_filter<T, 2, 1>(j2, pass, s); }
 }
 
-// Segment tables of one problem's neutron lists.
+// Segment tables of one problem's lists (c: a cap on q, ds: a 2M slot,
+// 2M(partner) = 2M(row) + 2(ds - K); entries are sorted by (2M, q, bits)).
 //   seg2[n][ds][c]: end (relative to ptr[n]) of the L2 entries whose key
 //   (2M, q) is <= (2M_n + 2(ds-K), c); with no Nmax cut the q part is ignored.
 //   seg4[n][c]: end (relative) of the L4 entries with q <= c (all same 2M).
+//   qmin2[n][ds]: q of the first L2 entry of slot ds (its smallest q), nq if
+//   the slot is empty.
+//   oseg2[p][ds][c], oseg4[p][c]: the same ends for the proton lists O2 and
+//   O4, read from the packed (q, slot) of each entry.
+// A row (p, n) then takes, per 2M slot of the proton partners, the q-prefix
+// that can still meet a neutron partner under the Nmax cut.
 template <class T>
 struct SegJob {
-    int64_t n;
+    int64_t n, np;
     int nds, nq, K, cut;
-    const int64_t *p2, *p4;
-    const ConnEntry<T> *e2, *e4;
+    const int64_t *p2, *p4, *po, *po4;
+    const ConnEntry<T> *e2, *e4, *eo, *eo4;
     const int32_t *twoM, *q;
-    int32_t *seg2, *seg4;
+    int32_t *seg2, *seg4, *qmin2, *oseg2, *oseg4;
 };
+
+// first entry of [lo, hi) whose key exceeds (slot, c); key(e) = (slot, q)
+template <class T, class KeyF>
+__device__ __forceinline__ int64_t upper_key(const ConnEntry<T> *e, int64_t lo, int64_t hi, int slot, int c, bool cut,
+                                             KeyF key) {
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        int ks, kq;
+        key(e[mid], ks, kq);
+        const bool le = ks < slot || (ks == slot && (!cut || kq <= c));
+        if (le) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
 
 template <class T>
 __global__ void k_seg(const SegJob<T> *jobs, const int64_t *job_off, int njobs) {
@@ -327,27 +351,26 @@ __global__ void k_seg(const SegJob<T> *jobs, const int64_t *job_off, int njobs) 
         }
         const SegJob<T> &j = jobs[jl];
         int64_t r = e - job_off[jl];
-        const int64_t n2 = j.n * j.nds * j.nq;
-        if (r < n2) {
+        const int64_t sz2 = j.n * j.nds * j.nq, sz4 = j.n * j.nq, szm = j.n * j.nds;
+        const int64_t szo2 = j.np * j.nds * j.nq;
+        const bool cut = j.cut != 0;
+        if (r < sz2) {   // seg2
             const int c = (int)(r % j.nq);
             const int ds = (int)((r / j.nq) % j.nds);
             const int64_t s = r / ((int64_t)j.nq * j.nds);
             const int mt = j.twoM[s] + 2 * (ds - j.K);
-            int64_t lo = j.p2[s], hi = j.p2[s + 1];  // first entry with key > (mt, c)
-            while (lo < hi) {
-                const int64_t mid = (lo + hi) >> 1;
-                const int tg = j.e2[mid].tgt;
-                const int mm = j.twoM[tg];
-                const bool le = mm < mt || (mm == mt && (!j.cut || j.q[tg] <= c));
-                if (le) lo = mid + 1; else hi = mid;
-            }
-            j.seg2[r] = (int32_t)(lo - j.p2[s]);
-        } else {
-            r -= n2;
+            const int64_t end = upper_key(j.e2, j.p2[s], j.p2[s + 1], mt, c, cut,
+                                          [&](const ConnEntry<T> &x, int &ks, int &kq) {
+                                              ks = j.twoM[x.tgt]; kq = j.q[x.tgt]; });
+            j.seg2[r] = (int32_t)(end - j.p2[s]);
+            continue;
+        }
+        r -= sz2;
+        if (r < sz4) {   // seg4
             const int c = (int)(r % j.nq);
             const int64_t s = r / j.nq;
             int64_t lo = j.p4[s], hi = j.p4[s + 1];
-            if (j.cut) {
+            if (cut) {
                 while (lo < hi) {
                     const int64_t mid = (lo + hi) >> 1;
                     if (j.q[j.e4[mid].tgt] <= c) lo = mid + 1; else hi = mid;
@@ -356,7 +379,84 @@ __global__ void k_seg(const SegJob<T> *jobs, const int64_t *job_off, int njobs) 
                 lo = hi;
             }
             j.seg4[r] = (int32_t)(lo - j.p4[s]);
+            continue;
         }
+        r -= sz4;
+        if (r < szm) {   // qmin2: first L2 entry of the slot
+            const int ds = (int)(r % j.nds);
+            const int64_t s = r / j.nds;
+            const int mt = j.twoM[s] + 2 * (ds - j.K);
+            const int64_t b = upper_key(j.e2, j.p2[s], j.p2[s + 1], mt - 2, 0, false,
+                                        [&](const ConnEntry<T> &x, int &ks, int &kq) {
+                                            ks = j.twoM[x.tgt]; kq = 0; });
+            int qm = j.nq;
+            if (b < j.p2[s + 1] && j.twoM[j.e2[b].tgt] == mt) qm = cut ? j.q[j.e2[b].tgt] : 0;
+            j.qmin2[r] = qm;
+            continue;
+        }
+        r -= szm;
+        if (r < szo2) {  // oseg2: keys from the packed proton entries
+            const int c = (int)(r % j.nq);
+            const int ds = (int)((r / j.nq) % j.nds) - j.K;
+            const int64_t s = r / ((int64_t)j.nq * j.nds);
+            const int64_t end = upper_key(j.eo, j.po[s], j.po[s + 1], ds, c, cut,
+                                          [&](const ConnEntry<T> &x, int &ks, int &kq) {
+                                              ks = info_dslot(x.info); kq = info_q(x.info); });
+            j.oseg2[r] = (int32_t)(end - j.po[s]);
+            continue;
+        }
+        r -= szo2;
+        {                // oseg4: all same 2M, q-prefix
+            const int c = (int)(r % j.nq);
+            const int64_t s = r / j.nq;
+            const int64_t end = upper_key(j.eo4, j.po4[s], j.po4[s + 1], 0, c, cut,
+                                          [&](const ConnEntry<T> &x, int &ks, int &kq) {
+                                              ks = 0; kq = info_q(x.info); });
+            j.oseg4[r] = (int32_t)(end - j.po4[s]);
+        }
+    }
+}
+
+// Cross ranks of the same-2M proton partners (one warp per proton row):
+// for an O2 entry of 2M slot 0, the number of the row's O4 entries with a
+// smaller partner index; for an O4 entry, the number of the row's slot-0 O2
+// entries with a smaller partner index.  The fill merges the two lists by
+// column with them.
+struct XrankJob {
+    int64_t np;
+    int K, nq;
+    const int64_t *po, *po4;
+    const int32_t *oseg2;
+    const int32_t *tgt;   // partner index per entry
+    int32_t *xr;
+};
+
+__device__ __forceinline__ int64_t lower_tgt(const int32_t *tgt, int64_t lo, int64_t hi, int32_t key) {
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (tgt[mid] < key) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void k_xrank(const XrankJob *jobs, const int64_t *job_row, int njobs) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t gr = warp; gr < job_row[njobs]; gr += nwarps) {
+        int lo = 0, hi = njobs - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (job_row[mid] <= gr) lo = mid; else hi = mid - 1;
+        }
+        const XrankJob &j = jobs[lo];
+        const int64_t p = gr - job_row[lo];
+        const int32_t *os = j.oseg2 + p * (2 * j.K + 1) * j.nq;
+        const int64_t a0 = j.po[p] + (j.K == 0 ? 0 : os[(j.K - 1) * j.nq + j.nq - 1]);
+        const int64_t a1 = j.po[p] + os[j.K * j.nq + j.nq - 1];
+        const int64_t b0 = j.po4[p], b1 = j.po4[p + 1];
+        for (int64_t e = a0 + lane; e < a1; e += 32) j.xr[e] = (int32_t)(lower_tgt(j.tgt, b0, b1, j.tgt[e]) - b0);
+        for (int64_t e = b0 + lane; e < b1; e += 32) j.xr[e] = (int32_t)(lower_tgt(j.tgt, a0, a1, j.tgt[e]) - a0);
     }
 }
 
@@ -388,7 +488,7 @@ void species_filter_group(const std::vector<Problem *> &ps_in, cudaStream_t s) {
     if (ps.empty()) return;
     for (Problem *p : ps) enumerate_basis(p, s);
     stage_tables_group<T>(ps, s);
-    // three lists per problem, their counts side by side in one array; one
+    // four lists per problem, their counts side by side in one array; one
     // sweep per species list (one per problem when the species coincide)
     std::vector<FilterArgs<T>> jobs;
     std::vector<ConnList<T> *> lists;
@@ -398,14 +498,16 @@ void species_filter_group(const std::vector<Problem *> &ps_in, cudaStream_t s) {
         Connectivity<T> &c = p->conn<T>();
         const bool same = p->Z == p->N;
         const int first = (int)jobs.size();
-        jobs.push_back(filter_job<T>(p, 0, same ? 7 : 1 << CONN_OUTER));
-        if (!same) jobs.push_back(filter_job<T>(p, 1, (1 << CONN_L2) | (1 << CONN_L4)));
-        ConnList<T> *ls[3] = {&c.outer, &c.l2, &c.l4};
-        for (int m = 0; m < 3; ++m) {
+        const int pmodes = (1 << CONN_OUTER) | (1 << CONN_O4), nmodes = (1 << CONN_L2) | (1 << CONN_L4);
+        jobs.push_back(filter_job<T>(p, 0, same ? pmodes | nmodes : pmodes));
+        if (!same) jobs.push_back(filter_job<T>(p, 1, nmodes));
+        ConnList<T> *ls[kModes] = {&c.outer, &c.l2, &c.l4, &c.outer4};
+        for (int m = 0; m < kModes; ++m) {
+            const bool prot = m == CONN_OUTER || m == CONN_O4;
             lists.push_back(ls[m]);
-            list_job.push_back(m == 0 || same ? first : first + 1);
+            list_job.push_back(prot || same ? first : first + 1);
             list_mode.push_back(m);
-            cnt_off.push_back(cnt_off.back() + (m == 0 ? p->sp[0].n : p->sp[1].n));
+            cnt_off.push_back(cnt_off.back() + (prot ? p->sp[0].n : p->sp[1].n));
         }
     }
     const int64_t ncnt = cnt_off.back();
@@ -418,12 +520,15 @@ void species_filter_group(const std::vector<Problem *> &ps_in, cudaStream_t s) {
     std::vector<int64_t> hb = gather_i64(offs->ptr, cnt_off, s);
     auto ents = std::make_shared<DevBuf<ConnEntry<T>>>((size_t)hb.back());
     auto tgts = std::make_shared<DevBuf<int32_t>>((size_t)hb.back());
+    auto xrs = std::make_shared<DevBuf<int32_t>>((size_t)hb.back());
     for (size_t i = 0; i < lists.size(); ++i) {
         ConnList<T> &L = *lists[i];
         L.ptr_buf = offs;
         L.ent_buf = ents;
         L.tgt_buf = tgts;
         L.tgt = tgts->ptr;
+        L.xr_buf = xrs;
+        L.xr = xrs->ptr;
         L.ptr = offs->ptr + cnt_off[i];
         L.ent = ents->ptr;
         L.n = cnt_off[i + 1] - cnt_off[i];
@@ -444,19 +549,26 @@ void species_filter_group(const std::vector<Problem *> &ps_in, cudaStream_t s) {
     }
     launch_entries<T, 1>(ej1, s);
     launch_entries<T, 2>(ej2, s);
-    // segment tables of the neutron lists
+    // segment tables
     std::vector<SegJob<T>> sj;
     std::vector<int64_t> soff(1, 0);
     for (Problem *p : ps) {
         Connectivity<T> &c = p->conn<T>();
-        SpeciesList &Nn = p->sp[1];
-        c.seg2.alloc((size_t)Nn.n * p->nds * Nn.nq);
-        c.seg4.alloc((size_t)Nn.n * Nn.nq);
+        SpeciesList &P = p->sp[0], &Nn = p->sp[1];
+        if (P.nq != Nn.nq) fail(CI_ERR_INTERNAL, "species q ranges differ");
+        const int nq = Nn.nq, nds = p->nds;
+        c.seg2.alloc((size_t)Nn.n * nds * nq);
+        c.seg4.alloc((size_t)Nn.n * nq);
+        c.qmin2.alloc((size_t)Nn.n * nds);
+        c.oseg2.alloc((size_t)P.n * nds * nq);
+        c.oseg4.alloc((size_t)P.n * nq);
         SegJob<T> j{};
-        j.n = Nn.n; j.nds = p->nds; j.nq = Nn.nq; j.K = p->K; j.cut = p->nmax >= 0;
-        j.p2 = c.l2.ptr; j.p4 = c.l4.ptr; j.e2 = c.l2.ent; j.e4 = c.l4.ent;
-        j.twoM = Nn.d_twoM.ptr; j.q = Nn.d_q.ptr; j.seg2 = c.seg2.ptr; j.seg4 = c.seg4.ptr;
-        const int64_t w = Nn.n * p->nds * Nn.nq + Nn.n * Nn.nq;
+        j.n = Nn.n; j.np = P.n; j.nds = nds; j.nq = nq; j.K = p->K; j.cut = p->nmax >= 0;
+        j.p2 = c.l2.ptr; j.p4 = c.l4.ptr; j.po = c.outer.ptr; j.po4 = c.outer4.ptr;
+        j.e2 = c.l2.ent; j.e4 = c.l4.ent; j.eo = c.outer.ent; j.eo4 = c.outer4.ent;
+        j.twoM = Nn.d_twoM.ptr; j.q = Nn.d_q.ptr;
+        j.seg2 = c.seg2.ptr; j.seg4 = c.seg4.ptr; j.qmin2 = c.qmin2.ptr; j.oseg2 = c.oseg2.ptr; j.oseg4 = c.oseg4.ptr;
+        const int64_t w = Nn.n * nds * nq + Nn.n * nq + Nn.n * nds + P.n * nds * nq + P.n * nq;
         if (w == 0) continue;
         sj.push_back(j);
         soff.push_back(soff.back() + w);
@@ -468,6 +580,28 @@ void species_filter_group(const std::vector<Problem *> &ps_in, cudaStream_t s) {
         CI_CUDA(cudaMemcpyAsync(dso.ptr, soff.data(), sizeof(int64_t) * soff.size(), cudaMemcpyHostToDevice, s));
         launch("k_seg", k_seg<T>, grid_for(soff.back(), 256, sm_count() * 16), 256, 0, s, (const SegJob<T> *)dsj.ptr,
                (const int64_t *)dso.ptr, (int)sj.size());
+    }
+    {
+        std::vector<XrankJob> xj;
+        std::vector<int64_t> xoff(1, 0);
+        for (Problem *p : ps) {
+            Connectivity<T> &c = p->conn<T>();
+            if (p->sp[0].n == 0) continue;
+            XrankJob j{};
+            j.np = p->sp[0].n; j.K = p->K; j.nq = p->sp[0].nq;
+            j.po = c.outer.ptr; j.po4 = c.outer4.ptr; j.oseg2 = c.oseg2.ptr;
+            j.tgt = tgts->ptr; j.xr = xrs->ptr;
+            xj.push_back(j);
+            xoff.push_back(xoff.back() + j.np);
+        }
+        if (!xj.empty()) {
+            DevBuf<XrankJob> dxj(xj.size());
+            DevBuf<int64_t> dxo(xoff.size());
+            CI_CUDA(cudaMemcpyAsync(dxj.ptr, xj.data(), sizeof(XrankJob) * xj.size(), cudaMemcpyHostToDevice, s));
+            CI_CUDA(cudaMemcpyAsync(dxo.ptr, xoff.data(), sizeof(int64_t) * xoff.size(), cudaMemcpyHostToDevice, s));
+            launch("k_xrank", k_xrank, grid_for(xoff.back() * 32, 256, sm_count() * 8), 256, 0, s,
+                   (const XrankJob *)dxj.ptr, (const int64_t *)dxo.ptr, (int)xj.size());
+        }
     }
     for (Problem *p : ps) p->conn<T>().ready = true;
 }

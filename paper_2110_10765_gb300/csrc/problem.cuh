@@ -95,25 +95,35 @@ template <class T>
 struct ConnList {
     std::shared_ptr<DevBuf<int64_t>> ptr_buf;
     std::shared_ptr<DevBuf<ConnEntry<T>>> ent_buf;
-    std::shared_ptr<DevBuf<int32_t>> tgt_buf;
+    std::shared_ptr<DevBuf<int32_t>> tgt_buf, xr_buf;
     const int64_t *ptr = nullptr;
     ConnEntry<T> *ent = nullptr;
     const int32_t *tgt = nullptr;   // partner index per entry (absolute positions, as ent)
+    // proton lists: for a same-2M entry, the number of same-2M entries of
+    // the other proton list (O2 <-> O4) of its row with a smaller partner
+    const int32_t *xr = nullptr;
     int64_t n = 0;      // determinants (rows of the list)
     int64_t first = 0;  // ptr[0]
     int64_t total = 0;  // ptr[n] - ptr[0]
 };
 
-// Which species pairs a list keeps (see ci_species_filter).
-enum ConnMode { CONN_OUTER = 0, CONN_L2 = 1, CONN_L4 = 2 };
+// Which species pairs a list keeps (see ci_species_filter).  The proton
+// pairs are split by their difference: O2 (d <= 2, any M) and O4 (d = 4,
+// same M); ci_get_species_conn merges them back into one list.
+enum ConnMode { CONN_OUTER = 0, CONN_L2 = 1, CONN_L4 = 2, CONN_O4 = 3 };
+constexpr int kModes = 4;
 
 template <class T>
 struct Connectivity {
-    ConnList<T> outer;   // protons: d <= 2 (any M) and d = 4 (same M)
+    ConnList<T> outer;   // protons: d <= 2 (any M)
+    ConnList<T> outer4;  // protons: d = 4 (same M)
     ConnList<T> l2;      // neutrons: d <= 2 (any M)
     ConnList<T> l4;      // neutrons: d <= 4, same M
-    DevBuf<int32_t> seg2; // [nN][nds][nq] end of L2 entries with slot<s or (slot==s, q<=c), relative
-    DevBuf<int32_t> seg4; // [nN][nq] end of L4 entries with q <= c, relative
+    DevBuf<int32_t> seg2;  // [nN][nds][nq] end of L2 entries with slot<s or (slot==s, q<=c), relative
+    DevBuf<int32_t> seg4;  // [nN][nq] end of L4 entries with q <= c, relative
+    DevBuf<int32_t> oseg2; // [nP][nds][nq] the same for the O2 list (slot of 2M(p') - 2M(p))
+    DevBuf<int32_t> oseg4; // [nP][nq] end of O4 entries with q(p') <= c, relative
+    DevBuf<int32_t> qmin2; // [nN][nds] smallest q of the L2 entries in a 2M slot (nq if none)
     bool ready = false;
 };
 

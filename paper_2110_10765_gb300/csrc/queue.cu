@@ -70,7 +70,7 @@ static size_t request_bytes(const Problem *p, int64_t nnz, int MB) {
     size_t b = (size_t)nnz * 8 + (size_t)(dim + 1) * 8 + (size_t)dim * 12;            // CSR + counts + row map
     b += (size_t)dim * ((size_t)MB * 8 + EB * 8 + 2 * EB * 4);                          // Q, W, X, Y
     const Connectivity<float> &c = p->c32;
-    b += (size_t)(c.outer.total + c.l2.total + c.l4.total) * sizeof(ConnEntry<float>);
+    b += (size_t)(c.outer.total + c.outer4.total + c.l2.total + c.l4.total) * (sizeof(ConnEntry<float>) + 4);
     const size_t S = (size_t)p->S;
     b += (S * S * S * 4 + p->like_size * 2 + p->tr_size + S * S * 3) * sizeof(float);  // staged tables
     return b;
