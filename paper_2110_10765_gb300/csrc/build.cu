@@ -178,12 +178,18 @@ __device__ __forceinline__ T sum_over_bits(const T *tab, uint64_t w0, uint64_t w
     return s;
 }
 
-// Row context of the fill.
+// Row context of the fill.  The bit strings of p and n are only needed by
+// the rare spectator sums and are loaded there.
 struct RowCtx {
     int p, n, n_local;
     int64_t l2b, l4b;
-    uint64_t pb0, pb1, nb0, nb1;
 };
+
+template <class T>
+__device__ __forceinline__ void row_bits(const RowArgs<T> &a, int s, const uint64_t *bits, uint64_t &b0, uint64_t &b1) {
+    b0 = bits[(int64_t)s * a.W];
+    b1 = a.W > 1 ? bits[(int64_t)s * a.W + 1] : 0ull;
+}
 
 // One chunk of up to 32 O2 partners (one per lane: entry ep, segment kind,
 // beg, len; extra = elements of other partners placed before this one's
@@ -213,48 +219,36 @@ __device__ __forceinline__ int fill_chunk(const RowArgs<T> &a, const RowCtx &x, 
     const int incl1 = warp_incl_scan_i32(len1);
     const int excl1 = incl1 - len1;
     const int total1 = __shfl_sync(0xffffffffu, incl1, 31);
-    // two elements per lane and pass: both dependent load chains (entry,
-    // then table) are in flight together
-    for (int t0 = 0; t0 < total1; t0 += 64) {
-        int jj[2], kk[2];
-        ConnEntry<T> en[2];
-        bool live[2];
+    for (int t0 = 0; t0 < total1; t0 += 32) {
+        const int t = t0 + lane;
+        int j = 0;  // last lane whose kind-1 segment starts at or before t
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int t = t0 + 32 * h + lane;
-            int j = 0;  // last lane whose kind-1 segment starts at or before t
-#pragma unroll
-            for (int step = 16; step > 0; step >>= 1) {
-                const int v = __shfl_sync(0xffffffffu, excl1, j + step);
-                if (v <= t) j += step;
-            }
-            jj[h] = j;
-            kk[h] = t - __shfl_sync(0xffffffffu, excl1, j);
-            live[h] = t < total1;
-            const int jbeg = __shfl_sync(0xffffffffu, beg, j);
-            if (live[h]) en[h] = a.l2_ent[x.l2b + jbeg + kk[h]];
+        for (int step = 16; step > 0; step >>= 1) {
+            const int v = __shfl_sync(0xffffffffu, excl1, j + step);
+            if (v <= t) j += step;
         }
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int j = jj[h];
-            const int64_t jpos = __shfl_sync(0xffffffffu, pos, j);
-            const int jcol = __shfl_sync(0xffffffffu, colbase, j);
-            const int jtb = __shfl_sync(0xffffffffu, ep.local, j);
-            const uint32_t pinfo = __shfl_sync(0xffffffffu, ep.info, j);
-            const T pval = __shfl_sync(0xffffffffu, ep.val, j);
-            if (live[h]) {
-                T v;
-                if (info_dcode(en[h].info) != 0) {   // (2,2): V^pn_{c_p c_n, a_p a_n}
-                    const T w = a.Tpn[jtb + info_tcol(en[h].info)];
-                    v = (info_neg(pinfo) ^ info_neg(en[h].info)) ? -w : w;
-                } else {                             // (2,0): neutrons are spectators
-                    const T *u = a.Upn + ((int64_t)info_c(pinfo) * S + info_a(pinfo)) * S;
-                    const T hv = pval + sum_over_bits<T>(u, x.nb0, x.nb1);
-                    v = info_neg(pinfo) ? -hv : hv;
-                }
-                a.col[jpos + kk[h]] = jcol + en[h].local;
-                a.val[jpos + kk[h]] = v;
+        const int k = t - __shfl_sync(0xffffffffu, excl1, j);
+        const int64_t jpos = __shfl_sync(0xffffffffu, pos, j);
+        const int jcol = __shfl_sync(0xffffffffu, colbase, j);
+        const int jtb = __shfl_sync(0xffffffffu, ep.local, j);
+        const uint32_t pinfo = __shfl_sync(0xffffffffu, ep.info, j);
+        const T pval = __shfl_sync(0xffffffffu, ep.val, j);
+        const int jbeg = __shfl_sync(0xffffffffu, beg, j);
+        if (t < total1) {
+            const ConnEntry<T> en = a.l2_ent[x.l2b + jbeg + k];
+            T v;
+            if (info_dcode(en.info) != 0) {   // (2,2): V^pn_{c_p c_n, a_p a_n}
+                const T w = a.Tpn[jtb + info_tcol(en.info)];
+                v = (info_neg(pinfo) ^ info_neg(en.info)) ? -w : w;
+            } else {                          // (2,0): neutrons are spectators
+                const T *u = a.Upn + ((int64_t)info_c(pinfo) * S + info_a(pinfo)) * S;
+                uint64_t nb0, nb1;
+                row_bits<T>(a, x.n, a.n_bits, nb0, nb1);
+                const T h = pval + sum_over_bits<T>(u, nb0, nb1);
+                v = info_neg(pinfo) ? -h : h;
             }
+            a.col[jpos + k] = jcol + en.local;
+            a.val[jpos + k] = v;
         }
     }
     // 2. p' = p: every same-2M neutron partner of n, L4(n)[0, len)
@@ -273,16 +267,20 @@ __device__ __forceinline__ int fill_chunk(const RowArgs<T> &a, const RowCtx &x, 
                 v = en.val;
             } else if (dn == 1) {             // (0,2): protons are spectators
                 const T *w = a.Wpn + ((int64_t)info_c(en.info) * S + info_a(en.info)) * S;
-                const T h = en.val + sum_over_bits<T>(w, x.pb0, x.pb1);
+                uint64_t pb0, pb1;
+                row_bits<T>(a, x.p, a.p_bits, pb0, pb1);
+                const T h = en.val + sum_over_bits<T>(w, pb0, pb1);
                 v = info_neg(en.info) ? -h : h;
             } else {                          // diagonal
                 T h = pval2 + en.val;
-                uint64_t x0 = x.pb0, x1 = x.pb1;
+                uint64_t x0, x1, nb0, nb1;
+                row_bits<T>(a, x.p, a.p_bits, x0, x1);
+                row_bits<T>(a, x.n, a.n_bits, nb0, nb1);
                 while (x0 | x1) {
                     int kp;
                     if (x0) { kp = __ffsll((long long)x0) - 1; x0 &= x0 - 1; }
                     else { kp = 64 + __ffsll((long long)x1) - 1; x1 &= x1 - 1; }
-                    h += sum_over_bits<T>(a.Dpn + (int64_t)kp * S, x.nb0, x.nb1);
+                    h += sum_over_bits<T>(a.Dpn + (int64_t)kp * S, nb0, nb1);
                 }
                 v = h;
             }
@@ -325,8 +323,6 @@ __global__ void __launch_bounds__(256) k_fill_rows(const RowArgs<T> *args, const
         x.p = a.row_p[r];
         x.n = a.row_n[r];
         const int p = x.p, n = x.n;
-        x.pb0 = a.p_bits[(int64_t)p * a.W]; x.pb1 = a.W > 1 ? a.p_bits[(int64_t)p * a.W + 1] : 0;
-        x.nb0 = a.n_bits[(int64_t)n * a.W]; x.nb1 = a.W > 1 ? a.n_bits[(int64_t)n * a.W + 1] : 0;
         x.n_local = a.n_local[n];
         x.l2b = a.l2_ptr[n];
         x.l4b = a.l4_ptr[n];

@@ -5,6 +5,8 @@
 // Three forms of the pair test, which give identical counts:
 //   HYBRID  popcount of the XOR of the bits of the lowest 64 s.p. states
 //           first; only pairs that pass compare their MBS lists (Listing 2);
+//           before it, a cheaper bound (the XOR folded to 32 bits) rejects
+//           most pairs with one population count;
 //   MBS     the MBS comparison for every pair (no prefilter);
 //   BITS    the complete bit representation (S <= 128): popcount only.
 // The MBS comparison counts the common states of the two lists; two
@@ -69,7 +71,11 @@ __device__ __forceinline__ void flush_counts(const CountArgs &a, int64_t row, un
     if ((threadIdx.x & 31) == 0 && s) atomicAdd(a.total, s);
 }
 
-// HYBRID (VAR 0) and BITS (VAR 2): R rows per thread.
+// HYBRID (VAR 0) and BITS (VAR 2): R rows per thread.  The population
+// count is first taken of the XOR folded to 32 bits with OR (a lower bound
+// of the true count, one POPC); the rare pairs whose folded count is within
+// max_diff then take the exact test: the 64-bit popcount (and, for HYBRID,
+// the MBS comparison; for BITS, the upper 64 states too).
 template <int VAR, int R>
 __global__ void __launch_bounds__(kCntThreads) k_count_bits(CountArgs a) {
     __shared__ uint64_t slo[kCntTile], shi[VAR == 2 ? kCntTile : 1];
@@ -85,6 +91,7 @@ __global__ void __launch_bounds__(kCntThreads) k_count_bits(CountArgs a) {
         hi[k] = r < a.n ? a.bits[2 * r + 1] : 0ull;
         cnt[k] = 0;
     }
+    const int md = a.max_diff;
     for (int64_t t0 = c0; t0 < c1; t0 += kCntTile) {
         const int nt = (int)min((int64_t)kCntTile, c1 - t0);
         __syncthreads();
@@ -96,16 +103,32 @@ __global__ void __launch_bounds__(kCntThreads) k_count_bits(CountArgs a) {
         for (int j = 0; j < nt; ++j) {
             const uint64_t blo = slo[j];
             const uint64_t bhi = VAR == 2 ? shi[j] : 0ull;
+            bool near[R];
+            bool any = false;
 #pragma unroll
             for (int k = 0; k < R; ++k) {
+                const uint64_t x = lo[k] ^ blo;
+                uint32_t f = (uint32_t)x | (uint32_t)(x >> 32);
                 if (VAR == 2) {
-                    cnt[k] += (__popcll(lo[k] ^ blo) + __popcll(hi[k] ^ bhi)) <= a.max_diff;
-                } else if (__popcll(lo[k] ^ blo) <= a.max_diff) {
-                    // rare: the lowest 64 states differ little; compare the MBS lists
+                    const uint64_t y = hi[k] ^ bhi;
+                    f |= (uint32_t)y | (uint32_t)(y >> 32);
+                }
+                near[k] = __popc(f) <= md;
+                any |= near[k];
+            }
+            if (!any) continue;
+            // rare: at least one row is near this column
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                if (!near[k]) continue;
+                if (VAR == 2) {
+                    cnt[k] += (__popcll(lo[k] ^ blo) + __popcll(hi[k] ^ bhi)) <= md;
+                } else if (__popcll(lo[k] ^ blo) <= md) {
+                    // the lowest 64 states differ little; compare the MBS lists
                     const int64_t r = r0 + (int64_t)k * kCntThreads;
                     if (r < a.n) {
                         const int c = common_states(a.mbs + r * a.N, a.mbs + (t0 + j) * a.N, a.N);
-                        cnt[k] += 2 * (a.N - c) <= a.max_diff;
+                        cnt[k] += 2 * (a.N - c) <= md;
                     }
                 }
             }
