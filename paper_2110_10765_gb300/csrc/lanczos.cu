@@ -19,6 +19,7 @@ constexpr int kTnThreads = 256;   // 8 warps: warp v owns column v of B
 constexpr int kMaxNa = 256;       // columns of A in one product
 
 constexpr int kTR = 32;           // rows of A and B staged per tile
+constexpr size_t kTnSmem = 96 * 1024;   // shared memory of the tiled product
 
 // part[blk][u][v] = sum over the block's rows i of A[i][u] B[i][v]
 // (u < na <= 256, v < nb <= 8).  Tiles of kTR rows of A and B are staged
@@ -63,6 +64,105 @@ __global__ void __launch_bounds__(kTnThreads) k_tn_partial(int64_t dim, const do
     for (int j = 0; j < kMaxNa * 8 / kTnThreads; ++j) {
         const int o = threadIdx.x + j * kTnThreads;
         if (o < nout) part[(int64_t)blockIdx.x * nout + o] = acc[j];
+    }
+}
+
+// Register-tiled form of the same product for the FP64 pipe (2 FMA per
+// clock per SM on this part, so the kernel is FMA-bound once every thread
+// carries enough independent accumulators).  Thread (g, s) owns the 4 x nb
+// outputs C[4g..4g+3][0..nb) and the rows s, s + S, ... of every staged
+// tile (G = ceil(na/4) groups, S = 256 / G row slices); each row costs it
+// two 32-byte A loads and nb/2 B loads from shared memory for 4 nb FMAs.
+// The slices are summed through shared memory at the end.
+template <int NB>
+__global__ void __launch_bounds__(kTnThreads) k_tn_tiled(int64_t dim, const double *__restrict__ A, int lda, int na,
+                                                         const double *__restrict__ B, int ldb,
+                                                         double *__restrict__ part, int64_t rows_per_blk, int tr) {
+    extern __shared__ double sm[];
+    const int nap = (na + 3) & ~3;       // A tile row length (padded to 4)
+    double *As = sm;                     // [tr][nap]
+    double *Bs = sm + (size_t)tr * nap;  // [tr][NB]
+    const int G = nap / 4;
+    const int S = kTnThreads / G;
+    const int g = threadIdx.x % G, sl = threadIdx.x / G;
+    const bool active = sl < S;
+    double acc[4][NB];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int v = 0; v < NB; ++v) acc[a][v] = 0.0;
+    const int64_t r0 = blockIdx.x * rows_per_blk;
+    const int64_t r1 = min(dim, r0 + rows_per_blk);
+    for (int64_t t0 = r0; t0 < r1; t0 += tr) {
+        const int rows = (int)min((int64_t)tr, r1 - t0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < rows * nap; e += kTnThreads) {
+            const int r = e / nap, u = e - r * nap;
+            As[e] = u < na ? A[(t0 + r) * lda + u] : 0.0;
+        }
+        for (int e = threadIdx.x; e < rows * NB; e += kTnThreads) {
+            const int r = e / NB, v = e - r * NB;
+            Bs[e] = B[(t0 + r) * ldb + v];
+        }
+        __syncthreads();
+        if (active) {
+            for (int r = sl; r < rows; r += S) {
+                const double *ar = As + (size_t)r * nap + 4 * g;
+                const double a0 = ar[0], a1 = ar[1], a2 = ar[2], a3 = ar[3];
+                const double *br = Bs + (size_t)r * NB;
+#pragma unroll
+                for (int v = 0; v < NB; ++v) {
+                    const double bv = br[v];
+                    acc[0][v] = fma(a0, bv, acc[0][v]);
+                    acc[1][v] = fma(a1, bv, acc[1][v]);
+                    acc[2][v] = fma(a2, bv, acc[2][v]);
+                    acc[3][v] = fma(a3, bv, acc[3][v]);
+                }
+            }
+        }
+    }
+    // sum the S row slices: red[sl][4g + a][v]
+    __syncthreads();
+    double *red = sm;
+    const int nout = nap * NB;
+    if (active) {
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int v = 0; v < NB; ++v) red[(size_t)sl * nout + (4 * g + a) * NB + v] = acc[a][v];
+    }
+    __syncthreads();
+    for (int o = threadIdx.x; o < na * NB; o += kTnThreads) {
+        double t = 0.0;
+        for (int q = 0; q < S; ++q) t += red[(size_t)q * nout + o];
+        part[(int64_t)blockIdx.x * na * NB + o] = t;
+    }
+}
+
+// W[i][v] = beta W[i][v] + alpha sum_u A[i][u] C[u][v] with one row per
+// thread and NB accumulators: each A element is loaded once for NB FMAs,
+// C is a shared-memory broadcast.
+template <int NB>
+__global__ void __launch_bounds__(256) k_nn_rows(int64_t dim, const double *__restrict__ A, int lda, int na,
+                                                 const double *__restrict__ C, double *__restrict__ W, int ldw,
+                                                 double alpha, double beta) {
+    __shared__ double Cs[kMaxNa * NB];
+    for (int e = threadIdx.x; e < na * NB; e += blockDim.x) Cs[e] = C[e];
+    __syncthreads();
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < dim; i += (int64_t)gridDim.x * blockDim.x) {
+        const double *Ai = A + i * lda;
+        double acc[NB];
+#pragma unroll
+        for (int v = 0; v < NB; ++v) acc[v] = 0.0;
+        for (int u = 0; u < na; ++u) {
+            const double a = Ai[u];
+            const double *cu = Cs + u * NB;
+#pragma unroll
+            for (int v = 0; v < NB; ++v) acc[v] = fma(a, cu[v], acc[v]);
+        }
+        double *w = W + i * ldw;
+#pragma unroll
+        for (int v = 0; v < NB; ++v) w[v] = beta == 0.0 ? alpha * acc[v] : fma(beta, w[v], alpha * acc[v]);
     }
 }
 
@@ -175,6 +275,8 @@ struct Solver {
         if (!attr) {
             CI_CUDA(cudaFuncSetAttribute(k_tn_partial, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)(sizeof(double) * kTR * (kMaxNa + 8))));
+            CI_CUDA(cudaFuncSetAttribute(k_tn_tiled<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)std::max(kTnSmem, sizeof(double) * kTnThreads * 8 * 4)));
             attr = true;
         }
         nblk = (int)std::min<int64_t>((int64_t)sms * 2, (dim + 63) / 64);
@@ -197,9 +299,21 @@ struct Solver {
     // host != null, copied to host.
     void tn(const double *A, int lda, int na, const double *B, int ldb, int nb, double *Cout,
             std::vector<double> *host) {
-        const size_t smem = sizeof(double) * kTR * (na + nb);
-        launch("k_tn_partial", k_tn_partial, nblk, kTnThreads, smem, s, dim, A, lda, na, B, ldb, nb, part.ptr,
-               rows_per_blk);
+        if (nb == 8) {
+            // rows per staged tile: the tile and the slice sums share one
+            // buffer of at most kTnSmem bytes
+            const int nap = (na + 3) & ~3;
+            const int S = kTnThreads / (nap / 4);
+            int tr = (int)(kTnSmem / sizeof(double)) / (nap + 8);
+            if (tr > 256) tr = 256;
+            const size_t smem = sizeof(double) * std::max((size_t)tr * (nap + 8), (size_t)S * nap * 8);
+            launch("k_tn_partial", k_tn_tiled<8>, nblk, kTnThreads, smem, s, dim, A, lda, na, B, ldb, part.ptr,
+                   rows_per_blk, tr);
+        } else {
+            const size_t smem = sizeof(double) * kTR * (na + nb);
+            launch("k_tn_partial", k_tn_partial, nblk, kTnThreads, smem, s, dim, A, lda, na, B, ldb, nb, part.ptr,
+                   rows_per_blk);
+        }
         launch("k_reduce_partial", k_reduce_partial, (na * nb + 31) / 32, 256, 0, s, part.ptr, nblk, na * nb, Cout);
         CI_CHECK_LAUNCH();
         if (host) {
@@ -211,7 +325,11 @@ struct Solver {
 
     void nn(const double *A, int lda, int na, const double *C, int nb, double *Wout, int ldw, double alpha,
             double beta) {
-        launch("k_nn_update", k_nn_update, grid(dim * nb), 256, 0, s, dim, A, lda, na, C, nb, Wout, ldw, alpha, beta);
+        if (nb == 8)
+            launch("k_nn_update", k_nn_rows<8>, grid(dim), 256, 0, s, dim, A, lda, na, C, Wout, ldw, alpha, beta);
+        else
+            launch("k_nn_update", k_nn_update, grid(dim * nb), 256, 0, s, dim, A, lda, na, C, nb, Wout, ldw, alpha,
+                   beta);
         CI_CHECK_LAUNCH();
     }
 
