@@ -69,73 +69,101 @@ __global__ void __launch_bounds__(kTnThreads) k_tn_partial(int64_t dim, const do
 
 // Register-tiled form of the same product for the FP64 pipe (2 FMA per
 // clock per SM on this part, so the kernel is FMA-bound once every thread
-// carries enough independent accumulators).  Thread (g, s) owns the 4 x nb
-// outputs C[4g..4g+3][0..nb) and the rows s, s + S, ... of every staged
-// tile (G = ceil(na/4) groups, S = 256 / G row slices); each row costs it
-// two 32-byte A loads and nb/2 B loads from shared memory for 4 nb FMAs.
-// The slices are summed through shared memory at the end.
-template <int NB>
+// carries enough independent accumulators and the loads are hidden).
+// Thread (g, s) owns the 4 x 8 outputs C[4g..4g+3][0..8) and the rows s,
+// s + S, ... of every staged tile (G = nap/4 groups, S = 256 / G row
+// slices); each row costs it two 32-byte A loads and four 16-byte B loads
+// from shared memory for 32 FMAs.  Tiles of tr rows (the first nap columns
+// of A, nap = na rounded up to 4, and the 8 columns of B) are copied into
+// two shared buffers with cp.async, the next while the current one is
+// used.  The slices are summed through shared memory at the end.
+// Requires 16-byte aligned rows (lda, ldb even, A and B 16-byte aligned)
+// and nap <= lda.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
 __global__ void __launch_bounds__(kTnThreads) k_tn_tiled(int64_t dim, const double *__restrict__ A, int lda, int na,
                                                          const double *__restrict__ B, int ldb,
                                                          double *__restrict__ part, int64_t rows_per_blk, int tr) {
     extern __shared__ double sm[];
-    const int nap = (na + 3) & ~3;       // A tile row length (padded to 4)
-    double *As = sm;                     // [tr][nap]
-    double *Bs = sm + (size_t)tr * nap;  // [tr][NB]
+    const int nap = (na + 3) & ~3;
+    const int rowlen = nap + 8;                  // one staged row: A part, then B part
+    double *buf[2] = {sm, sm + (size_t)tr * rowlen};
     const int G = nap / 4;
     const int S = kTnThreads / G;
     const int g = threadIdx.x % G, sl = threadIdx.x / G;
     const bool active = sl < S;
-    double acc[4][NB];
+    double acc[4][8];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int v = 0; v < NB; ++v) acc[a][v] = 0.0;
+        for (int v = 0; v < 8; ++v) acc[a][v] = 0.0;
     const int64_t r0 = blockIdx.x * rows_per_blk;
     const int64_t r1 = min(dim, r0 + rows_per_blk);
-    for (int64_t t0 = r0; t0 < r1; t0 += tr) {
+    const int ntiles = (int)((r1 - r0 + tr - 1) / tr);
+    const int chunks = rowlen / 2;               // 16-byte pieces per staged row
+    auto stage = [&](int tile, double *dst) {
+        const int64_t t0 = r0 + (int64_t)tile * tr;
         const int rows = (int)min((int64_t)tr, r1 - t0);
-        __syncthreads();
-        for (int e = threadIdx.x; e < rows * nap; e += kTnThreads) {
-            const int r = e / nap, u = e - r * nap;
-            As[e] = u < na ? A[(t0 + r) * lda + u] : 0.0;
+        for (int e = threadIdx.x; e < rows * chunks; e += kTnThreads) {
+            const int r = e / chunks, c = e - r * chunks;
+            const double *src = 2 * c < nap ? A + (t0 + r) * lda + 2 * c : B + (t0 + r) * ldb + (2 * c - nap);
+            cp_async16(dst + (size_t)r * rowlen + 2 * c, src);
         }
-        for (int e = threadIdx.x; e < rows * NB; e += kTnThreads) {
-            const int r = e / NB, v = e - r * NB;
-            Bs[e] = B[(t0 + r) * ldb + v];
+        cp_async_commit();
+    };
+    if (ntiles > 0) stage(0, buf[0]);
+    for (int tile = 0; tile < ntiles; ++tile) {
+        if (tile + 1 < ntiles) {
+            stage(tile + 1, buf[(tile + 1) & 1]);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
         }
         __syncthreads();
+        const double *T = buf[tile & 1];
+        const int rows = (int)min((int64_t)tr, r1 - (r0 + (int64_t)tile * tr));
         if (active) {
             for (int r = sl; r < rows; r += S) {
-                const double *ar = As + (size_t)r * nap + 4 * g;
-                const double a0 = ar[0], a1 = ar[1], a2 = ar[2], a3 = ar[3];
-                const double *br = Bs + (size_t)r * NB;
+                const double *ar = T + (size_t)r * rowlen;
+                const double2 a01 = *reinterpret_cast<const double2 *>(ar + 4 * g);
+                const double2 a23 = *reinterpret_cast<const double2 *>(ar + 4 * g + 2);
+                const double2 *br = reinterpret_cast<const double2 *>(ar + nap);
 #pragma unroll
-                for (int v = 0; v < NB; ++v) {
-                    const double bv = br[v];
-                    acc[0][v] = fma(a0, bv, acc[0][v]);
-                    acc[1][v] = fma(a1, bv, acc[1][v]);
-                    acc[2][v] = fma(a2, bv, acc[2][v]);
-                    acc[3][v] = fma(a3, bv, acc[3][v]);
+                for (int q = 0; q < 4; ++q) {
+                    const double2 bv = br[q];
+                    acc[0][2 * q] = fma(a01.x, bv.x, acc[0][2 * q]);
+                    acc[1][2 * q] = fma(a01.y, bv.x, acc[1][2 * q]);
+                    acc[2][2 * q] = fma(a23.x, bv.x, acc[2][2 * q]);
+                    acc[3][2 * q] = fma(a23.y, bv.x, acc[3][2 * q]);
+                    acc[0][2 * q + 1] = fma(a01.x, bv.y, acc[0][2 * q + 1]);
+                    acc[1][2 * q + 1] = fma(a01.y, bv.y, acc[1][2 * q + 1]);
+                    acc[2][2 * q + 1] = fma(a23.x, bv.y, acc[2][2 * q + 1]);
+                    acc[3][2 * q + 1] = fma(a23.y, bv.y, acc[3][2 * q + 1]);
                 }
             }
         }
+        __syncthreads();   // the buffer is refilled two tiles later
     }
     // sum the S row slices: red[sl][4g + a][v]
-    __syncthreads();
     double *red = sm;
-    const int nout = nap * NB;
+    const int nout = nap * 8;
     if (active) {
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int v = 0; v < NB; ++v) red[(size_t)sl * nout + (4 * g + a) * NB + v] = acc[a][v];
+            for (int v = 0; v < 8; ++v) red[(size_t)sl * nout + (4 * g + a) * 8 + v] = acc[a][v];
     }
     __syncthreads();
-    for (int o = threadIdx.x; o < na * NB; o += kTnThreads) {
+    for (int o = threadIdx.x; o < na * 8; o += kTnThreads) {
         double t = 0.0;
         for (int q = 0; q < S; ++q) t += red[(size_t)q * nout + o];
-        part[(int64_t)blockIdx.x * na * NB + o] = t;
+        part[(int64_t)blockIdx.x * na * 8 + o] = t;
     }
 }
 
@@ -275,7 +303,7 @@ struct Solver {
         if (!attr) {
             CI_CUDA(cudaFuncSetAttribute(k_tn_partial, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)(sizeof(double) * kTR * (kMaxNa + 8))));
-            CI_CUDA(cudaFuncSetAttribute(k_tn_tiled<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            CI_CUDA(cudaFuncSetAttribute(k_tn_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)std::max(kTnSmem, sizeof(double) * kTnThreads * 8 * 4)));
             attr = true;
         }
@@ -299,15 +327,17 @@ struct Solver {
     // host != null, copied to host.
     void tn(const double *A, int lda, int na, const double *B, int ldb, int nb, double *Cout,
             std::vector<double> *host) {
-        if (nb == 8) {
-            // rows per staged tile: the tile and the slice sums share one
-            // buffer of at most kTnSmem bytes
-            const int nap = (na + 3) & ~3;
+        const int nap = (na + 3) & ~3;
+        const bool aligned = ((uintptr_t)A % 16 == 0) && ((uintptr_t)B % 16 == 0) && lda % 2 == 0 && ldb % 2 == 0 &&
+                             nap <= lda;
+        if (nb == 8 && aligned) {
+            // two staged tiles, later reused for the slice sums, in at most
+            // kTnSmem bytes
             const int S = kTnThreads / (nap / 4);
-            int tr = (int)(kTnSmem / sizeof(double)) / (nap + 8);
-            if (tr > 256) tr = 256;
-            const size_t smem = sizeof(double) * std::max((size_t)tr * (nap + 8), (size_t)S * nap * 8);
-            launch("k_tn_partial", k_tn_tiled<8>, nblk, kTnThreads, smem, s, dim, A, lda, na, B, ldb, part.ptr,
+            int tr = (int)(kTnSmem / sizeof(double)) / (2 * (nap + 8));
+            if (tr > 128) tr = 128;
+            const size_t smem = sizeof(double) * std::max((size_t)2 * tr * (nap + 8), (size_t)S * nap * 8);
+            launch("k_tn_partial", k_tn_tiled, nblk, kTnThreads, smem, s, dim, A, lda, na, B, ldb, part.ptr,
                    rows_per_blk, tr);
         } else {
             const size_t smem = sizeof(double) * kTR * (na + nb);
