@@ -21,6 +21,24 @@ std::mutex g_mu;
 bool g_on = false;
 std::vector<Pending *> g_pending;
 std::map<std::string, Stat> g_stats;
+std::vector<cudaEvent_t> g_free;   // recycled events (creating one per launch costs host time)
+
+cudaEvent_t take_event() {
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (!g_free.empty()) {
+            cudaEvent_t e = g_free.back();
+            g_free.pop_back();
+            return e;
+        }
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
 
 void drain_locked() {
     for (Pending *p : g_pending) {
@@ -30,8 +48,8 @@ void drain_locked() {
             s.launches += 1;
             s.ms += ms;
         }
-        cudaEventDestroy(p->a);
-        cudaEventDestroy(p->b);
+        g_free.push_back(p->a);
+        g_free.push_back(p->b);
         delete p;
     }
     g_pending.clear();
@@ -42,9 +60,11 @@ void drain_locked() {
 bool trace_on() { return g_on; }
 
 void trace_begin(const char *name, cudaStream_t s, void **token) {
-    Pending *p = new Pending{name, nullptr, nullptr};
-    if (cudaEventCreate(&p->a) != cudaSuccess || cudaEventCreate(&p->b) != cudaSuccess) {
-        cudaGetLastError();
+    Pending *p = new Pending{name, take_event(), take_event()};
+    if (!p->a || !p->b) {
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (p->a) g_free.push_back(p->a);
+        if (p->b) g_free.push_back(p->b);
         delete p;
         *token = nullptr;
         return;
