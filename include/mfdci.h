@@ -178,6 +178,21 @@ ci_status ci_get_species_conn(const ci_problem *p, int32_t species, int64_t *ptr
  * total; row_cnt (nullable, host or device, int32 [dim]) the per-row counts. */
 ci_status ci_count_nnz(ci_problem *p, int64_t *nnz, int32_t *row_cnt, void *stream);
 
+/* ---- Observables (Fig. 1 lines 16-20, Sec. 2.4, Eq. 2) ------------------ */
+
+/* Expectation values a[k][v] = sum_ij X[i][v] (O_k)_ij X[j][v] of m two-body
+ * operators O_k over the problem's basis, for n vectors.  O_k has the pp, nn
+ * and pn TBMEs of the CI_TBME_SEED recipe with seed op_seeds[k] and no
+ * one-body part; its elements are evaluated on the fly by the Slater-Condon
+ * rules of the Hamiltonian build (FP64 tables) and never stored.
+ *   op_seeds  host, m seeds; m in 1..4096.
+ *   X         device, double [dim][n] in basis order, n in 1..8.
+ *   a         host, double [m][n] (written; the stream is synchronised).
+ * The problem's basis and FP64 species connectivity are built on first use.
+ * Errors: CI_ERR_INVALID_ARG (sizes, NULL or host X). */
+ci_status ci_observables(ci_problem *p, const uint64_t *op_seeds, int32_t m, const double *X, int32_t n,
+                         double *a, void *stream);
+
 /* ---- Nonzero-count benchmark (Sec. 3.1, Listings 1-2, Figs. 3-4) ------- */
 
 /* Forms of the pair test of ci_count_pairs; all give the same counts. */

@@ -18,9 +18,9 @@ than itself):
   plain definition of "lowest k eigenvalues".
 """
 
-from .core import OracleProblem, build_library, count_pairs, exclusive_scan, spmm
+from .core import OracleProblem, build_library, count_pairs, exclusive_scan, expectation_values, spmm
 from .eig import lowest_dense, lowest_sparse, dense_from_csr
 from . import brute
 
-__all__ = ["OracleProblem", "build_library", "count_pairs", "exclusive_scan", "spmm",
+__all__ = ["OracleProblem", "build_library", "count_pairs", "exclusive_scan", "expectation_values", "spmm",
            "lowest_dense", "lowest_sparse", "dense_from_csr", "brute"]

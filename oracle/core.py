@@ -202,6 +202,17 @@ class OracleProblem:
         return self.lib.orc_count_difference(_ptr(x), _ptr(y), occ.shape[1])
 
 
+def expectation_values(row_ptr, cols, vals, X):
+    """a[v] = sum_ij X[i, v] O_ij X[j, v] for a CSR operator O (Fig. 1 line 20,
+    Eq. 2 with the vectors c_i of line 20): the row sums of O X, dotted with X
+    column by column (the SpMM of ``spmm`` is the one product)."""
+    X = np.asarray(X, dtype=np.float64)
+    if X.ndim == 1:
+        X = X[:, None]
+    Y = spmm(row_ptr, cols, vals, X)
+    return np.einsum("iv,iv->v", X, Y)
+
+
 def count_pairs(mbs, rows=None, max_diff=4):
     """Count benchmark of Sec. 3.1 (Listing 2): for each state i in rows (all
     states by default) the number of states j of mbs [n][N] (uint16,

@@ -153,6 +153,18 @@ class Problem:
         check(lib().ci_count_nnz(self._h, C.byref(nnz), _ptr(row_cnt), _stream(stream)), "ci_count_nnz")
         return nnz.value
 
+    # -- Fig. 1 lines 16-20 ----------------------------------------------
+    def observables(self, op_seeds, X, stream=None):
+        """Expectation values a[k, v] = X[:, v]^T O_k X[:, v] (numpy [m, n]) of
+        the seeded two-body operators op_seeds; X is a device float64 tensor
+        [dim, n] (n <= 8)."""
+        seeds = np.ascontiguousarray(np.asarray(op_seeds, dtype=np.uint64).reshape(-1))
+        n = 1 if X.dim() == 1 else int(X.shape[1])
+        a = np.zeros((len(seeds), n), np.float64)
+        check(lib().ci_observables(self._h, _ptr(seeds), len(seeds), _ptr(X), n, _ptr(a), _stream(stream)),
+              "ci_observables")
+        return a
+
     # -- Fig. 1 lines 9-14 -----------------------------------------------
     def build_H(self, vtype="f32", stream=None):
         h = C.c_void_p()

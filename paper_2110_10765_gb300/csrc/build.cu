@@ -200,9 +200,9 @@ __device__ __forceinline__ void row_bits(const RowArgs<T> &a, int s, const uint6
 //      lanes balanced over the elements (a search over segment starts);
 //   2. p' = p: the warp walks the row's L4(n) segment contiguously.
 // Returns the chunk's element count.
-template <class T>
+template <class T, class Emit>
 __device__ __forceinline__ int fill_chunk(const RowArgs<T> &a, const RowCtx &x, const ConnEntry<T> &ep, int kind,
-                                          int beg, int len, int extra, int64_t out) {
+                                          int beg, int len, int extra, int64_t out, Emit &em) {
     const int lane = threadIdx.x & 31;
     const int S = a.S;
     const int incl = warp_incl_scan_i32(len);
@@ -210,10 +210,7 @@ __device__ __forceinline__ int fill_chunk(const RowArgs<T> &a, const RowCtx &x, 
     const int64_t pos = out + (incl - len) + extra;
     const int colbase = ep.tgt;   // first basis row of the proton partner
     // 0. four protons moved: the neutrons stay, one element
-    if (kind == 0 && len == 1) {
-        a.col[pos] = colbase + x.n_local;
-        a.val[pos] = ep.val;
-    }
+    if (kind == 0 && len == 1) em.put(a, pos, colbase + x.n_local, ep.val);
     // 1. one proton moved (a -> c): L2(n)[beg, beg+len)
     const int len1 = kind == 1 ? len : 0;
     const int incl1 = warp_incl_scan_i32(len1);
@@ -247,8 +244,7 @@ __device__ __forceinline__ int fill_chunk(const RowArgs<T> &a, const RowCtx &x, 
                 const T h = pval + sum_over_bits<T>(u, nb0, nb1);
                 v = info_neg(pinfo) ? -h : h;
             }
-            a.col[jpos + k] = jcol + en.local;
-            a.val[jpos + k] = v;
+            em.put(a, jpos + k, jcol + en.local, v);
         }
     }
     // 2. p' = p: every same-2M neutron partner of n, L4(n)[0, len)
@@ -284,8 +280,7 @@ __device__ __forceinline__ int fill_chunk(const RowArgs<T> &a, const RowCtx &x, 
                 }
                 v = h;
             }
-            a.col[pos2 + k] = col2 + en.local;
-            a.val[pos2 + k] = v;
+            em.put(a, pos2 + k, col2 + en.local, v);
         }
     }
     return total;
@@ -309,8 +304,68 @@ __device__ __forceinline__ void load_partner(const RowArgs<T> &a, const RowCtx &
 // m4), a partner of a higher slot by all m4 of them.  Then the O4 partners
 // (one element each) go between, after as many slot-0 O2 elements as their
 // own cross rank says.
+// Every element (pos, col, value) of a row goes to an emitter: StoreEmit
+// writes the CSR arrays; ApplyEmit multiplies by X on the fly (no storage)
+// for the expectation values of Fig. 1 lines 16-20.
 template <class T>
-__global__ void __launch_bounds__(256) k_fill_rows(const RowArgs<T> *args, const int64_t *row_off, int G) {
+struct StoreEmit {
+    __device__ __forceinline__ void init() {}
+    __device__ __forceinline__ void put(const RowArgs<T> &a, int64_t pos, int c, T v) {
+        a.col[pos] = c;
+        a.val[pos] = v;
+    }
+    __device__ __forceinline__ void end_row(int64_t) {}
+    __device__ __forceinline__ void finish(double *) {}
+};
+
+// y_i = sum_j O_ij X[j][0..8) accumulated per lane, reduced per row, then
+// tot += X[i] * y_i (lane 0); at the end the block's tot goes to part.
+template <class T>
+struct ApplyEmit {
+    const double *X = nullptr;   // [dim][8]
+    double acc[8], tot[8];
+    __device__ __forceinline__ void init() {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[q] = tot[q] = 0.0;
+    }
+    __device__ __forceinline__ void put(const RowArgs<T> &, int64_t, int c, T v) {
+        const double2 *xc = reinterpret_cast<const double2 *>(X + (int64_t)c * 8);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const double2 t = __ldg(xc + q);
+            acc[2 * q] = fma((double)v, t.x, acc[2 * q]);
+            acc[2 * q + 1] = fma((double)v, t.y, acc[2 * q + 1]);
+        }
+    }
+    __device__ __forceinline__ void end_row(int64_t r) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            double y = acc[q];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
+            if ((threadIdx.x & 31) == 0) tot[q] = fma(X[r * 8 + q], y, tot[q]);
+            acc[q] = 0.0;
+        }
+    }
+    __device__ __forceinline__ void finish(double *part) {
+        __shared__ double red[8][8];
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        if (lane == 0)
+#pragma unroll
+            for (int q = 0; q < 8; ++q) red[w][q] = tot[q];
+        __syncthreads();
+        if (threadIdx.x < 8) {
+            double t = 0.0;
+            for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i][threadIdx.x];
+            part[(int64_t)blockIdx.x * 8 + threadIdx.x] = t;
+        }
+    }
+};
+
+template <class T, class Emit>
+__global__ void __launch_bounds__(256) k_rows(const RowArgs<T> *args, const int64_t *row_off, int G, Emit em,
+                                              double *part) {
+    em.init();
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -327,7 +382,7 @@ __global__ void __launch_bounds__(256) k_fill_rows(const RowArgs<T> *args, const
         x.l2b = a.l2_ptr[n];
         x.l4b = a.l4_ptr[n];
         const int m4 = o4_count<T>(a, p, n);
-        const int64_t row0 = a.row_ptr[r];
+        const int64_t row0 = a.row_ptr ? a.row_ptr[r] : 0;   // no output positions when applying
         int64_t out = row0;       // O2 elements placed so far (O4 ones not counted)
         int below = 0;            // O2 elements of the slots below p's own
         int m2 = 0;               // admissible O2 partners of p's own slot
@@ -343,7 +398,7 @@ __global__ void __launch_bounds__(256) k_fill_rows(const RowArgs<T> *args, const
             for (int o = 16; o > 0; o >>= 1) bl += __shfl_xor_sync(0xffffffffu, bl, o);
             below += bl;
             m2 += __popc(__ballot_sync(0xffffffffu, ok && ds == 0));
-            out += fill_chunk<T>(a, x, ep, kind, beg, len, extra, out);
+            out += fill_chunk<T, Emit>(a, x, ep, kind, beg, len, extra, out, em);
         });
         if (m4 > 0) {
             // slot-0 O2 partners: the admissible ones are the first m2 of the
@@ -376,20 +431,18 @@ __global__ void __launch_bounds__(256) k_fill_rows(const RowArgs<T> *args, const
                     const int part = __shfl_sync(0xffffffffu, incl, idx > 0 ? idx - 1 : 0);
                     lensum += idx >= 32 ? tot : (idx > 0 ? part : 0);
                 }
-                if (ok) {
-                    const int64_t pos = row0 + below + k + lensum;
-                    a.col[pos] = e4.tgt + x.n_local;
-                    a.val[pos] = e4.val;
-                }
+                if (ok) em.put(a, row0 + below + k + lensum, e4.tgt + x.n_local, e4.val);
             }
         }
+        em.end_row(r);
     }
+    em.finish(part);
 }
 
 template <class T>
-static RowArgs<T> row_args(Problem *p) {
+static RowArgs<T> row_args(Problem *p, const Tables<T> *tab = nullptr, const ConnEntry<T> *ents = nullptr) {
     Connectivity<T> &c = p->conn<T>();
-    Tables<T> &t = p->tables<T>();
+    const Tables<T> &t = tab ? *tab : p->tables<T>();
     SpeciesList &P = p->sp[0], &Nn = p->sp[1];
     RowArgs<T> a{};
     a.dim = p->dim; a.S = p->S; a.W = P.W; a.nq = Nn.nq; a.nds = p->nds; a.K = p->K;
@@ -400,6 +453,9 @@ static RowArgs<T> row_args(Problem *p) {
     a.o_ptr = c.outer.ptr; a.o4_ptr = c.outer4.ptr; a.l2_ptr = c.l2.ptr; a.l4_ptr = c.l4.ptr;
     a.o_ent = c.outer.ent; a.o4_ent = c.outer4.ent; a.l2_ent = c.l2.ent; a.l4_ent = c.l4.ent;
     a.o_xr = c.outer.xr;
+    if (ents) {  // another operator's entries in the same layout
+        a.o_ent = ents; a.o4_ent = ents; a.l2_ent = ents; a.l4_ent = ents;
+    }
     a.seg2 = c.seg2.ptr; a.seg4 = c.seg4.ptr; a.qmin2 = c.qmin2.ptr; a.oseg2 = c.oseg2.ptr; a.oseg4 = c.oseg4.ptr;
     a.Upn = t.Upn.ptr; a.Wpn = t.Wpn.ptr; a.Dpn = t.Dpn.ptr; a.Tpn = t.Tpn.ptr;
     return a;
@@ -465,8 +521,8 @@ static void fill_group_t(const std::vector<Problem *> &ps, GroupCSR *g, cudaStre
     DevBuf<unsigned char> dargs;
     DevBuf<int64_t> doff;
     upload_args<T>(args, g->row_off, dargs, doff, s);
-    launch("k_fill_rows", k_fill_rows<T>, row_grid(rows), 256, 0, s, (const RowArgs<T> *)dargs.ptr,
-           (const int64_t *)doff.ptr, (int)ps.size());
+    launch("k_fill_rows", k_rows<T, StoreEmit<T>>, row_grid(rows), 256, 0, s, (const RowArgs<T> *)dargs.ptr,
+           (const int64_t *)doff.ptr, (int)ps.size(), StoreEmit<T>{}, (double *)nullptr);
 }
 
 // Fig. 1 lines 9-14 for a counted group: allocate and fill col / val.
@@ -476,6 +532,28 @@ void fill_group(const std::vector<Problem *> &ps, GroupCSR *g, cudaStream_t s) {
     if (g->prec == 0) fill_group_t<float>(ps, g, s);
     else fill_group_t<double>(ps, g, s);
 }
+
+template <class T>
+int observable_apply(Problem *p, const Tables<T> &t, const ConnEntry<T> *ents, const double *X8, double *part,
+                     cudaStream_t s) {
+    std::vector<RowArgs<T>> args{row_args<T>(p, &t, ents)};
+    std::vector<int64_t> row_off{0, p->dim};
+    if (p->dim == 0) return 0;
+    DevBuf<unsigned char> dargs;
+    DevBuf<int64_t> doff;
+    upload_args<T>(args, row_off, dargs, doff, s);
+    ApplyEmit<T> em{};
+    em.X = X8;
+    const int grid = row_grid(p->dim);
+    launch("k_observable_rows", k_rows<T, ApplyEmit<T>>, grid, 256, 0, s, (const RowArgs<T> *)dargs.ptr,
+           (const int64_t *)doff.ptr, 1, em, part);
+    return grid;
+}
+
+template int observable_apply<float>(Problem *, const Tables<float> &, const ConnEntry<float> *, const double *,
+                                     double *, cudaStream_t);
+template int observable_apply<double>(Problem *, const Tables<double> &, const ConnEntry<double> *, const double *,
+                                      double *, cudaStream_t);
 
 void build_matrix(Problem *p, int vtype, Matrix *m, cudaStream_t s) {
     if (vtype != CI_F32 && vtype != CI_F64)

@@ -461,9 +461,9 @@ __global__ void k_xrank(const XrankJob *jobs, const int64_t *job_row, int njobs)
 }
 
 template <class T>
-static FilterArgs<T> filter_job(Problem *p, int species, int modes) {
+static FilterArgs<T> filter_job(Problem *p, int species, int modes, const Tables<T> *tab = nullptr) {
     SpeciesList &sp = p->sp[species];
-    Tables<T> &t = p->tables<T>();
+    const Tables<T> &t = tab ? *tab : p->tables<T>();
     FilterArgs<T> a{};
     a.n = sp.n; a.A = sp.A; a.S = p->S; a.W = sp.W; a.modes = modes;
     a.bits = sp.d_bits.ptr; a.twoM = sp.d_twoM.ptr; a.local = sp.d_local.ptr; a.occ = sp.d_occ.ptr;
@@ -606,6 +606,27 @@ void species_filter_group(const std::vector<Problem *> &ps_in, cudaStream_t s) {
     for (Problem *p : ps) p->conn<T>().ready = true;
 }
 
+template <class T>
+void operator_entries(Problem *p, const Tables<T> &t, ConnEntry<T> *ents, cudaStream_t s) {
+    Connectivity<T> &c = p->conn<T>();
+    if (!c.ready) fail(CI_ERR_STATE, "species connectivity not built");
+    std::vector<FilterArgs<T>> ej1, ej2;
+    const ConnList<T> *ls[kModes] = {&c.outer, &c.l2, &c.l4, &c.outer4};
+    for (int m = 0; m < kModes; ++m) {
+        const bool prot = m == CONN_OUTER || m == CONN_O4;
+        FilterArgs<T> j = filter_job<T>(p, prot ? 0 : 1, 1 << m, &t);
+        j.n = ls[m]->n;
+        j.ptr[m] = ls[m]->ptr;
+        j.ent = ents;
+        j.tgt = const_cast<int32_t *>(ls[m]->tgt);
+        (j.W == 1 ? ej1 : ej2).push_back(j);
+    }
+    launch_entries<T, 1>(ej1, s);
+    launch_entries<T, 2>(ej2, s);
+}
+
+template void operator_entries<float>(Problem *, const Tables<float> &, ConnEntry<float> *, cudaStream_t);
+template void operator_entries<double>(Problem *, const Tables<double> &, ConnEntry<double> *, cudaStream_t);
 template void species_filter_group<float>(const std::vector<Problem *> &, cudaStream_t);
 template void species_filter_group<double>(const std::vector<Problem *> &, cudaStream_t);
 

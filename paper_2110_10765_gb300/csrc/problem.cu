@@ -312,58 +312,47 @@ void problem_create(const ci_problem_desc *d, Problem *p) {
 
 // Stage the tables of precision T of every problem in ps that lacks them,
 // in one launch.
+// Staging jobs that fill the tables t of problem p from the TBME sources
+// src[pp, nn, pn] and the one-body energies eps64 (device, S doubles).
 template <class T>
-void stage_tables_group(const std::vector<Problem *> &ps, cudaStream_t s) {
-    std::vector<StageJob<T>> jobs;
-    std::vector<int64_t> off(1, 0);
+static void add_stage_jobs(Problem *p, Tables<T> &t, const TbmeSrc src[3], const double *eps64,
+                           std::vector<StageJob<T>> &jobs, std::vector<int64_t> &off) {
     auto add = [&](const StageJob<T> &j) {
         if (j.total <= 0) return;
         jobs.push_back(j);
         off.push_back(off.back() + j.total);
     };
-    std::vector<Problem *> todo;
-    for (Problem *p : ps) {
-        Tables<T> &t = p->tables<T>();
-        if (t.ready) continue;
-        todo.push_back(p);
-        const int S = p->S;
-        const int64_t S3 = (int64_t)S * S * S, S2 = (int64_t)S * S;
-        t.eps.alloc(S);
-        t.Cpp.alloc(p->like_size); t.Cnn.alloc(p->like_size); t.Tpn.alloc(p->tr_size);
-        t.Upp.alloc(S3); t.Unn.alloc(S3); t.Upn.alloc(S3); t.Wpn.alloc(S3);
-        t.Dpp.alloc(S2); t.Dnn.alloc(S2); t.Dpn.alloc(S2);
-        TbmeSrc src[3];
-        for (int c = 0; c < 3; ++c) {
-            src[c].S = S;
-            src[c].source = p->tbme_source;
-            src[c].dtype = p->tbme_dtype;
-            src[c].flat = p->flat[c].ptr;
-            src[c].seed = p->tbme_seed;
-            src[c].channel = c;
-            src[c].twom = p->d_twom.ptr;
-        }
-        StageJob<T> j{};
-        j.kind = 0; j.mode = 0; j.G = p->like_G; j.goff = p->lg_off.ptr; j.gncol = p->lg_ncol.ptr;
-        j.grows = p->lg_rows.ptr; j.gcols = p->lg_cols.ptr; j.items = p->lg_items.ptr; j.total = p->like_size;
-        j.src = src[0]; j.out = t.Cpp.ptr; add(j);
-        j.src = src[1]; j.out = t.Cnn.ptr; add(j);
-        j.mode = 1; j.G = p->tr_G; j.goff = p->tg_off.ptr; j.gncol = p->tg_ncol.ptr; j.grows = p->tg_rows.ptr;
-        j.gcols = p->tg_cols.ptr; j.items = p->tg_items.ptr; j.total = p->tr_size; j.src = src[2]; j.out = t.Tpn.ptr;
-        add(j);
-        StageJob<T> k{};
-        k.kind = 1; k.total = S3;
-        k.src = src[0]; k.mode = 0; k.out = t.Upp.ptr; add(k);
-        k.src = src[1]; k.out = t.Unn.ptr; add(k);
-        k.src = src[2]; k.out = t.Upn.ptr; add(k);
-        k.mode = 1; k.out = t.Wpn.ptr; add(k);
-        StageJob<T> d{};
-        d.kind = 2; d.total = S2;
-        d.src = src[0]; d.out = t.Dpp.ptr; add(d);
-        d.src = src[1]; d.out = t.Dnn.ptr; add(d);
-        d.src = src[2]; d.out = t.Dpn.ptr; add(d);
-        StageJob<T> e{};
-        e.kind = 3; e.total = S; e.src = src[0]; e.eps64 = p->d_eps.ptr; e.out = t.eps.ptr; add(e);
-    }
+    const int S = p->S;
+    const int64_t S3 = (int64_t)S * S * S, S2 = (int64_t)S * S;
+    t.eps.alloc(S);
+    t.Cpp.alloc(p->like_size); t.Cnn.alloc(p->like_size); t.Tpn.alloc(p->tr_size);
+    t.Upp.alloc(S3); t.Unn.alloc(S3); t.Upn.alloc(S3); t.Wpn.alloc(S3);
+    t.Dpp.alloc(S2); t.Dnn.alloc(S2); t.Dpn.alloc(S2);
+    StageJob<T> j{};
+    j.kind = 0; j.mode = 0; j.G = p->like_G; j.goff = p->lg_off.ptr; j.gncol = p->lg_ncol.ptr;
+    j.grows = p->lg_rows.ptr; j.gcols = p->lg_cols.ptr; j.items = p->lg_items.ptr; j.total = p->like_size;
+    j.src = src[0]; j.out = t.Cpp.ptr; add(j);
+    j.src = src[1]; j.out = t.Cnn.ptr; add(j);
+    j.mode = 1; j.G = p->tr_G; j.goff = p->tg_off.ptr; j.gncol = p->tg_ncol.ptr; j.grows = p->tg_rows.ptr;
+    j.gcols = p->tg_cols.ptr; j.items = p->tg_items.ptr; j.total = p->tr_size; j.src = src[2]; j.out = t.Tpn.ptr;
+    add(j);
+    StageJob<T> k{};
+    k.kind = 1; k.total = S3;
+    k.src = src[0]; k.mode = 0; k.out = t.Upp.ptr; add(k);
+    k.src = src[1]; k.out = t.Unn.ptr; add(k);
+    k.src = src[2]; k.out = t.Upn.ptr; add(k);
+    k.mode = 1; k.out = t.Wpn.ptr; add(k);
+    StageJob<T> d{};
+    d.kind = 2; d.total = S2;
+    d.src = src[0]; d.out = t.Dpp.ptr; add(d);
+    d.src = src[1]; d.out = t.Dnn.ptr; add(d);
+    d.src = src[2]; d.out = t.Dpn.ptr; add(d);
+    StageJob<T> e{};
+    e.kind = 3; e.total = S; e.src = src[0]; e.eps64 = eps64; e.out = t.eps.ptr; add(e);
+}
+
+template <class T>
+static void run_stage_jobs(const std::vector<StageJob<T>> &jobs, const std::vector<int64_t> &off, cudaStream_t s) {
     if (jobs.empty()) return;
     DevBuf<StageJob<T>> djobs((size_t)jobs.size());
     DevBuf<int64_t> doff(off.size());
@@ -371,9 +360,56 @@ void stage_tables_group(const std::vector<Problem *> &ps, cudaStream_t s) {
     CI_CUDA(cudaMemcpyAsync(doff.ptr, off.data(), sizeof(int64_t) * off.size(), cudaMemcpyHostToDevice, s));
     launch("k_stage", k_stage<T>, grid_for(off.back(), 256, sm_count() * 16), 256, 0, s, (const StageJob<T> *)djobs.ptr,
            (const int64_t *)doff.ptr, (int)jobs.size());
+}
+
+template <class T>
+void stage_tables_group(const std::vector<Problem *> &ps, cudaStream_t s) {
+    std::vector<StageJob<T>> jobs;
+    std::vector<int64_t> off(1, 0);
+    std::vector<Problem *> todo;
+    for (Problem *p : ps) {
+        Tables<T> &t = p->tables<T>();
+        if (t.ready) continue;
+        todo.push_back(p);
+        TbmeSrc src[3];
+        for (int c = 0; c < 3; ++c) {
+            src[c].S = p->S;
+            src[c].source = p->tbme_source;
+            src[c].dtype = p->tbme_dtype;
+            src[c].flat = p->flat[c].ptr;
+            src[c].seed = p->tbme_seed;
+            src[c].channel = c;
+            src[c].twom = p->d_twom.ptr;
+        }
+        add_stage_jobs<T>(p, t, src, p->d_eps.ptr, jobs, off);
+    }
+    run_stage_jobs<T>(jobs, off, s);
     for (Problem *p : todo) p->tables<T>().ready = true;
 }
 
+// Tables of a two-body operator with the seeded TBMEs of `seed` (the
+// recipe of CI_TBME_SEED) and no one-body part.
+template <class T>
+void stage_operator_tables(Problem *p, uint64_t seed, Tables<T> &t, const double *zero_eps, cudaStream_t s) {
+    std::vector<StageJob<T>> jobs;
+    std::vector<int64_t> off(1, 0);
+    TbmeSrc src[3];
+    for (int c = 0; c < 3; ++c) {
+        src[c].S = p->S;
+        src[c].source = CI_TBME_SEED;
+        src[c].dtype = CI_F64;
+        src[c].flat = nullptr;
+        src[c].seed = seed;
+        src[c].channel = c;
+        src[c].twom = p->d_twom.ptr;
+    }
+    add_stage_jobs<T>(p, t, src, zero_eps, jobs, off);
+    run_stage_jobs<T>(jobs, off, s);
+    t.ready = true;
+}
+
+template void stage_operator_tables<float>(Problem *, uint64_t, Tables<float> &, const double *, cudaStream_t);
+template void stage_operator_tables<double>(Problem *, uint64_t, Tables<double> &, const double *, cudaStream_t);
 template void stage_tables_group<float>(const std::vector<Problem *> &, cudaStream_t);
 template void stage_tables_group<double>(const std::vector<Problem *> &, cudaStream_t);
 

@@ -210,6 +210,20 @@ struct GroupCSR {
 void problem_create(const ci_problem_desc *d, Problem *p);
 void enumerate_basis(Problem *p, cudaStream_t s);
 template <class T> void stage_tables_group(const std::vector<Problem *> &ps, cudaStream_t s);
+// Tables of a two-body operator drawn by the seeded recipe (no one-body
+// part; zero_eps: S zero doubles on the device).
+template <class T>
+void stage_operator_tables(Problem *p, uint64_t seed, Tables<T> &t, const double *zero_eps, cudaStream_t s);
+// Slater-Condon entries of every connectivity list with the tables t into
+// ents (the layout of the lists' shared entry array).
+template <class T>
+void operator_entries(Problem *p, const Tables<T> &t, ConnEntry<T> *ents, cudaStream_t s);
+// sum_i X[i][q] (O X)[i][q] for q < 8 of the operator with tables t and
+// entries ents; X [dim][8] FP64 on the device; one partial per block in
+// part (nblk x 8, device); returns nblk.
+template <class T>
+int observable_apply(Problem *p, const Tables<T> &t, const ConnEntry<T> *ents, const double *X8, double *part,
+                     cudaStream_t s);
 template <class T> void species_filter_group(const std::vector<Problem *> &ps, cudaStream_t s);
 template <class T> void species_filter(Problem *p, cudaStream_t s) { species_filter_group<T>({p}, s); }
 // count (and optionally fill) the rows of every problem of ps in one launch each

@@ -1,0 +1,71 @@
+"""Expectation values of seeded two-body operators (Fig. 1 lines 16-20)
+evaluated on the fly on the GPU, against the oracle's operator CSR."""
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from helpers import inputs, preset_inputs, gpu_problem
+
+pytestmark = pytest.mark.gpu
+
+
+def _oracle_values(inp, seeds, X):
+    out, bound = [], []
+    for sd in seeds:
+        T = synth.tbme_tables(inp["sp"], int(sd), np.float64)
+        o = oracle.OracleProblem(inp["sp"], inp["Z"], inp["N"], inp["nmax"], inp["twoM"],
+                                 np.zeros(len(inp["sp"]["N"])), T)
+        rp, col, val, ab = o.csr()
+        out.append(oracle.expectation_values(rp, col, val, X))
+        bound.append(oracle.expectation_values(rp, col, np.abs(val), np.abs(X)))
+    return np.array(out), np.array(bound)
+
+
+def _check(inp, seeds, n, xseed=0):
+    import torch
+    g = gpu_problem(inp)
+    dim = g.enumerate_basis()
+    X = np.random.default_rng(xseed).standard_normal((dim, n))
+    a = g.observables(seeds, torch.from_numpy(X).cuda())
+    ref, bound = _oracle_values(inp, seeds, X)
+    assert a.shape == (len(seeds), n)
+    assert np.all(np.abs(a - ref) <= 1e-11 * bound + 1e-300), np.max(np.abs(a - ref) / bound)
+
+
+@pytest.mark.parametrize("case,n", [((1, 2, 2, -1), 8), ((1, 3, 2, -1), 3), ((2, 2, 2, 1), 5),
+                                    ((2, 3, 1, 2), 1), ((2, 1, 1, -1), 8)])
+def test_observables_small(case, n):
+    _check(inputs(*case, seed=3), [11, 12, 13], n)
+
+
+def test_observables_config0():
+    _check(preset_inputs("c0"), [101, 102, 103, 104], 8, xseed=1)
+
+
+def test_observables_nmax2_subspace():
+    _check(preset_inputs("c2_sub"), [7, 8], 5, xseed=2)
+
+
+def test_observables_zero_vectors_and_single_operator():
+    import torch
+    inp = inputs(1, 2, 2, -1, seed=3)
+    g = gpu_problem(inp)
+    dim = g.enumerate_basis()
+    a = g.observables([5], torch.zeros((dim, 4), dtype=torch.float64, device="cuda"))
+    assert a.shape == (1, 4) and np.all(a == 0.0)
+
+
+def test_observables_invalid():
+    import torch
+    import paper_2110_10765_gb300 as ci
+    inp = inputs(1, 2, 2, -1, seed=3)
+    g = gpu_problem(inp)
+    dim = g.enumerate_basis()
+    with pytest.raises(ci.CIError):
+        g.observables([1], torch.zeros((dim, 9), dtype=torch.float64, device="cuda"))
+    with pytest.raises(ci.CIError):
+        g.observables([1], torch.zeros((dim, 2), dtype=torch.float64))       # host X
+    with pytest.raises(ci.CIError):
+        g.observables([], torch.zeros((dim, 2), dtype=torch.float64, device="cuda"))

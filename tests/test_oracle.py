@@ -388,3 +388,42 @@ def test_count_pairs_duplicates_and_singletons():
     mbs = np.array([[0, 1, 2, 3], [0, 1, 2, 3], [0, 1, 2, 4], [10, 11, 12, 13]], np.uint16)
     assert oracle.count_pairs(mbs).tolist() == [3, 3, 3, 1]
     assert oracle.count_pairs(mbs[:0]).tolist() == []
+
+
+# ---- observables (Fig. 1 lines 16-20) ------------------------------------------
+
+def _operator(n_shell, Z, N, nmax, seed, twoM=None):
+    """Oracle problem of the two-body operator with the TBMEs of `seed` and
+    no one-body part (oracle Slater-Condon rules), and its CSR."""
+    sp = synth.ho_sp_table(n_shell)
+    T = synth.tbme_tables(sp, seed, np.float64)
+    if twoM is None:
+        twoM = (Z + N) % 2
+    o = oracle.OracleProblem(sp, Z, N, nmax, twoM, np.zeros(len(sp["N"])), T)
+    return o, o.csr()
+
+
+def test_expectation_values_dense_and_unit_vectors():
+    o, (rp, col, val, ab) = _operator(1, 2, 2, -1, 77)
+    dense = oracle.dense_from_csr(rp, col, val, o.dim)
+    X = np.random.default_rng(1).standard_normal((o.dim, 3))
+    a = oracle.expectation_values(rp, col, val, X)
+    assert np.allclose(a, np.einsum("iv,ij,jv->v", X, dense, X), rtol=1e-13, atol=1e-12)
+    for i in (0, o.dim // 2, o.dim - 1):     # unit vector: the diagonal element
+        e = np.zeros(o.dim)
+        e[i] = 1.0
+        assert oracle.expectation_values(rp, col, val, e)[0] == o.element(i, i)[0]
+
+
+def test_operator_has_no_one_body_part_and_scales():
+    """The same TBMEs with eps = 0: H(seed) - O(seed) is the one-body
+    diagonal; a scaled vector scales the value quadratically."""
+    _, _, _, oh = _problem(1, 2, 2, -1, seed=4)
+    _, (rp, col, val, _) = _operator(1, 2, 2, -1, 4)
+    hrp, hcol, hval, _ = oh.csr()
+    assert np.array_equal(rp, hrp) and np.array_equal(col, hcol)
+    diff = oracle.dense_from_csr(hrp, hcol, hval, oh.dim) - oracle.dense_from_csr(rp, col, val, oh.dim)
+    assert np.allclose(diff - np.diag(np.diag(diff)), 0.0, atol=1e-12)
+    x = np.random.default_rng(2).standard_normal(oh.dim)
+    a1 = oracle.expectation_values(rp, col, val, x)[0]
+    assert np.isclose(oracle.expectation_values(rp, col, val, 3 * x)[0], 9 * a1, rtol=1e-12)
