@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--fp64-sample", type=int, default=12, help="problems solved one by one in FP64")
     ap.add_argument("--no-count", action="store_true", help="skip the count-benchmark leg")
     ap.add_argument("--count-n", type=int, default=131072, help="states of the count benchmark")
+    ap.add_argument("--no-observables", action="store_true", help="skip the observables leg")
+    ap.add_argument("--obs-m", type=int, default=16, help="operators of the observables leg")
     return ap.parse_args()
 
 
@@ -330,6 +332,8 @@ def run_ours(args):
                       "d2h_bytes_per_step": int(8 * p.k + 8), "ms_per_step": e2e_s / args.steps * 1e3}
     if not args.no_count:
         rec["count"] = run_count_leg(args.count_n, clock_mhz=(clk or {}).get("sm_mhz"))
+    if not args.no_observables:
+        rec["observables"] = run_observables_leg(sp, p, eps, dtab, args.obs_m)
     if not args.no_batch:
         rec["batch"], pool = run_batch_leg(args)
         if not args.no_serve:
@@ -342,6 +346,36 @@ def run_ours(args):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(rec))
+
+
+# ---------------------------------------------------------------- observables
+
+def run_observables_leg(sp, p, eps, tables, m, reps=2):
+    """Fig. 1 lines 16-20 on the benchmark workload: expectation values of m
+    seeded two-body operators in the k = 5 lowest eigenvectors, elements
+    evaluated on the fly (never stored)."""
+    import torch
+
+    import paper_2110_10765_gb300 as ci
+    prob = ci.Problem(sp, p.Z, p.N, p.nmax, p.twoM, eps, tables=tables)
+    M = prob.build_H("f32")
+    E = torch.zeros((M.dim, p.k), dtype=torch.float64, device="cuda")
+    M.lowest_eigs(k=p.k, block=p.block, evecs=E)
+    seeds = [7000 + i for i in range(m)]
+    prob.observables(seeds[:1], E)           # builds the FP64 connectivity once
+    stream = torch.cuda.current_stream()
+    ms = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        vals = prob.observables(seeds, E)
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    t = min(ms)
+    return {"operators": m, "vectors": p.k, "ms": t, "ms_per_operator": t / m,
+            "elements_per_s": M.nnz * m / (t * 1e-3), "nnz": M.nnz,
+            "first_values": [round(float(x), 9) for x in vals[0]]}
 
 
 # ---------------------------------------------------------------- count benchmark
