@@ -389,7 +389,7 @@ SMS = 152
 
 
 def run_count_leg(n, N=8, S=128, reps=5, clock_mhz=None):
-    """The paper's nonzero-count benchmark (Sec. 3.1, Figs. 3-4): n random
+    """The paper's nonzero-count benchmark (Sec. 2.1, Figs. 3-4): n random
     8-particle states over 128 s.p. states biased to low states; rate =
     n^2 / time for the three forms of the pair test."""
     import numpy as np

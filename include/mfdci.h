@@ -193,7 +193,7 @@ ci_status ci_count_nnz(ci_problem *p, int64_t *nnz, int32_t *row_cnt, void *stre
 ci_status ci_observables(ci_problem *p, const uint64_t *op_seeds, int32_t m, const double *X, int32_t n,
                          double *a, void *stream);
 
-/* ---- Nonzero-count benchmark (Sec. 3.1, Listings 1-2, Figs. 3-4) ------- */
+/* ---- Nonzero-count benchmark (Sec. 2.1, Listings 1-2, Figs. 3-4) ------- */
 
 /* Forms of the pair test of ci_count_pairs; all give the same counts. */
 typedef enum {

@@ -11,7 +11,7 @@ than itself):
 * ``ci_oracle.c`` (plain C, FP64): species determinant lists, product basis,
   difference counts, Slater-Condon matrix elements, rows / CSR of H, FP64
   SpMM, the exclusive scan of Eq. 1 and the per-state counts of the count
-  benchmark (Sec. 3.1);
+  benchmark (Sec. 2.1);
 * ``brute.py`` (pure Python): H built by applying every second-quantised
   operator term to every basis state, for tiny spaces;
 * ``eig.py``: lowest eigenvalues by LAPACK (dense) or ARPACK (sparse), the

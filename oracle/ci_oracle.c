@@ -18,7 +18,7 @@
  *     annihilation operators one at a time to the ket's occupation list;
  *   - rows of H in ascending column order, visiting every column j as in the
  *     dense count of Listing 2, and the full CSR matrix;
- *   - the count benchmark of Sec. 3.1 (Listing 2 over independent random
+ *   - the count benchmark of Sec. 2.1 (Listing 2 over independent random
  *     states in MBS form): per state, the number of states that differ from
  *     it in at most max_diff single-particle states.
  *
@@ -489,7 +489,7 @@ void orc_exclusive_scan(const int64_t *x, int64_t n, int64_t *y)
     for (int64_t i = 0; i < n; ++i) y[i + 1] = y[i] + x[i];
 }
 
-/* Count benchmark (Sec. 3.1, Listing 2).  mbs holds n states of N
+/* Count benchmark (Sec. 2.1, Listing 2).  mbs holds n states of N
  * particles, each the ascending list of its occupied s.p. states.  For each
  * of the nrows states rows[r], out[r] = the number of states j (all n,
  * j = rows[r] included) whose occupations differ from it in at most

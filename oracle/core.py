@@ -214,7 +214,7 @@ def expectation_values(row_ptr, cols, vals, X):
 
 
 def count_pairs(mbs, rows=None, max_diff=4):
-    """Count benchmark of Sec. 3.1 (Listing 2): for each state i in rows (all
+    """Count benchmark of Sec. 2.1 (Listing 2): for each state i in rows (all
     states by default) the number of states j of mbs [n][N] (uint16,
     ascending) that differ from it in at most max_diff s.p. states."""
     lib = _load()

@@ -361,7 +361,7 @@ COUNT_VARIANTS = {"hybrid": 0, "mbs": 1, "bits": 2}
 
 
 def count_pairs(mbs, S, variant="hybrid", max_diff=4, row_counts=None, stream=None):
-    """Count benchmark of Sec. 3.1 (Listing 2) on the device.
+    """Count benchmark of Sec. 2.1 (Listing 2) on the device.
 
     mbs: device uint16-compatible tensor [n, N] (torch.int16 / uint16 bits),
     each row the ascending occupied s.p. states of one state.  Returns the

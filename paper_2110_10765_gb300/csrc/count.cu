@@ -1,4 +1,4 @@
-// Nonzero-count benchmark (Sec. 3.1, Listings 1-2, Figs. 3-4): for n
+// Nonzero-count benchmark (Sec. 2.1, Listings 1-2, Figs. 3-4): for n
 // independent N-particle states in MBS form (ascending s.p. indices), the
 // number of states that differ from each in at most max_diff s.p. states.
 //

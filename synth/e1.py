@@ -1,4 +1,4 @@
-"""Inputs of the paper's nonzero-count benchmark (Sec. 3.1, Figs. 3-4).
+"""Inputs of the paper's nonzero-count benchmark (Sec. 2.1, Figs. 3-4).
 
 A state is N occupied single-particle states out of S, stored in the MBS
 form of Sec. 2.1: the ascending tuple of occupied state indices (uint16).

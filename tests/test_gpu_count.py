@@ -1,4 +1,4 @@
-"""Count benchmark (Sec. 3.1, Listings 1-2) on the GPU against the oracle.
+"""Count benchmark (Sec. 2.1, Listings 1-2) on the GPU against the oracle.
 
 Every form of the pair test (64-state prefilter + MBS, MBS only, full bit
 representation) must give the oracle's per-state counts exactly."""

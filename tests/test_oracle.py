@@ -353,7 +353,7 @@ def test_sparse_lowest_matches_dense():
     assert np.all(rq >= wd[0] - 1e-9)
 
 
-# ---- count benchmark (Sec. 3.1, Listing 2) -------------------------------------
+# ---- count benchmark (Sec. 2.1, Listing 2) -------------------------------------
 
 def _all_subsets(S, N):
     import itertools
