@@ -88,12 +88,23 @@ __global__ void __launch_bounds__(256) k_e_spmm(SlotDev *slots, const Tile *tile
             float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
             const int64_t e1 = s.rp[r + 1];
             int64_t e = s.rp[r] + pair;
-            for (; e + 16 < e1; e += 32) {
-                const int c0 = __ldcs(s.col + e), c1 = __ldcs(s.col + e + 16);
-                const float v0 = __ldcs(s.val + e), v1 = __ldcs(s.val + e + 16);
-                const float4 x0 = __ldg(X4 + (int64_t)c0 * 2 + half), x1 = __ldg(X4 + (int64_t)c1 * 2 + half);
-                a0 = fmaf(v0, x0.x, a0); a1 = fmaf(v0, x0.y, a1); a2 = fmaf(v0, x0.z, a2); a3 = fmaf(v0, x0.w, a3);
-                a0 = fmaf(v1, x1.x, a0); a1 = fmaf(v1, x1.y, a1); a2 = fmaf(v1, x1.z, a2); a3 = fmaf(v1, x1.w, a3);
+            constexpr int U = 4;   // nonzeros in flight per lane pair
+            for (; e + 16 * (U - 1) < e1; e += 16 * U) {
+                int c[U];
+                float v[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    c[u] = __ldcs(s.col + e + 16 * u);
+                    v[u] = __ldcs(s.val + e + 16 * u);
+                }
+                float4 x[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) x[u] = __ldg(X4 + (int64_t)c[u] * 2 + half);
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    a0 = fmaf(v[u], x[u].x, a0); a1 = fmaf(v[u], x[u].y, a1);
+                    a2 = fmaf(v[u], x[u].z, a2); a3 = fmaf(v[u], x[u].w, a3);
+                }
             }
             for (; e < e1; e += 16) {
                 const int c = __ldcs(s.col + e);
@@ -205,6 +216,9 @@ __global__ void __launch_bounds__(256) k_e_reduce(SlotDev *slots, int nslots, in
 // Row updates: LOC / FULL: W -= Q_cols C; QR1: Q[:, m:m+8] = W M; RAND:
 // Q[:, m+rank:m+8] -= Q[:, 0:m+rank] Cr; QR2: V = V M (in place per row);
 // RITZ: W = Q[:, 0:m_act] S[:, c0:c0+nc] (final phase).
+// QR2 (the in-place 8 x 8 update) is its own instantiation: its loop-invariant
+// 8 x 8 matrix lives in registers, which the other modes must not pay for.
+template <bool QR2>
 __global__ void __launch_bounds__(256) k_e_nn(SlotDev *slots, const Tile *tiles, const int32_t *ntiles, int MB,
                                               int phase, int mode, DensePtrs d, int c0) {
     __shared__ double Cs[EMBMAX * EB];
@@ -241,7 +255,7 @@ __global__ void __launch_bounds__(256) k_e_nn(SlotDev *slots, const Tile *tiles,
             for (int e = threadIdx.x; e < na * nb; e += blockDim.x) Cs[e] = C[e];
         }
         __syncthreads();
-        if (mode == M_QR2) {  // in place: each thread owns a whole row
+        if (QR2) {  // in place: each thread owns a whole row
             for (int rr = threadIdx.x; rr < tl.nr; rr += blockDim.x) {
                 double *row = s.Q + (tl.r0 + rr) * MB + s.m_cur;
                 double x[EB], y[EB];
@@ -256,6 +270,35 @@ __global__ void __launch_bounds__(256) k_e_nn(SlotDev *slots, const Tile *tiles,
                 }
 #pragma unroll
                 for (int v = 0; v < EB; ++v) row[v] = y[v];
+            }
+            continue;
+        }
+        if (nb == EB) {  // one row per thread, 8 accumulators, C broadcast from shared memory
+            double *dst;     // row r of the output starts at dst + r * ldd
+            int ldd;
+            bool sub;        // subtract from it (projections) or overwrite
+            switch (mode) {
+                case M_LOC:
+                case M_FULL: dst = s.W; ldd = EB; sub = true; break;
+                case M_QR1: dst = s.Q + s.m_cur; ldd = MB; sub = false; break;
+                case M_RAND: dst = s.Q + s.m_cur + s.rank; ldd = MB; sub = true; break;
+                default: dst = s.W; ldd = EB; sub = false; break;  // M_RITZ
+            }
+            for (int rr = threadIdx.x; rr < tl.nr; rr += blockDim.x) {
+                const int64_t r = tl.r0 + rr;
+                const double *Ar = A + r * lda;
+                double acc[EB];
+#pragma unroll
+                for (int v = 0; v < EB; ++v) acc[v] = 0.0;
+#pragma unroll 2
+                for (int u = 0; u < na; ++u) {
+                    const double av = Ar[u];
+#pragma unroll
+                    for (int v = 0; v < EB; ++v) acc[v] = fma(av, Cs[u * EB + v], acc[v]);
+                }
+                double *w = dst + r * ldd;
+#pragma unroll
+                for (int v = 0; v < EB; ++v) w[v] = sub ? w[v] - acc[v] : acc[v];
             }
             continue;
         }
@@ -861,8 +904,12 @@ static void tn_reduce(Engine *e, int phase, int mode) {
 }
 
 static void nn(Engine *e, int phase, int mode, int c0 = 0) {
-    launch("k_e_nn", k_e_nn, tile_grid(), 256, 0, e->stream, e->slots.ptr, (const Tile *)e->tiles.ptr,
-           (const int32_t *)e->ntiles.ptr, e->MB, phase, mode, dense_ptrs(e), c0);
+    if (mode == M_QR2)
+        launch("k_e_nn", k_e_nn<true>, tile_grid(), 256, 0, e->stream, e->slots.ptr, (const Tile *)e->tiles.ptr,
+               (const int32_t *)e->ntiles.ptr, e->MB, phase, mode, dense_ptrs(e), c0);
+    else
+        launch("k_e_nn", k_e_nn<false>, sm_count() * 5, 256, 0, e->stream, e->slots.ptr, (const Tile *)e->tiles.ptr,
+               (const int32_t *)e->ntiles.ptr, e->MB, phase, mode, dense_ptrs(e), c0);
 }
 
 // Block QR of W into Q[:, m:m+8] with rank test and random completion.
@@ -897,7 +944,7 @@ static void record_step(Engine *e) {
     const Tile *tp = e->tiles.ptr;
     const int32_t *nt = e->ntiles.ptr;
     launch("k_e_prepx", k_e_prepx, tile_grid(), 256, 0, e->stream, e->slots.ptr, tp, nt, e->MB, (int)PH_STEP);
-    launch("k_e_spmm", k_e_spmm, tile_grid(), 256, 0, e->stream, e->slots.ptr, tp, nt, (int)PH_STEP);
+    launch("k_e_spmm", k_e_spmm, sm_count() * 8, 256, 0, e->stream, e->slots.ptr, tp, nt, (int)PH_STEP);
     tn_reduce(e, PH_STEP, M_LOC);
     nn(e, PH_STEP, M_LOC);
     tn_reduce(e, PH_STEP, M_FULL);
