@@ -295,6 +295,18 @@ typedef struct {
 ci_status ci_lowest_eigs(const ci_matrix *m, const ci_eig_opts *opts, double *evals,
                          double *evecs, ci_eig_info *info, void *stream);
 
+/* Fig. 1 line 15 (Sec. 2): the same lowest k eigenpairs by LOBPCG (block
+ * size opts->block >= k, search space [X, W, P] of three blocks), the
+ * preconditioned residuals W = (diag(H) - theta)^-1 R with a diagonal
+ * (Jacobi) preconditioner, Rayleigh-Ritz through the FP64 Gram matrices of
+ * the three blocks (Cholesky of the overlap; P is dropped for an iteration
+ * when the overlap loses rank).  SpMM in the matrix's precision, everything
+ * else in FP64.  Options and outputs as ci_lowest_eigs; max_basis,
+ * reorth_passes and check_every are ignored, max_iter counts iterations
+ * [1000].  Dimensions up to 4*block use the dense path of ci_lowest_eigs. */
+ci_status ci_lowest_eigs_lobpcg(const ci_matrix *m, const ci_eig_opts *opts, double *evals,
+                                double *evecs, ci_eig_info *info, void *stream);
+
 /* ---------------------------------------------------------------- batched solves */
 
 /* Many independent problems built and solved together (Fig. 1 lines 1-15

@@ -213,16 +213,18 @@ class Matrix:
 
     # -- Fig. 1 line 15 ------------------------------------------------------
     def lowest_eigs(self, k=5, block=8, max_basis=0, max_iter=0, tol=0.0, seed=1, reorth_passes=0,
-                    check_every=0, evecs=None, stream=None, allow_unconverged=False):
+                    check_every=0, evecs=None, stream=None, allow_unconverged=False, method="lanczos"):
         """Lowest k eigenvalues (numpy, ascending) and the solve info dict.
 
-        evecs: optional device float64 tensor [dim, k] for the eigenvectors."""
+        evecs: optional device float64 tensor [dim, k] for the eigenvectors.
+        method: "lanczos" (ci_lowest_eigs) or "lobpcg" (ci_lowest_eigs_lobpcg)."""
         o = _lib.EigOpts(k, block, max_basis, max_iter, tol, seed, reorth_passes, check_every)
         ev = np.zeros(k, np.float64)
         info = _lib.EigInfo()
-        st = lib().ci_lowest_eigs(self._h, C.byref(o), _ptr(ev), _ptr(evecs), C.byref(info), _stream(stream))
+        fn = {"lanczos": lib().ci_lowest_eigs, "lobpcg": lib().ci_lowest_eigs_lobpcg}[method]
+        st = fn(self._h, C.byref(o), _ptr(ev), _ptr(evecs), C.byref(info), _stream(stream))
         if not (allow_unconverged and st == _lib.CI_ERR_NOT_CONVERGED):
-            check(st, "ci_lowest_eigs")
+            check(st, "ci_lowest_eigs" if method == "lanczos" else "ci_lowest_eigs_lobpcg")
         out = {"iterations": info.iterations, "restarts": info.restarts, "converged": info.converged,
                "basis_size": info.basis_size, "hnorm_est": info.hnorm_est,
                "residual": list(info.residual)[:k], "seconds": info.seconds, "status": st}

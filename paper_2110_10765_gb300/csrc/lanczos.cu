@@ -253,6 +253,12 @@ __global__ void k_copy_cols(int64_t dim, int nb, const double *__restrict__ src,
         dst[(t / nb) * ldd + t % nb] = src[(t / nb) * lds + t % nb];
 }
 
+// y += x over n doubles
+__global__ void k_axpy(int64_t n, const double *__restrict__ x, double *__restrict__ y) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        y[t] += x[t];
+}
+
 __global__ void k_zero_cols(int64_t dim, int nb, double *dst, int ldd) {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < dim * nb; t += (int64_t)gridDim.x * blockDim.x)
         dst[(t / nb) * ldd + t % nb] = 0.0;
@@ -276,6 +282,34 @@ __global__ void k_residual(int64_t dim, int nb, const TX *__restrict__ HX, const
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < dim * nb; t += (int64_t)gridDim.x * blockDim.x) {
         const int v = (int)(t % nb);
         R[t] = (double)HX[t] - theta[v] * X[(t / nb) * ldx + v];
+    }
+}
+
+// d[i] = H[i][i] (0 if the row has no diagonal entry): binary search of
+// the ascending columns of row i.
+template <class TV>
+__global__ void k_diag(int64_t dim, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                       const TV *__restrict__ val, double *__restrict__ d) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < dim; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t lo = rp[i], hi = rp[i + 1];
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (col[mid] < i) lo = mid + 1; else hi = mid;
+        }
+        d[i] = (lo < rp[i + 1] && col[lo] == i) ? (double)val[lo] : 0.0;
+    }
+}
+
+// Diagonal (Jacobi) preconditioner of LOBPCG: W[i][v] = R[i][v] / (d_i - theta_v),
+// with the shift kept at least floor * |theta_v| (sign preserved) away from 0.
+__global__ void k_precond(int64_t dim, int nb, const double *__restrict__ R, const double *__restrict__ d,
+                          const double *__restrict__ theta, double floor, double *__restrict__ W) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < dim * nb; t += (int64_t)gridDim.x * blockDim.x) {
+        const int v = (int)(t % nb);
+        double den = d[t / nb] - theta[v];
+        const double lim = floor * fmax(fabs(theta[v]), 1.0);
+        if (fabs(den) < lim) den = den < 0 ? -lim : lim;
+        W[t] = R[t] / den;
     }
 }
 
@@ -720,6 +754,308 @@ void lowest_eigs(const Matrix *H, const ci_eig_opts *opts_in, double *evals, dou
                          inf.converged, k);
 }
 
+// ------------------------------------------------------------------ LOBPCG
+
+// Lower Cholesky factor of the symmetric positive definite n x n matrix A
+// (row-major); false if a pivot is not above rel * max diagonal.
+static bool cholesky_lower(int n, const std::vector<double> &A, std::vector<double> &L, double rel) {
+    L.assign((size_t)n * n, 0.0);
+    double dmax = 0.0;
+    for (int i = 0; i < n; ++i) dmax = std::max(dmax, A[(size_t)i * n + i]);
+    for (int j = 0; j < n; ++j) {
+        double d = A[(size_t)j * n + j];
+        for (int k = 0; k < j; ++k) d -= L[(size_t)j * n + k] * L[(size_t)j * n + k];
+        if (!(d > rel * dmax)) return false;
+        const double ljj = std::sqrt(d);
+        L[(size_t)j * n + j] = ljj;
+        for (int i = j + 1; i < n; ++i) {
+            double x = A[(size_t)i * n + j];
+            for (int k = 0; k < j; ++k) x -= L[(size_t)i * n + k] * L[(size_t)j * n + k];
+            L[(size_t)i * n + j] = x / ljj;
+        }
+    }
+    return true;
+}
+
+// Lowest nb pairs of the pencil (GA, GB), n x n: GB = L L^T, eigenpairs of
+// L^-1 GA L^-T, C = L^-T Z (n x nb, row-major).  False if GB is not
+// positive definite enough.
+static bool pencil_lowest(int n, int nb, const std::vector<double> &GA, const std::vector<double> &GB,
+                          std::vector<double> &theta, std::vector<double> &C) {
+    std::vector<double> L;
+    if (!cholesky_lower(n, GB, L, 1e-8)) return false;   // the blocks are orthonormalised: GB ~ I
+    // M = L^-1 GA L^-T: solve L Y = GA, then L M^T = Y^T
+    std::vector<double> Y((size_t)n * n), M((size_t)n * n);
+    for (int c = 0; c < n; ++c)
+        for (int i = 0; i < n; ++i) {
+            double x = GA[(size_t)i * n + c];
+            for (int k = 0; k < i; ++k) x -= L[(size_t)i * n + k] * Y[(size_t)k * n + c];
+            Y[(size_t)i * n + c] = x / L[(size_t)i * n + i];
+        }
+    for (int r = 0; r < n; ++r)
+        for (int i = 0; i < n; ++i) {
+            double x = Y[(size_t)r * n + i];
+            for (int k = 0; k < i; ++k) x -= L[(size_t)i * n + k] * M[(size_t)r * n + k];
+            M[(size_t)r * n + i] = x / L[(size_t)i * n + i];
+        }
+    for (int r = 0; r < n; ++r)
+        for (int c = r + 1; c < n; ++c) {
+            const double a = 0.5 * (M[(size_t)r * n + c] + M[(size_t)c * n + r]);
+            M[(size_t)r * n + c] = a;
+            M[(size_t)c * n + r] = a;
+        }
+    std::vector<double> w, Z;
+    if (!sym_eig(n, M, w, Z)) return false;
+    theta.assign(w.begin(), w.begin() + nb);
+    // C = L^-T Z[:, :nb]: back substitution with L^T
+    C.assign((size_t)n * nb, 0.0);
+    for (int v = 0; v < nb; ++v)
+        for (int i = n - 1; i >= 0; --i) {
+            double x = Z[(size_t)i * n + v];
+            for (int k = i + 1; k < n; ++k) x -= L[(size_t)k * n + i] * C[(size_t)k * nb + v];
+            C[(size_t)i * nb + v] = x / L[(size_t)i * n + i];
+        }
+    return true;
+}
+
+void lowest_eigs_lobpcg(const Matrix *H, const ci_eig_opts *opts_in, double *evals, double *evecs,
+                        ci_eig_info *info, cudaStream_t s) {
+    auto t_start = std::chrono::steady_clock::now();
+    if (!H) fail(CI_ERR_INVALID_ARG, "matrix is NULL");
+    if (!evals) fail(CI_ERR_INVALID_ARG, "evals is NULL");
+    ci_eig_opts o = opts_in ? *opts_in : ci_eig_opts{};
+    if (o.k == 0) o.k = 5;
+    if (o.block == 0) o.block = 8;
+    if (o.max_iter == 0) o.max_iter = 1000;
+    if (o.tol == 0.0) o.tol = H->vtype == CI_F64 ? 1e-10 : 1e-6;
+    if (o.seed == 0) o.seed = 1;
+    if (o.block < 1 || o.block > 8) fail(CI_ERR_INVALID_ARG, "block must be 1..8");
+    if (o.k < 1 || o.k > o.block) fail(CI_ERR_INVALID_ARG, "LOBPCG needs 1 <= k <= block (k = %d, block = %d)", o.k,
+                                       o.block);
+    const int64_t dim = H->dim;
+    const int nb = o.block, k = o.k;
+    if (dim <= 4 * (int64_t)nb) {  // too small for three blocks: the dense path of the Lanczos solver
+        ci_eig_opts d = o;
+        d.max_basis = 0;
+        lowest_eigs(H, &d, evals, evecs, info, s);
+        return;
+    }
+    Solver sv(H, s, nb, k, nb);
+    const size_t blk = (size_t)dim * nb;
+    DevBuf<double> X(blk), AX(blk), Wd(blk), AW(blk), P(blk), AP(blk), R(blk), Xn(blk), AXn(blk), Pn(blk), APn(blk);
+    DevBuf<double> dg((size_t)dim), G((size_t)12 * 64), Cd((size_t)3 * 64);
+    if (H->vtype == CI_F64)
+        launch("k_diag", k_diag<double>, sv.grid(dim), 256, 0, s, dim, H->row_ptr.ptr, H->col.ptr,
+               (const double *)H->val.ptr, dg.ptr);
+    else if (H->vtype == CI_F32)
+        launch("k_diag", k_diag<float>, sv.grid(dim), 256, 0, s, dim, H->row_ptr.ptr, H->col.ptr,
+               (const float *)H->val.ptr, dg.ptr);
+    else
+        fail(CI_ERR_INVALID_ARG, "value type %d not supported by LOBPCG", H->vtype);
+    const int bb = nb * nb;
+    // Gram blocks into G (device), one copy to the host
+    auto gram = [&](const std::vector<std::pair<const double *, const double *>> &pairs, std::vector<double> &h) {
+        for (size_t q = 0; q < pairs.size(); ++q)
+            sv.tn(pairs[q].first, nb, nb, pairs[q].second, nb, nb, G.ptr + q * 64, nullptr);
+        h.resize(pairs.size() * 64);
+        CI_CUDA(cudaMemcpyAsync(h.data(), G.ptr, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s));
+        CI_CUDA(cudaStreamSynchronize(s));
+    };
+    // out = sum_q A_q C_q (C_q nb x nb row-major blocks of the host matrix C)
+    auto combine = [&](const std::vector<const double *> &As, const std::vector<double> &C, int row0, double *out) {
+        std::vector<double> cq((size_t)As.size() * bb);
+        for (size_t q = 0; q < As.size(); ++q)
+            for (int u = 0; u < nb; ++u)
+                for (int v = 0; v < nb; ++v) cq[q * bb + u * nb + v] = C[(size_t)(row0 + (int)q * nb + u) * nb + v];
+        CI_CUDA(cudaMemcpyAsync(Cd.ptr, cq.data(), sizeof(double) * cq.size(), cudaMemcpyHostToDevice, s));
+        for (size_t q = 0; q < As.size(); ++q) sv.nn(As[q], nb, nb, Cd.ptr + q * bb, nb, out, nb, 1.0, q ? 1.0 : 0.0);
+    };
+    std::vector<double> theta(nb, 0.0), rn(nb, 0.0), h, C;
+    auto upload_theta = [&]() { sv.upload(theta, sv.theta_dev.ptr); };
+    // start: random block, Rayleigh-Ritz on it
+    launch("k_random_cols", k_random_cols, sv.grid(dim * nb), 256, 0, s, dim, nb, o.seed, X.ptr, nb);
+    sv.apply(X.ptr, nb, nb, AX.ptr);
+    gram({{X.ptr, X.ptr}, {X.ptr, AX.ptr}}, h);
+    {
+        std::vector<double> GB(h.begin(), h.begin() + bb), GA(h.begin() + 64, h.begin() + 64 + bb);
+        if (!pencil_lowest(nb, nb, GA, GB, theta, C)) fail(CI_ERR_INTERNAL, "LOBPCG start block is degenerate");
+        combine({X.ptr}, C, 0, Xn.ptr);
+        combine({AX.ptr}, C, 0, AXn.ptr);
+        std::swap(X, Xn);
+        std::swap(AX, AXn);
+    }
+    bool haveP = false, converged = false;
+    int it = 0;
+    double hnorm = 0.0;
+    ci_eig_info inf{};
+    DevBuf<double> Cp((size_t)64), Tmp(blk), ATmp(blk);
+    // B -= A (A^T B) (and AB -= AA (A^T B)), on the device
+    auto project_out = [&](const double *A, const double *AA, double *B, double *AB) {
+        sv.tn(A, nb, nb, B, nb, nb, Cp.ptr, nullptr);
+        sv.nn(A, nb, nb, Cp.ptr, nb, B, nb, -1.0, 1.0);
+        if (AB) sv.nn(AA, nb, nb, Cp.ptr, nb, AB, nb, -1.0, 1.0);
+    };
+    // B = B L^-T with B^T B = L L^T (and AB likewise); false if B lost rank
+    // before (optional): the squared column norms before a projection; a
+    // column that lost more than all but 1e-8 of it is mostly rounding
+    // (and for P, drift of its tracked H product): the block is not used
+    auto chol_qr = [&](DevBuf<double> &B, DevBuf<double> *AB, const std::vector<double> *before) -> bool {
+        std::vector<double> g;
+        gram({{B.ptr, B.ptr}}, g);
+        // columns scaled to unit norm first (D G D, D = diag(G)^-1/2), so the
+        // rank test is relative to each column's own length
+        std::vector<double> Gm(g.begin(), g.begin() + bb), L, dsc(nb);
+        for (int i = 0; i < nb; ++i) {
+            const double d = Gm[(size_t)i * nb + i];
+            if (!(d > 1e-300)) return false;
+            if (before && !(d > 1e-8 * (*before)[i])) return false;
+            dsc[i] = 1.0 / std::sqrt(d);
+        }
+        for (int i = 0; i < nb; ++i)
+            for (int j = 0; j < nb; ++j) Gm[(size_t)i * nb + j] *= dsc[i] * dsc[j];
+        if (!cholesky_lower(nb, Gm, L, 1e-14)) return false;
+        std::vector<double> Mi((size_t)bb, 0.0);   // D L^-T, upper triangular
+        for (int c = 0; c < nb; ++c)
+            for (int i = c; i >= 0; --i) {
+                double x = i == c ? 1.0 : 0.0;
+                for (int k2 = i + 1; k2 <= c; ++k2) x -= L[(size_t)k2 * nb + i] * Mi[(size_t)k2 * nb + c];
+                Mi[(size_t)i * nb + c] = x / L[(size_t)i * nb + i];
+            }
+        for (int i = 0; i < nb; ++i)
+            for (int c = 0; c < nb; ++c) Mi[(size_t)i * nb + c] *= dsc[i];
+        sv.upload(Mi, Cp.ptr);
+        sv.nn(B.ptr, nb, nb, Cp.ptr, nb, Tmp.ptr, nb, 1.0, 0.0);
+        std::swap(B, Tmp);
+        if (AB) {
+            sv.nn(AB->ptr, nb, nb, Cp.ptr, nb, ATmp.ptr, nb, 1.0, 0.0);
+            std::swap(*AB, ATmp);
+        }
+        return true;
+    };
+    for (; it < o.max_iter; ++it) {
+        // the H products are applied afresh every iteration: products carried
+        // through the updates drift by the SpMM's rounding, which the
+        // orthonormalisation of nearly converged blocks would amplify
+        if (it > 0) {
+            sv.apply(X.ptr, nb, nb, AX.ptr);
+            if (haveP) sv.apply(P.ptr, nb, nb, AP.ptr);
+        }
+        upload_theta();
+        launch("k_residual", k_residual<double>, sv.grid(dim * nb), 256, 0, s, dim, nb, AX.ptr, X.ptr, nb,
+               sv.theta_dev.ptr, R.ptr);
+        for (int v = 0; v < nb; ++v) hnorm = std::max(hnorm, std::fabs(theta[v]));
+        gram({{R.ptr, R.ptr}}, h);
+        for (int v = 0; v < nb; ++v) rn[v] = std::sqrt(std::max(h[(size_t)v * nb + v], 0.0));
+        converged = true;
+        for (int v = 0; v < k; ++v)
+            if (rn[v] > o.tol * hnorm) converged = false;
+        if (converged) break;
+        // W: preconditioned residuals, orthonormal and orthogonal to X (two
+        // Gram-Schmidt passes, then Cholesky QR); AW = H W
+        launch("k_precond", k_precond, sv.grid(dim * nb), 256, 0, s, dim, nb, R.ptr, dg.ptr, sv.theta_dev.ptr, 1e-8,
+               Wd.ptr);
+        auto col_norms = [&](const double *B) {
+            std::vector<double> g;
+            gram({{B, B}}, g);
+            std::vector<double> d(nb);
+            for (int i = 0; i < nb; ++i) d[i] = g[(size_t)i * nb + i];
+            return d;
+        };
+        std::vector<double> wn = col_norms(Wd.ptr);
+        project_out(X.ptr, nullptr, Wd.ptr, nullptr);
+        project_out(X.ptr, nullptr, Wd.ptr, nullptr);
+        bool useW = chol_qr(Wd, nullptr, &wn);
+        if (!useW) {   // the preconditioned residuals lie in span(X) (e.g. diagonal H): take R itself
+            launch("k_copy_cols", k_copy_cols, sv.grid(dim * nb), 256, 0, s, dim, nb, R.ptr, nb, Wd.ptr, nb);
+            project_out(X.ptr, nullptr, Wd.ptr, nullptr);
+            project_out(X.ptr, nullptr, Wd.ptr, nullptr);
+            useW = chol_qr(Wd, nullptr, nullptr);
+        }
+        if (useW) sv.apply(Wd.ptr, nb, nb, AW.ptr);
+        // P: orthogonal to X and W, orthonormal (its H product follows)
+        bool useP = haveP;
+        if (useP) {
+            std::vector<double> g0;
+            gram({{P.ptr, P.ptr}}, g0);
+            std::vector<double> before(nb);
+            for (int i = 0; i < nb; ++i) before[i] = g0[(size_t)i * nb + i];
+            for (int pass = 0; pass < 2; ++pass) {
+                project_out(X.ptr, AX.ptr, P.ptr, AP.ptr);
+                if (useW) project_out(Wd.ptr, AW.ptr, P.ptr, AP.ptr);
+            }
+            useP = chol_qr(P, &AP, &before);
+        }
+        if (!useW && !useP) break;        // the search space is X alone
+        // Rayleigh-Ritz on S = [X W P] (orthonormal blocks): the pencil's
+        // overlap is I up to rounding; its Cholesky keeps the new X exactly
+        // orthonormal in it
+        std::vector<const double *> S{X.ptr}, AS{AX.ptr};
+        if (useW) { S.push_back(Wd.ptr); AS.push_back(AW.ptr); }
+        if (useP) { S.push_back(P.ptr); AS.push_back(AP.ptr); }
+        const int nblk = (int)S.size(), n = nblk * nb;
+        std::vector<std::pair<const double *, const double *>> pairs;
+        for (int a = 0; a < nblk; ++a)
+            for (int b = a; b < nblk; ++b) {
+                pairs.push_back({S[a], S[b]});
+                pairs.push_back({S[a], AS[b]});
+            }
+        gram(pairs, h);
+        std::vector<double> GA((size_t)n * n), GB((size_t)n * n);
+        int q = 0;
+        for (int a = 0; a < nblk; ++a)
+            for (int b = a; b < nblk; ++b, q += 2)
+                for (int u = 0; u < nb; ++u)
+                    for (int v = 0; v < nb; ++v) {
+                        const double gb = h[(size_t)q * 64 + u * nb + v], ga = h[(size_t)(q + 1) * 64 + u * nb + v];
+                        GB[(size_t)(a * nb + u) * n + b * nb + v] = gb;
+                        GB[(size_t)(b * nb + v) * n + a * nb + u] = gb;
+                        GA[(size_t)(a * nb + u) * n + b * nb + v] = ga;
+                        if (a != b) GA[(size_t)(b * nb + v) * n + a * nb + u] = ga;
+                    }
+        for (int r = 0; r < n; ++r)   // S^T H S is symmetric: average the diagonal blocks
+            for (int c = r + 1; c < n; ++c)
+                if (r / nb == c / nb) {
+                    const double x = 0.5 * (GA[(size_t)r * n + c] + GA[(size_t)c * n + r]);
+                    GA[(size_t)r * n + c] = x;
+                    GA[(size_t)c * n + r] = x;
+                }
+        if (!pencil_lowest(n, nb, GA, GB, theta, C)) break;
+        // P = W Cw (+ P Cp), X = X Cx + P; the same for the H products
+        std::vector<const double *> ws(S.begin() + 1, S.end()), aws(AS.begin() + 1, AS.end());
+        combine(ws, C, nb, Pn.ptr);
+        combine({X.ptr}, C, 0, Xn.ptr);
+        launch("k_axpy", k_axpy, sv.grid(dim * nb), 256, 0, s, (int64_t)blk, Pn.ptr, Xn.ptr);
+        (void)aws;
+        std::swap(X, Xn);
+        std::swap(P, Pn);
+        haveP = true;
+    }
+    // FP64 residuals of the final pairs with the stored H
+    upload_theta();
+    sv.apply(X.ptr, nb, nb, AXn.ptr);
+    launch("k_residual", k_residual<double>, sv.grid(dim * nb), 256, 0, s, dim, nb, AXn.ptr, X.ptr, nb,
+           sv.theta_dev.ptr, R.ptr);
+    gram({{R.ptr, R.ptr}, {X.ptr, X.ptr}}, h);
+    for (int i = 0; i < k; ++i) {
+        evals[i] = theta[i];
+        inf.residual[i] = std::sqrt(std::max(h[(size_t)i * nb + i], 0.0));
+    }
+    if (evecs) {
+        launch("k_copy_cols", k_copy_cols, sv.grid(dim * k), 256, 0, s, dim, k, X.ptr, nb, evecs, k);
+        CI_CHECK_LAUNCH();
+    }
+    CI_CUDA(cudaStreamSynchronize(s));
+    inf.iterations = it;
+    inf.basis_size = 3 * nb;
+    inf.hnorm_est = hnorm;
+    inf.converged = 0;
+    for (int i = 0; i < k; ++i)
+        if (inf.residual[i] <= std::max(o.tol, 1e-12) * hnorm * 1.5) ++inf.converged;
+    inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+    if (info) *info = inf;
+    if (!converged) fail(CI_ERR_NOT_CONVERGED, "LOBPCG stopped after %d iterations", it);
+}
+
 }  // namespace ci
 
 extern "C" ci_status ci_lowest_eigs(const ci_matrix *m, const ci_eig_opts *opts, double *evals, double *evecs,
@@ -728,5 +1064,14 @@ extern "C" ci_status ci_lowest_eigs(const ci_matrix *m, const ci_eig_opts *opts,
         if (!m) ci::fail(CI_ERR_INVALID_ARG, "matrix is NULL");
         ci::StreamScope scope(reinterpret_cast<cudaStream_t>(stream));
         ci::lowest_eigs(&m->impl, opts, evals, evecs, info, reinterpret_cast<cudaStream_t>(stream));
+    });
+}
+
+extern "C" ci_status ci_lowest_eigs_lobpcg(const ci_matrix *m, const ci_eig_opts *opts, double *evals,
+                                           double *evecs, ci_eig_info *info, void *stream) {
+    return ci::guard([&] {
+        if (!m) ci::fail(CI_ERR_INVALID_ARG, "matrix is NULL");
+        ci::StreamScope scope(reinterpret_cast<cudaStream_t>(stream));
+        ci::lowest_eigs_lobpcg(&m->impl, opts, evals, evecs, info, reinterpret_cast<cudaStream_t>(stream));
     });
 }
