@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--no-count", action="store_true", help="skip the count-benchmark leg")
     ap.add_argument("--count-n", type=int, default=131072, help="states of the count benchmark")
     ap.add_argument("--no-observables", action="store_true", help="skip the observables leg")
+    ap.add_argument("--no-c2", action="store_true", help="skip the Nmax=6 precision-study leg")
     ap.add_argument("--obs-m", type=int, default=16, help="operators of the observables leg")
     return ap.parse_args()
 
@@ -334,6 +335,8 @@ def run_ours(args):
         rec["count"] = run_count_leg(args.count_n, clock_mhz=(clk or {}).get("sm_mhz"))
     if not args.no_observables:
         rec["observables"] = run_observables_leg(sp, p, eps, dtab, args.obs_m)
+    if not args.no_c2:
+        rec["c2_precision"] = run_c2_leg(hbm)
     if not args.no_batch:
         rec["batch"], pool = run_batch_leg(args)
         if not args.no_serve:
@@ -346,6 +349,56 @@ def run_ours(args):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(rec))
+
+
+# ---------------------------------------------------------------- precision study
+
+def run_c2_leg(hbm):
+    """The same generator at Nmax = 6 (dim 2,680,018, 3.2e9 nonzeros): build
+    and SpMM in FP32, lowest 10 eigenvalues with the FP32 H and with the FP64
+    H (the FP64 GPU run is the reference at this size)."""
+    import numpy as np
+    import torch
+
+    import synth
+    import paper_2110_10765_gb300 as ci
+    p = synth.preset("c2")
+    sp = synth.ho_sp_table(p.n_shell_max)
+    eps = synth.sp_energies(sp, p.hbar_omega)
+    T = {k: torch.from_numpy(v).cuda() for k, v in synth.tbme_tables(sp, p.seed, np.float32).items()}
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        out = fn()
+        b.record(stream)
+        b.synchronize()
+        return out, a.elapsed_time(b)
+
+    prob = ci.Problem(sp, p.Z, p.N, p.nmax, p.twoM, eps, tables=T)
+    prob.enumerate_basis()
+    M, build_ms = timed(lambda: prob.build_H("f32"))
+    X = torch.randn(M.dim, 8, device="cuda")
+    Y = torch.empty_like(X)
+    M.apply_H(X, Y)
+    sp_ms = min(timed(lambda: M.apply_H(X, Y))[1] for _ in range(3))
+    b = algorithmic_bytes("k_spmm", M.dim, M.nnz)
+    del X, Y
+    (ev32, info32), s32 = timed(lambda: M.lowest_eigs(k=p.k))
+    dim, nnz = M.dim, M.nnz
+    del M
+    M64 = prob.build_H("f64")
+    (ev64, info64), s64 = timed(lambda: M64.lowest_eigs(k=p.k))
+    del M64
+    return {"workload": "4p+4n N<=4 Nmax=6 (dim %d, nnz %d), k=%d" % (dim, nnz, p.k), "dim": dim, "nnz": nnz,
+            "build_f32_ms": build_ms, "build_nnz_per_s": nnz / (build_ms * 1e-3),
+            "spmm_f32_ms": sp_ms, "spmm_gbs": b / (sp_ms * 1e-3) / 1e9, "spmm_frac": b / (sp_ms * 1e-3) / 1e9 / hbm,
+            "solve_f32_s": s32 * 1e-3, "solve_f32_iterations": info32["iterations"],
+            "solve_f64_s": s64 * 1e-3, "solve_f64_iterations": info64["iterations"],
+            "lowest_f64": [round(float(x), 7) for x in ev64],
+            "max_abs_diff_f32_vs_f64": float(np.max(np.abs(ev32 - ev64))),
+            "max_rel_diff_f32_vs_f64": float(np.max(np.abs(ev32 - ev64) / np.abs(ev64)))}
 
 
 # ---------------------------------------------------------------- observables

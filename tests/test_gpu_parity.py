@@ -271,3 +271,38 @@ def test_lowest_eigs_small_dense_path(case):
                                                                                               max_basis=16)
     ref = oracle.lowest_dense(oracle.dense_from_csr(*o.csr()[:3], o.dim), len(ev))
     assert np.allclose(ev, ref, atol=1e-9)
+
+
+def test_config2_full_size_sampled_rows_and_precision():
+    """Nmax=6 (dim 2,680,018, 3.2e9 nonzeros): sampled rows against the oracle
+    (pattern bit-exact, values within the FP32 bound), structural symmetry on
+    them, and the lowest 10 eigenvalues of the FP32 H against the FP64 GPU
+    run (the precision study of the workload)."""
+    import torch
+    inp = preset_inputs("c2")
+    o, g = oracle_problem(inp), gpu_problem(inp)
+    M = g.build_H("f32")
+    assert M.dim == golden()["c2"]["dim"]
+    rp = torch.empty(M.dim + 1, dtype=torch.int64, device="cuda")
+    col = torch.empty(M.nnz, dtype=torch.int32, device="cuda")
+    val = torch.empty(M.nnz, dtype=torch.float32, device="cuda")
+    M.export_device(rp, col, val)
+    rph = rp.cpu().numpy()
+    assert rph[-1] == M.nnz
+    rng = np.random.default_rng(21)
+    rows = sorted(set(rng.integers(0, M.dim, 12).tolist()) | {0, M.dim - 1})
+    for i in rows:
+        ocol, oval, oab, _ = o.row(i)
+        c = col[rph[i]:rph[i + 1]].cpu().numpy()
+        v = val[rph[i]:rph[i + 1]].cpu().numpy()
+        assert np.array_equal(c.astype(np.int64), ocol), i
+        assert np.all(np.abs(v.astype(np.float64) - oval) <= value_bound(oval, oab, REL32)), i
+        for j in c[:: max(1, len(c) // 16)].tolist():      # the transposed entry exists
+            seg = col[rph[j]:rph[j + 1]].cpu().numpy()
+            k = np.searchsorted(seg, i)
+            assert k < len(seg) and seg[k] == i
+    del rp, col, val
+    ev32, info32 = M.lowest_eigs(k=10)
+    del M
+    ev64, info64 = g.build_H("f64").lowest_eigs(k=10)
+    assert np.all(np.abs(ev32 - ev64) <= EIG_REL * np.maximum(np.abs(ev64), 1)), ev32 - ev64
