@@ -388,6 +388,15 @@ def run_c2_leg(hbm):
     (ev32, info32), s32 = timed(lambda: M.lowest_eigs(k=p.k))
     dim, nnz = M.dim, M.nnz
     del M
+    # BF16 values with a per-row FP32 scale (6 bytes per nonzero)
+    Mb = prob.build_H("bf16")
+    X = torch.randn(dim, 8, device="cuda")
+    Y = torch.empty_like(X)
+    Mb.apply_H(X, Y)
+    spb_ms = min(timed(lambda: Mb.apply_H(X, Y))[1] for _ in range(3))
+    del X, Y
+    (evb, infob), sb = timed(lambda: Mb.lowest_eigs(k=p.k, allow_unconverged=True))
+    del Mb
     M64 = prob.build_H("f64")
     (ev64, info64), s64 = timed(lambda: M64.lowest_eigs(k=p.k))
     del M64
@@ -398,7 +407,10 @@ def run_c2_leg(hbm):
             "solve_f64_s": s64 * 1e-3, "solve_f64_iterations": info64["iterations"],
             "lowest_f64": [round(float(x), 7) for x in ev64],
             "max_abs_diff_f32_vs_f64": float(np.max(np.abs(ev32 - ev64))),
-            "max_rel_diff_f32_vs_f64": float(np.max(np.abs(ev32 - ev64) / np.abs(ev64)))}
+            "max_rel_diff_f32_vs_f64": float(np.max(np.abs(ev32 - ev64) / np.abs(ev64))),
+            "bf16_rowscale": {"spmm_ms": spb_ms, "solve_s": sb * 1e-3, "iterations": infob["iterations"],
+                              "max_abs_diff_vs_f64": float(np.max(np.abs(evb - ev64))),
+                              "max_rel_diff_vs_f64": float(np.max(np.abs(evb - ev64) / np.abs(ev64)))}}
 
 
 # ---------------------------------------------------------------- observables

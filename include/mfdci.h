@@ -70,7 +70,11 @@ typedef enum {
 /* Precision of the stored H values (and of the arithmetic that makes them).
  * CI_F32: float values, FP32 accumulation of matrix-element terms.
  * CI_F64: double values, FP64 accumulation (the plain FP64 form).
- * CI_BF16_ROWSCALE: bf16 values times a per-row float scale (FP32 compute). */
+ * CI_BF16_ROWSCALE: bf16 values times a per-row float scale (FP32 compute):
+ *   the row is built in FP32, scale_r = max_j |H_rj| (1 for a zero row) and
+ *   the stored value is H_rj / scale_r rounded to the nearest bf16; the SpMM
+ *   multiplies each row's sum by scale_r (6 bytes per nonzero, values to
+ *   about 2^-9 of the row's largest). */
 typedef enum { CI_F32 = 0, CI_F64 = 1, CI_BF16_ROWSCALE = 2 } ci_value_type;
 
 /* Where the two-body matrix elements come from. */

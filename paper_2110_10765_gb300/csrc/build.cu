@@ -13,6 +13,8 @@
 // atomic capture).
 #include <climits>
 
+#include <cuda_bf16.h>
+
 #include "problem.cuh"
 
 namespace ci {
@@ -555,8 +557,29 @@ template int observable_apply<float>(Problem *, const Tables<float> &, const Con
 template int observable_apply<double>(Problem *, const Tables<double> &, const ConnEntry<double> *, const double *,
                                       double *, cudaStream_t);
 
+// BF16 storage with a per-row scale: scale_r = max_j |v_rj| (1 for an
+// all-zero row), stored value bf16(v / scale_r) rounded to nearest; one
+// warp per row.
+__global__ void k_to_bf16_rows(int64_t dim, const int64_t *__restrict__ rp, const float *__restrict__ v32,
+                               __nv_bfloat16 *__restrict__ v16, float *__restrict__ scale) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = warp; r < dim; r += nwarps) {
+        const int64_t e0 = rp[r], e1 = rp[r + 1];
+        float m = 0.f;
+        for (int64_t e = e0 + lane; e < e1; e += 32) m = fmaxf(m, fabsf(v32[e]));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        const float sc = m > 0.f ? m : 1.f;
+        const float inv = 1.f / sc;
+        for (int64_t e = e0 + lane; e < e1; e += 32) v16[e] = __float2bfloat16_rn(v32[e] * inv);
+        if (lane == 0) scale[r] = sc;
+    }
+}
+
 void build_matrix(Problem *p, int vtype, Matrix *m, cudaStream_t s) {
-    if (vtype != CI_F32 && vtype != CI_F64)
+    if (vtype != CI_F32 && vtype != CI_F64 && vtype != CI_BF16_ROWSCALE)
         fail(CI_ERR_INVALID_ARG, "value type %d is not supported by ci_build_H", vtype);
     GroupCSR g;
     count_group({p}, vtype == CI_F64 ? 1 : 0, &g, s);
@@ -566,7 +589,16 @@ void build_matrix(Problem *p, int vtype, Matrix *m, cudaStream_t s) {
     m->nnz = g.nnz;
     m->row_ptr = std::move(g.row_ptr);
     m->col = std::move(g.col);
-    m->val = std::move(g.val);
+    if (vtype != CI_BF16_ROWSCALE) {
+        m->val = std::move(g.val);
+        return;
+    }
+    // values filled in FP32, then scaled per row and rounded to bf16
+    m->val.alloc((size_t)g.nnz * sizeof(__nv_bfloat16));
+    m->row_scale.alloc((size_t)p->dim);
+    if (p->dim > 0)
+        launch("k_to_bf16_rows", k_to_bf16_rows, row_grid(p->dim), 256, 0, s, p->dim, m->row_ptr.ptr,
+               (const float *)g.val.ptr, (__nv_bfloat16 *)m->val.ptr, m->row_scale.ptr);
 }
 
 }  // namespace ci

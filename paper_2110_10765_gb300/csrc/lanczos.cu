@@ -8,6 +8,8 @@
 #include <chrono>
 #include <cmath>
 
+#include <cuda_bf16.h>
+
 #include "dense.h"
 #include "problem.cuh"
 
@@ -285,18 +287,23 @@ __global__ void k_residual(int64_t dim, int nb, const TX *__restrict__ HX, const
     }
 }
 
+__device__ __forceinline__ double as_double(float v) { return v; }
+__device__ __forceinline__ double as_double(double v) { return v; }
+__device__ __forceinline__ double as_double(__nv_bfloat16 v) { return __bfloat162float(v); }
+
 // d[i] = H[i][i] (0 if the row has no diagonal entry): binary search of
-// the ascending columns of row i.
+// the ascending columns of row i; BF16 values times the row's scale.
 template <class TV>
 __global__ void k_diag(int64_t dim, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
-                       const TV *__restrict__ val, double *__restrict__ d) {
+                       const TV *__restrict__ val, const float *__restrict__ row_scale, double *__restrict__ d) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < dim; i += (int64_t)gridDim.x * blockDim.x) {
         int64_t lo = rp[i], hi = rp[i + 1];
         while (lo < hi) {
             const int64_t mid = (lo + hi) >> 1;
             if (col[mid] < i) lo = mid + 1; else hi = mid;
         }
-        d[i] = (lo < rp[i + 1] && col[lo] == i) ? (double)val[lo] : 0.0;
+        const double v = (lo < rp[i + 1] && col[lo] == i) ? as_double(val[lo]) : 0.0;
+        d[i] = row_scale ? v * row_scale[i] : v;
     }
 }
 
@@ -846,10 +853,13 @@ void lowest_eigs_lobpcg(const Matrix *H, const ci_eig_opts *opts_in, double *eva
     DevBuf<double> dg((size_t)dim), G((size_t)12 * 64), Cd((size_t)3 * 64);
     if (H->vtype == CI_F64)
         launch("k_diag", k_diag<double>, sv.grid(dim), 256, 0, s, dim, H->row_ptr.ptr, H->col.ptr,
-               (const double *)H->val.ptr, dg.ptr);
+               (const double *)H->val.ptr, (const float *)nullptr, dg.ptr);
     else if (H->vtype == CI_F32)
         launch("k_diag", k_diag<float>, sv.grid(dim), 256, 0, s, dim, H->row_ptr.ptr, H->col.ptr,
-               (const float *)H->val.ptr, dg.ptr);
+               (const float *)H->val.ptr, (const float *)nullptr, dg.ptr);
+    else if (H->vtype == CI_BF16_ROWSCALE)
+        launch("k_diag", k_diag<__nv_bfloat16>, sv.grid(dim), 256, 0, s, dim, H->row_ptr.ptr, H->col.ptr,
+               (const __nv_bfloat16 *)H->val.ptr, (const float *)H->row_scale.ptr, dg.ptr);
     else
         fail(CI_ERR_INVALID_ARG, "value type %d not supported by LOBPCG", H->vtype);
     const int bb = nb * nb;

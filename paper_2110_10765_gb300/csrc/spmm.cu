@@ -2,6 +2,8 @@
 // j-th vector element), X and Y row-major [dim][NV].  One warp per row:
 // lanes stride over the row's nonzeros with coalesced col/val loads and one
 // vector load of X's row per nonzero, then a butterfly reduction.
+#include <cuda_bf16.h>
+
 #include "problem.cuh"
 
 namespace ci {
@@ -40,10 +42,23 @@ struct VecLoad<double, 8> {
     }
 };
 
+// Value of a stored element in the arithmetic type (bf16 widened to float).
+__device__ __forceinline__ float load_val(const float *p) { return __ldcs(p); }
+__device__ __forceinline__ float load_val(const double *p) { return (float)__ldcs(p); }
+__device__ __forceinline__ float load_val(const __nv_bfloat16 *p) {
+    return __bfloat162float(__ushort_as_bfloat16(__ldcs(reinterpret_cast<const unsigned short *>(p))));
+}
+template <class TX, class TV>
+__device__ __forceinline__ TX load_as(const TV *p) { return (TX)load_val(p); }
+template <>
+__device__ __forceinline__ double load_as<double, double>(const double *p) { return __ldcs(p); }
+
+// row_scale: null, or a per-row factor of the stored values (BF16 form)
 template <class TV, class TX, int NV>
 __global__ void __launch_bounds__(256) k_spmm(int64_t dim, const int64_t *__restrict__ rp,
                                               const int32_t *__restrict__ col, const TV *__restrict__ val,
-                                              const TX *__restrict__ X, TX *__restrict__ Y) {
+                                              const TX *__restrict__ X, TX *__restrict__ Y,
+                                              const float *__restrict__ row_scale) {
     constexpr int U = 4;  // nonzeros in flight per lane
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -60,7 +75,7 @@ __global__ void __launch_bounds__(256) k_spmm(int64_t dim, const int64_t *__rest
 #pragma unroll
             for (int u = 0; u < U; ++u) {  // col/val stream once: evict-first loads
                 c[u] = __ldcs(col + e + 32 * u);
-                v[u] = (TX)__ldcs(val + e + 32 * u);
+                v[u] = load_as<TX>(val + e + 32 * u);
             }
             TX x[U][NV];
 #pragma unroll
@@ -72,7 +87,7 @@ __global__ void __launch_bounds__(256) k_spmm(int64_t dim, const int64_t *__rest
         }
         for (; e < e1; e += 32) {
             const int c = __ldcs(col + e);
-            const TX v = (TX)__ldcs(val + e);
+            const TX v = load_as<TX>(val + e);
             TX x[NV];
             VecLoad<TX, NV>::load(X + (int64_t)c * NV, x);
 #pragma unroll
@@ -88,7 +103,7 @@ __global__ void __launch_bounds__(256) k_spmm(int64_t dim, const int64_t *__rest
 #pragma unroll
             for (int i = 1; i < NV; ++i)
                 if (lane == i) y = acc[i];
-            Y[r * NV + lane] = y;
+            Y[r * NV + lane] = row_scale ? y * (TX)row_scale[r] : y;
         }
     }
 }
@@ -99,10 +114,13 @@ __global__ void __launch_bounds__(256) k_spmm(int64_t dim, const int64_t *__rest
 // issuing two loads per row.  Lanes accumulate their four components over
 // the row's nonzeros j, j+16, ... in ascending order, then reduce over the
 // 16 lanes of the same parity.
+
+// row_scale: null, or a per-row factor of the stored values (BF16 form)
 template <class TV>
 __global__ void __launch_bounds__(256) k_spmm8_half(int64_t dim, const int64_t *__restrict__ rp,
                                                     const int32_t *__restrict__ col, const TV *__restrict__ val,
-                                                    const float *__restrict__ X, float *__restrict__ Y) {
+                                                    const float *__restrict__ X, float *__restrict__ Y,
+                                                    const float *__restrict__ row_scale) {
     constexpr int U = 4;  // nonzeros in flight per lane pair
     const int lane = threadIdx.x & 31, half = lane & 1, pair = lane >> 1;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -118,7 +136,7 @@ __global__ void __launch_bounds__(256) k_spmm8_half(int64_t dim, const int64_t *
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 c[u] = __ldcs(col + e + 16 * u);
-                v[u] = (float)__ldcs(val + e + 16 * u);
+                v[u] = load_val(val + e + 16 * u);
             }
             float4 x[U];
 #pragma unroll
@@ -133,7 +151,7 @@ __global__ void __launch_bounds__(256) k_spmm8_half(int64_t dim, const int64_t *
         }
         for (; e < e1; e += 16) {
             const int c = __ldcs(col + e);
-            const float v = (float)__ldcs(val + e);
+            const float v = load_val(val + e);
             const float4 x = __ldg(X4 + (int64_t)c * 2 + half);
             a0 = fmaf(v, x.x, a0);
             a1 = fmaf(v, x.y, a1);
@@ -147,20 +165,24 @@ __global__ void __launch_bounds__(256) k_spmm8_half(int64_t dim, const int64_t *
             a2 += __shfl_xor_sync(0xffffffffu, a2, o);
             a3 += __shfl_xor_sync(0xffffffffu, a3, o);
         }
-        if (lane < 2) reinterpret_cast<float4 *>(Y)[r * 2 + half] = make_float4(a0, a1, a2, a3);
+        if (lane < 2) {
+            const float sc = row_scale ? row_scale[r] : 1.f;
+            reinterpret_cast<float4 *>(Y)[r * 2 + half] = make_float4(a0 * sc, a1 * sc, a2 * sc, a3 * sc);
+        }
     }
 }
 
 template <class TV, class TX, int NV>
 static void launch_spmm(const Matrix *m, const void *X, void *Y, cudaStream_t s) {
     int grid = grid_for(m->dim * 32, 256, sm_count() * 8);
+    const float *scale = m->vtype == CI_BF16_ROWSCALE ? m->row_scale.ptr : nullptr;
     if (NV == 8 && sizeof(TX) == 4) {
         launch("k_spmm", k_spmm8_half<TV>, grid, 256, 0, s, m->dim, m->row_ptr.ptr, m->col.ptr,
-               (const TV *)m->val.ptr, (const float *)X, (float *)Y);
+               (const TV *)m->val.ptr, (const float *)X, (float *)Y, (const float *)scale);
         return;
     }
     launch("k_spmm", k_spmm<TV, TX, NV>, grid, 256, 0, s, m->dim, m->row_ptr.ptr, m->col.ptr,
-           (const TV *)m->val.ptr, (const TX *)X, (TX *)Y);
+           (const TV *)m->val.ptr, (const TX *)X, (TX *)Y, (const float *)scale);
 }
 
 template <class TV, class TX>
@@ -182,12 +204,13 @@ void apply_matrix(const Matrix *m, const void *X, void *Y, int nvec, cudaStream_
     if (nvec < 1 || nvec > 8) fail(CI_ERR_INVALID_ARG, "nvec must be 1..8 (got %d)", nvec);
     if (m->dim == 0) return;
     if (!X || !Y) fail(CI_ERR_INVALID_ARG, "X and Y must be device pointers");
-    size_t esz = m->vtype == CI_F64 ? 8 : 4;
+    size_t esz = m->vtype == CI_F64 ? 8 : 4;   // X and Y element size (float for F32 and BF16)
     size_t align = (nvec == 8 || nvec == 4) ? 16 : esz;
     if (((uintptr_t)X % align) != 0 || ((uintptr_t)Y % align) != 0)
         fail(CI_ERR_INVALID_ARG, "X and Y must be %zu-byte aligned", align);
     if (m->vtype == CI_F32) dispatch<float, float>(m, X, Y, nvec, s);
     else if (m->vtype == CI_F64) dispatch<double, double>(m, X, Y, nvec, s);
+    else if (m->vtype == CI_BF16_ROWSCALE) dispatch<__nv_bfloat16, float>(m, X, Y, nvec, s);
     else fail(CI_ERR_INVALID_ARG, "value type %d not supported by ci_apply_H", m->vtype);
     CI_CHECK_LAUNCH();
 }

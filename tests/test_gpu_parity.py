@@ -306,3 +306,56 @@ def test_config2_full_size_sampled_rows_and_precision():
     del M
     ev64, info64 = g.build_H("f64").lowest_eigs(k=10)
     assert np.all(np.abs(ev32 - ev64) <= EIG_REL * np.maximum(np.abs(ev64), 1)), ev32 - ev64
+
+
+def _bf16_rn(x32):
+    """Round float32 values to bfloat16 bits, to nearest even (finite input)."""
+    b = np.ascontiguousarray(x32, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    return ((b + 0x7FFF + ((b >> 16) & 1)) >> 16).astype(np.uint16)
+
+
+def _bf16_to_f64(h16):
+    return (h16.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("case", ["small", "c2_sub"])
+def test_build_H_bf16_rowscale(case):
+    """BF16 storage (the precision-study option): per row, scale = max |v|
+    of the FP32 row and the stored value is bf16(v * (1/scale)) rounded to
+    nearest even; bit-exact against the FP32 build."""
+    inp = inputs(2, 3, 2, 2, seed=5) if case == "small" else preset_inputs("c2_sub")
+    g = gpu_problem(inp)
+    M32 = g.build_H("f32")
+    Mb = g.build_H("bf16")
+    rp, col, v32, _ = M32.export()
+    rpb, colb, v16, scale = Mb.export()
+    assert np.array_equal(rp, rpb) and np.array_equal(col, colb)
+    for r in range(M32.dim):
+        row = v32[rp[r]:rp[r + 1]]
+        m = np.float32(np.max(np.abs(row))) if len(row) else np.float32(0)
+        sc = m if m > 0 else np.float32(1)
+        assert scale[r] == sc
+        inv = np.float32(1) / sc
+        assert np.array_equal(v16[rp[r]:rp[r + 1]], _bf16_rn(row * inv)), r
+
+
+def test_apply_and_eigs_bf16_rowscale():
+    """SpMM of the BF16 form against its own values in FP64, and the lowest
+    eigenvalues within the perturbation bound of the BF16 rounding (Weyl:
+    |d lambda| <= ||dH||_2 <= max row sum of |dH|, |dH_rj| <= 2^-9 scale_r)."""
+    import torch
+    inp = preset_inputs("c2_sub")
+    g = gpu_problem(inp)
+    Mb = g.build_H("bf16")
+    rp, col, v16, scale = Mb.export()
+    vals = _bf16_to_f64(v16) * np.repeat(scale.astype(np.float64), np.diff(rp))
+    X = np.random.default_rng(4).standard_normal((Mb.dim, 8)).astype(np.float32)
+    Y = torch.empty((Mb.dim, 8), dtype=torch.float32, device="cuda")
+    Mb.apply_H(torch.from_numpy(X).cuda(), Y)
+    ref = oracle.spmm(rp, col, vals, X.astype(np.float64))
+    absref = oracle.spmm(rp, col, np.abs(vals), np.abs(X.astype(np.float64)))
+    assert np.all(np.abs(Y.cpu().numpy() - ref) <= 1e-6 * absref + 1e-30)
+    ev, info = Mb.lowest_eigs(k=10)
+    exact = np.array(golden()["c2_sub"]["lowest"])
+    bound = np.max(np.diff(rp) * scale.astype(np.float64)) * 2.0 ** -9
+    assert np.all(np.abs(ev - exact) <= bound + 1e-5 * np.abs(exact)), (np.abs(ev - exact).max(), bound)
