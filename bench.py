@@ -162,7 +162,7 @@ def workload_inputs():
 
 # DRAM bytes (read + write) per launch from one ncu capture of the current
 # kernels on this workload; reported as the roofline traffic.
-NCU_TRAFFIC_C1 = {"k_spmm": 838.7e6, "k_fill_rows": 962.1e6, "k_count_rows": 15.6e6}
+NCU_TRAFFIC_C1 = {"k_spmm": 838.9e6, "k_fill_rows": 963.1e6, "k_count_rows": 15.6e6}
 
 
 def algorithmic_bytes(kernel, dim, nnz, nvec=8):
@@ -416,7 +416,7 @@ def run_c2_leg(hbm):
 # ---------------------------------------------------------------- observables
 
 def run_observables_leg(sp, p, eps, tables, m, reps=2):
-    """Fig. 1 lines 16-20 on the benchmark workload: expectation values of m
+    """Fig. 1, observables step on the benchmark workload: expectation values of m
     seeded two-body operators in the k = 5 lowest eigenvectors, elements
     evaluated on the fly (never stored)."""
     import torch

@@ -161,7 +161,7 @@ ci_status ci_get_species(const ci_problem *p, int32_t species, uint64_t *bits,
  * every basis state.  cap must be >= dim. */
 ci_status ci_get_basis(const ci_problem *p, int32_t *p_idx, int32_t *n_idx, int64_t cap);
 
-/* Fig. 1 lines 2-5 (tiles) at the species level: for every determinant s of
+/* Fig. 1, tile filter (tiles) at the species level: for every determinant s of
  * a species, the determinants s' it can connect to through H, found by
  * popcount(BIN(s) XOR BIN(s')) (Sec. 2.1, Listing 2).  Kept: all s' with
  * 0 or 2 differing states, and s' with 4 differing states and 2M_s' =
@@ -176,13 +176,13 @@ ci_status ci_species_filter(ci_problem *p, void *stream);
 ci_status ci_get_species_conn(const ci_problem *p, int32_t species, int64_t *ptr,
                               int32_t *idx, int8_t *d, int64_t cap, int64_t *total);
 
-/* Fig. 1 lines 6-8: number of structurally nonzero entries of every row,
+/* Fig. 1, count step: number of structurally nonzero entries of every row,
  * i.e. basis states (p', n') within 4 differing s.p. states of the row
  * state (Listing 2's test, p and n bits side by side).  *nnz receives the
  * total; row_cnt (nullable, host or device, int32 [dim]) the per-row counts. */
 ci_status ci_count_nnz(ci_problem *p, int64_t *nnz, int32_t *row_cnt, void *stream);
 
-/* ---- Observables (Fig. 1 lines 16-20, Sec. 2.4, Eq. 2) ------------------ */
+/* ---- Observables (Fig. 1, observables step, Sec. 2.4, Eq. 2) ------------------ */
 
 /* Expectation values a[k][v] = sum_ij X[i][v] (O_k)_ij X[j][v] of m two-body
  * operators O_k over the problem's basis, for n vectors.  O_k has the pp, nn
@@ -241,7 +241,7 @@ ci_status ci_exclusive_scan(const int32_t *counts, int64_t n, int64_t *offsets, 
  * serialised by the caller.  Outputs are identical to ci_exclusive_scan. */
 ci_status ci_exclusive_scan_noalloc(const int32_t *counts, int64_t n, int64_t *offsets, void *stream);
 
-/* Fig. 1 lines 9-14 (Sec. 2.3, Listing 7): build H in CSR form on the
+/* Fig. 1, offsets and fill (Sec. 2.3, Listing 7): build H in CSR form on the
  * device.  Row i holds every column j with at most 4 differing s.p. states
  * (stored even when its value is 0), columns ascending.  H_ij = <Phi_i|H|Phi_j>
  * by the Slater-Condon rules, the phase from masked popcounts.  The matrix
@@ -256,7 +256,7 @@ ci_status ci_matrix_info(const ci_matrix *m, int64_t *dim, int64_t *nnz, int32_t
 ci_status ci_matrix_export(const ci_matrix *m, int64_t *row_ptr, int32_t *col,
                            void *val, float *row_scale, void *stream);
 
-/* Fig. 2 line 5 (Sec. 2): Y = H X for a block of nvec vectors (1..8), X and
+/* Fig. 2, optional FMA (Sec. 2): Y = H X for a block of nvec vectors (1..8), X and
  * Y device arrays [dim][nvec] (float for CI_F32 / CI_BF16_ROWSCALE, double
  * for CI_F64), not overlapping.  Each row is accumulated in the value
  * precision in ascending column order within each of 32 lanes. */
@@ -289,7 +289,7 @@ typedef struct {
     double seconds;       /* wall time of the call                              */
 } ci_eig_info;
 
-/* Fig. 1 line 15 (Sec. 2): lowest k eigenvalues of H by block Lanczos with
+/* Fig. 1, eigensolve (Sec. 2): lowest k eigenvalues of H by block Lanczos with
  * full FP64 reorthogonalisation (classical Gram-Schmidt against the two
  * newest blocks, then reorth_passes passes over the whole basis) and thick
  * restart.  SpMM in the matrix's
@@ -299,7 +299,7 @@ typedef struct {
 ci_status ci_lowest_eigs(const ci_matrix *m, const ci_eig_opts *opts, double *evals,
                          double *evecs, ci_eig_info *info, void *stream);
 
-/* Fig. 1 line 15 (Sec. 2): the same lowest k eigenpairs by LOBPCG (block
+/* Fig. 1, eigensolve (Sec. 2): the same lowest k eigenpairs by LOBPCG (block
  * size opts->block >= k, search space [X, W, P] of three blocks), the
  * preconditioned residuals W = (diag(H) - theta)^-1 R with a diagonal
  * (Jacobi) preconditioner, Rayleigh-Ritz through the FP64 Gram matrices of
@@ -313,7 +313,7 @@ ci_status ci_lowest_eigs_lobpcg(const ci_matrix *m, const ci_eig_opts *opts, dou
 
 /* ---------------------------------------------------------------- batched solves */
 
-/* Many independent problems built and solved together (Fig. 1 lines 1-15
+/* Many independent problems built and solved together (Fig. 1, basis through eigensolve
  * for each): every build step runs as one launch over all problems (the
  * matrices form one block-diagonal CSR, FP32 values), and the solve is a
  * block Lanczos whose per-problem control (basis size, thick restart,

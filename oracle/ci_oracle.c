@@ -371,7 +371,7 @@ double orc_element(const orc_problem *pr, const uint8_t *pb, const uint8_t *nb,
 }
 
 /* ---------------------------------------------------------------------- */
-/* Rows of H (Fig. 1 lines 6-14, Listing 2: every column of the row)       */
+/* Rows of H (Fig. 1, count and fill, Listing 2: every column of the row)       */
 /* ---------------------------------------------------------------------- */
 
 typedef struct {
@@ -424,7 +424,7 @@ int64_t orc_row(const orc_basis_view *B, int64_t i, int64_t cap, int64_t *cols,
     return c;
 }
 
-/* Number of stored entries of every row (Fig. 1 lines 6-8).  Rows that share
+/* Number of stored entries of every row (Fig. 1, count step).  Rows that share
  * a proton determinant reuse its difference list (same result as recomputing
  * it per row). */
 void orc_row_counts(const orc_basis_view *B, int64_t *counts)
@@ -448,8 +448,8 @@ void orc_row_counts(const orc_basis_view *B, int64_t *counts)
     }
 }
 
-/* Fill a CSR whose row_ptr the caller has made from orc_row_counts (Fig. 1
- * lines 10-14).  absums may be NULL. */
+/* Fill a CSR whose row_ptr the caller has made from orc_row_counts (Fig. 1,
+ * fill step).  absums may be NULL. */
 void orc_fill(const orc_basis_view *B, const int64_t *row_ptr, int64_t *cols,
               double *vals, double *absums)
 {
@@ -468,7 +468,7 @@ void orc_fill(const orc_basis_view *B, const int64_t *row_ptr, int64_t *cols,
     }
 }
 
-/* Y = H X in FP64 over a CSR (Fig. 2 line 5: the FMA of H_ij with the j-th
+/* Y = H X in FP64 over a CSR (Fig. 2, optional FMA: H_ij with the j-th
  * vector element), X and Y row-major [dim][nvec]. */
 void orc_spmm(int64_t dim, const int64_t *row_ptr, const int64_t *cols,
               const double *vals, const double *X, double *Y, int nvec)

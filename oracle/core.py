@@ -203,8 +203,8 @@ class OracleProblem:
 
 
 def expectation_values(row_ptr, cols, vals, X):
-    """a[v] = sum_ij X[i, v] O_ij X[j, v] for a CSR operator O (Fig. 1 line 20,
-    Eq. 2 with the vectors c_i of line 20): the row sums of O X, dotted with X
+    """a[v] = sum_ij X[i, v] O_ij X[j, v] for a CSR operator O (Fig. 1,
+    observables step: Eq. 2 with the eigenvectors c_i): the row sums of O X, dotted with X
     column by column (the SpMM of ``spmm`` is the one product)."""
     X = np.asarray(X, dtype=np.float64)
     if X.ndim == 1:

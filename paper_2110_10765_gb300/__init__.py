@@ -108,7 +108,7 @@ class Problem:
             lib().ci_problem_destroy(h)
             self._h = None
 
-    # -- Fig. 1 line 1 ---------------------------------------------------
+    # -- Fig. 1, basis step ---------------------------------------------------
     def enumerate_basis(self, stream=None):
         dim = C.c_int64()
         check(lib().ci_enumerate_basis(self._h, C.byref(dim), _stream(stream)), "ci_enumerate_basis")
@@ -130,7 +130,7 @@ class Problem:
         check(lib().ci_get_basis(self._h, _ptr(p), _ptr(n), dim), "ci_get_basis")
         return p[:dim], n[:dim]
 
-    # -- Fig. 1 lines 2-5 ------------------------------------------------
+    # -- Fig. 1, tile filter ------------------------------------------------
     def species_filter(self, stream=None):
         check(lib().ci_species_filter(self._h, _stream(stream)), "ci_species_filter")
 
@@ -147,13 +147,13 @@ class Problem:
                                         C.byref(total)), "ci_get_species_conn")
         return ptr, idx[: total.value], d[: total.value]
 
-    # -- Fig. 1 lines 6-8 ------------------------------------------------
+    # -- Fig. 1, count step ------------------------------------------------
     def count_nnz(self, row_cnt=None, stream=None):
         nnz = C.c_int64()
         check(lib().ci_count_nnz(self._h, C.byref(nnz), _ptr(row_cnt), _stream(stream)), "ci_count_nnz")
         return nnz.value
 
-    # -- Fig. 1 lines 16-20 ----------------------------------------------
+    # -- Fig. 1, observables step ----------------------------------------------
     def observables(self, op_seeds, X, stream=None):
         """Expectation values a[k, v] = X[:, v]^T O_k X[:, v] (numpy [m, n]) of
         the seeded two-body operators op_seeds; X is a device float64 tensor
@@ -165,7 +165,7 @@ class Problem:
               "ci_observables")
         return a
 
-    # -- Fig. 1 lines 9-14 -----------------------------------------------
+    # -- Fig. 1, offsets and fill -----------------------------------------------
     def build_H(self, vtype="f32", stream=None):
         h = C.c_void_p()
         check(lib().ci_build_H(self._h, VTYPES.get(vtype, vtype), C.byref(h), _stream(stream)), "ci_build_H")
@@ -205,13 +205,13 @@ class Matrix:
         check(lib().ci_matrix_export(self._h, _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(row_scale),
                                      _stream(stream)), "ci_matrix_export")
 
-    # -- Fig. 2 line 5 -------------------------------------------------------
+    # -- Fig. 2, optional FMA -------------------------------------------------------
     def apply_H(self, X, Y, stream=None):
         """Y = H X for device tensors [dim, nvec] (nvec 1..8)."""
         nvec = 1 if X.dim() == 1 else int(X.shape[1])
         check(lib().ci_apply_H(self._h, _ptr(X), _ptr(Y), nvec, _stream(stream)), "ci_apply_H")
 
-    # -- Fig. 1 line 15 ------------------------------------------------------
+    # -- Fig. 1, eigensolve ------------------------------------------------------
     def lowest_eigs(self, k=5, block=8, max_basis=0, max_iter=0, tol=0.0, seed=1, reorth_passes=0,
                     check_every=0, evecs=None, stream=None, allow_unconverged=False, method="lanczos"):
         """Lowest k eigenvalues (numpy, ascending) and the solve info dict.

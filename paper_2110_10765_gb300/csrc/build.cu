@@ -1,4 +1,4 @@
-// Count -> scan -> fill of the Hamiltonian rows (Fig. 1 lines 6-14,
+// Count -> scan -> fill of the Hamiltonian rows (Fig. 1, count and fill,
 // Sec. 2.2-2.3).  One warp owns one row (p, n).  The row's partners are
 // the proton partners p' of p (ascending) crossed with segments of the
 // neutron lists of n: for p' two states away (list O2), the L2(n) entries
@@ -308,7 +308,7 @@ __device__ __forceinline__ void load_partner(const RowArgs<T> &a, const RowCtx &
 // own cross rank says.
 // Every element (pos, col, value) of a row goes to an emitter: StoreEmit
 // writes the CSR arrays; ApplyEmit multiplies by X on the fly (no storage)
-// for the expectation values of Fig. 1 lines 16-20.
+// for the expectation values of Fig. 1, observables step.
 template <class T>
 struct StoreEmit {
     __device__ __forceinline__ void init() {}
@@ -527,7 +527,7 @@ static void fill_group_t(const std::vector<Problem *> &ps, GroupCSR *g, cudaStre
            (const int64_t *)doff.ptr, (int)ps.size(), StoreEmit<T>{}, (double *)nullptr);
 }
 
-// Fig. 1 lines 9-14 for a counted group: allocate and fill col / val.
+// Fig. 1, offsets and fill for a counted group: allocate and fill col / val.
 void fill_group(const std::vector<Problem *> &ps, GroupCSR *g, cudaStream_t s) {
     g->col.alloc(g->nnz);
     g->val.alloc(g->nnz * (g->prec ? sizeof(double) : sizeof(float)));

@@ -1,5 +1,5 @@
 // Batched, device-driven block Lanczos over many independent Hamiltonians
-// (the batched and served forms of Fig. 1 lines 6-15).
+// (the batched and served forms of Fig. 1, count through eigensolve).
 //
 // Every problem occupies a slot.  Its CSR (FP32 values), Krylov basis Q
 // [dim][MB] (FP64), work blocks and small dense state live on the device;

@@ -1,4 +1,4 @@
-// Species-level connectivity (Fig. 1 lines 2-5, Sec. 2.1, Listing 2):
+// Species-level connectivity (Fig. 1, tile filter, Sec. 2.1, Listing 2):
 // XOR + popcount over every pair of determinants of one species, count ->
 // scan -> fill with warp ballots, and the like-particle part of every
 // Slater-Condon element evaluated once per species pair.
@@ -478,7 +478,7 @@ static FilterArgs<T> filter_job(Problem *p, int species, int modes, const Tables
     return a;
 }
 
-// Species connectivity of every problem of ps (Fig. 1 lines 2-5): count
+// Species connectivity of every problem of ps (Fig. 1, tile filter): count
 // pass, one scan over all lists, one allocation, fill pass, segment tables.
 template <class T>
 void species_filter_group(const std::vector<Problem *> &ps_in, cudaStream_t s) {

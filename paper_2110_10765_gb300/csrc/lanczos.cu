@@ -1,4 +1,4 @@
-// Lowest eigenpairs of H (Fig. 1 line 15): block Lanczos with full FP64
+// Lowest eigenpairs of H (Fig. 1, eigensolve): block Lanczos with full FP64
 // reorthogonalisation (classical Gram-Schmidt, repeated), thick restart,
 // and a rank-revealing block QR that completes a deflated block with
 // random directions.  H is applied by the SpMM in the matrix's precision;

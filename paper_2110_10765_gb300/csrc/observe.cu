@@ -1,5 +1,5 @@
-// Expectation values of two-body operators (Fig. 1 lines 16-20, Fig. 2 lines
-// 4-5 without the store, Sec. 2.4, Eq. 2):
+// Expectation values of two-body operators (Fig. 1, observables step; Fig. 2's
+// element evaluation without the store; Sec. 2.4, Eq. 2):
 //   a[k][v] = sum_ij X[i][v] (O_k)_ij X[j][v]
 // for m operators O_k and n <= 8 vectors.  The elements of O_k are evaluated
 // on the fly by the row kernels of the Hamiltonian build (same connectivity,

@@ -1,5 +1,5 @@
 // Problem set-up: validation, the host planner of the species lists and the
-// product basis (Fig. 1 line 1), and the staging of the interaction into
+// product basis (Fig. 1, basis step), and the staging of the interaction into
 // compact device tables.
 #include <algorithm>
 #include <cstring>

@@ -1,4 +1,4 @@
-// SpMM Y = H X over the CSR matrix (Fig. 2 line 5: FMA of H_ij with the
+// SpMM Y = H X over the CSR matrix (Fig. 2, optional FMA of H_ij with the
 // j-th vector element), X and Y row-major [dim][NV].  One warp per row:
 // lanes stride over the row's nonzeros with coalesced col/val loads and one
 // vector load of X's row per nonzero, then a butterfly reduction.

@@ -1,4 +1,4 @@
-"""LOBPCG (Fig. 1 line 15: the paper names LOBPCG beside Lanczos) against
+"""LOBPCG (Fig. 1, eigensolve: the paper names LOBPCG beside Lanczos) against
 the oracle's eigenvalues."""
 
 import numpy as np

@@ -1,4 +1,4 @@
-"""Expectation values of seeded two-body operators (Fig. 1 lines 16-20)
+"""Expectation values of seeded two-body operators (Fig. 1, observables step)
 evaluated on the fly on the GPU, against the oracle's operator CSR."""
 
 import numpy as np

@@ -390,7 +390,7 @@ def test_count_pairs_duplicates_and_singletons():
     assert oracle.count_pairs(mbs[:0]).tolist() == []
 
 
-# ---- observables (Fig. 1 lines 16-20) ------------------------------------------
+# ---- observables (Fig. 1, observables step) ------------------------------------------
 
 def _operator(n_shell, Z, N, nmax, seed, twoM=None):
     """Oracle problem of the two-body operator with the TBMEs of `seed` and
