@@ -438,9 +438,21 @@ def run_observables_leg(sp, p, eps, tables, m, reps=2):
         b.synchronize()
         ms.append(a.elapsed_time(b))
     t = min(ms)
+    # transition elements x_v^T O_k y_v for 16 seeded vector pairs (two
+    # passes of eight vectors per operator)
+    g = torch.Generator(device="cuda").manual_seed(11)
+    X = torch.randn((M.dim, 16), dtype=torch.float64, device="cuda", generator=g)
+    Y = torch.randn((M.dim, 16), dtype=torch.float64, device="cuda", generator=g)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    prob.observables(seeds, X, Y)
+    b.record(stream)
+    b.synchronize()
+    t16 = a.elapsed_time(b)
     return {"operators": m, "vectors": p.k, "ms": t, "ms_per_operator": t / m,
             "elements_per_s": M.nnz * m / (t * 1e-3), "nnz": M.nnz,
-            "first_values": [round(float(x), 9) for x in vals[0]]}
+            "first_values": [round(float(x), 9) for x in vals[0]],
+            "transition_16_vectors": {"ms": t16, "ms_per_operator": t16 / m}}
 
 
 # ---------------------------------------------------------------- count benchmark

@@ -184,18 +184,23 @@ ci_status ci_count_nnz(ci_problem *p, int64_t *nnz, int32_t *row_cnt, void *stre
 
 /* ---- Observables (Fig. 1, observables step, Sec. 2.4, Eq. 2) ------------------ */
 
-/* Expectation values a[k][v] = sum_ij X[i][v] (O_k)_ij X[j][v] of m two-body
- * operators O_k over the problem's basis, for n vectors.  O_k has the pp, nn
- * and pn TBMEs of the CI_TBME_SEED recipe with seed op_seeds[k] and no
+/* Expectation values and transition elements
+ *   a[k][v] = sum_ij X[i][v] (O_k)_ij Y[j][v]
+ * of m two-body operators O_k over the problem's basis, for n vector pairs
+ * (Y = NULL means Y = X: the expectation values of Eq. 2).  O_k has the pp,
+ * nn and pn TBMEs of the CI_TBME_SEED recipe with seed op_seeds[k] and no
  * one-body part; its elements are evaluated on the fly by the Slater-Condon
  * rules of the Hamiltonian build (FP64 tables) and never stored.
  *   op_seeds  host, m seeds; m in 1..4096.
- *   X         device, double [dim][n] in basis order, n in 1..8.
+ *   X, Y      device, double [dim][n] in basis order, n in 1..16; Y may be
+ *             NULL.  Both are only read.
  *   a         host, double [m][n] (written; the stream is synchronised).
- * The problem's basis and FP64 species connectivity are built on first use.
- * Errors: CI_ERR_INVALID_ARG (sizes, NULL or host X). */
-ci_status ci_observables(ci_problem *p, const uint64_t *op_seeds, int32_t m, const double *X, int32_t n,
-                         double *a, void *stream);
+ * The row kernel takes the vectors eight at a time, so n in 9..16 costs two
+ * element evaluations per operator.  The problem's basis and FP64 species
+ * connectivity are built on first use.
+ * Errors: CI_ERR_INVALID_ARG (sizes, NULL or host X, host Y). */
+ci_status ci_observables(ci_problem *p, const uint64_t *op_seeds, int32_t m, const double *X, const double *Y,
+                         int32_t n, double *a, void *stream);
 
 /* ---- Nonzero-count benchmark (Sec. 2.1, Listings 1-2, Figs. 3-4) ------- */
 

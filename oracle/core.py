@@ -202,15 +202,25 @@ class OracleProblem:
         return self.lib.orc_count_difference(_ptr(x), _ptr(y), occ.shape[1])
 
 
-def expectation_values(row_ptr, cols, vals, X):
-    """a[v] = sum_ij X[i, v] O_ij X[j, v] for a CSR operator O (Fig. 1,
-    observables step: Eq. 2 with the eigenvectors c_i): the row sums of O X, dotted with X
-    column by column (the SpMM of ``spmm`` is the one product)."""
+def expectation_values(row_ptr, cols, vals, X, Y=None):
+    """a[v] = sum_ij X[i, v] O_ij Y[j, v] for a CSR operator O (Fig. 1,
+    observables step: Eq. 2 with the eigenvectors c_i; Y = None means Y = X,
+    the expectation values, another Y gives transition elements): the rows
+    of O Y, dotted with X column by column (the SpMM of ``spmm`` is the one
+    product)."""
     X = np.asarray(X, dtype=np.float64)
     if X.ndim == 1:
         X = X[:, None]
-    Y = spmm(row_ptr, cols, vals, X)
-    return np.einsum("iv,iv->v", X, Y)
+    if Y is None:
+        Y = X
+    else:
+        Y = np.asarray(Y, dtype=np.float64)
+        if Y.ndim == 1:
+            Y = Y[:, None]
+        if Y.shape != X.shape:
+            raise ValueError("X and Y must have the same shape")
+    OY = spmm(row_ptr, cols, vals, Y)
+    return np.einsum("iv,iv->v", X, OY)
 
 
 def count_pairs(mbs, rows=None, max_diff=4):

@@ -154,15 +154,17 @@ class Problem:
         return nnz.value
 
     # -- Fig. 1, observables step ----------------------------------------------
-    def observables(self, op_seeds, X, stream=None):
-        """Expectation values a[k, v] = X[:, v]^T O_k X[:, v] (numpy [m, n]) of
-        the seeded two-body operators op_seeds; X is a device float64 tensor
-        [dim, n] (n <= 8)."""
+    def observables(self, op_seeds, X, Y=None, stream=None):
+        """a[k, v] = X[:, v]^T O_k Y[:, v] (numpy [m, n]) for the seeded
+        two-body operators op_seeds; X and Y are device float64 tensors
+        [dim, n] (n <= 16), Y = None meaning Y = X (expectation values)."""
         seeds = np.ascontiguousarray(np.asarray(op_seeds, dtype=np.uint64).reshape(-1))
         n = 1 if X.dim() == 1 else int(X.shape[1])
+        if Y is not None and tuple(Y.shape) != tuple(X.shape):
+            raise ValueError("X and Y must have the same shape")
         a = np.zeros((len(seeds), n), np.float64)
-        check(lib().ci_observables(self._h, _ptr(seeds), len(seeds), _ptr(X), n, _ptr(a), _stream(stream)),
-              "ci_observables")
+        check(lib().ci_observables(self._h, _ptr(seeds), len(seeds), _ptr(X), None if Y is None else _ptr(Y), n,
+                                   _ptr(a), _stream(stream)), "ci_observables")
         return a
 
     # -- Fig. 1, offsets and fill -----------------------------------------------

@@ -88,7 +88,7 @@ _SIGS = {
     "ci_exclusive_scan_noalloc": (C.c_int, [_P, C.c_int64, _P, _P]),
     "ci_count_pairs": (C.c_int, [_P, C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
                                  C.POINTER(C.c_int64), _P, _P]),
-    "ci_observables": (C.c_int, [_P, _P, C.c_int32, _P, C.c_int32, _P, _P]),
+    "ci_observables": (C.c_int, [_P, _P, C.c_int32, _P, _P, C.c_int32, _P, _P]),
     "ci_build_H": (C.c_int, [_P, C.c_int32, C.POINTER(_P), _P]),
     "ci_matrix_destroy": (None, [_P]),
     "ci_matrix_info": (C.c_int, [_P, _I64P, _I64P, C.POINTER(C.c_int32)]),

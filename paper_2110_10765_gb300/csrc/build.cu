@@ -320,18 +320,19 @@ struct StoreEmit {
     __device__ __forceinline__ void finish(double *) {}
 };
 
-// y_i = sum_j O_ij X[j][0..8) accumulated per lane, reduced per row, then
-// tot += X[i] * y_i (lane 0); at the end the block's tot goes to part.
+// y_i = sum_j O_ij R[j][0..8) accumulated per lane, reduced per row, then
+// tot += L[i] * y_i (lane 0); at the end the block's tot goes to part.
 template <class T>
 struct ApplyEmit {
-    const double *X = nullptr;   // [dim][8]
+    const double *R = nullptr;   // right vectors [dim][8], gathered by column
+    const double *L = nullptr;   // left vectors [dim][8], one row per row end
     double acc[8], tot[8];
     __device__ __forceinline__ void init() {
 #pragma unroll
         for (int q = 0; q < 8; ++q) acc[q] = tot[q] = 0.0;
     }
     __device__ __forceinline__ void put(const RowArgs<T> &, int64_t, int c, T v) {
-        const double2 *xc = reinterpret_cast<const double2 *>(X + (int64_t)c * 8);
+        const double2 *xc = reinterpret_cast<const double2 *>(R + (int64_t)c * 8);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const double2 t = __ldg(xc + q);
@@ -345,7 +346,7 @@ struct ApplyEmit {
             double y = acc[q];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
-            if ((threadIdx.x & 31) == 0) tot[q] = fma(X[r * 8 + q], y, tot[q]);
+            if ((threadIdx.x & 31) == 0) tot[q] = fma(L[r * 8 + q], y, tot[q]);
             acc[q] = 0.0;
         }
     }
@@ -536,8 +537,8 @@ void fill_group(const std::vector<Problem *> &ps, GroupCSR *g, cudaStream_t s) {
 }
 
 template <class T>
-int observable_apply(Problem *p, const Tables<T> &t, const ConnEntry<T> *ents, const double *X8, double *part,
-                     cudaStream_t s) {
+int observable_apply(Problem *p, const Tables<T> &t, const ConnEntry<T> *ents, const double *L8, const double *R8,
+                     double *part, cudaStream_t s) {
     std::vector<RowArgs<T>> args{row_args<T>(p, &t, ents)};
     std::vector<int64_t> row_off{0, p->dim};
     if (p->dim == 0) return 0;
@@ -545,7 +546,8 @@ int observable_apply(Problem *p, const Tables<T> &t, const ConnEntry<T> *ents, c
     DevBuf<int64_t> doff;
     upload_args<T>(args, row_off, dargs, doff, s);
     ApplyEmit<T> em{};
-    em.X = X8;
+    em.L = L8;
+    em.R = R8;
     const int grid = row_grid(p->dim);
     launch("k_observable_rows", k_rows<T, ApplyEmit<T>>, grid, 256, 0, s, (const RowArgs<T> *)dargs.ptr,
            (const int64_t *)doff.ptr, 1, em, part);
@@ -553,9 +555,9 @@ int observable_apply(Problem *p, const Tables<T> &t, const ConnEntry<T> *ents, c
 }
 
 template int observable_apply<float>(Problem *, const Tables<float> &, const ConnEntry<float> *, const double *,
-                                     double *, cudaStream_t);
+                                     const double *, double *, cudaStream_t);
 template int observable_apply<double>(Problem *, const Tables<double> &, const ConnEntry<double> *, const double *,
-                                      double *, cudaStream_t);
+                                      const double *, double *, cudaStream_t);
 
 // BF16 storage with a per-row scale: scale_r = max_j |v_rj| (1 for an
 // all-zero row), stored value bf16(v / scale_r) rounded to nearest; one

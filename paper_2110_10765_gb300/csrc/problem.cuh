@@ -222,8 +222,8 @@ void operator_entries(Problem *p, const Tables<T> &t, ConnEntry<T> *ents, cudaSt
 // entries ents; X [dim][8] FP64 on the device; one partial per block in
 // part (nblk x 8, device); returns nblk.
 template <class T>
-int observable_apply(Problem *p, const Tables<T> &t, const ConnEntry<T> *ents, const double *X8, double *part,
-                     cudaStream_t s);
+int observable_apply(Problem *p, const Tables<T> &t, const ConnEntry<T> *ents, const double *L8, const double *R8,
+                     double *part, cudaStream_t s);
 template <class T> void species_filter_group(const std::vector<Problem *> &ps, cudaStream_t s);
 template <class T> void species_filter(Problem *p, cudaStream_t s) { species_filter_group<T>({p}, s); }
 // count (and optionally fill) the rows of every problem of ps in one launch each

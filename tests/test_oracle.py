@@ -415,6 +415,36 @@ def test_expectation_values_dense_and_unit_vectors():
         assert oracle.expectation_values(rp, col, val, e)[0] == o.element(i, i)[0]
 
 
+def test_transition_elements_dense_units_and_polarisation():
+    """x^T O y against the dense operator and against single elements
+    (unit vectors pick O_ij); the polarisation identity ties it to the
+    expectation values, x^T O y = (a(x + y) - a(x - y)) / 4 for a symmetric
+    O; a non-symmetric CSR catches swapped X and Y."""
+    o, (rp, col, val, ab) = _operator(1, 2, 2, -1, 78)
+    dense = oracle.dense_from_csr(rp, col, val, o.dim)
+    rng = np.random.default_rng(3)
+    X = rng.standard_normal((o.dim, 4))
+    Y = rng.standard_normal((o.dim, 4))
+    t = oracle.expectation_values(rp, col, val, X, Y)
+    assert np.allclose(t, np.einsum("iv,ij,jv->v", X, dense, Y), rtol=1e-13, atol=1e-12)
+    pol = (oracle.expectation_values(rp, col, val, X + Y) - oracle.expectation_values(rp, col, val, X - Y)) / 4
+    assert np.allclose(t, pol, rtol=1e-12, atol=1e-12)
+    nz = [(i, int(col[e])) for i in range(o.dim) for e in range(rp[i], rp[i + 1]) if col[e] != i]
+    for i, j in nz[:: max(1, len(nz) // 5)]:
+        ei = np.zeros(o.dim); ei[i] = 1.0
+        ej = np.zeros(o.dim); ej[j] = 1.0
+        assert oracle.expectation_values(rp, col, val, ei, ej)[0] == o.element(i, j)[0]
+    with pytest.raises(ValueError):
+        oracle.expectation_values(rp, col, val, X, Y[:, :2])
+    A = np.triu(rng.standard_normal((6, 6)))          # not symmetric
+    arp = np.concatenate([[0], np.cumsum((A != 0).sum(1))]).astype(np.int64)
+    acol = np.nonzero(A)[1].astype(np.int64)
+    x, y = rng.standard_normal((6, 2)), rng.standard_normal((6, 2))
+    ta = oracle.expectation_values(arp, acol, A[A != 0], x, y)
+    assert np.allclose(ta, np.einsum("iv,ij,jv->v", x, A, y), rtol=1e-13)
+    assert not np.allclose(ta, np.einsum("iv,ij,jv->v", y, A, x))
+
+
 def test_operator_has_no_one_body_part_and_scales():
     """The same TBMEs with eps = 0: H(seed) - O(seed) is the one-body
     diagonal; a scaled vector scales the value quadratically."""
