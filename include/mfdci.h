@@ -305,16 +305,57 @@ ci_status ci_lowest_eigs(const ci_matrix *m, const ci_eig_opts *opts, double *ev
                          double *evecs, ci_eig_info *info, void *stream);
 
 /* Fig. 1, eigensolve (Sec. 2): the same lowest k eigenpairs by LOBPCG (block
- * size opts->block >= k, search space [X, W, P] of three blocks), the
- * preconditioned residuals W = (diag(H) - theta)^-1 R with a diagonal
- * (Jacobi) preconditioner, Rayleigh-Ritz through the FP64 Gram matrices of
- * the three blocks (Cholesky of the overlap; P is dropped for an iteration
- * when the overlap loses rank).  SpMM in the matrix's precision, everything
- * else in FP64.  Options and outputs as ci_lowest_eigs; max_basis,
- * reorth_passes and check_every are ignored, max_iter counts iterations
- * [1000].  Dimensions up to 4*block use the dense path of ci_lowest_eigs. */
-ci_status ci_lowest_eigs_lobpcg(const ci_matrix *m, const ci_eig_opts *opts, double *evals,
-                                double *evecs, ci_eig_info *info, void *stream);
+ * size opts->block >= k, search space [X, W, P] of three blocks), W = T R
+ * the preconditioned residuals, Rayleigh-Ritz through the FP64 Gram
+ * matrices of the three blocks (Cholesky of the overlap; P is dropped for an
+ * iteration when the overlap loses rank).  SpMM in the matrix's precision,
+ * everything else in FP64.
+ *   row_block, nblocks  NULL / 0: the diagonal (Jacobi) preconditioner
+ *             T = (diag(H) - theta_v)^-1 per vector.  Otherwise a device
+ *             int32 [dim] group index in 0..nblocks-1 of every row (e.g.
+ *             from ci_orbital_blocks) and the block-diagonal preconditioner
+ *             of ci_block_precond_apply over those groups, its shift sigma =
+ *             theta_1 - |r_1| taken from the Rayleigh-Ritz of iterations
+ *             0, 2, 6, 14, 30, ... (the blocks are re-inverted then).
+ * Options and outputs as ci_lowest_eigs; max_basis, reorth_passes and
+ * check_every are ignored, max_iter counts iterations [1000].  Dimensions up
+ * to 4*block use the dense path of ci_lowest_eigs.  Errors as
+ * ci_lowest_eigs, plus CI_ERR_INVALID_ARG for a row_block entry outside
+ * 0..nblocks-1 or a host row_block. */
+ci_status ci_lowest_eigs_lobpcg(const ci_matrix *m, const ci_eig_opts *opts, const int32_t *row_block,
+                                int64_t nblocks, double *evals, double *evecs, ci_eig_info *info, void *stream);
+
+/* Many-body basis orbitals (Sec. 2): the basis states that put the
+ * nucleons of each species into the same single-particle orbitals, i.e.
+ * differ only in the orbitals' magnetic substates, form one group; a
+ * group of the product basis is a pair (proton group, neutron group).
+ *   sp_orbital  host int32 [S]: orbital label (>= 0) of every s.p. state;
+ *               states with equal labels belong to one orbital (n, l, j).
+ *   block       device int32 [dim] or NULL: group of every basis state,
+ *               numbered 0, 1, ... in order of first appearance by row.
+ *   nblocks     host int64: number of groups.
+ * Errors: CI_ERR_INVALID_ARG (NULL or negative labels, host block). */
+ci_status ci_orbital_blocks(ci_problem *p, const int32_t *sp_orbital, int32_t *block, int64_t *nblocks,
+                            void *stream);
+
+/* The block-diagonal preconditioner of LOBPCG (Sec. 2: the diagonal blocks
+ * of H over many-body orbitals), applied once:
+ *   W = T R,  T = blockdiag_b (H_bb - sigma_b I)^-1.
+ * The blocks are the groups of row_block, each cut into consecutive
+ * sub-blocks of at most 128 rows (member rows ascending, split into
+ * ceil(c/128) parts whose sizes differ by at most one, the larger first).
+ * sigma_b = sigma when H_bb - sigma I is positive definite (every pivot of
+ * the Gauss-Jordan inversion > 1e-12 (||H_bb||_inf + |sigma|)), else
+ * min(sigma, g_b) - 1e-3 max(||H_bb||_inf, |sigma|) with g_b the Gershgorin
+ * lower bound min_i (H_ii - sum_{j != i} |H_ij|) over the sub-block.
+ * Inverses are formed in FP64, stored and applied in FP32.
+ *   row_block, nblocks  as ci_lowest_eigs_lobpcg (device, required).
+ *   R, W        device double [dim][nvec], nvec 1..8.
+ *   row_shift   device double [dim] or NULL: sigma_b of each row's sub-block.
+ * The stream is synchronised.  Errors: CI_ERR_INVALID_ARG (pointers, sizes,
+ * group indices, non-finite sigma). */
+ci_status ci_block_precond_apply(const ci_matrix *m, const int32_t *row_block, int64_t nblocks, double sigma,
+                                 const double *R, double *W, int32_t nvec, double *row_shift, void *stream);
 
 /* ---------------------------------------------------------------- batched solves */
 

@@ -15,12 +15,14 @@ than itself):
 * ``brute.py`` (pure Python): H built by applying every second-quantised
   operator term to every basis state, for tiny spaces;
 * ``eig.py``: lowest eigenvalues by LAPACK (dense) or ARPACK (sparse), the
-  plain definition of "lowest k eigenvalues".
+  plain definition of "lowest k eigenvalues";
+* ``precond.py``: many-body basis orbitals and the block-diagonal
+  preconditioner of LOBPCG (dense solves per block).
 """
 
 from .core import OracleProblem, build_library, count_pairs, exclusive_scan, expectation_values, spmm
 from .eig import lowest_dense, lowest_sparse, dense_from_csr
-from . import brute
+from . import brute, precond
 
 __all__ = ["OracleProblem", "build_library", "count_pairs", "exclusive_scan", "expectation_values", "spmm",
-           "lowest_dense", "lowest_sparse", "dense_from_csr", "brute"]
+           "lowest_dense", "lowest_sparse", "dense_from_csr", "brute", "precond"]

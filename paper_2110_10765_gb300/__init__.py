@@ -167,6 +167,18 @@ class Problem:
                                    _ptr(a), _stream(stream)), "ci_observables")
         return a
 
+    def orbital_blocks(self, sp_orbital, stream=None):
+        """Many-body basis orbitals: (device int32 tensor [dim] of group
+        indices, number of groups) for the s.p. orbital labels sp_orbital."""
+        import torch
+        lab = np.ascontiguousarray(np.asarray(sp_orbital, dtype=np.int32))
+        nb = C.c_int64()
+        dim = self.enumerate_basis(stream)
+        blk = torch.empty(dim, dtype=torch.int32, device="cuda")
+        check(lib().ci_orbital_blocks(self._h, _ptr(lab), _ptr(blk), C.byref(nb), _stream(stream)),
+              "ci_orbital_blocks")
+        return blk, nb.value
+
     # -- Fig. 1, offsets and fill -----------------------------------------------
     def build_H(self, vtype="f32", stream=None):
         h = C.c_void_p()
@@ -207,6 +219,18 @@ class Matrix:
         check(lib().ci_matrix_export(self._h, _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(row_scale),
                                      _stream(stream)), "ci_matrix_export")
 
+    def block_precond_apply(self, blocks, sigma, R, stream=None):
+        """W = T R with the block-diagonal preconditioner of LOBPCG over the
+        groups blocks = (row_block, nblocks) and shift sigma; R a device
+        float64 tensor [dim, nvec] (nvec <= 8).  Returns (W, row_shift)."""
+        import torch
+        nvec = 1 if R.dim() == 1 else int(R.shape[1])
+        W = torch.empty_like(R)
+        shift = torch.empty(self.dim, dtype=torch.float64, device=R.device)
+        check(lib().ci_block_precond_apply(self._h, _ptr(blocks[0]), int(blocks[1]), float(sigma), _ptr(R), _ptr(W),
+                                           nvec, _ptr(shift), _stream(stream)), "ci_block_precond_apply")
+        return W, shift
+
     # -- Fig. 2, optional FMA -------------------------------------------------------
     def apply_H(self, X, Y, stream=None):
         """Y = H X for device tensors [dim, nvec] (nvec 1..8)."""
@@ -215,16 +239,28 @@ class Matrix:
 
     # -- Fig. 1, eigensolve ------------------------------------------------------
     def lowest_eigs(self, k=5, block=8, max_basis=0, max_iter=0, tol=0.0, seed=1, reorth_passes=0,
-                    check_every=0, evecs=None, stream=None, allow_unconverged=False, method="lanczos"):
+                    check_every=0, evecs=None, stream=None, allow_unconverged=False, method="lanczos",
+                    blocks=None):
         """Lowest k eigenvalues (numpy, ascending) and the solve info dict.
 
         evecs: optional device float64 tensor [dim, k] for the eigenvectors.
-        method: "lanczos" (ci_lowest_eigs) or "lobpcg" (ci_lowest_eigs_lobpcg)."""
+        method: "lanczos" (ci_lowest_eigs) or "lobpcg" (ci_lowest_eigs_lobpcg).
+        blocks: for LOBPCG, (row_block device int32 tensor, nblocks) from
+        ``Problem.orbital_blocks`` for the block-diagonal preconditioner;
+        None for the diagonal one."""
         o = _lib.EigOpts(k, block, max_basis, max_iter, tol, seed, reorth_passes, check_every)
         ev = np.zeros(k, np.float64)
         info = _lib.EigInfo()
-        fn = {"lanczos": lib().ci_lowest_eigs, "lobpcg": lib().ci_lowest_eigs_lobpcg}[method]
-        st = fn(self._h, C.byref(o), _ptr(ev), _ptr(evecs), C.byref(info), _stream(stream))
+        if method == "lanczos":
+            if blocks is not None:
+                raise ValueError("blocks is a LOBPCG option")
+            st = lib().ci_lowest_eigs(self._h, C.byref(o), _ptr(ev), _ptr(evecs), C.byref(info), _stream(stream))
+        elif method == "lobpcg":
+            rb, nb = (None, 0) if blocks is None else (_ptr(blocks[0]), int(blocks[1]))
+            st = lib().ci_lowest_eigs_lobpcg(self._h, C.byref(o), rb, nb, _ptr(ev), _ptr(evecs), C.byref(info),
+                                             _stream(stream))
+        else:
+            raise ValueError(f"unknown method {method!r}")
         if not (allow_unconverged and st == _lib.CI_ERR_NOT_CONVERGED):
             check(st, "ci_lowest_eigs" if method == "lanczos" else "ci_lowest_eigs_lobpcg")
         out = {"iterations": info.iterations, "restarts": info.restarts, "converged": info.converged,

@@ -7,6 +7,7 @@
 // from the Gram-Schmidt coefficients and diagonalised there (dense.h).
 #include <chrono>
 #include <cmath>
+#include <memory>
 
 #include <cuda_bf16.h>
 
@@ -825,8 +826,8 @@ static bool pencil_lowest(int n, int nb, const std::vector<double> &GA, const st
     return true;
 }
 
-void lowest_eigs_lobpcg(const Matrix *H, const ci_eig_opts *opts_in, double *evals, double *evecs,
-                        ci_eig_info *info, cudaStream_t s) {
+void lowest_eigs_lobpcg(const Matrix *H, const ci_eig_opts *opts_in, const int32_t *row_block, int64_t nblocks,
+                        double *evals, double *evecs, ci_eig_info *info, cudaStream_t s) {
     auto t_start = std::chrono::steady_clock::now();
     if (!H) fail(CI_ERR_INVALID_ARG, "matrix is NULL");
     if (!evals) fail(CI_ERR_INVALID_ARG, "evals is NULL");
@@ -862,6 +863,15 @@ void lowest_eigs_lobpcg(const Matrix *H, const ci_eig_opts *opts_in, double *eva
                (const __nv_bfloat16 *)H->val.ptr, (const float *)H->row_scale.ptr, dg.ptr);
     else
         fail(CI_ERR_INVALID_ARG, "value type %d not supported by LOBPCG", H->vtype);
+    // many-body-orbital block preconditioner (else the diagonal of H): the
+    // shifted blocks are inverted at iterations 0, 2, 6, 14, ... with the
+    // shift sigma = theta_1 - |r_1| of the latest Rayleigh-Ritz
+    std::unique_ptr<BlockPrecond> bp;
+    if (row_block) {
+        bp.reset(new BlockPrecond);
+        precond_setup(*bp, H, row_block, nblocks, s);
+    }
+    int next_factor = 0;
     const int bb = nb * nb;
     // Gram blocks into G (device), one copy to the host
     auto gram = [&](const std::vector<std::pair<const double *, const double *>> &pairs, std::vector<double> &h) {
@@ -962,8 +972,16 @@ void lowest_eigs_lobpcg(const Matrix *H, const ci_eig_opts *opts_in, double *eva
         if (converged) break;
         // W: preconditioned residuals, orthonormal and orthogonal to X (two
         // Gram-Schmidt passes, then Cholesky QR); AW = H W
-        launch("k_precond", k_precond, sv.grid(dim * nb), 256, 0, s, dim, nb, R.ptr, dg.ptr, sv.theta_dev.ptr, 1e-8,
-               Wd.ptr);
+        if (bp) {
+            if (it == next_factor) {
+                precond_factor(*bp, H, theta[0] - rn[0], s);
+                next_factor = 2 * it + 2;
+            }
+            precond_apply(*bp, R.ptr, nb, Wd.ptr, s);
+        } else {
+            launch("k_precond", k_precond, sv.grid(dim * nb), 256, 0, s, dim, nb, R.ptr, dg.ptr, sv.theta_dev.ptr,
+                   1e-8, Wd.ptr);
+        }
         auto col_norms = [&](const double *B) {
             std::vector<double> g;
             gram({{B, B}}, g);
@@ -1077,11 +1095,12 @@ extern "C" ci_status ci_lowest_eigs(const ci_matrix *m, const ci_eig_opts *opts,
     });
 }
 
-extern "C" ci_status ci_lowest_eigs_lobpcg(const ci_matrix *m, const ci_eig_opts *opts, double *evals,
-                                           double *evecs, ci_eig_info *info, void *stream) {
+extern "C" ci_status ci_lowest_eigs_lobpcg(const ci_matrix *m, const ci_eig_opts *opts, const int32_t *row_block,
+                                           int64_t nblocks, double *evals, double *evecs, ci_eig_info *info,
+                                           void *stream) {
     return ci::guard([&] {
         if (!m) ci::fail(CI_ERR_INVALID_ARG, "matrix is NULL");
         ci::StreamScope scope(reinterpret_cast<cudaStream_t>(stream));
-        ci::lowest_eigs_lobpcg(&m->impl, opts, evals, evecs, info, reinterpret_cast<cudaStream_t>(stream));
+        ci::lowest_eigs_lobpcg(&m->impl, opts, row_block, nblocks, evals, evecs, info, reinterpret_cast<cudaStream_t>(stream));
     });
 }

@@ -529,7 +529,8 @@ void enumerate_basis(Problem *p, cudaStream_t s) {
     }
     SpeciesList &P = p->sp[0], &Nn = p->sp[1];
     p->p_row_base.assign(P.n + 1, 0);
-    std::vector<int64_t> p_nstart(P.n ? P.n : 1, 0);
+    std::vector<int64_t> &p_nstart = p->p_nstart;
+    p_nstart.assign(P.n ? P.n : 1, 0);
     for (int64_t i = 0; i < P.n; ++i) {
         int b = Nn.block_of(p->twoM - P.twoM[i]);
         int64_t cnt = 0;

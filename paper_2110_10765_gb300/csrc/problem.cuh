@@ -162,6 +162,7 @@ struct Problem {
     SpeciesList sp[2];
     int64_t dim = 0;
     std::vector<int64_t> p_row_base;   // [nP+1]
+    std::vector<int64_t> p_nstart;     // [nP] first neutron index of each proton's rows
     DevBuf<int64_t> d_p_row_base, d_p_nstart;
     DevBuf<int32_t> d_row_p, d_row_n;  // [dim]
 
@@ -190,6 +191,26 @@ struct Matrix {
     DevBuf<unsigned char> val;       // float, double or bf16 bits
     DevBuf<float> row_scale;         // BF16 only
 };
+
+// Block-diagonal preconditioner over many-body basis orbitals: sub-blocks of
+// at most kSubMax rows, their shifted inverses in FP32 (precond.cu).
+constexpr int kSubMax = 128;
+struct BlockPrecond {
+    int64_t dim = 0, nsub = 0;
+    int smax = 0;                    // rows of the largest sub-block
+    DevBuf<int32_t> rows;            // [dim] rows grouped by sub-block, ascending inside
+    DevBuf<int32_t> sub_of, loc_of;  // [dim] sub-block of a row, index inside it
+    DevBuf<int64_t> sub_start;       // [nsub+1] into rows
+    DevBuf<int64_t> inv_off;         // [nsub+1] into inv
+    DevBuf<float> inv;               // row-major inverses of the shifted sub-blocks
+    DevBuf<double> shift;            // [nsub] shift used by each sub-block
+    DevBuf<int32_t> status;          // [1] set when a sub-block could not be inverted
+};
+void orbital_blocks(Problem *p, const int32_t *sp_orbital, int32_t *block, int64_t *nblocks, cudaStream_t s);
+void precond_setup(BlockPrecond &bp, const Matrix *H, const int32_t *row_block, int64_t nblocks, cudaStream_t s);
+void precond_factor(BlockPrecond &bp, const Matrix *H, double sigma, cudaStream_t s);
+void precond_apply(const BlockPrecond &bp, const double *R, int nv, double *W, cudaStream_t s);
+void precond_row_shift(const BlockPrecond &bp, double *out, cudaStream_t s);
 
 // ------------------------------------------------------------------ steps
 

@@ -16,7 +16,7 @@ Every function is deterministic in its seed.  Nothing here depends on numpy's
 own random streams.
 """
 
-from .sp import ho_sp_table, sp_energies
+from .sp import ho_sp_table, sp_energies, sp_orbitals
 from .tbme import (CH_PP, CH_NN, CH_PN, splitmix64_mix, tbme_gaussian,
                    tbme_tables, tbme_tables_zero)
 from .workloads import (PRESETS, Preset, preset, batch_candidates,
@@ -24,7 +24,7 @@ from .workloads import (PRESETS, Preset, preset, batch_candidates,
 from .e1 import E1_RATIO, e1_states
 
 __all__ = [
-    "ho_sp_table", "sp_energies",
+    "ho_sp_table", "sp_energies", "sp_orbitals",
     "CH_PP", "CH_NN", "CH_PN", "splitmix64_mix", "tbme_gaussian",
     "tbme_tables", "tbme_tables_zero",
     "PRESETS", "Preset", "preset", "batch_candidates", "serve_requests",

@@ -35,6 +35,15 @@ def ho_sp_table(n_shell_max):
             "twoj": a[:, 2].copy(), "twom": a[:, 3].copy()}
 
 
+def sp_orbitals(sp):
+    """Orbital label of every s.p. state: states with the same (N, l, 2j)
+    (one orbital, differing only in 2m) share a label, numbered 0, 1, ... in
+    table order."""
+    ids = {}
+    return np.array([ids.setdefault((int(N), int(l), int(j)), len(ids))
+                     for N, l, j in zip(sp["N"], sp["l"], sp["twoj"])], dtype=np.int32)
+
+
 def sp_energies(sp, hbar_omega):
     """One-body energies eps_a = hbar_omega * (N_a + 3/2) of the HO basis.
 
