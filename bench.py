@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--count-n", type=int, default=131072, help="states of the count benchmark")
     ap.add_argument("--no-observables", action="store_true", help="skip the observables leg")
     ap.add_argument("--no-c2", action="store_true", help="skip the Nmax=6 precision-study leg")
+    ap.add_argument("--no-eigensolvers", action="store_true", help="skip the Lanczos / LOBPCG comparison leg")
     ap.add_argument("--obs-m", type=int, default=16, help="operators of the observables leg")
     return ap.parse_args()
 
@@ -335,6 +336,8 @@ def run_ours(args):
         rec["count"] = run_count_leg(args.count_n, clock_mhz=(clk or {}).get("sm_mhz"))
     if not args.no_observables:
         rec["observables"] = run_observables_leg(sp, p, eps, dtab, args.obs_m)
+    if not args.no_eigensolvers:
+        rec["eigensolvers"] = run_eigensolver_leg(sp, p, eps, dtab)
     if not args.no_c2:
         rec["c2_precision"] = run_c2_leg(hbm)
     if not args.no_batch:
@@ -411,6 +414,52 @@ def run_c2_leg(hbm):
             "bf16_rowscale": {"spmm_ms": spb_ms, "solve_s": sb * 1e-3, "iterations": infob["iterations"],
                               "max_abs_diff_vs_f64": float(np.max(np.abs(evb - ev64))),
                               "max_rel_diff_vs_f64": float(np.max(np.abs(evb - ev64) / np.abs(ev64)))}}
+
+
+# ---------------------------------------------------------------- eigensolvers
+
+def run_eigensolver_leg(sp, p, eps, tables):
+    """Fig. 1, eigensolve on the benchmark workload (FP32 H): block Lanczos
+    against LOBPCG with the diagonal and with the many-body-orbital
+    block-diagonal preconditioner (Sec. 2), each timed with CUDA events
+    around the whole solve (the orbital grouping, the block inversions and
+    their applications included)."""
+    import torch
+
+    import synth
+    import paper_2110_10765_gb300 as ci
+    prob = ci.Problem(sp, p.Z, p.N, p.nmax, p.twoM, eps, tables=tables)
+    M = prob.build_H("f32")
+    stream = torch.cuda.current_stream()
+    labels = synth.sp_orbitals(sp)
+    out = {}
+    for name in ("lanczos", "lobpcg_diagonal", "lobpcg_orbital_blocks"):
+        def solve():
+            if name == "lanczos":
+                return M.lowest_eigs(k=p.k, block=p.block)
+            blocks = prob.orbital_blocks(labels) if name == "lobpcg_orbital_blocks" else None
+            return M.lowest_eigs(k=p.k, block=p.block, method="lobpcg", blocks=blocks)
+        solve()                                            # warm-up
+        ci.trace_enable(True)
+        ci.trace_read(reset=True)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ev, info = solve()
+        b.record(stream)
+        b.synchronize()
+        kern = ci.trace_read(reset=True)
+        ci.trace_enable(False)
+        rec = {"ms": round(a.elapsed_time(b), 3), "iterations": info["iterations"],
+               "max_residual": max(info["residual"]), "evals": [round(float(x), 6) for x in ev]}
+        for kname in ("k_block_inv", "k_block_apply"):
+            if kname in kern:
+                n_l, ms = kern[kname]
+                rec[kname] = {"launches": int(n_l), "ms_per_launch": round(ms / max(n_l, 1), 4)}
+        out[name] = rec
+    blk, nb = prob.orbital_blocks(labels)
+    sizes = torch.bincount(blk.long(), minlength=nb).cpu()
+    out["orbital_groups"] = {"groups": nb, "largest": int(sizes.max()), "mean": round(float(sizes.float().mean()), 2)}
+    return out
 
 
 # ---------------------------------------------------------------- observables

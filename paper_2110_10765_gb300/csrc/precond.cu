@@ -53,10 +53,11 @@ __device__ __forceinline__ double block_max(double v, double *red) {
     return r;
 }
 
-// One CTA per sub-block: gather H_bb from the CSR rows of its members into
-// shared memory (FP64, row-major n x n), shift, invert in place by
-// Gauss-Jordan elimination without pivoting (for a symmetric matrix every
-// pivot is positive exactly when it is positive definite), store FP32.
+// One CTA per sub-block (the sub-block ids of one size bin): gather H_bb
+// from the CSR rows of its members into shared memory (FP64, row-major
+// n x n), shift, invert in place by Gauss-Jordan elimination without
+// pivoting (for a symmetric matrix every pivot is positive exactly when it
+// is positive definite), store FP32.  Warps own rows, lanes columns.
 template <class TV>
 __global__ void __launch_bounds__(256) k_block_inv(const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
                                                    const TV *__restrict__ val, const float *__restrict__ rscale,
@@ -64,12 +65,13 @@ __global__ void __launch_bounds__(256) k_block_inv(const int64_t *__restrict__ r
                                                    const int64_t *__restrict__ sub_start,
                                                    const int32_t *__restrict__ sub_of,
                                                    const int32_t *__restrict__ loc_of,
-                                                   const int64_t *__restrict__ inv_off, double sigma,
+                                                   const int64_t *__restrict__ inv_off,
+                                                   const int32_t *__restrict__ ids, double sigma,
                                                    float *__restrict__ inv, double *__restrict__ shift,
                                                    int32_t *__restrict__ status) {
     extern __shared__ double sm[];
     __shared__ double red[8];
-    const int sb = blockIdx.x;
+    const int sb = ids[blockIdx.x];
     const int64_t r0 = sub_start[sb];
     const int n = (int)(sub_start[sb + 1] - r0);
     const int nn = n * n;
@@ -86,19 +88,30 @@ __global__ void __launch_bounds__(256) k_block_inv(const int64_t *__restrict__ r
         for (int li = warp; li < n; li += nwarp) {
             const int r = rows[r0 + li];
             const double sc = rscale ? (double)rscale[r] : 1.0;
-            for (int64_t e = rp[r] + lane; e < rp[r + 1]; e += 32) {
-                const int c = col[e];
-                if (sub_of[c] == sb) A[li * n + loc_of[c]] = pc_val(val[e]) * sc;
+            const int64_t e1 = rp[r + 1];
+            // four entries per lane in flight: the column, its sub-block and
+            // the value are independent loads
+            for (int64_t e = rp[r] + lane; e < e1; e += 128) {
+                int c[4], b[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) c[u] = e + 32 * u < e1 ? col[e + 32 * u] : -1;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) b[u] = c[u] >= 0 ? sub_of[c[u]] : -1;
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (b[u] == sb) A[li * n + loc_of[c[u]]] = pc_val(val[e + 32 * u]) * sc;
             }
         }
         __syncthreads();
         if (attempt == 0) {
             // Gershgorin lower bound and largest absolute row sum of H_bb
             double g = INFINITY, a = 0.0;
-            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            for (int i = warp; i < n; i += nwarp) {
                 double off = 0.0;
-                for (int j = 0; j < n; ++j)
+                for (int j = lane; j < n; j += 32)
                     if (j != i) off += fabs(A[i * n + j]);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) off += __shfl_xor_sync(0xffffffffu, off, o);
                 g = fmin(g, A[i * n + i] - off);
                 a = fmax(a, off + fabs(A[i * n + i]));
             }
@@ -125,12 +138,14 @@ __global__ void __launch_bounds__(256) k_block_inv(const int64_t *__restrict__ r
             }
             __syncthreads();
             const double ip = 1.0 / p;
-            for (int t = threadIdx.x; t < nn; t += blockDim.x) {
-                const int i = t / n, j = t - i * n;
-                if (i != k && j != k) A[t] = fma(-ck[i] * ip, rk[j], A[t]);
-                else if (i == k && j != k) A[t] = rk[j] * ip;
-                else if (j == k && i != k) A[t] = -ck[i] * ip;
-                else A[t] = ip;
+            for (int i = warp; i < n; i += nwarp) {
+                const double f = -ck[i] * ip;
+                double *Ai = A + i * n;
+                if (i != k) {
+                    for (int j = lane; j < n; j += 32) Ai[j] = j != k ? fma(f, rk[j], Ai[j]) : f;
+                } else {
+                    for (int j = lane; j < n; j += 32) Ai[j] = j != k ? rk[j] * ip : ip;
+                }
             }
             __syncthreads();
         }
@@ -264,6 +279,26 @@ void precond_setup(BlockPrecond &bp, const Matrix *H, const int32_t *row_block, 
     bp.dim = dim;
     bp.nsub = (int64_t)sub_start.size() - 1;
     bp.smax = smax;
+    {
+        static const int kBinTop[3] = {32, 64, kSubMax};
+        std::vector<int32_t> ids((size_t)bp.nsub);
+        for (int64_t u = 0; u < bp.nsub; ++u) ids[u] = (int32_t)u;
+        auto size_of = [&](int32_t u) { return sub_start[u + 1] - sub_start[u]; };
+        auto bin_of = [&](int32_t u) { return size_of(u) <= kBinTop[0] ? 0 : size_of(u) <= kBinTop[1] ? 1 : 2; };
+        std::stable_sort(ids.begin(), ids.end(), [&](int32_t x, int32_t y) {
+            const int bx = bin_of(x), by = bin_of(y);
+            return bx != by ? bx < by : size_of(x) > size_of(y);
+        });
+        for (int q = 0; q < 4; ++q) bp.bin_off[q] = 0;
+        for (int q = 0; q < 3; ++q) bp.bin_max[q] = 0;
+        for (int64_t u = 0; u < bp.nsub; ++u) {
+            const int q = bin_of(ids[u]);
+            bp.bin_off[q + 1] = u + 1;
+            bp.bin_max[q] = std::max(bp.bin_max[q], (int)size_of(ids[u]));
+        }
+        for (int q = 1; q < 4; ++q) bp.bin_off[q] = std::max(bp.bin_off[q], bp.bin_off[q - 1]);
+        bp.bin_ids.upload(ids, s);
+    }
     bp.rows.upload(rows, s);
     bp.sub_of.upload(sub_of, s);
     bp.loc_of.upload(loc_of, s);
@@ -278,13 +313,17 @@ void precond_factor(BlockPrecond &bp, const Matrix *H, double sigma, cudaStream_
     if (!std::isfinite(sigma)) fail(CI_ERR_INVALID_ARG, "sigma must be finite");
     if (bp.nsub == 0) return;
     CI_CUDA(cudaMemsetAsync(bp.status.ptr, 0, sizeof(int32_t), s));
-    const size_t smem = inv_smem(bp.smax);
     auto run = [&](auto kern, const auto *val, const float *rscale) {
         CI_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)inv_smem(kSubMax)));
-        launch("k_block_inv", kern, (unsigned)bp.nsub, 256, smem, s, (const int64_t *)H->row_ptr.ptr,
-               (const int32_t *)H->col.ptr, val, rscale, (const int32_t *)bp.rows.ptr,
-               (const int64_t *)bp.sub_start.ptr, (const int32_t *)bp.sub_of.ptr, (const int32_t *)bp.loc_of.ptr,
-               (const int64_t *)bp.inv_off.ptr, sigma, bp.inv.ptr, bp.shift.ptr, bp.status.ptr);
+        for (int q = 0; q < 3; ++q) {
+            const int64_t nq = bp.bin_off[q + 1] - bp.bin_off[q];
+            if (nq == 0) continue;
+            launch("k_block_inv", kern, (unsigned)nq, 256, inv_smem(bp.bin_max[q]), s,
+                   (const int64_t *)H->row_ptr.ptr, (const int32_t *)H->col.ptr, val, rscale,
+                   (const int32_t *)bp.rows.ptr, (const int64_t *)bp.sub_start.ptr, (const int32_t *)bp.sub_of.ptr,
+                   (const int32_t *)bp.loc_of.ptr, (const int64_t *)bp.inv_off.ptr,
+                   (const int32_t *)bp.bin_ids.ptr + bp.bin_off[q], sigma, bp.inv.ptr, bp.shift.ptr, bp.status.ptr);
+        }
     };
     if (H->vtype == CI_F32) run(k_block_inv<float>, (const float *)H->val.ptr, (const float *)nullptr);
     else if (H->vtype == CI_F64) run(k_block_inv<double>, (const double *)H->val.ptr, (const float *)nullptr);

@@ -204,6 +204,11 @@ struct BlockPrecond {
     DevBuf<int64_t> inv_off;         // [nsub+1] into inv
     DevBuf<float> inv;               // row-major inverses of the shifted sub-blocks
     DevBuf<double> shift;            // [nsub] shift used by each sub-block
+    // sub-blocks of <= 32, <= 64 and <= kSubMax rows (largest first in each
+    // bin): one inversion launch per bin, its shared memory sized to the bin
+    DevBuf<int32_t> bin_ids;         // [nsub]
+    int64_t bin_off[4] = {0, 0, 0, 0};
+    int bin_max[3] = {0, 0, 0};
     DevBuf<int32_t> status;          // [1] set when a sub-block could not be inverted
 };
 void orbital_blocks(Problem *p, const int32_t *sp_orbital, int32_t *block, int64_t *nblocks, cudaStream_t s);
