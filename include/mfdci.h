@@ -254,6 +254,17 @@ ci_status ci_exclusive_scan_noalloc(const int32_t *counts, int64_t n, int64_t *o
  * CI_BF16_ROWSCALE adds float row_scale [dim]). */
 ci_status ci_build_H(ci_problem *p, int32_t vtype, ci_matrix **out, void *stream);
 void ci_matrix_destroy(ci_matrix *m);
+
+/* Half storage of the symmetric H (Fig. 2, optional FMA: a stored H_ij also
+ * updates the j-th output with the i-th input): a new matrix holding the
+ * upper triangle (col >= row, diagonal included) of m, same value type and
+ * row scales, nnz = (nnz(m) + dim) / 2 for H's symmetric pattern.
+ * ci_apply_H on it zeroes Y and adds H_ij X_j to Y_i and H_ij X_i to Y_j with
+ * atomic adds (run-to-run differences in the last bits of Y); the
+ * eigensolvers and the block preconditioner accept it (the preconditioner
+ * mirrors the stored elements).  ci_matrix_export returns the stored
+ * triangle.  Errors: CI_ERR_INVALID_ARG (NULL, m already half-stored). */
+ci_status ci_matrix_upper(const ci_matrix *m, ci_matrix **out, void *stream);
 ci_status ci_matrix_info(const ci_matrix *m, int64_t *dim, int64_t *nnz, int32_t *vtype);
 /* Copy H out to caller buffers (each host or device, each nullable):
  * row_ptr [dim+1] int64, col [nnz] int32, val [nnz] (float, double or

@@ -194,6 +194,7 @@ class Matrix:
         dim, nnz, vt = C.c_int64(), C.c_int64(), C.c_int32()
         check(lib().ci_matrix_info(handle, C.byref(dim), C.byref(nnz), C.byref(vt)), "ci_matrix_info")
         self.dim, self.nnz, self.vtype = dim.value, nnz.value, vt.value
+        self.half = False
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -218,6 +219,14 @@ class Matrix:
     def export_device(self, row_ptr, col, val, row_scale=None, stream=None):
         check(lib().ci_matrix_export(self._h, _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(row_scale),
                                      _stream(stream)), "ci_matrix_export")
+
+    def upper(self, stream=None):
+        """A new half-stored copy (upper triangle, ``ci_matrix_upper``)."""
+        h = C.c_void_p()
+        check(lib().ci_matrix_upper(self._h, C.byref(h), _stream(stream)), "ci_matrix_upper")
+        m = Matrix(h)
+        m.half = True
+        return m
 
     def block_precond_apply(self, blocks, sigma, R, stream=None):
         """W = T R with the block-diagonal preconditioner of LOBPCG over the

@@ -91,6 +91,7 @@ _SIGS = {
     "ci_observables": (C.c_int, [_P, _P, C.c_int32, _P, _P, C.c_int32, _P, _P]),
     "ci_build_H": (C.c_int, [_P, C.c_int32, C.POINTER(_P), _P]),
     "ci_matrix_destroy": (None, [_P]),
+    "ci_matrix_upper": (C.c_int, [_P, C.POINTER(_P), _P]),
     "ci_matrix_info": (C.c_int, [_P, _I64P, _I64P, C.POINTER(C.c_int32)]),
     "ci_matrix_export": (C.c_int, [_P, _P, _P, _P, _P, _P]),
     "ci_apply_H": (C.c_int, [_P, _P, _P, C.c_int32, _P]),

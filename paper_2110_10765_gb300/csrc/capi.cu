@@ -241,6 +241,18 @@ ci_status ci_build_H(ci_problem *p, int32_t vtype, ci_matrix **out, void *stream
     });
 }
 
+ci_status ci_matrix_upper(const ci_matrix *m, ci_matrix **out, void *stream) {
+    return guard([&] {
+        StreamScope scope(as_stream(stream));
+        if (!m || !out) fail(CI_ERR_INVALID_ARG, "matrix or out is NULL");
+        *out = nullptr;
+        std::unique_ptr<ci_matrix> u(new ci_matrix());
+        upper_matrix(&m->impl, &u->impl, as_stream(stream));
+        CI_CUDA(cudaStreamSynchronize(as_stream(stream)));
+        *out = u.release();
+    });
+}
+
 void ci_matrix_destroy(ci_matrix *m) {
     if (!m) return;
     HandleRelease hr;

@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(256) k_block_inv(const int64_t *__restrict__ r
                                                    const int32_t *__restrict__ sub_of,
                                                    const int32_t *__restrict__ loc_of,
                                                    const int64_t *__restrict__ inv_off,
-                                                   const int32_t *__restrict__ ids, double sigma,
+                                                   const int32_t *__restrict__ ids, bool upper, double sigma,
                                                    float *__restrict__ inv, double *__restrict__ shift,
                                                    int32_t *__restrict__ status) {
     extern __shared__ double sm[];
@@ -99,7 +99,13 @@ __global__ void __launch_bounds__(256) k_block_inv(const int64_t *__restrict__ r
                 for (int u = 0; u < 4; ++u) b[u] = c[u] >= 0 ? sub_of[c[u]] : -1;
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
-                    if (b[u] == sb) A[li * n + loc_of[c[u]]] = pc_val(val[e + 32 * u]) * sc;
+                    if (b[u] == sb) {
+                        const int lc = loc_of[c[u]];
+                        const double v = pc_val(val[e + 32 * u]) * sc;
+                        A[li * n + lc] = v;
+                        // half storage: the mirror element (only the upper one is stored)
+                        if (upper && lc != li) A[lc * n + li] = v;
+                    }
             }
         }
         __syncthreads();
@@ -322,7 +328,8 @@ void precond_factor(BlockPrecond &bp, const Matrix *H, double sigma, cudaStream_
                    (const int64_t *)H->row_ptr.ptr, (const int32_t *)H->col.ptr, val, rscale,
                    (const int32_t *)bp.rows.ptr, (const int64_t *)bp.sub_start.ptr, (const int32_t *)bp.sub_of.ptr,
                    (const int32_t *)bp.loc_of.ptr, (const int64_t *)bp.inv_off.ptr,
-                   (const int32_t *)bp.bin_ids.ptr + bp.bin_off[q], sigma, bp.inv.ptr, bp.shift.ptr, bp.status.ptr);
+                   (const int32_t *)bp.bin_ids.ptr + bp.bin_off[q], H->upper, sigma, bp.inv.ptr, bp.shift.ptr,
+                   bp.status.ptr);
         }
     };
     if (H->vtype == CI_F32) run(k_block_inv<float>, (const float *)H->val.ptr, (const float *)nullptr);

@@ -190,6 +190,7 @@ struct Matrix {
     DevBuf<int32_t> col;
     DevBuf<unsigned char> val;       // float, double or bf16 bits
     DevBuf<float> row_scale;         // BF16 only
+    bool upper = false;              // only the upper triangle (col >= row) is stored
 };
 
 // Block-diagonal preconditioner over many-body basis orbitals: sub-blocks of
@@ -260,6 +261,7 @@ void exclusive_scan_i32(const int32_t *counts, int64_t n, int64_t *offsets,
 // src[idx[i]] for every i, copied to the host (synchronises s)
 std::vector<int64_t> gather_i64(const int64_t *src, const std::vector<int64_t> &idx, cudaStream_t s);
 void build_matrix(Problem *p, int vtype, Matrix *m, cudaStream_t s);
+void upper_matrix(const Matrix *full, Matrix *out, cudaStream_t s);
 void apply_matrix(const Matrix *m, const void *X, void *Y, int nvec, cudaStream_t s);
 void lowest_eigs(const Matrix *H, const ci_eig_opts *opts, double *evals, double *evecs, ci_eig_info *info,
                  cudaStream_t s);

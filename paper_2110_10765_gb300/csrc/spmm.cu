@@ -172,8 +172,90 @@ __global__ void __launch_bounds__(256) k_spmm8_half(int64_t dim, const int64_t *
     }
 }
 
+// ---- half storage (Fig. 2, optional FMA: the stored H_ij also updates the
+// j-th output with the i-th input).  Row i keeps the columns j >= i; the
+// stored element adds H_ij X_j to Y_i and, for j > i, H_ij X_i to Y_j.  Y is
+// zeroed first and every update is an atomic add, so the summation order
+// (and the last bits of Y) vary from run to run.
+
+// 8 FP32 vectors, two lanes per nonzero as k_spmm8_half, vector atomics.
+template <class TV>
+__global__ void __launch_bounds__(256) k_spmm8_upper(int64_t dim, const int64_t *__restrict__ rp,
+                                                     const int32_t *__restrict__ col, const TV *__restrict__ val,
+                                                     const float *__restrict__ X, float *__restrict__ Y,
+                                                     const float *__restrict__ row_scale) {
+    const int lane = threadIdx.x & 31, half = lane & 1, pair = lane >> 1;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const float4 *X4 = reinterpret_cast<const float4 *>(X);
+    float4 *Y4 = reinterpret_cast<float4 *>(Y);
+    for (int64_t r = warp; r < dim; r += nwarps) {
+        const float sc = row_scale ? row_scale[r] : 1.f;
+        const float4 xr = __ldg(X4 + r * 2 + half);
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        const int64_t e1 = rp[r + 1];
+        for (int64_t e = rp[r] + pair; e < e1; e += 16) {
+            const int c = __ldcs(col + e);
+            const float v = load_val(val + e) * sc;
+            const float4 x = __ldg(X4 + (int64_t)c * 2 + half);
+            a0 = fmaf(v, x.x, a0);
+            a1 = fmaf(v, x.y, a1);
+            a2 = fmaf(v, x.z, a2);
+            a3 = fmaf(v, x.w, a3);
+            if (c != r) atomicAdd(Y4 + (int64_t)c * 2 + half, make_float4(v * xr.x, v * xr.y, v * xr.z, v * xr.w));
+        }
+#pragma unroll
+        for (int o = 16; o > 1; o >>= 1) {
+            a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+            a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+            a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+            a3 += __shfl_xor_sync(0xffffffffu, a3, o);
+        }
+        if (lane < 2) atomicAdd(Y4 + r * 2 + half, make_float4(a0, a1, a2, a3));
+    }
+}
+
+// Any vector count and type: one thread per (row, vector), scalar atomics.
+template <class TV, class TX, int NV>
+__global__ void k_spmm_upper(int64_t dim, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                             const TV *__restrict__ val, const TX *__restrict__ X, TX *__restrict__ Y,
+                             const float *__restrict__ row_scale) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < dim * NV;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = t / NV;
+        const int q = (int)(t - r * NV);
+        const TX sc = row_scale ? (TX)row_scale[r] : (TX)1;
+        const TX xr = X[r * NV + q];
+        TX acc = 0;
+        for (int64_t e = rp[r]; e < rp[r + 1]; ++e) {
+            const int c = col[e];
+            const TX v = load_as<TX>(val + e) * sc;
+            acc += v * X[(int64_t)c * NV + q];
+            if (c != r) atomicAdd(Y + (int64_t)c * NV + q, v * xr);
+        }
+        atomicAdd(Y + r * NV + q, acc);
+    }
+}
+
+template <class TV, class TX, int NV>
+static void launch_spmm_upper(const Matrix *m, const void *X, void *Y, cudaStream_t s) {
+    CI_CUDA(cudaMemsetAsync(Y, 0, sizeof(TX) * (size_t)m->dim * NV, s));
+    const float *scale = m->vtype == CI_BF16_ROWSCALE ? m->row_scale.ptr : nullptr;
+    if (NV == 8 && sizeof(TX) == 4) {
+        launch("k_spmm_upper", k_spmm8_upper<TV>, grid_for(m->dim * 32, 256, sm_count() * 8), 256, 0, s, m->dim,
+               m->row_ptr.ptr, m->col.ptr, (const TV *)m->val.ptr, (const float *)X, (float *)Y, scale);
+        return;
+    }
+    launch("k_spmm_upper", k_spmm_upper<TV, TX, NV>, grid_for(m->dim * NV, 256), 256, 0, s, m->dim, m->row_ptr.ptr,
+           m->col.ptr, (const TV *)m->val.ptr, (const TX *)X, (TX *)Y, scale);
+}
+
 template <class TV, class TX, int NV>
 static void launch_spmm(const Matrix *m, const void *X, void *Y, cudaStream_t s) {
+    if (m->upper) {
+        launch_spmm_upper<TV, TX, NV>(m, X, Y, s);
+        return;
+    }
     int grid = grid_for(m->dim * 32, 256, sm_count() * 8);
     const float *scale = m->vtype == CI_BF16_ROWSCALE ? m->row_scale.ptr : nullptr;
     if (NV == 8 && sizeof(TX) == 4) {
@@ -198,6 +280,81 @@ static void dispatch(const Matrix *m, const void *X, void *Y, int nvec, cudaStre
         case 8: launch_spmm<TV, TX, 8>(m, X, Y, s); break;
         default: fail(CI_ERR_INVALID_ARG, "nvec must be 1..8 (got %d)", nvec);
     }
+}
+
+// Upper triangle of a full CSR: per row the entries from the first column
+// >= row (columns are ascending), counted, scanned, copied.
+__global__ void k_upper_count(int64_t dim, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                              int32_t *__restrict__ cnt, int64_t *__restrict__ first) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < dim; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t lo = rp[i], hi = rp[i + 1];
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (col[mid] < i) lo = mid + 1; else hi = mid;
+        }
+        first[i] = lo;
+        cnt[i] = (int32_t)(rp[i + 1] - lo);
+    }
+}
+
+template <class TV>
+__global__ void k_upper_copy(int64_t dim, const int64_t *__restrict__ rp, const int64_t *__restrict__ first,
+                             const int32_t *__restrict__ col, const TV *__restrict__ val,
+                             const int64_t *__restrict__ urp, int32_t *__restrict__ ucol, TV *__restrict__ uval) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = warp; r < dim; r += nwarps) {
+        const int64_t src = first[r], dst = urp[r], n = urp[r + 1] - urp[r];
+        for (int64_t k = lane; k < n; k += 32) {
+            ucol[dst + k] = col[src + k];
+            uval[dst + k] = val[src + k];
+        }
+    }
+}
+
+void upper_matrix(const Matrix *full, Matrix *out, cudaStream_t s) {
+    if (full->upper) fail(CI_ERR_INVALID_ARG, "the matrix already stores only its upper triangle");
+    const int64_t dim = full->dim;
+    out->dim = dim;
+    out->vtype = full->vtype;
+    out->upper = true;
+    out->row_ptr.alloc((size_t)dim + 1);
+    if (dim == 0) {
+        CI_CUDA(cudaMemsetAsync(out->row_ptr.ptr, 0, sizeof(int64_t), s));
+        out->nnz = 0;
+        return;
+    }
+    DevBuf<int32_t> cnt((size_t)dim);
+    DevBuf<int64_t> first((size_t)dim), scratch;
+    launch("k_upper_count", k_upper_count, grid_for(dim, 256), 256, 0, s, dim, (const int64_t *)full->row_ptr.ptr,
+           (const int32_t *)full->col.ptr, cnt.ptr, first.ptr);
+    exclusive_scan_i32(cnt.ptr, dim, out->row_ptr.ptr, scratch, s);
+    CI_CUDA(cudaMemcpyAsync(&out->nnz, out->row_ptr.ptr + dim, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CI_CUDA(cudaStreamSynchronize(s));
+    const size_t esz = full->vtype == CI_F64 ? 8 : full->vtype == CI_F32 ? 4 : 2;
+    out->col.alloc((size_t)std::max<int64_t>(out->nnz, 1));
+    out->val.alloc(esz * (size_t)std::max<int64_t>(out->nnz, 1));
+    const int grid = grid_for(dim * 32, 256, sm_count() * 8);
+    if (esz == 8)
+        launch("k_upper_copy", k_upper_copy<double>, grid, 256, 0, s, dim, (const int64_t *)full->row_ptr.ptr,
+               (const int64_t *)first.ptr, (const int32_t *)full->col.ptr, (const double *)full->val.ptr,
+               (const int64_t *)out->row_ptr.ptr, out->col.ptr, (double *)out->val.ptr);
+    else if (esz == 4)
+        launch("k_upper_copy", k_upper_copy<float>, grid, 256, 0, s, dim, (const int64_t *)full->row_ptr.ptr,
+               (const int64_t *)first.ptr, (const int32_t *)full->col.ptr, (const float *)full->val.ptr,
+               (const int64_t *)out->row_ptr.ptr, out->col.ptr, (float *)out->val.ptr);
+    else
+        launch("k_upper_copy", k_upper_copy<__nv_bfloat16>, grid, 256, 0, s, dim,
+               (const int64_t *)full->row_ptr.ptr, (const int64_t *)first.ptr, (const int32_t *)full->col.ptr,
+               (const __nv_bfloat16 *)full->val.ptr, (const int64_t *)out->row_ptr.ptr, out->col.ptr,
+               (__nv_bfloat16 *)out->val.ptr);
+    if (full->vtype == CI_BF16_ROWSCALE) {
+        out->row_scale.alloc((size_t)dim);
+        CI_CUDA(cudaMemcpyAsync(out->row_scale.ptr, full->row_scale.ptr, sizeof(float) * dim,
+                                cudaMemcpyDeviceToDevice, s));
+    }
+    CI_CHECK_LAUNCH();
 }
 
 void apply_matrix(const Matrix *m, const void *X, void *Y, int nvec, cudaStream_t s) {
