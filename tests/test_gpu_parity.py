@@ -130,6 +130,51 @@ def test_build_H_small(case, vtype):
     _check_matrix(o, M, REL64 if vtype == "f64" else REL32)
 
 
+def _sliced_inputs(S, Z, N, nmax, twoM, seed, dtype):
+    """The first S states of the HO table up to shell 4: S = 63, 64, 65 put
+    the highest state on either side of the 64-bit word boundary."""
+    import synth
+    sp = {k: v[:S].copy() for k, v in synth.ho_sp_table(4).items()}
+    return dict(sp=sp, Z=Z, N=N, nmax=nmax, twoM=twoM, eps=synth.sp_energies(sp, 20.0),
+                tables=synth.tbme_tables(sp, seed, dtype))
+
+
+@pytest.mark.parametrize("S", [63, 64, 65])
+@pytest.mark.parametrize("case", [(1, 1, -1, 0), (1, 2, 5, 3), (2, 2, 4, 0)])
+def test_word_boundary_states(S, case):
+    """Bit 63 and bit 64 of the determinant strings: basis, pattern and FP64
+    values against the oracle, and the SpMM."""
+    inp = _sliced_inputs(S, *case, seed=8, dtype=np.float64)
+    o, g = oracle_problem(inp), gpu_problem(inp)
+    assert g.enumerate_basis() == o.dim
+    _species_eq(o, g, 0)
+    _species_eq(o, g, 1)
+    M = g.build_H("f64")
+    rp, col, val = _check_matrix(o, M, REL64)
+    X = np.random.default_rng(1).standard_normal((o.dim, 8))
+    Y = torch.empty((o.dim, 8), dtype=torch.float64, device="cuda")
+    M.apply_H(torch.from_numpy(X).cuda(), Y)
+    orp, ocol, oval, oab = o.csr()
+    ref = oracle.spmm(orp, ocol, oval, X)
+    bound = oracle.spmm(orp, ocol, np.maximum(np.abs(oval), oab), np.abs(X))
+    assert np.all(np.abs(Y.cpu().numpy() - ref) <= 1e-11 * bound + 1e-300)
+
+
+@pytest.mark.parametrize("case", [(16, 0, -1, 0), (16, 1, 2, 1), (15, 2, 2, 1), (16, 16, 0, 0), (16, 2, 1, 0)])
+def test_maximum_particle_number(case):
+    """16 nucleons of a species (the ABI's maximum) in the 20 states of the
+    shells N <= 2: hole-like determinants, long phase strings."""
+    Z, N, nmax, twoM = case
+    inp = inputs(2, Z, N, nmax, seed=9, dtype=np.float64, twoM=twoM)
+    o, g = oracle_problem(inp), gpu_problem(inp)
+    assert g.enumerate_basis() == o.dim
+    _species_eq(o, g, 0)
+    _species_eq(o, g, 1)
+    M = g.build_H("f64")
+    rows = None if o.dim < 5000 else np.random.default_rng(0).choice(o.dim, 300, replace=False)
+    _check_matrix(o, M, REL64, rows)
+
+
 def test_build_H_config0_fp64():
     inp = preset_inputs("c0")
     o, g = oracle_problem(inp), gpu_problem(inp)
