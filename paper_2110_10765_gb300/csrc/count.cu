@@ -50,11 +50,11 @@ __global__ void k_cnt_bits(const uint16_t *mbs, int64_t n, int N, uint64_t *bits
     }
 }
 
-// Common states of two ascending lists (runtime N): used on the rare pairs
-// that pass the 64-state prefilter.
-__device__ __noinline__ int common_states(const uint16_t *a, const uint16_t *b, int N) {
+// Common states of two ascending lists of na and nb entries: used on the
+// rare pairs that pass the 64-state prefilter.
+__device__ __noinline__ int common_states(const uint16_t *a, const uint16_t *b, int na, int nb) {
     int i = 0, j = 0, c = 0;
-    while (i < N && j < N) {
+    while (i < na && j < nb) {
         const int x = a[i], y = b[j];
         c += x == y;
         i += x <= y;
@@ -71,24 +71,31 @@ __device__ __forceinline__ void flush_counts(const CountArgs &a, int64_t row, un
     if ((threadIdx.x & 31) == 0 && s) atomicAdd(a.total, s);
 }
 
-// HYBRID (VAR 0) and BITS (VAR 2): R rows per thread.  The population
-// count is first taken of the XOR folded to 32 bits with OR (a lower bound
-// of the true count, one POPC); the rare pairs whose folded count is within
-// max_diff then take the exact test: the 64-bit popcount (and, for HYBRID,
-// the MBS comparison; for BITS, the upper 64 states too).
+// HYBRID (VAR 0) and BITS (VAR 2): R rows per thread, kept as 32-bit
+// halves.  The population count is first taken of the XOR folded to 32 bits
+// with OR (a lower bound of the true count, one POPC); a column goes to the
+// exact test only when the smallest folded count over the thread's R rows is
+// within max_diff (the common case is two LOP3, a POPC and a min per pair):
+// the 64-bit popcount (and, for HYBRID, the MBS comparison; for BITS, the
+// upper 64 states too).
 template <int VAR, int R>
 __global__ void __launch_bounds__(kCntThreads) k_count_bits(CountArgs a) {
-    __shared__ uint64_t slo[kCntTile], shi[VAR == 2 ? kCntTile : 1];
+    __shared__ uint2 slo[kCntTile];
+    __shared__ uint2 shi[VAR == 2 ? kCntTile : 1];
     const int64_t r0 = (int64_t)blockIdx.x * kCntThreads * R + threadIdx.x;
     const int64_t c0 = (int64_t)blockIdx.y * a.chunk;
     const int64_t c1 = min(a.n, c0 + a.chunk);
-    uint64_t lo[R], hi[R];
-    unsigned long long cnt[R];
+    uint32_t l0[R], l1[R], h0[R], h1[R];
+    unsigned cnt[R];
 #pragma unroll
     for (int k = 0; k < R; ++k) {
         const int64_t r = r0 + (int64_t)k * kCntThreads;
-        lo[k] = r < a.n ? a.bits[2 * r] : 0ull;
-        hi[k] = r < a.n ? a.bits[2 * r + 1] : 0ull;
+        const uint64_t lo = r < a.n ? a.bits[2 * r] : 0ull;
+        const uint64_t hi = r < a.n ? a.bits[2 * r + 1] : 0ull;
+        l0[k] = (uint32_t)lo;
+        l1[k] = (uint32_t)(lo >> 32);
+        h0[k] = (uint32_t)hi;
+        h1[k] = (uint32_t)(hi >> 32);
         cnt[k] = 0;
     }
     const int md = a.max_diff;
@@ -96,38 +103,46 @@ __global__ void __launch_bounds__(kCntThreads) k_count_bits(CountArgs a) {
         const int nt = (int)min((int64_t)kCntTile, c1 - t0);
         __syncthreads();
         for (int e = threadIdx.x; e < nt; e += kCntThreads) {
-            slo[e] = a.bits[2 * (t0 + e)];
-            if (VAR == 2) shi[e] = a.bits[2 * (t0 + e) + 1];
+            const uint64_t lo = a.bits[2 * (t0 + e)];
+            slo[e] = make_uint2((uint32_t)lo, (uint32_t)(lo >> 32));
+            if (VAR == 2) {
+                const uint64_t hi = a.bits[2 * (t0 + e) + 1];
+                shi[e] = make_uint2((uint32_t)hi, (uint32_t)(hi >> 32));
+            }
         }
         __syncthreads();
+#pragma unroll 2
         for (int j = 0; j < nt; ++j) {
-            const uint64_t blo = slo[j];
-            const uint64_t bhi = VAR == 2 ? shi[j] : 0ull;
-            bool near[R];
-            bool any = false;
+            const uint2 b = slo[j];
+            const uint2 bh = VAR == 2 ? shi[j] : make_uint2(0u, 0u);
+            int m = 64;
 #pragma unroll
             for (int k = 0; k < R; ++k) {
-                const uint64_t x = lo[k] ^ blo;
-                uint32_t f = (uint32_t)x | (uint32_t)(x >> 32);
-                if (VAR == 2) {
-                    const uint64_t y = hi[k] ^ bhi;
-                    f |= (uint32_t)y | (uint32_t)(y >> 32);
-                }
-                near[k] = __popc(f) <= md;
-                any |= near[k];
+                uint32_t f = (l0[k] ^ b.x) | (l1[k] ^ b.y);
+                if (VAR == 2) f |= (h0[k] ^ bh.x) | (h1[k] ^ bh.y);
+                m = min(m, __popc(f));
             }
-            if (!any) continue;
+            if (m > md) continue;
             // rare: at least one row is near this column
 #pragma unroll
             for (int k = 0; k < R; ++k) {
-                if (!near[k]) continue;
+                uint32_t f = (l0[k] ^ b.x) | (l1[k] ^ b.y);
+                if (VAR == 2) f |= (h0[k] ^ bh.x) | (h1[k] ^ bh.y);
+                if (__popc(f) > md) continue;
+                const int d64 = __popc(l0[k] ^ b.x) + __popc(l1[k] ^ b.y);
                 if (VAR == 2) {
-                    cnt[k] += (__popcll(lo[k] ^ blo) + __popcll(hi[k] ^ bhi)) <= md;
-                } else if (__popcll(lo[k] ^ blo) <= md) {
-                    // the lowest 64 states differ little; compare the MBS lists
+                    cnt[k] += (d64 + __popc(h0[k] ^ bh.x) + __popc(h1[k] ^ bh.y)) <= md;
+                } else if (d64 <= md) {
+                    // the lowest 64 states differ little; compare the MBS
+                    // lists.  Their first popc(lo) entries are those states
+                    // (ascending order), whose common count the bits give:
+                    // only the entries from state 64 on are walked.
                     const int64_t r = r0 + (int64_t)k * kCntThreads;
                     if (r < a.n) {
-                        const int c = common_states(a.mbs + r * a.N, a.mbs + (t0 + j) * a.N, a.N);
+                        const int na = __popc(l0[k]) + __popc(l1[k]), nb = __popc(b.x) + __popc(b.y);
+                        const int c = (na + nb - d64) / 2 +
+                                      common_states(a.mbs + r * a.N + na, a.mbs + (t0 + j) * a.N + nb, a.N - na,
+                                                    a.N - nb);
                         cnt[k] += 2 * (a.N - c) <= md;
                     }
                 }
@@ -198,7 +213,7 @@ __global__ void __launch_bounds__(kCntThreads) k_count_mbs_any(CountArgs a) {
         __syncthreads();
         if (r < a.n)
             for (int j = 0; j < nt; ++j)
-                cnt += 2 * (a.N - common_states(x, smbs_any + j * a.N, a.N)) <= a.max_diff;
+                cnt += 2 * (a.N - common_states(x, smbs_any + j * a.N, a.N, a.N)) <= a.max_diff;
     }
     flush_counts(a, r, cnt);
 }
@@ -256,11 +271,11 @@ void count_pairs(const uint16_t *mbs, int64_t n, int N, int S, int variant, int 
         a.bits = bits.ptr;
     }
     if (variant == CI_COUNT_HYBRID) {
-        dim3 g = count_grid<4>(n, a.chunk);
-        launch("k_count_hybrid", k_count_bits<0, 4>, g, kCntThreads, 0, s, a);
+        dim3 g = count_grid<8>(n, a.chunk);
+        launch("k_count_hybrid", k_count_bits<0, 8>, g, kCntThreads, 0, s, a);
     } else if (variant == CI_COUNT_BITS) {
-        dim3 g = count_grid<4>(n, a.chunk);
-        launch("k_count_bits", k_count_bits<2, 4>, g, kCntThreads, 0, s, a);
+        dim3 g = count_grid<8>(n, a.chunk);
+        launch("k_count_bits", k_count_bits<2, 8>, g, kCntThreads, 0, s, a);
     } else {
         switch (N) {
             case 4: launch_mbs<4>(a, s); break;
