@@ -336,6 +336,23 @@ ci_status ci_lowest_eigs(const ci_matrix *m, const ci_eig_opts *opts, double *ev
 ci_status ci_lowest_eigs_lobpcg(const ci_matrix *m, const ci_eig_opts *opts, const int32_t *row_block,
                                 int64_t nblocks, double *evals, double *evecs, ci_eig_info *info, void *stream);
 
+/* Refinement of Ritz pairs found with a reduced-precision H (an FP32 or
+ * BF16 build): the FP64 Hamiltonian of the problem, its elements evaluated
+ * on the fly by the Slater-Condon rules of the build (nothing stored), is
+ * applied to the k vectors; Rayleigh-Ritz in FP64 on their span, then
+ * `iters` Rayleigh-Ritz steps on span[X, R] with the FP64 residuals
+ * R = H X - X Theta.  The Ritz values then carry the FP64 operator's
+ * rounding instead of the FP32 matrix's.
+ *   k          1..16 vectors; iters 0..16 (each costs one FP64 application
+ *              of H to k vectors, eight per pass).
+ *   evecs      device double [dim][k], the approximate eigenvectors in basis
+ *              order; overwritten with the refined, orthonormal vectors.
+ *   evals      host [k]: refined Ritz values, ascending.
+ *   residuals  host [k] or NULL: ||H x - theta x|| with the FP64 H.
+ * Errors: CI_ERR_INVALID_ARG (sizes, host evecs, dependent vectors). */
+ci_status ci_refine_eigs(ci_problem *p, int32_t k, int32_t iters, double *evecs, double *evals,
+                         double *residuals, void *stream);
+
 /* Many-body basis orbitals (Sec. 2): the basis states that put the
  * nucleons of each species into the same single-particle orbitals, i.e.
  * differ only in the orbitals' magnetic substates, form one group; a

@@ -167,6 +167,17 @@ class Problem:
                                    _ptr(a), _stream(stream)), "ci_observables")
         return a
 
+    def refine_eigs(self, evecs, iters=1, stream=None):
+        """Refine the Ritz pairs in evecs (device float64 [dim, k], k <= 16,
+        overwritten) with the FP64 H applied on the fly: (evals, residuals),
+        numpy, ascending (``ci_refine_eigs``)."""
+        k = 1 if evecs.dim() == 1 else int(evecs.shape[1])
+        ev = np.zeros(k, np.float64)
+        rn = np.zeros(k, np.float64)
+        check(lib().ci_refine_eigs(self._h, k, int(iters), _ptr(evecs), _ptr(ev), _ptr(rn), _stream(stream)),
+              "ci_refine_eigs")
+        return ev, rn
+
     def orbital_blocks(self, sp_orbital, stream=None):
         """Many-body basis orbitals: (device int32 tensor [dim] of group
         indices, number of groups) for the s.p. orbital labels sp_orbital."""

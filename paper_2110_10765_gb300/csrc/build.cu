@@ -536,6 +536,54 @@ void fill_group(const std::vector<Problem *> &ps, GroupCSR *g, cudaStream_t s) {
     else fill_group_t<double>(ps, g, s);
 }
 
+// y_i = sum_j H_ij R[j][0..8), each element evaluated on the fly (nothing
+// stored), written to Y [dim][8]: the FP64 product of the Ritz refinement.
+template <class T>
+struct ProductEmit {
+    const double *R = nullptr;   // [dim][8], gathered by column
+    double *Y = nullptr;         // [dim][8]
+    double acc[8];
+    __device__ __forceinline__ void init() {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[q] = 0.0;
+    }
+    __device__ __forceinline__ void put(const RowArgs<T> &, int64_t, int c, T v) {
+        const double2 *xc = reinterpret_cast<const double2 *>(R + (int64_t)c * 8);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const double2 t = __ldg(xc + q);
+            acc[2 * q] = fma((double)v, t.x, acc[2 * q]);
+            acc[2 * q + 1] = fma((double)v, t.y, acc[2 * q + 1]);
+        }
+    }
+    __device__ __forceinline__ void end_row(int64_t r) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            double y = acc[q];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
+            if ((threadIdx.x & 31) == 0) Y[r * 8 + q] = y;
+            acc[q] = 0.0;
+        }
+    }
+    __device__ __forceinline__ void finish(double *) {}
+};
+
+void h64_apply(Problem *p, const double *R8, double *Y8, cudaStream_t s) {
+    species_filter<double>(p, s);
+    if (p->dim == 0) return;
+    std::vector<RowArgs<double>> args{row_args<double>(p)};
+    std::vector<int64_t> row_off{0, p->dim};
+    DevBuf<unsigned char> dargs;
+    DevBuf<int64_t> doff;
+    upload_args<double>(args, row_off, dargs, doff, s);
+    ProductEmit<double> em{};
+    em.R = R8;
+    em.Y = Y8;
+    launch("k_h64_rows", k_rows<double, ProductEmit<double>>, row_grid(p->dim), 256, 0, s,
+           (const RowArgs<double> *)dargs.ptr, (const int64_t *)doff.ptr, 1, em, (double *)nullptr);
+}
+
 template <class T>
 int observable_apply(Problem *p, const Tables<T> &t, const ConnEntry<T> *ents, const double *L8, const double *R8,
                      double *part, cudaStream_t s) {

@@ -1084,6 +1084,117 @@ void lowest_eigs_lobpcg(const Matrix *H, const ci_eig_opts *opts_in, const int32
     if (!converged) fail(CI_ERR_NOT_CONVERGED, "LOBPCG stopped after %d iterations", it);
 }
 
+// Refinement of k Ritz pairs with the FP64 Hamiltonian applied on the fly:
+// Rayleigh-Ritz on span(X) with H in FP64, then `iters` Rayleigh-Ritz steps
+// on span[X, R] (R = H X - X Theta, the FP64 residuals).  X [dim][k] is
+// overwritten with the refined vectors (orthonormal), evals / resid (host)
+// receive the Ritz values and the FP64 residual norms.
+void refine_eigs(Problem *P, int k, int iters, double *X, double *evals, double *resid, cudaStream_t s) {
+    if (k < 1 || k > 16) fail(CI_ERR_INVALID_ARG, "k must be 1..16 (got %d)", k);
+    if (iters < 0 || iters > 16) fail(CI_ERR_INVALID_ARG, "iters must be 0..16 (got %d)", iters);
+    if (!evals) fail(CI_ERR_INVALID_ARG, "evals is NULL");
+    enumerate_basis(P, s);
+    const int64_t dim = P->dim;
+    if (dim < 2 * (int64_t)k) fail(CI_ERR_INVALID_ARG, "dimension %lld too small for k = %d", (long long)dim, k);
+    if (!X || !is_device_pointer(X)) fail(CI_ERR_INVALID_ARG, "evecs must be a device pointer");
+    Matrix shape;   // only the dimension: the products below are dense
+    shape.dim = dim;
+    shape.vtype = CI_F64;
+    const int n2 = 2 * k;
+    Solver sv(&shape, s, 8, k, 8);
+    DevBuf<double> S((size_t)dim * n2), HS((size_t)dim * n2), T8((size_t)dim * 8), Y8((size_t)dim * 8),
+        Tmp((size_t)dim * n2), Rb((size_t)dim * k), G((size_t)n2 * n2);
+    // HS[:, c0:c0+nc] = H S[:, c0:c0+nc], eight columns per on-the-fly pass
+    auto apply_cols = [&](int c0, int nc) {
+        for (int g = 0; g < nc; g += 8) {
+            const int m = std::min(8, nc - g);
+            CI_CUDA(cudaMemsetAsync(T8.ptr, 0, sizeof(double) * dim * 8, s));
+            launch("k_copy_cols", k_copy_cols, sv.grid(dim * m), 256, 0, s, dim, m, S.ptr + c0 + g, n2, T8.ptr, 8);
+            h64_apply(P, T8.ptr, Y8.ptr, s);
+            launch("k_copy_cols", k_copy_cols, sv.grid(dim * m), 256, 0, s, dim, m, Y8.ptr, 8, HS.ptr + c0 + g, n2);
+        }
+    };
+    auto gram = [&](const double *A, const double *B, int n, std::vector<double> &h) {
+        sv.tn(A, n2, n, B, n2, n, G.ptr, &h);
+    };
+    // [S HS][:, 0:k] = [S HS][:, 0:n] C (n x k, host)
+    auto rotate = [&](int n, const std::vector<double> &C) {
+        sv.upload(C, sv.Cdev.ptr);
+        sv.nn(S.ptr, n2, n, sv.Cdev.ptr, k, Tmp.ptr, k, 1.0, 0.0);
+        launch("k_copy_cols", k_copy_cols, sv.grid(dim * k), 256, 0, s, dim, k, Tmp.ptr, k, S.ptr, n2);
+        sv.nn(HS.ptr, n2, n, sv.Cdev.ptr, k, Tmp.ptr, k, 1.0, 0.0);
+        launch("k_copy_cols", k_copy_cols, sv.grid(dim * k), 256, 0, s, dim, k, Tmp.ptr, k, HS.ptr, n2);
+    };
+    std::vector<double> theta(k), C, ga, gb;
+    // Rayleigh-Ritz on n columns of S (pencil S^T H S, S^T S)
+    auto rayleigh_ritz = [&](int n) -> bool {
+        gram(S.ptr, HS.ptr, n, ga);
+        gram(S.ptr, S.ptr, n, gb);
+        for (int r = 0; r < n; ++r)   // S^T H S is symmetric: average the rounding
+            for (int c = r + 1; c < n; ++c) {
+                const double a = 0.5 * (ga[(size_t)r * n + c] + ga[(size_t)c * n + r]);
+                ga[(size_t)r * n + c] = ga[(size_t)c * n + r] = a;
+            }
+        if (!pencil_lowest(n, k, ga, gb, theta, C)) return false;
+        rotate(n, C);
+        return true;
+    };
+    launch("k_copy_cols", k_copy_cols, sv.grid(dim * k), 256, 0, s, dim, k, X, k, S.ptr, n2);
+    apply_cols(0, k);
+    if (!rayleigh_ritz(k)) fail(CI_ERR_INVALID_ARG, "the k vectors are linearly dependent");
+    std::vector<double> rn(k, 0.0);
+    auto residuals = [&]() {
+        sv.upload(theta, sv.theta_dev.ptr);
+        // R = HX - X Theta into the second half of S (HX made contiguous first)
+        launch("k_copy_cols", k_copy_cols, sv.grid(dim * k), 256, 0, s, dim, k, HS.ptr, n2, Tmp.ptr, k);
+        launch("k_residual", k_residual<double>, sv.grid(dim * k), 256, 0, s, dim, k, Tmp.ptr, S.ptr, n2,
+               sv.theta_dev.ptr, Rb.ptr);
+        launch("k_copy_cols", k_copy_cols, sv.grid(dim * k), 256, 0, s, dim, k, Rb.ptr, k, S.ptr + k, n2);
+        std::vector<double> h;
+        gram(S.ptr + k, S.ptr + k, k, h);
+        for (int v = 0; v < k; ++v) rn[v] = std::sqrt(std::max(h[(size_t)v * k + v], 0.0));
+        return h;
+    };
+    for (int it = 0; it < iters; ++it) {
+        std::vector<double> h = residuals();
+        // unit residual columns, orthonormal (Cholesky QR), then Rayleigh-Ritz
+        // on [X, R]; stop when R has no usable direction left
+        std::vector<double> L, dsc(k);
+        bool ok = true;
+        for (int v = 0; v < k; ++v) {
+            const double d = h[(size_t)v * k + v];
+            if (!(d > 1e-300)) { ok = false; break; }
+            dsc[v] = 1.0 / std::sqrt(d);
+        }
+        if (!ok) break;
+        std::vector<double> Gm(h);
+        for (int i = 0; i < k; ++i)
+            for (int j = 0; j < k; ++j) Gm[(size_t)i * k + j] *= dsc[i] * dsc[j];
+        if (!cholesky_lower(k, Gm, L, 1e-10)) break;
+        std::vector<double> Mi((size_t)k * k, 0.0);   // D L^-T
+        for (int c = 0; c < k; ++c)
+            for (int i = c; i >= 0; --i) {
+                double x = i == c ? 1.0 : 0.0;
+                for (int q = i + 1; q <= c; ++q) x -= L[(size_t)q * k + i] * Mi[(size_t)q * k + c];
+                Mi[(size_t)i * k + c] = x / L[(size_t)i * k + i];
+            }
+        for (int i = 0; i < k; ++i)
+            for (int c = 0; c < k; ++c) Mi[(size_t)i * k + c] *= dsc[i];
+        sv.upload(Mi, sv.Cdev.ptr);
+        sv.nn(S.ptr + k, n2, k, sv.Cdev.ptr, k, Tmp.ptr, k, 1.0, 0.0);
+        launch("k_copy_cols", k_copy_cols, sv.grid(dim * k), 256, 0, s, dim, k, Tmp.ptr, k, S.ptr + k, n2);
+        apply_cols(k, k);
+        if (!rayleigh_ritz(n2)) break;
+    }
+    residuals();
+    launch("k_copy_cols", k_copy_cols, sv.grid(dim * k), 256, 0, s, dim, k, S.ptr, n2, X, k);
+    CI_CUDA(cudaStreamSynchronize(s));
+    for (int v = 0; v < k; ++v) {
+        evals[v] = theta[v];
+        if (resid) resid[v] = rn[v];
+    }
+}
+
 }  // namespace ci
 
 extern "C" ci_status ci_lowest_eigs(const ci_matrix *m, const ci_eig_opts *opts, double *evals, double *evecs,
@@ -1102,5 +1213,15 @@ extern "C" ci_status ci_lowest_eigs_lobpcg(const ci_matrix *m, const ci_eig_opts
         if (!m) ci::fail(CI_ERR_INVALID_ARG, "matrix is NULL");
         ci::StreamScope scope(reinterpret_cast<cudaStream_t>(stream));
         ci::lowest_eigs_lobpcg(&m->impl, opts, row_block, nblocks, evals, evecs, info, reinterpret_cast<cudaStream_t>(stream));
+    });
+}
+
+extern "C" ci_status ci_refine_eigs(ci_problem *p, int32_t k, int32_t iters, double *evecs, double *evals,
+                                    double *residuals, void *stream) {
+    return ci::guard([&] {
+        if (!p) ci::fail(CI_ERR_INVALID_ARG, "problem is NULL");
+        cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+        ci::StreamScope scope(s);
+        ci::refine_eigs(&p->impl, k, iters, evecs, evals, residuals, s);
     });
 }
