@@ -407,9 +407,13 @@ def run_c2_leg(hbm):
     sp_ms = min(timed(lambda: M.apply_H(X, Y))[1] for _ in range(3))
     b = algorithmic_bytes("k_spmm", M.dim, M.nnz)
     del X, Y
-    (ev32, info32), s32 = timed(lambda: M.lowest_eigs(k=p.k))
+    E32 = torch.zeros((M.dim, p.k), dtype=torch.float64, device="cuda")
+    (ev32, info32), s32 = timed(lambda: M.lowest_eigs(k=p.k, evecs=E32))
     dim, nnz = M.dim, M.nnz
     del M
+    # the FP32 Ritz pairs refined with the FP64 H applied on the fly
+    (evr, rnr), sr = timed(lambda: prob.refine_eigs(E32, iters=1))
+    del E32
     # BF16 values with a per-row FP32 scale (6 bytes per nonzero)
     Mb = prob.build_H("bf16")
     X = torch.randn(dim, 8, device="cuda")
@@ -430,6 +434,9 @@ def run_c2_leg(hbm):
             "lowest_f64": [round(float(x), 7) for x in ev64],
             "max_abs_diff_f32_vs_f64": float(np.max(np.abs(ev32 - ev64))),
             "max_rel_diff_f32_vs_f64": float(np.max(np.abs(ev32 - ev64) / np.abs(ev64))),
+            "refined_f32": {"s": sr * 1e-3, "iters": 1, "max_abs_diff_vs_f64": float(np.max(np.abs(evr - ev64))),
+                            "max_rel_diff_vs_f64": float(np.max(np.abs(evr - ev64) / np.abs(ev64))),
+                            "max_residual_f64": float(np.max(rnr))},
             "bf16_rowscale": {"spmm_ms": spb_ms, "solve_s": sb * 1e-3, "iterations": infob["iterations"],
                               "max_abs_diff_vs_f64": float(np.max(np.abs(evb - ev64))),
                               "max_rel_diff_vs_f64": float(np.max(np.abs(evb - ev64) / np.abs(ev64)))}}
@@ -475,6 +482,27 @@ def run_eigensolver_leg(sp, p, eps, tables):
                 n_l, ms = kern[kname]
                 rec[kname] = {"launches": int(n_l), "ms_per_launch": round(ms / max(n_l, 1), 4)}
         out[name] = rec
+    # FP32 Lanczos pairs refined with the FP64 H on the fly, against the FP64 solve
+    import numpy as np
+    E = torch.zeros((M.dim, p.k), dtype=torch.float64, device="cuda")
+    ev32, _ = M.lowest_eigs(k=p.k, block=p.block, evecs=E)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    evr, rnr = prob.refine_eigs(E, iters=1)
+    b.record(stream)
+    b.synchronize()
+    M64 = prob.build_H("f64")
+    a2, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a2.record(stream)
+    ev64, info64 = M64.lowest_eigs(k=p.k, block=p.block)
+    b2.record(stream)
+    b2.synchronize()
+    del M64
+    out["refine_fp64"] = {"ms": round(a.elapsed_time(b), 3), "iters": 1,
+                          "fp32_max_abs_diff_vs_fp64_solve": float(np.max(np.abs(ev32 - ev64))),
+                          "refined_max_abs_diff_vs_fp64_solve": float(np.max(np.abs(evr - ev64))),
+                          "max_residual_f64": float(np.max(rnr)),
+                          "fp64_solve_ms": round(a2.elapsed_time(b2), 3), "fp64_iterations": info64["iterations"]}
     blk, nb = prob.orbital_blocks(labels)
     sizes = torch.bincount(blk.long(), minlength=nb).cpu()
     out["orbital_groups"] = {"groups": nb, "largest": int(sizes.max()), "mean": round(float(sizes.float().mean()), 2)}
