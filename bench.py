@@ -663,6 +663,7 @@ def run_batch_leg(args):
     return {"problems": len(probs), "converged": int(nconv), "rows": int(sum(dims)), "nnz": st["nnz"],
             "dim_min": int(min(dims)), "dim_median": float(np.median(dims)), "dim_max": int(max(dims)),
             "build_s": st["build_s"], "solve_s": st["solve_s"], "steps": st["steps"], "wall_s": t_batch,
+            "autotuned_launch": b.tuning(),
             "solves_per_s": len(probs) / t_batch,
             "fp64_single": {"sample": len(sample), "rows_fraction": frac, "seconds": t_single,
                             "solves_per_s": single_rate,

@@ -411,6 +411,17 @@ ci_status ci_batch_run(ci_batch *b, void *stream);
 ci_status ci_batch_result(const ci_batch *b, int32_t i, double *evals, ci_eig_info *info);
 /* Wall time of the build and of the solve, engine steps, total nonzeros. */
 ci_status ci_batch_stats(const ci_batch *b, double *build_s, double *solve_s, int32_t *steps, int64_t *nnz);
+
+/* The launch shape the autotuner picked for the batch's persistent kernels
+ * (CTAs per SM of the row-tile kernels and of the SpMM; every tile is
+ * handled by one CTA and every row by one warp, so results do not depend
+ * on it), and the best step time it measured (0 when the choice came from
+ * its cache).  ci_batch_run times two real Lanczos steps per candidate
+ * (tile kernels 2, 4, 8, 16 CTAs per SM, then SpMM 4, 8, 16) and caches the
+ * choice per device, slot count and row count (to a power of two).
+ * Errors: CI_ERR_STATE before ci_batch_run. */
+ci_status ci_batch_tuning(const ci_batch *b, int32_t *tile_ctas_per_sm, int32_t *spmm_ctas_per_sm,
+                          double *best_step_ms);
 void ci_batch_destroy(ci_batch *b);
 
 /* ---------------------------------------------------------------- serving */

@@ -333,6 +333,12 @@ class Batch:
         check(lib().ci_batch_stats(self._h, C.byref(b), C.byref(s), C.byref(st), C.byref(nnz)), "ci_batch_stats")
         return {"build_s": b.value, "solve_s": s.value, "steps": st.value, "nnz": nnz.value}
 
+    def tuning(self):
+        """Launch shape picked by the autotuner (``ci_batch_tuning``)."""
+        tm, sm, ms = C.c_int32(), C.c_int32(), C.c_double()
+        check(lib().ci_batch_tuning(self._h, C.byref(tm), C.byref(sm), C.byref(ms)), "ci_batch_tuning")
+        return {"tile_ctas_per_sm": tm.value, "spmm_ctas_per_sm": sm.value, "best_step_ms": ms.value}
+
 
 def _desc(sp, Z, N, nmax, twoM, eps, keep, tables=None, seed=None):
     """Fill a ProblemDesc; arrays it points to are appended to keep."""

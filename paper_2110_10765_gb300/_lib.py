@@ -104,6 +104,7 @@ _SIGS = {
     "ci_batch_run": (C.c_int, [_P, _P]),
     "ci_batch_result": (C.c_int, [_P, C.c_int32, _P, C.POINTER(EigInfo)]),
     "ci_batch_stats": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int32), _I64P]),
+    "ci_batch_tuning": (C.c_int, [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
     "ci_batch_destroy": (None, [_P]),
     "ci_queue_create": (C.c_int, [C.POINTER(QueueDesc), C.POINTER(_P)]),
     "ci_submit": (C.c_int, [_P, C.POINTER(Request), C.POINTER(C.c_uint64)]),

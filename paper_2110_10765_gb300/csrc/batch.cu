@@ -67,7 +67,7 @@ void batch_run(Batch *b, cudaStream_t s) {
     }
     engine_retile(&b->eng);
     engine_init_slots(&b->eng);
-    int steps = 0;
+    int steps = engine_autotune(&b->eng);   // real steps, timed per launch shape
     while (true) {
         engine_step(&b->eng);
         ++steps;
@@ -128,6 +128,17 @@ ci_status ci_batch_run(ci_batch *b, void *stream) {
         if (b->impl.ran) fail(CI_ERR_STATE, "batch already ran");
         StreamScope scope(reinterpret_cast<cudaStream_t>(stream));
         batch_run(&b->impl, reinterpret_cast<cudaStream_t>(stream));
+    });
+}
+
+ci_status ci_batch_tuning(const ci_batch *b, int32_t *tile_ctas_per_sm, int32_t *spmm_ctas_per_sm,
+                          double *best_step_ms) {
+    return guard([&] {
+        if (!b) fail(CI_ERR_INVALID_ARG, "batch is NULL");
+        if (!b->impl.ran) fail(CI_ERR_STATE, "call ci_batch_run first");
+        if (tile_ctas_per_sm) *tile_ctas_per_sm = b->impl.eng.tile_mult;
+        if (spmm_ctas_per_sm) *spmm_ctas_per_sm = b->impl.eng.spmm_mult;
+        if (best_step_ms) *best_step_ms = b->impl.eng.tuned_step_ms;
     });
 }
 

@@ -14,6 +14,9 @@
 #include <algorithm>
 #include <cmath>
 
+#include <map>
+#include <mutex>
+
 #include "engine.cuh"
 
 namespace ci {
@@ -794,7 +797,7 @@ Engine::~Engine() {
     if (stream) cudaStreamDestroy(stream);
 }
 
-static int tile_grid() { return sm_count() * 4; }
+static int tile_grid(const Engine *e) { return sm_count() * e->tile_mult; }
 
 static size_t tn_smem(int MB) { return sizeof(double) * kER * (MB + EB); }
 static size_t ritz_smem(int MB) {
@@ -897,7 +900,7 @@ void engine_retile(Engine *e) {
 // tn + reduce for one mode
 static void tn_reduce(Engine *e, int phase, int mode) {
     const DensePtrs d = dense_ptrs(e);
-    launch("k_e_tn", k_e_tn, tile_grid(), 256, tn_smem(e->MB), e->stream, e->slots.ptr, (const Tile *)e->tiles.ptr,
+    launch("k_e_tn", k_e_tn, tile_grid(e), 256, tn_smem(e->MB), e->stream, e->slots.ptr, (const Tile *)e->tiles.ptr,
            (const int32_t *)e->ntiles.ptr, e->MB, phase, mode, e->part.ptr);
     launch("k_e_reduce", k_e_reduce, dim3(e->max_slots, (e->MB * EB + 31) / 32), 256, 0, e->stream, e->slots.ptr,
            e->max_slots, e->MB, phase, mode, (const double *)e->part.ptr, d);
@@ -905,7 +908,7 @@ static void tn_reduce(Engine *e, int phase, int mode) {
 
 static void nn(Engine *e, int phase, int mode, int c0 = 0) {
     if (mode == M_QR2)
-        launch("k_e_nn", k_e_nn<true>, tile_grid(), 256, 0, e->stream, e->slots.ptr, (const Tile *)e->tiles.ptr,
+        launch("k_e_nn", k_e_nn<true>, tile_grid(e), 256, 0, e->stream, e->slots.ptr, (const Tile *)e->tiles.ptr,
                (const int32_t *)e->ntiles.ptr, e->MB, phase, mode, dense_ptrs(e), c0);
     else
         launch("k_e_nn", k_e_nn<false>, sm_count() * 5, 256, 0, e->stream, e->slots.ptr, (const Tile *)e->tiles.ptr,
@@ -919,7 +922,7 @@ static void block_qr(Engine *e, int phase) {
     tn_reduce(e, phase, M_GRAM);
     launch("k_e_small", k_e_small, sb, 64, 0, e->stream, e->slots.ptr, e->max_slots, phase, 1, d);
     nn(e, phase, M_QR1);
-    launch("k_e_rand", k_e_rand, tile_grid(), 256, 0, e->stream, e->slots.ptr, (const Tile *)e->tiles.ptr,
+    launch("k_e_rand", k_e_rand, tile_grid(e), 256, 0, e->stream, e->slots.ptr, (const Tile *)e->tiles.ptr,
            (const int32_t *)e->ntiles.ptr, e->MB, phase, 0);
     for (int pass = 0; pass < 2; ++pass) {
         tn_reduce(e, phase, M_RAND);
@@ -932,7 +935,7 @@ static void block_qr(Engine *e, int phase) {
 
 void engine_init_slots(Engine *e) {
     const DensePtrs d = dense_ptrs(e);
-    launch("k_e_rand", k_e_rand, tile_grid(), 256, 0, e->stream, e->slots.ptr, (const Tile *)e->tiles.ptr,
+    launch("k_e_rand", k_e_rand, tile_grid(e), 256, 0, e->stream, e->slots.ptr, (const Tile *)e->tiles.ptr,
            (const int32_t *)e->ntiles.ptr, e->MB, (int)PH_INIT, 1);
     block_qr(e, PH_INIT);
     launch("k_e_advance", k_e_advance, (e->max_slots + 63) / 64, 64, 0, e->stream, e->slots.ptr, e->max_slots, e->MB,
@@ -943,8 +946,8 @@ static void record_step(Engine *e) {
     const DensePtrs d = dense_ptrs(e);
     const Tile *tp = e->tiles.ptr;
     const int32_t *nt = e->ntiles.ptr;
-    launch("k_e_prepx", k_e_prepx, tile_grid(), 256, 0, e->stream, e->slots.ptr, tp, nt, e->MB, (int)PH_STEP);
-    launch("k_e_spmm", k_e_spmm, sm_count() * 8, 256, 0, e->stream, e->slots.ptr, tp, nt, (int)PH_STEP);
+    launch("k_e_prepx", k_e_prepx, tile_grid(e), 256, 0, e->stream, e->slots.ptr, tp, nt, e->MB, (int)PH_STEP);
+    launch("k_e_spmm", k_e_spmm, sm_count() * e->spmm_mult, 256, 0, e->stream, e->slots.ptr, tp, nt, (int)PH_STEP);
     tn_reduce(e, PH_STEP, M_LOC);
     nn(e, PH_STEP, M_LOC);
     tn_reduce(e, PH_STEP, M_FULL);
@@ -954,7 +957,7 @@ static void record_step(Engine *e) {
     launch("k_e_advance", k_e_advance, (e->max_slots + 63) / 64, 64, 0, e->stream, e->slots.ptr, e->max_slots, e->MB,
            (int)PH_STEP, d);
     launch("k_e_ritz", k_e_ritz, e->max_slots, 256, ritz_smem(e->MB), e->stream, e->slots.ptr, e->max_slots, e->MB, d);
-    launch("k_e_restart_rows", k_e_restart_rows, tile_grid(), 256, restart_smem(e->MB), e->stream, e->slots.ptr, tp,
+    launch("k_e_restart_rows", k_e_restart_rows, tile_grid(e), 256, restart_smem(e->MB), e->stream, e->slots.ptr, tp,
            nt, e->MB, d);
     launch("k_e_restart_slot", k_e_restart_slot, e->max_slots, 256, 0, e->stream, e->slots.ptr, e->max_slots, e->MB,
            d);
@@ -988,6 +991,77 @@ void engine_step(Engine *e) {
     CI_CUDA(cudaGraphLaunch(e->exec, e->stream));
 }
 
+static void drop_graph(Engine *e) {
+    CI_CUDA(cudaStreamSynchronize(e->stream));
+    if (e->exec) cudaGraphExecDestroy(e->exec);
+    if (e->graph) cudaGraphDestroy(e->graph);
+    e->exec = nullptr;
+    e->graph = nullptr;
+}
+
+int engine_autotune(Engine *e) {
+    // cache key: device, slots, total rows (to a power of two)
+    int dev = 0;
+    CI_CUDA(cudaGetDevice(&dev));
+    int64_t rows = 0;
+    for (const Tile &t : e->host_tiles) rows += t.nr;
+    int lg = 0;
+    while ((int64_t)1 << lg < rows) ++lg;
+    const int64_t key = ((int64_t)dev << 48) | ((int64_t)e->max_slots << 8) | lg;
+    static std::mutex mu;
+    static std::map<int64_t, std::pair<int, int>> cache;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            if (e->tile_mult != it->second.first || e->spmm_mult != it->second.second) drop_graph(e);
+            e->tile_mult = it->second.first;
+            e->spmm_mult = it->second.second;
+            e->tuned = true;
+            return 0;
+        }
+    }
+    cudaEvent_t a, b;
+    CI_CUDA(cudaEventCreate(&a));
+    CI_CUDA(cudaEventCreate(&b));
+    int steps = 0;
+    double best = 1e300;
+    int best_t = e->tile_mult, best_s = e->spmm_mult;
+    auto trial = [&](int tm, int smult) -> bool {
+        drop_graph(e);
+        e->tile_mult = tm;
+        e->spmm_mult = smult;
+        engine_step(e);   // capture and run
+        CI_CUDA(cudaEventRecord(a, e->stream));
+        engine_step(e);   // timed replay
+        CI_CUDA(cudaEventRecord(b, e->stream));
+        CI_CUDA(cudaEventSynchronize(b));
+        steps += 2;
+        float ms = 0.f;
+        CI_CUDA(cudaEventElapsedTime(&ms, a, b));
+        if (ms < best) { best = ms; best_t = tm; best_s = smult; }
+        return engine_running(e) > 0;
+    };
+    bool live = true;
+    for (int tm : {4, 2, 8, 16})
+        if (live) live = trial(tm, 8);
+    const int bt = best_t;
+    for (int smult : {4, 16})
+        if (live) live = trial(bt, smult);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (e->tile_mult != best_t || e->spmm_mult != best_s) drop_graph(e);
+    e->tile_mult = best_t;
+    e->spmm_mult = best_s;
+    e->tuned = true;
+    e->tuned_step_ms = best;
+    if (live) {   // a finished batch says little about the others
+        std::lock_guard<std::mutex> lk(mu);
+        cache[key] = {best_t, best_s};
+    }
+    return steps;
+}
+
 int engine_running(Engine *e) {
     CI_CUDA(cudaMemcpyAsync(e->pinned_counter, e->counters.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, e->stream));
     CI_CUDA(cudaStreamSynchronize(e->stream));
@@ -1001,9 +1075,9 @@ void engine_true_residuals(Engine *e) {
     const int sb = (e->max_slots + 63) / 64;
     for (int c0 = 0; c0 < EKMAX; c0 += EB) {
         nn(e, PH_FINAL, M_RITZ, c0);  // W = Q S[:, c0:c0+8]
-        launch("k_e_prepx", k_e_prepx, tile_grid(), 256, 0, e->stream, e->slots.ptr, tp, nt, e->MB, (int)PH_FINAL);
-        launch("k_e_spmm", k_e_spmm, tile_grid(), 256, 0, e->stream, e->slots.ptr, tp, nt, (int)PH_FINAL);
-        launch("k_e_resid", k_e_resid, tile_grid(), 256, 0, e->stream, e->slots.ptr, tp, nt, d, e->MB, c0);
+        launch("k_e_prepx", k_e_prepx, tile_grid(e), 256, 0, e->stream, e->slots.ptr, tp, nt, e->MB, (int)PH_FINAL);
+        launch("k_e_spmm", k_e_spmm, tile_grid(e), 256, 0, e->stream, e->slots.ptr, tp, nt, (int)PH_FINAL);
+        launch("k_e_resid", k_e_resid, tile_grid(e), 256, 0, e->stream, e->slots.ptr, tp, nt, d, e->MB, c0);
         tn_reduce(e, PH_FINAL, M_RESID);
         launch("k_e_store_resid", k_e_store_resid, sb, 64, 0, e->stream, e->slots.ptr, e->max_slots, d, c0);
     }

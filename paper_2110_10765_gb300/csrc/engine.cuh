@@ -53,7 +53,13 @@ struct EngineDense {
 struct Engine {
     int MB = 64;                  // basis columns
     int max_slots = 0, max_tiles = 0;
-    int autotune_variant = 0;     // SpMM variant picked by the autotuner
+    // launch shape of the persistent kernels, CTAs per SM: the tile kernels
+    // (prepx, tn, QR nn, rand, restart rows, residuals) and the SpMM; picked
+    // by engine_autotune.  Every tile is still handled by one CTA and every
+    // row by one warp, so results do not depend on it.
+    int tile_mult = 4, spmm_mult = 8;
+    bool tuned = false;
+    double tuned_step_ms = 0.0;   // best step time seen by the autotuner
     DevBuf<SlotDev> slots;
     DevBuf<Tile> tiles;
     DevBuf<int32_t> ntiles;       // [1]
@@ -78,6 +84,10 @@ void engine_free_slot(Engine *e, int i);
 void engine_retile(Engine *e);
 // Initialise the start blocks of every S_INIT slot (random, orthonormal).
 void engine_init_slots(Engine *e);
+// Pick the launch shape by timing real steps of the running slots with each
+// candidate (two steps per candidate: capture, then a timed replay); the
+// choice is cached per device and workload size.  Returns the steps taken.
+int engine_autotune(Engine *e);
 // One block-Lanczos step of every running slot (graph replay).
 void engine_step(Engine *e);
 // Number of running slots (synchronises the engine stream).
