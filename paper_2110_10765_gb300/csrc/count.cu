@@ -79,7 +79,7 @@ __device__ __forceinline__ void flush_counts(const CountArgs &a, int64_t row, un
 // the 64-bit popcount (and, for HYBRID, the MBS comparison; for BITS, the
 // upper 64 states too).
 template <int VAR, int R>
-__global__ void __launch_bounds__(kCntThreads) k_count_bits(CountArgs a) {
+__global__ void __launch_bounds__(kCntThreads, VAR == 2 ? 2 : 3) k_count_bits(CountArgs a) {
     __shared__ uint2 slo[kCntTile];
     __shared__ uint2 shi[VAR == 2 ? kCntTile : 1];
     const int64_t r0 = (int64_t)blockIdx.x * kCntThreads * R + threadIdx.x;
@@ -111,7 +111,6 @@ __global__ void __launch_bounds__(kCntThreads) k_count_bits(CountArgs a) {
             }
         }
         __syncthreads();
-#pragma unroll 2
         for (int j = 0; j < nt; ++j) {
             const uint2 b = slo[j];
             const uint2 bh = VAR == 2 ? shi[j] : make_uint2(0u, 0u);
