@@ -477,13 +477,18 @@ void ci_queue_destroy(ci_queue *q);
 
 /* ---------------------------------------------------------------- tracing */
 
-/* Kernel tracing.  While on, every kernel the library launches is
- * bracketed by two CUDA events on its launch stream (a small overhead per
- * launch).  No paper counterpart beyond timing regions (Listing 10). */
+/* Kernel tracing.  While on, every kernel the library launches is counted
+ * per name and bracketed by two CUDA events on its launch stream: every
+ * launch (on = 1) or, sampled, the first of every `on` launches of each
+ * kernel (on >= 2; total_ms is then the timed launches' mean times the
+ * launch count).  Each timed launch costs two event records on the host.
+ * on = 0 turns tracing off.  No paper counterpart beyond timing regions
+ * (Listing 10). */
 typedef struct {
     char name[48];       /* kernel name                                  */
     int64_t launches;    /* launches recorded since the last reset       */
-    double total_ms;     /* sum of their event-measured durations (ms)   */
+    double total_ms;     /* their event-measured durations (ms), summed;
+                            sampled: mean of the timed ones x launches  */
 } ci_trace_entry;
 
 ci_status ci_trace_enable(int32_t on);

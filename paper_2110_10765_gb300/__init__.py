@@ -409,9 +409,10 @@ class Queue:
                 "mem_used": m.value}
 
 
-def trace_enable(on=True):
-    """Bracket every library kernel launch with CUDA events (ci_trace_enable)."""
-    check(lib().ci_trace_enable(1 if on else 0), "ci_trace_enable")
+def trace_enable(on=True, sample=1):
+    """Count every library kernel launch and bracket every `sample`-th launch
+    of each kernel with CUDA events (ci_trace_enable)."""
+    check(lib().ci_trace_enable((max(int(sample), 1)) if on else 0), "ci_trace_enable")
 
 
 def trace_read(reset=True):

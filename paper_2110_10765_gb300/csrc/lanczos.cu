@@ -337,6 +337,12 @@ struct Solver {
     DevBuf<float> X32, Y32;
     DevBuf<double> X64;
     double hnorm = 0.0;
+    // pinned copy of the projection coefficients of the latest step, read
+    // after the next host sync instead of a sync of its own
+    double *pin_coef = nullptr;
+    size_t pin_len = 0;
+    int pend_m = 0, pend_lo = 0, pend_nb = 0, pend_passes = 0;
+    bool pend = false;
 
     Solver(const Matrix *H_, cudaStream_t s_, int b_, int k_, int mmax_)
         : H(H_), s(s_), dim(H_->dim), b(b_), k(k_), mmax(mmax_), f64(H_->vtype == CI_F64) {
@@ -362,6 +368,15 @@ struct Solver {
         if (f64) X64.alloc((size_t)dim * b);
         else { X32.alloc((size_t)dim * b); Y32.alloc((size_t)dim * b); }
     }
+
+    ~Solver() {
+        if (pin_coef) {
+            cudaStreamSynchronize(s);
+            cudaFreeHost(pin_coef);
+        }
+    }
+    Solver(const Solver &) = delete;
+    Solver &operator=(const Solver &) = delete;
 
     int grid(int64_t work) const { return grid_for(work, 256, sm_count() * 8); }
 
@@ -448,10 +463,43 @@ struct Solver {
         std::vector<double> h((size_t)(passes + 1) * kMaxNa * 8);
         CI_CUDA(cudaMemcpyAsync(h.data(), Cacc.ptr, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s));
         CI_CUDA(cudaStreamSynchronize(s));
-        for (int i = 0; i < nl; ++i)
+        fold_coef(h.data(), nb, m, lo, passes, coef);
+    }
+
+    // coef (m x nb) = the summed coefficients held in h (layout of Cacc)
+    static void fold_coef(const double *h, int nb, int m, int lo, int passes, std::vector<double> *coef) {
+        coef->assign((size_t)m * nb, 0.0);
+        for (int i = 0; i < m - lo; ++i)
             for (int v = 0; v < nb; ++v) (*coef)[(size_t)(lo + i) * nb + v] += h[(size_t)i * nb + v];
         for (int p = 0; p < passes; ++p)
             for (size_t e = 0; e < (size_t)m * nb; ++e) (*coef)[e] += h[(size_t)(p + 1) * kMaxNa * 8 + e];
+    }
+
+    // project() whose coefficients are copied to pinned memory without a
+    // sync; take_coef() reads them after the stream has been synchronised
+    // (block_qr synchronises on its Gram matrix).
+    void project_deferred(double *Wb, int nb, int m, int lo, int passes) {
+        project(Wb, nb, m, lo, passes, nullptr);
+        if (m == 0) return;
+        const size_t len = (size_t)(passes + 1) * kMaxNa * 8;
+        if (pin_len < len) {
+            if (pin_coef) {
+                CI_CUDA(cudaStreamSynchronize(s));
+                cudaFreeHost(pin_coef);
+                pin_coef = nullptr;
+            }
+            CI_CUDA(cudaMallocHost(&pin_coef, sizeof(double) * len));
+            pin_len = len;
+        }
+        CI_CUDA(cudaMemcpyAsync(pin_coef, Cacc.ptr, sizeof(double) * len, cudaMemcpyDeviceToHost, s));
+        pend = true;
+        pend_m = m; pend_lo = lo; pend_nb = nb; pend_passes = passes;
+    }
+    void take_coef(std::vector<double> *coef, bool synced) {
+        if (!pend) { coef->assign((size_t)pend_m * pend_nb, 0.0); return; }
+        if (!synced) CI_CUDA(cudaStreamSynchronize(s));
+        fold_coef(pin_coef, pend_nb, pend_m, pend_lo, pend_passes, coef);
+        pend = false;
     }
 
     // Orthonormalise Wb [dim][b] (already orthogonal to Q[:, 0:m]) into
@@ -657,7 +705,12 @@ void lowest_eigs(const Matrix *H, const ci_eig_opts *opts_in, double *evals, dou
     while (true) {
         // W = H V_j, orthogonalised against the whole basis
         sv.apply(sv.Q.ptr + j0, mmax, b, sv.W.ptr);
-        sv.project(sv.W.ptr, b, m_cur, std::max(0, j0 - b), o.reorth_passes, &coef);
+        sv.project_deferred(sv.W.ptr, b, m_cur, std::max(0, j0 - b), o.reorth_passes);
+        ++it;
+        // next block (its Gram matrix is the step's one host sync; the
+        // projection coefficients copied before it are then on the host)
+        sv.block_qr(sv.W.ptr, m_cur, o.seed + 0x9E37ull * (uint64_t)(it + 1), Rlast);
+        sv.take_coef(&coef, true);
         for (int i = 0; i < j0; ++i)
             for (int v = 0; v < b; ++v) {
                 T[(size_t)i * mmax + j0 + v] = coef[(size_t)i * b + v];
@@ -667,9 +720,6 @@ void lowest_eigs(const Matrix *H, const ci_eig_opts *opts_in, double *evals, dou
             for (int v = 0; v < b; ++v)
                 T[(size_t)(j0 + u) * mmax + j0 + v] =
                     0.5 * (coef[(size_t)(j0 + u) * b + v] + coef[(size_t)(j0 + v) * b + u]);
-        ++it;
-        // next block
-        sv.block_qr(sv.W.ptr, m_cur, o.seed + 0x9E37ull * (uint64_t)(it + 1), Rlast);
         for (int r = 0; r < b; ++r)
             for (int c = 0; c < b; ++c) {
                 T[(size_t)(m_cur + r) * mmax + j0 + c] = Rlast[(size_t)r * b + c];
