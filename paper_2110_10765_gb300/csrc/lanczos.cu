@@ -702,9 +702,11 @@ void lowest_eigs(const Matrix *H, const ci_eig_opts *opts_in, double *evals, dou
     Ritz last;
     int m_act = 0;
     std::vector<double> Rlast;
+    bool applied = false;   // H V_j already enqueued (before the last host Ritz check)
     while (true) {
         // W = H V_j, orthogonalised against the whole basis
-        sv.apply(sv.Q.ptr + j0, mmax, b, sv.W.ptr);
+        if (!applied) sv.apply(sv.Q.ptr + j0, mmax, b, sv.W.ptr);
+        applied = false;
         sv.project_deferred(sv.W.ptr, b, m_cur, std::max(0, j0 - b), o.reorth_passes);
         ++it;
         // next block (its Gram matrix is the step's one host sync; the
@@ -732,6 +734,13 @@ void lowest_eigs(const Matrix *H, const ci_eig_opts *opts_in, double *evals, dou
         ++since_check;
         if (since_check >= o.check_every || full || it >= o.max_iter) {
             since_check = 0;
+            // the next product only needs the new block: the GPU computes it
+            // while the host solves the projected problem (wasted once, at
+            // convergence)
+            if (!full && it < o.max_iter) {
+                sv.apply(sv.Q.ptr + j0, mmax, b, sv.W.ptr);
+                applied = true;
+            }
             last = ritz(T, mmax, m_act, b, Rlast, k);
             sv.hnorm = std::max(sv.hnorm, std::max(std::fabs(last.theta.front()), std::fabs(last.theta.back())));
             converged = (int)last.res.size() >= k;
