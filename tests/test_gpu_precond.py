@@ -169,3 +169,23 @@ def test_block_precond_invalid():
         g.orbital_blocks(-np.ones(len(inp["sp"]["N"]), np.int32))
     with pytest.raises(ValueError):
         M.lowest_eigs(k=3, blocks=(blk, nb))                          # blocks with Lanczos
+
+
+def test_lobpcg_block_precond_bf16_rowscale():
+    """BF16 values with row scales: the blocks are gathered from the scaled
+    values (not exactly symmetric); LOBPCG still reaches the lowest
+    eigenvalues within the Weyl bound of the BF16 rounding, and refining
+    with the FP64 H recovers the FP64 values."""
+    inp = preset_inputs("c2_sub")
+    g = gpu_problem(inp)
+    Mb = g.build_H("bf16")
+    rp, col, v16, scale = Mb.export()
+    blocks = g.orbital_blocks(synth.sp_orbitals(inp["sp"]))
+    E = torch.zeros((Mb.dim, 8), dtype=torch.float64, device="cuda")
+    ev, info = Mb.lowest_eigs(k=8, method="lobpcg", blocks=blocks, evecs=E, tol=1e-5)
+    exact = np.array(golden()["c2_sub"]["lowest"])[:8]
+    bound = np.max(np.diff(rp) * scale.astype(np.float64)) * 2.0 ** -9
+    assert np.all(np.abs(ev - exact) <= bound + 1e-5 * np.abs(exact)), (np.abs(ev - exact).max(), bound)
+    evr, rn = g.refine_eigs(E, iters=2)
+    assert np.all(evr >= exact - 1e-9)          # Ritz values of the exact operator bound from above
+    assert np.max(np.abs(evr - exact)) < np.max(np.abs(ev - exact))
