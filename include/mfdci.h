@@ -329,8 +329,11 @@ ci_status ci_lowest_eigs(const ci_matrix *m, const ci_eig_opts *opts, double *ev
  *             theta_1 - |r_1| taken from the Rayleigh-Ritz of iterations
  *             0, 2, 6, 14, 30, ... (the blocks are re-inverted then).
  * Options and outputs as ci_lowest_eigs; max_basis, reorth_passes and
- * check_every are ignored, max_iter counts iterations [1000].  Dimensions up
- * to 4*block use the dense path of ci_lowest_eigs.  Errors as
+ * check_every are ignored, max_iter counts iterations [1000].  The default
+ * tol is 4e-3 for a CI_BF16_ROWSCALE matrix: its per-row scales round H_ij
+ * and H_ji differently, and the true residuals of the nearly symmetric
+ * operator stop near that rounding (2^-9).  Dimensions up to 4*block use the
+ * dense path of ci_lowest_eigs.  Errors as
  * ci_lowest_eigs, plus CI_ERR_INVALID_ARG for a row_block entry outside
  * 0..nblocks-1 or a host row_block. */
 ci_status ci_lowest_eigs_lobpcg(const ci_matrix *m, const ci_eig_opts *opts, const int32_t *row_block,

@@ -182,7 +182,7 @@ def test_lobpcg_block_precond_bf16_rowscale():
     rp, col, v16, scale = Mb.export()
     blocks = g.orbital_blocks(synth.sp_orbitals(inp["sp"]))
     E = torch.zeros((Mb.dim, 8), dtype=torch.float64, device="cuda")
-    ev, info = Mb.lowest_eigs(k=8, method="lobpcg", blocks=blocks, evecs=E, tol=1e-5)
+    ev, info = Mb.lowest_eigs(k=8, method="lobpcg", blocks=blocks, evecs=E)   # default tol for BF16: 4e-3
     exact = np.array(golden()["c2_sub"]["lowest"])[:8]
     bound = np.max(np.diff(rp) * scale.astype(np.float64)) * 2.0 ** -9
     assert np.all(np.abs(ev - exact) <= bound + 1e-5 * np.abs(exact)), (np.abs(ev - exact).max(), bound)
