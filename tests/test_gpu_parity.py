@@ -404,3 +404,50 @@ def test_apply_and_eigs_bf16_rowscale():
     exact = np.array(golden()["c2_sub"]["lowest"])
     bound = np.max(np.diff(rp) * scale.astype(np.float64)) * 2.0 ** -9
     assert np.all(np.abs(ev - exact) <= bound + 1e-5 * np.abs(exact)), (np.abs(ev - exact).max(), bound)
+
+
+def _sp128():
+    import synth
+    sp6 = synth.ho_sp_table(6)                  # 168 states: the first 128 (shells 0..5 and part of 6)
+    return {k: v[:128].copy() for k, v in sp6.items()}
+
+
+def test_maximum_sp_states_seeded_tables():
+    """S = 128 (the ABI's maximum, both 64-bit words full) with TBMEs from the
+    seeded generator (no flat tables): one proton and one neutron, no Nmax
+    cut, so every basis pair is within four differences.  The matrix is
+    symmetric, dense, and the solver agrees with LAPACK on it."""
+    import synth
+    sp = _sp128()
+    eps = synth.sp_energies(sp, 20.0)
+    inp = dict(sp=sp, Z=1, N=1, nmax=-1, twoM=0, eps=eps)
+    g = gpu_problem(inp, seed=12)
+    dim = g.enumerate_basis()
+    assert g.species(0)["bits"].shape[1] == 2
+    assert int(g.species(0)["bits"][:, 1].max()) >> 63 == 1        # state 127 occurs
+    M = g.build_H("f64")
+    assert M.nnz == dim * dim
+    rp, col, val, _ = M.export()
+    H = oracle.dense_from_csr(rp, col.astype(np.int64), val, dim)
+    assert np.array_equal(H, H.T)
+    ev, info = M.lowest_eigs(k=5)
+    ref = np.linalg.eigvalsh(H)[:5]
+    assert np.allclose(ev, ref, rtol=0, atol=1e-8 * np.abs(ref).max())
+
+
+def test_maximum_sp_states_zero_interaction_closed_form():
+    """S = 128 with zero TBMEs (device tables): the levels of one proton and
+    one neutron are eps_a + eps_b over the pairs with m_a + m_b = 0."""
+    import synth
+    sp = _sp128()
+    eps = synth.sp_energies(sp, 20.0)
+    S = 128
+    zeros = {k: torch.zeros(S ** 4, dtype=torch.float32, device="cuda") for k in ("pp", "nn", "pn")}
+    inp = dict(sp=sp, Z=1, N=1, nmax=-1, twoM=0, eps=eps, tables=zeros)
+    g = gpu_problem(inp)
+    M = g.build_H("f32")
+    ev, info = M.lowest_eigs(k=5)
+    m = np.asarray(sp["twom"])
+    levels = np.sort([eps[a] + eps[b] for a in range(S) for b in range(S) if m[a] + m[b] == 0])
+    assert np.allclose(ev, levels[:5], rtol=0, atol=1e-4)
+    del zeros
