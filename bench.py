@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--no-observables", action="store_true", help="skip the observables leg")
     ap.add_argument("--no-c2", action="store_true", help="skip the Nmax=6 precision-study leg")
     ap.add_argument("--no-eigensolvers", action="store_true", help="skip the Lanczos / LOBPCG comparison leg")
+    ap.add_argument("--no-motifs", action="store_true", help="skip the scan / fill / array-reduction motif leg")
     ap.add_argument("--obs-m", type=int, default=16, help="operators of the observables leg")
     return ap.parse_args()
 
@@ -362,6 +363,8 @@ def run_ours(args):
         rec["observables"] = run_observables_leg(sp, p, eps, dtab, args.obs_m)
     if not args.no_eigensolvers:
         rec["eigensolvers"] = run_eigensolver_leg(sp, p, eps, dtab)
+    if not args.no_motifs:
+        rec["motifs"] = run_motifs_leg(hbm, (clk or {}).get("sm_mhz"))
     if not args.no_c2:
         rec["c2_precision"] = run_c2_leg(hbm)
     if not args.no_batch:
@@ -445,6 +448,66 @@ def run_c2_leg(hbm):
             "bf16_rowscale": {"spmm_ms": spb_ms, "solve_s": sb * 1e-3, "iterations": infob["iterations"],
                               "max_abs_diff_vs_f64": float(np.max(np.abs(evb - ev64))),
                               "max_rel_diff_vs_f64": float(np.max(np.abs(evb - ev64) / np.abs(ev64)))}}
+
+
+# ---------------------------------------------------------------- motifs
+
+# FP32 FMAs per clock per SM (CUDA arithmetic-throughput table): the ALU
+# roofline of the array-reduction motif
+FMA32_PER_CLK_SM = 128
+
+
+def run_motifs_leg(hbm, clock_mhz=None, reps=5):
+    """The paper's motif benchmarks (Sec. 2.2-2.4): serial vs parallel scan of
+    2^24 counts (Fig. 5), the shared-array fill of Listing 7 with m = 512,
+    p = 1 over 2^20 rows (Fig. 6), and the small-array reduction with m = 64
+    over n = 2^14 columns, n^2 pairs (Fig. 7)."""
+    import torch
+
+    import paper_2110_10765_gb300 as ci
+    stream = torch.cuda.current_stream()
+
+    def best(fn, r=reps):
+        fn()
+        ms = []
+        for _ in range(r):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        return min(ms)
+
+    g = torch.Generator(device="cuda").manual_seed(5)
+    out = {}
+    n = 1 << 24
+    c = torch.randint(0, 10, (n,), dtype=torch.int32, device="cuda", generator=g)
+    off = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+    par = best(lambda: ci.exclusive_scan(c, off))
+    ser = best(lambda: ci.scan_serial(c, off), r=1)
+    out["scan"] = {"n": n, "parallel_ms": par, "serial_ms": ser, "speedup": ser / par,
+                   "parallel_gbs": (4 * n + 8 * (n + 1)) / (par * 1e-3) / 1e9,
+                   "parallel_frac_hbm": (4 * n + 8 * (n + 1)) / (par * 1e-3) / 1e9 / hbm}
+    del c, off
+    rows, m, p = 1 << 20, 512, 1
+    offset = torch.arange(rows, dtype=torch.int64, device="cuda") * (m // p)
+    arr = torch.empty(rows * (m // p), dtype=torch.int32, device="cuda")
+    fm = best(lambda: ci.fill_shared(offset, m, p, arr))
+    fb = 4 * rows * (m // p) + 8 * rows
+    out["fill"] = {"rows": rows, "m": m, "p": p, "ms": fm, "gbs": fb / (fm * 1e-3) / 1e9,
+                   "frac_hbm": fb / (fm * 1e-3) / 1e9 / hbm}
+    del offset, arr
+    nr, mr = 1 << 14, 64
+    x = torch.randn((nr, mr), device="cuda", generator=g)
+    y = torch.randn((nr, mr), device="cuda", generator=g)
+    rm = best(lambda: ci.array_reduction(x, y))
+    rate = nr * nr * mr / (rm * 1e-3)
+    peak = FMA32_PER_CLK_SM * SMS * (clock_mhz or 2070.0) * 1e6
+    out["array_reduction"] = {"n": nr, "m": mr, "ms": rm, "updates_per_s": rate, "bound": "alu",
+                              "peak_updates_per_s": peak, "frac": rate / peak,
+                              "peak_basis": "%d FP32 FMA/clk/SM x %d SMs x clock" % (FMA32_PER_CLK_SM, SMS)}
+    return out
 
 
 # ---------------------------------------------------------------- eigensolvers

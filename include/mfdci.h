@@ -478,6 +478,32 @@ ci_status ci_queue_stats(ci_queue *q, int64_t *submitted, int64_t *admitted, int
 /* Cancels what is left, waits for the worker and frees everything. */
 void ci_queue_destroy(ci_queue *q);
 
+/* ---------------------------------------------------------------- motifs */
+
+/* The paper's motif benchmarks (Sec. 2.2-2.4), as measured primitives.
+ *
+ * Listing 5 / Fig. 5: the serial prefix sum on the device, one thread:
+ * offsets[0] = 0, offsets[i+1] = offsets[i] + counts[i].  The control for
+ * the parallel ci_exclusive_scan (same inputs and outputs, device
+ * pointers).  The stream is synchronised. */
+ci_status ci_scan_serial(const int32_t *counts, int64_t n, int64_t *offsets, void *stream);
+
+/* Listing 7 / Fig. 6: fill a shared array from per-row offsets.  Row i
+ * (0..n-1) stores the values j in 1..m with j mod p == 0, ascending, at
+ * arr[offset[i] + r], r = 0, 1, ... (the rank replaces the listing's
+ * atomic counter, so the result is deterministic).  offset: device int64
+ * [n] (e.g. the exclusive scan of m/p per row); arr: device int32, large
+ * enough for every row.  m >= 0, p >= 1.  The stream is synchronised. */
+ci_status ci_fill_shared(const int64_t *offset, int64_t n, int32_t m, int32_t p, int32_t *arr, void *stream);
+
+/* Eq. 2 / Listings 8-9 / Fig. 7: the small-array reduction
+ *   a[k] = sum_{i,j < n} x[k + m i] * y[k + m j],   k < m,
+ * over all n^2 pairs (x, y: device float, column-major m x n, as the
+ * listings' x(k,i)).  FP32 products and per-lane FP32 sums; the block and
+ * grid partials are added in a fixed order in FP64; a: device float [m].
+ * m in {8, 16, 32, 64, 128, 256}.  The stream is synchronised. */
+ci_status ci_array_reduction(const float *x, const float *y, int64_t n, int32_t m, float *a, void *stream);
+
 /* ---------------------------------------------------------------- tracing */
 
 /* Kernel tracing.  While on, every kernel the library launches is counted

@@ -17,12 +17,14 @@ than itself):
 * ``eig.py``: lowest eigenvalues by LAPACK (dense) or ARPACK (sparse), the
   plain definition of "lowest k eigenvalues";
 * ``precond.py``: many-body basis orbitals and the block-diagonal
-  preconditioner of LOBPCG (dense solves per block).
+  preconditioner of LOBPCG (dense solves per block);
+* ``motifs.py``: the shared-array fill and small-array reduction motifs of
+  Sec. 2.3-2.4 (plain loops).
 """
 
 from .core import OracleProblem, build_library, count_pairs, exclusive_scan, expectation_values, spmm
 from .eig import lowest_dense, lowest_sparse, dense_from_csr
-from . import brute, precond
+from . import brute, motifs, precond
 
 __all__ = ["OracleProblem", "build_library", "count_pairs", "exclusive_scan", "expectation_values", "spmm",
-           "lowest_dense", "lowest_sparse", "dense_from_csr", "brute", "precond"]
+           "lowest_dense", "lowest_sparse", "dense_from_csr", "brute", "motifs", "precond"]

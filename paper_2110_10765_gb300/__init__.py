@@ -445,3 +445,28 @@ def exclusive_scan(counts, offsets, stream=None):
     """Eq. 1 on the device: int32 counts [n] -> int64 offsets [n+1]."""
     check(lib().ci_exclusive_scan(_ptr(counts), int(counts.numel()), _ptr(offsets), _stream(stream)),
           "ci_exclusive_scan")
+
+
+# -- motif benchmarks of Sec. 2.2-2.4 ----------------------------------------
+def scan_serial(counts, offsets, stream=None):
+    """Listing 5's serial prefix sum on the device (one thread):
+    int32 counts [n] -> int64 offsets [n+1] (ci_scan_serial)."""
+    check(lib().ci_scan_serial(_ptr(counts), int(counts.numel()), _ptr(offsets), _stream(stream)), "ci_scan_serial")
+
+
+def fill_shared(offset, m, p, arr, stream=None):
+    """Listing 7's shared-array fill: row i stores j = p, 2p, ... <= m at
+    arr[offset[i]:] (ci_fill_shared); offset device int64 [n], arr device int32."""
+    check(lib().ci_fill_shared(_ptr(offset), int(offset.numel()), int(m), int(p), _ptr(arr), _stream(stream)),
+          "ci_fill_shared")
+
+
+def array_reduction(x, y, stream=None):
+    """Eq. 2's small-array reduction a[k] = sum_ij x[i, k] y[j, k] over all
+    n^2 pairs; x, y device float32 [n, m] (row i = the listings' column
+    x(:, i)); returns a device float32 [m] (ci_array_reduction)."""
+    import torch
+    n, m = int(x.shape[0]), int(x.shape[1])
+    a = torch.empty(m, dtype=torch.float32, device=x.device)
+    check(lib().ci_array_reduction(_ptr(x), _ptr(y), n, m, _ptr(a), _stream(stream)), "ci_array_reduction")
+    return a

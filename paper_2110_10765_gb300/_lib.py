@@ -99,6 +99,9 @@ _SIGS = {
     "ci_lowest_eigs_lobpcg": (C.c_int, [_P, C.POINTER(EigOpts), _P, C.c_int64, _P, _P, C.POINTER(EigInfo), _P]),
     "ci_orbital_blocks": (C.c_int, [_P, _P, _P, _I64P, _P]),
     "ci_refine_eigs": (C.c_int, [_P, C.c_int32, C.c_int32, _P, _P, _P, _P]),
+    "ci_scan_serial": (C.c_int, [_P, C.c_int64, _P, _P]),
+    "ci_fill_shared": (C.c_int, [_P, C.c_int64, C.c_int32, C.c_int32, _P, _P]),
+    "ci_array_reduction": (C.c_int, [_P, _P, C.c_int64, C.c_int32, _P, _P]),
     "ci_block_precond_apply": (C.c_int, [_P, _P, C.c_int64, C.c_double, _P, _P, C.c_int32, _P, _P]),
     "ci_batch_create": (C.c_int, [C.POINTER(_P), C.c_int32, _P, C.POINTER(EigOpts), C.POINTER(_P)]),
     "ci_batch_run": (C.c_int, [_P, _P]),
