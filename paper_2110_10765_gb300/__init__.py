@@ -447,6 +447,12 @@ def exclusive_scan(counts, offsets, stream=None):
           "ci_exclusive_scan")
 
 
+def exclusive_scan_noalloc(counts, offsets, stream=None):
+    """The same scan without device allocation (ci_exclusive_scan_noalloc)."""
+    check(lib().ci_exclusive_scan_noalloc(_ptr(counts), int(counts.numel()), _ptr(offsets), _stream(stream)),
+          "ci_exclusive_scan_noalloc")
+
+
 # -- motif benchmarks of Sec. 2.2-2.4 ----------------------------------------
 def scan_serial(counts, offsets, stream=None):
     """Listing 5's serial prefix sum on the device (one thread):

@@ -79,7 +79,6 @@ __global__ void __launch_bounds__(256) k_array_reduce(const float *__restrict__ 
     float acc[KL];
 #pragma unroll
     for (int c = 0; c < KL; ++c) acc[c] = 0.f;
-#pragma unroll 4
     for (int64_t j = j0; j < j1; ++j) {
 #pragma unroll
         for (int c = 0; c < KL; ++c) {

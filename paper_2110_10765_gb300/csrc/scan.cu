@@ -43,13 +43,30 @@ __device__ int64_t block_excl_scan(int64_t v, int64_t *total) {
     return r;
 }
 
+// The kItems counts of a thread: two 16-byte loads when they are all in
+// range and x is 16-byte aligned (VEC), else one load each.
+template <bool VEC>
+__device__ __forceinline__ void load_items(const int32_t *x, int64_t n, int64_t base, int32_t (&v)[kItems]) {
+    if (VEC && base + kItems <= n) {
+        const int4 a = *reinterpret_cast<const int4 *>(x + base);
+        const int4 b = *reinterpret_cast<const int4 *>(x + base + 4);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+        v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+        return;
+    }
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) v[i] = base + i < n ? x[base + i] : 0;
+}
+
+template <bool VEC>
 __global__ void __launch_bounds__(kScanThreads) k_tile_sums(const int32_t *x, int64_t n, int64_t *sums) {
     __shared__ int64_t tot;
     int64_t base = (int64_t)blockIdx.x * kTile + (int64_t)threadIdx.x * kItems;
+    int32_t c[kItems];
+    load_items<VEC>(x, n, base, c);
     int64_t v = 0;
 #pragma unroll
-    for (int i = 0; i < kItems; ++i)
-        if (base + i < n) v += x[base + i];
+    for (int i = 0; i < kItems; ++i) v += c[i];
     block_excl_scan(v, &tot);
     if (threadIdx.x == 0) sums[blockIdx.x] = tot;
 }
@@ -68,18 +85,31 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_sums(int64_t *sums, int64
     }
 }
 
+// VEC: y is 16-byte aligned too, and full runs are stored as pairs
+template <bool VEC>
 __global__ void __launch_bounds__(kScanThreads) k_tile_apply(const int32_t *x, int64_t n, const int64_t *sums,
                                                              int64_t *y) {
     __shared__ int64_t tot;
     int64_t base = (int64_t)blockIdx.x * kTile + (int64_t)threadIdx.x * kItems;
-    int64_t v[kItems];
+    int32_t v[kItems];
+    load_items<VEC>(x, n, base, v);
     int64_t s = 0;
 #pragma unroll
-    for (int i = 0; i < kItems; ++i) {
-        v[i] = base + i < n ? x[base + i] : 0;
-        s += v[i];
-    }
+    for (int i = 0; i < kItems; ++i) s += v[i];
     int64_t e = block_excl_scan(s, &tot) + sums[blockIdx.x];
+    if (VEC && base + kItems <= n) {
+        int64_t o[kItems];
+#pragma unroll
+        for (int i = 0; i < kItems; ++i) {
+            o[i] = e;
+            e += v[i];
+        }
+#pragma unroll
+        for (int i = 0; i < kItems; i += 2)
+            *reinterpret_cast<longlong2 *>(y + base + i) = make_longlong2(o[i], o[i + 1]);
+        if (base + kItems == n) y[n] = e;   // the total
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < kItems; ++i) {
         if (base + i < n) y[base + i] = e;
@@ -101,9 +131,17 @@ void exclusive_scan_i32(const int32_t *counts, int64_t n, int64_t *offsets, DevB
     int64_t nb = (n + kTile - 1) / kTile;
     if (nb > INT32_MAX) fail(CI_ERR_CAPACITY, "scan too long");
     scratch.ensure((size_t)nb);
-    launch("k_tile_sums", k_tile_sums, (unsigned)nb, kScanThreads, 0, s, counts, n, scratch.ptr);
-    launch("k_scan_sums", k_scan_sums, 1, kScanThreads, 0, s, scratch.ptr, nb);
-    launch("k_tile_apply", k_tile_apply, (unsigned)nb, kScanThreads, 0, s, counts, n, scratch.ptr, offsets);
+    const bool vec = (uintptr_t)counts % 16 == 0 && (uintptr_t)offsets % 16 == 0;
+    if (vec) {
+        launch("k_tile_sums", k_tile_sums<true>, (unsigned)nb, kScanThreads, 0, s, counts, n, scratch.ptr);
+        launch("k_scan_sums", k_scan_sums, 1, kScanThreads, 0, s, scratch.ptr, nb);
+        launch("k_tile_apply", k_tile_apply<true>, (unsigned)nb, kScanThreads, 0, s, counts, n, scratch.ptr, offsets);
+    } else {
+        launch("k_tile_sums", k_tile_sums<false>, (unsigned)nb, kScanThreads, 0, s, counts, n, scratch.ptr);
+        launch("k_scan_sums", k_scan_sums, 1, kScanThreads, 0, s, scratch.ptr, nb);
+        launch("k_tile_apply", k_tile_apply<false>, (unsigned)nb, kScanThreads, 0, s, counts, n, scratch.ptr,
+               offsets);
+    }
     CI_CHECK_LAUNCH();
 }
 
@@ -186,9 +224,11 @@ extern "C" ci_status ci_exclusive_scan_noalloc(const int32_t *counts, int64_t n,
             return;
         }
         // every tile sum is written by k_tile_sums before it is read
-        launch("k_tile_sums", k_tile_sums, (unsigned)nb, kScanThreads, 0, s, counts, n, tiles);
+        const bool vec = (uintptr_t)counts % 16 == 0 && (uintptr_t)offsets % 16 == 0;
+        launch("k_tile_sums", vec ? k_tile_sums<true> : k_tile_sums<false>, (unsigned)nb, kScanThreads, 0, s, counts,
+               n, tiles);
         launch("k_scan_sums", k_scan_sums, 1, kScanThreads, 0, s, tiles, nb);
-        launch("k_tile_apply", k_tile_apply, (unsigned)nb, kScanThreads, 0, s, counts, n, (const int64_t *)tiles,
-               offsets);
+        launch("k_tile_apply", vec ? k_tile_apply<true> : k_tile_apply<false>, (unsigned)nb, kScanThreads, 0, s,
+               counts, n, (const int64_t *)tiles, offsets);
     });
 }

@@ -93,6 +93,28 @@ def test_exclusive_scan_bit_exact(n):
     assert np.array_equal(y.cpu().numpy(), oracle.exclusive_scan(x))
 
 
+@pytest.mark.parametrize("n", [1, 8, 4097, 123457])
+@pytest.mark.parametrize("shift", [(1, 0), (0, 1), (3, 1)])
+def test_exclusive_scan_unaligned(n, shift):
+    """Counts or offsets off a 16-byte boundary take the one-load-per-item
+    path (and the no-allocation variant the same), with identical results."""
+    import paper_2110_10765_gb300 as ci
+    sx, sy = shift
+    x = np.random.default_rng(n + sx).integers(0, 2000, n).astype(np.int32)
+    xb = torch.zeros(n + 4, dtype=torch.int32, device="cuda")
+    xb[sx:sx + n] = torch.from_numpy(x).cuda()
+    yb = torch.full((n + 3,), -7, dtype=torch.int64, device="cuda")
+    ci.exclusive_scan(xb[sx:sx + n], yb[sy:sy + n + 1])
+    assert np.array_equal(yb[sy:sy + n + 1].cpu().numpy(), oracle.exclusive_scan(x))
+    if sy:
+        assert int(yb[0]) == -7
+    yb.fill_(-7)
+    check = ci.exclusive_scan_noalloc if hasattr(ci, "exclusive_scan_noalloc") else None
+    if check is not None:
+        check(xb[sx:sx + n], yb[sy:sy + n + 1])
+        assert np.array_equal(yb[sy:sy + n + 1].cpu().numpy(), oracle.exclusive_scan(x))
+
+
 def test_exclusive_scan_large_total_int64():
     import paper_2110_10765_gb300 as ci
     n = 3_000_000
