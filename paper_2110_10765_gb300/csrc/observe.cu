@@ -8,6 +8,7 @@
 // multiplied into Y at once; no operator is stored.  Vectors go through the
 // row kernel eight at a time.  Each block leaves a partial of its eight sums,
 // the host adds them in block order (deterministic).
+#include <algorithm>
 #include <cstring>
 
 #include "problem.cuh"
@@ -50,30 +51,36 @@ void observables(Problem *P, const uint64_t *seeds, int m, const double *X, cons
     CI_CUDA(cudaMemsetAsync(zero_eps.ptr, 0, sizeof(double) * P->S, s));
     DevBuf<ConnEntry<double>> ents(c.outer.ent_buf->n);
     const int nblk_max = sm_count() * 8;
-    const size_t slots = (size_t)m * ng;   // one partial array per (operator, group)
+    // operators in chunks: one partial array per (operator, group) of a chunk
+    constexpr int kChunk = 64;
+    const size_t slots = (size_t)std::min(m, kChunk) * ng;
     DevBuf<double> part(slots * nblk_max * 8);
-    std::vector<int> nblk(slots, 0);
-    for (int k = 0; k < m; ++k) {
-        Tables<double> t;
-        stage_operator_tables<double>(P, seeds[k], t, zero_eps.ptr, s);
-        operator_entries<double>(P, t, ents.ptr, s);
-        for (int g = 0; g < ng; ++g) {
-            const size_t sl = (size_t)k * ng + g;
-            nblk[sl] = observable_apply<double>(P, t, ents.ptr, L8.ptr + (size_t)g * dim * 8,
-                                                right + (size_t)g * dim * 8, part.ptr + sl * nblk_max * 8, s);
-            if (nblk[sl] > nblk_max) fail(CI_ERR_INTERNAL, "observable grid above its partial buffer");
-        }
-    }
     std::vector<double> h(slots * nblk_max * 8);
-    CI_CUDA(cudaMemcpyAsync(h.data(), part.ptr, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s));
-    CI_CUDA(cudaStreamSynchronize(s));
-    for (int k = 0; k < m; ++k)
-        for (int v = 0; v < n; ++v) {
-            const size_t sl = (size_t)k * ng + v / 8;
-            double t = 0.0;
-            for (int b = 0; b < nblk[sl]; ++b) t += h[(sl * nblk_max + b) * 8 + v % 8];
-            a[(size_t)k * n + v] = t;
+    for (int k0 = 0; k0 < m; k0 += kChunk) {
+        const int kn = std::min(kChunk, m - k0);
+        std::vector<int> nblk((size_t)kn * ng, 0);
+        for (int kk = 0; kk < kn; ++kk) {
+            Tables<double> t;
+            stage_operator_tables<double>(P, seeds[k0 + kk], t, zero_eps.ptr, s);
+            operator_entries<double>(P, t, ents.ptr, s);
+            for (int g = 0; g < ng; ++g) {
+                const size_t sl = (size_t)kk * ng + g;
+                nblk[sl] = observable_apply<double>(P, t, ents.ptr, L8.ptr + (size_t)g * dim * 8,
+                                                    right + (size_t)g * dim * 8, part.ptr + sl * nblk_max * 8, s);
+                if (nblk[sl] > nblk_max) fail(CI_ERR_INTERNAL, "observable grid above its partial buffer");
+            }
         }
+        const size_t used = (size_t)kn * ng * nblk_max * 8;
+        CI_CUDA(cudaMemcpyAsync(h.data(), part.ptr, sizeof(double) * used, cudaMemcpyDeviceToHost, s));
+        CI_CUDA(cudaStreamSynchronize(s));
+        for (int kk = 0; kk < kn; ++kk)
+            for (int v = 0; v < n; ++v) {
+                const size_t sl = (size_t)kk * ng + v / 8;
+                double t = 0.0;
+                for (int b = 0; b < nblk[sl]; ++b) t += h[(sl * nblk_max + b) * 8 + v % 8];
+                a[(size_t)(k0 + kk) * n + v] = t;
+            }
+    }
 }
 
 }  // namespace ci

@@ -78,6 +78,11 @@ def test_transition_same_vectors_equal_expectation():
     assert np.array_equal(a, b)
 
 
+def test_observables_more_operators_than_one_chunk():
+    """70 operators: the library processes them in chunks of 64."""
+    _check(inputs(1, 2, 2, -1, seed=3), list(range(200, 270)), 3, xseed=4)
+
+
 def test_observables_zero_vectors_and_single_operator():
     import torch
     inp = inputs(1, 2, 2, -1, seed=3)
