@@ -51,11 +51,11 @@ __global__ void k_fill_shared(const int64_t *__restrict__ offset, int64_t n, int
     }
 }
 
-constexpr int kRedI = 8;       // columns i per warp
+constexpr int kRedI = 16;      // columns i per warp
 constexpr int kRedWarps = 8;
 
-// Block (bi, bj): columns i in [bi*64, bi*64+64) (8 per warp), columns j in
-// its chunk.  Lane l owns k = l, l + 32, ... (M/32 of them, M >= 32) or, for
+// Block (bi, bj): columns i in [bi*128, bi*128+128) (16 per warp), columns j
+// in its chunk.  Lane l owns k = l, l + 32, ... (M/32 of them, M >= 32) or, for
 // M < 32, k = l % M with the lanes split over i.
 template <int M>
 __global__ void __launch_bounds__(256) k_array_reduce(const float *__restrict__ x, const float *__restrict__ y,
