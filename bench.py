@@ -165,7 +165,7 @@ def workload_inputs():
 # DRAM bytes (read + write) per launch from one ncu capture of the current
 # kernels on this workload; reported as the roofline traffic.
 TRACE_SAMPLE = 8
-NCU_TRAFFIC_C1 = {"k_spmm": 838.9e6, "k_fill_rows": 963.1e6, "k_count_rows": 15.6e6}
+NCU_TRAFFIC_C1 = {"k_spmm": 838.9e6, "k_fill_rows": 963.1e6}
 
 
 def algorithmic_bytes(kernel, dim, nnz, nvec=8):
@@ -174,9 +174,7 @@ def algorithmic_bytes(kernel, dim, nnz, nvec=8):
         return 8 * nnz + 8 * (dim + 1)
     if kernel == "k_spmm":           # CSR streamed once, X read once, Y written
         return 8 * nnz + 8 * (dim + 1) + 2 * 4 * nvec * dim
-    if kernel == "k_count_rows":     # counts written
-        return 4 * dim
-    return None
+    return None   # k_count_rows walks per-row segment tables: latency-bound, no byte roofline
 
 
 def run_ours(args):
