@@ -10,10 +10,17 @@ species filter, count, scan, fill H (FP32), and block Lanczos (b = 8,
 FP64 reorthogonalisation) for the lowest 5 eigenvalues, whose SpMMs apply
 H.  ``value`` = H nonzeros built per second of whole step time.
 
-Also measured in the same run: the standalone SpMM (H X, 8 vectors) as a
-fraction of the HBM roofline, per-kernel live durations (CUDA events on the
-launch stream), the end-to-end time through the public API with host
-buffers, and the FP64 oracle on the host cores (``cpu_baseline``).
+Also measured in the same run: the standalone SpMM (H X, 8 vectors, full
+and half storage) as a fraction of the HBM roofline, per-kernel live
+durations (CUDA events on the launch stream, one launch in 8 of each kernel
+timed, every launch counted), the end-to-end time through the public API
+with host buffers, and the FP64 oracle on the host cores (``cpu_baseline``);
+then, each skippable with its flag: the count benchmark of Sec. 2.1
+(``--no-count``), observables and transition elements (``--no-observables``),
+the eigensolvers with FP64 Ritz refinement (``--no-eigensolvers``), the motif
+benchmarks of Sec. 2.2-2.4 (``--no-motifs``), the Nmax = 6 precision study
+(``--no-c2``), the 256-problem batch (``--no-batch``) and the served stream
+(``--no-serve``).
 
 ``--impl reference`` times the oracle (the plain FP64 CPU program) on a
 bounded sample of the same workload instead.
