@@ -250,6 +250,26 @@ __global__ void k_cvt_to_f64(int64_t dim, int nb, const float *__restrict__ src,
         dst[(t / nb) * ldd + t % nb] = (double)src[t];
 }
 
+// X16[i][0..8) = V1[i][0..8), X16[i][8..16) = V2[i][0..8) in FP32
+__global__ void k_pack16(int64_t dim, const double *__restrict__ V1, int ld1, const double *__restrict__ V2, int ld2,
+                         float *__restrict__ X16) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < dim * 16; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t >> 4;
+        const int c = (int)(t & 15);
+        X16[t] = (float)(c < 8 ? V1[i * ld1 + c] : V2[i * ld2 + c - 8]);
+    }
+}
+
+// W1[i][0..8) = Y16[i][0..8), W2[i][0..8) = Y16[i][8..16) in FP64 (ld 8)
+__global__ void k_unpack16(int64_t dim, const float *__restrict__ Y16, double *__restrict__ W1, double *__restrict__ W2) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < dim * 16; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t >> 4;
+        const int c = (int)(t & 15);
+        if (c < 8) W1[i * 8 + c] = Y16[t];
+        else W2[i * 8 + c - 8] = Y16[t];
+    }
+}
+
 __global__ void k_copy_cols(int64_t dim, int nb, const double *__restrict__ src, int lds, double *__restrict__ dst,
                             int ldd) {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < dim * nb; t += (int64_t)gridDim.x * blockDim.x)
@@ -434,6 +454,23 @@ struct Solver {
             apply_matrix(H, X32.ptr, Y32.ptr, nb, s);
             launch("k_cvt_to_f64", k_cvt_to_f64, grid(dim * nb), 256, 0, s, dim, nb, Y32.ptr, Wout, nb);
         }
+        CI_CHECK_LAUNCH();
+    }
+
+    // W1 = H V1 and W2 = H V2 (8 vectors each, outputs ld 8): one 16-vector
+    // product for an FP32 or BF16 H, else two 8-vector ones
+    DevBuf<float> X16, Y16;
+    void apply2(const double *V1, int ld1, const double *V2, int ld2, double *W1, double *W2) {
+        if (f64 || b != 8 || H->upper) {
+            apply(V1, ld1, 8, W1);
+            apply(V2, ld2, 8, W2);
+            return;
+        }
+        X16.ensure((size_t)dim * 16);
+        Y16.ensure((size_t)dim * 16);
+        launch("k_pack16", k_pack16, grid(dim * 16), 256, 0, s, dim, V1, ld1, V2, ld2, X16.ptr);
+        apply_matrix16(H, X16.ptr, Y16.ptr, s);
+        launch("k_unpack16", k_unpack16, grid(dim * 16), 256, 0, s, dim, (const float *)Y16.ptr, W1, W2);
         CI_CHECK_LAUNCH();
     }
 
@@ -1018,8 +1055,11 @@ void lowest_eigs_lobpcg(const Matrix *H, const ci_eig_opts *opts_in, const int32
         // through the updates drift by the SpMM's rounding, which the
         // orthonormalisation of nearly converged blocks would amplify
         if (it > 0) {
-            sv.apply(X.ptr, nb, nb, AX.ptr);
-            if (haveP) sv.apply(P.ptr, nb, nb, AP.ptr);
+            if (haveP && nb == 8) sv.apply2(X.ptr, nb, P.ptr, nb, AX.ptr, AP.ptr);
+            else {
+                sv.apply(X.ptr, nb, nb, AX.ptr);
+                if (haveP) sv.apply(P.ptr, nb, nb, AP.ptr);
+            }
         }
         upload_theta();
         launch("k_residual", k_residual<double>, sv.grid(dim * nb), 256, 0, s, dim, nb, AX.ptr, X.ptr, nb,

@@ -262,6 +262,8 @@ void exclusive_scan_i32(const int32_t *counts, int64_t n, int64_t *offsets,
 std::vector<int64_t> gather_i64(const int64_t *src, const std::vector<int64_t> &idx, cudaStream_t s);
 void build_matrix(Problem *p, int vtype, Matrix *m, cudaStream_t s);
 void upper_matrix(const Matrix *full, Matrix *out, cudaStream_t s);
+// Y = H X for 16 FP32 vectors [dim][16] (FP32 or BF16 values, full storage)
+void apply_matrix16(const Matrix *m, const float *X, float *Y, cudaStream_t s);
 // Y8 = H R8 ([dim][8]) in FP64 with every element evaluated on the fly
 void h64_apply(Problem *p, const double *R8, double *Y8, cudaStream_t s);
 void apply_matrix(const Matrix *m, const void *X, void *Y, int nvec, cudaStream_t s);

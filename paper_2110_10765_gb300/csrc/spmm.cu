@@ -357,6 +357,67 @@ void upper_matrix(const Matrix *full, Matrix *out, cudaStream_t s) {
     CI_CHECK_LAUNCH();
 }
 
+// 16 FP32 vectors (two 8-vector blocks side by side, 64-byte rows of X): one
+// warp per row, four lanes per nonzero (a 16-byte quarter of the X row each),
+// eight nonzeros per warp step.  One gather serves twice the vectors of the
+// 8-wide kernel for the same L2 transactions.
+template <class TV>
+__global__ void __launch_bounds__(256) k_spmm16(int64_t dim, const int64_t *__restrict__ rp,
+                                                const int32_t *__restrict__ col, const TV *__restrict__ val,
+                                                const float *__restrict__ X, float *__restrict__ Y,
+                                                const float *__restrict__ row_scale) {
+    const int lane = threadIdx.x & 31, q = lane & 3, grp = lane >> 2;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const float4 *X4 = reinterpret_cast<const float4 *>(X);
+    for (int64_t r = warp; r < dim; r += nwarps) {
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        const int64_t e1 = rp[r + 1];
+        int64_t e = rp[r] + grp;
+        for (; e + 8 < e1; e += 16) {   // two nonzeros in flight per lane quad
+            const int c0 = __ldcs(col + e), c1 = __ldcs(col + e + 8);
+            const float v0 = load_val(val + e), v1 = load_val(val + e + 8);
+            const float4 x0 = __ldg(X4 + (int64_t)c0 * 4 + q), x1 = __ldg(X4 + (int64_t)c1 * 4 + q);
+            a0 = fmaf(v0, x0.x, a0); a1 = fmaf(v0, x0.y, a1); a2 = fmaf(v0, x0.z, a2); a3 = fmaf(v0, x0.w, a3);
+            a0 = fmaf(v1, x1.x, a0); a1 = fmaf(v1, x1.y, a1); a2 = fmaf(v1, x1.z, a2); a3 = fmaf(v1, x1.w, a3);
+        }
+        for (; e < e1; e += 8) {
+            const int c = __ldcs(col + e);
+            const float v = load_val(val + e);
+            const float4 x = __ldg(X4 + (int64_t)c * 4 + q);
+            a0 = fmaf(v, x.x, a0); a1 = fmaf(v, x.y, a1); a2 = fmaf(v, x.z, a2); a3 = fmaf(v, x.w, a3);
+        }
+#pragma unroll
+        for (int o = 16; o > 2; o >>= 1) {
+            a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+            a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+            a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+            a3 += __shfl_xor_sync(0xffffffffu, a3, o);
+        }
+        if (lane < 4) {
+            const float sc = row_scale ? row_scale[r] : 1.f;
+            reinterpret_cast<float4 *>(Y)[r * 4 + q] = make_float4(a0 * sc, a1 * sc, a2 * sc, a3 * sc);
+        }
+    }
+}
+
+void apply_matrix16(const Matrix *m, const float *X, float *Y, cudaStream_t s) {
+    if (m->dim == 0) return;
+    if (((uintptr_t)X % 16) != 0 || ((uintptr_t)Y % 16) != 0) fail(CI_ERR_INVALID_ARG, "X and Y must be 16-byte aligned");
+    const int grid = grid_for(m->dim * 32, 256, sm_count() * 8);
+    const float *scale = m->vtype == CI_BF16_ROWSCALE ? m->row_scale.ptr : nullptr;
+    if (m->upper) fail(CI_ERR_INVALID_ARG, "the 16-vector product takes a full-storage matrix");
+    if (m->vtype == CI_F32)
+        launch("k_spmm", k_spmm16<float>, grid, 256, 0, s, m->dim, m->row_ptr.ptr, m->col.ptr,
+               (const float *)m->val.ptr, X, Y, scale);
+    else if (m->vtype == CI_BF16_ROWSCALE)
+        launch("k_spmm", k_spmm16<__nv_bfloat16>, grid, 256, 0, s, m->dim, m->row_ptr.ptr, m->col.ptr,
+               (const __nv_bfloat16 *)m->val.ptr, X, Y, scale);
+    else
+        fail(CI_ERR_INVALID_ARG, "the 16-vector product takes FP32 or BF16 values");
+    CI_CHECK_LAUNCH();
+}
+
 void apply_matrix(const Matrix *m, const void *X, void *Y, int nvec, cudaStream_t s) {
     if (nvec < 1 || nvec > 8) fail(CI_ERR_INVALID_ARG, "nvec must be 1..8 (got %d)", nvec);
     if (m->dim == 0) return;
