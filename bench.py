@@ -50,7 +50,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle sample budget")
+    ap.add_argument("--cpu-seconds", type=float, default=16.0, help="oracle sample budget (build part)")
+    ap.add_argument("--cpu-sample", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-row0", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--spmm-reps", type=int, default=20)
@@ -169,18 +171,51 @@ def workload_inputs():
     return p, sp, eps, T
 
 
-# DRAM bytes (read + write) per launch from one ncu capture of the current
-# kernels on this workload; reported as the roofline traffic.
 TRACE_SAMPLE = 8
-NCU_TRAFFIC_C1 = {"k_spmm": 838.9e6, "k_fill_rows": 963.1e6}
+
+# DRAM bytes (read + write) per launch of a kernel, from one ncu capture
+# summarised in profiles/dram_traffic_c1.txt; each line names the source
+# file of the kernel and the SHA-256 prefix of that file when it was
+# captured.  A kernel whose source has changed since reports null traffic.
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic_c1.txt")
+
+
+def _source_digest(rel):
+    import hashlib
+    path = os.path.join(ROOT, rel)
+    if not os.path.exists(path):
+        return None
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def ncu_traffic():
+    """kernel -> DRAM bytes per launch, for the kernels whose source still
+    matches the capture."""
+    out = {}
+    if not os.path.exists(TRAFFIC_FILE):
+        return out
+    with open(TRAFFIC_FILE) as f:
+        for line in f:
+            parts = line.split()
+            if len(parts) < 4 or line.startswith("#"):
+                continue
+            name, nbytes, src, digest = parts[:4]
+            if _source_digest(src) == digest:
+                out[name] = float(nbytes)
+    return out
 
 
 def algorithmic_bytes(kernel, dim, nnz, nvec=8):
     """Algorithmic DRAM bytes of one launch of the kernels with a byte roofline."""
     if kernel == "k_fill_rows":      # col i32 + val f32 written, row_ptr read
         return 8 * nnz + 8 * (dim + 1)
+    if kernel == "build_H":          # col + val written, row counts written and read, row_ptr written
+        return 8 * nnz + 12 * dim + 8
     if kernel == "k_spmm":           # CSR streamed once, X read once, Y written
         return 8 * nnz + 8 * (dim + 1) + 2 * 4 * nvec * dim
+    if kernel == "k_spmm16":         # the same with 16-vector X and Y rows
+        return 8 * nnz + 8 * (dim + 1) + 2 * 4 * 16 * dim
     return None   # k_count_rows walks per-row segment tables: latency-bound, no byte roofline
 
 
@@ -225,6 +260,7 @@ def run_ours(args):
     ci.trace_enable(True, sample=TRACE_SAMPLE)
     ci.trace_read(reset=True)
     ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev_h = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev_b = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     barrier()
@@ -237,6 +273,7 @@ def run_ours(args):
         ev_s[i].record(stream)
         prob = ci.Problem(sp, p.Z, p.N, p.nmax, p.twoM, eps, tables=dtab)
         dim = prob.enumerate_basis()
+        ev_h[i].record(stream)
         M = prob.build_H("f32")
         ev_b[i].record(stream)
         evals, info = M.lowest_eigs(k=p.k, block=p.block)
@@ -249,8 +286,10 @@ def run_ours(args):
     kern = ci.trace_read(reset=True)
     ci.trace_enable(False)
     clk = clocks.stop()
+    hbm, peak_kind, peaks = load_peaks()
     step_ms = [ev_s[i].elapsed_time(ev_e[i]) for i in range(args.steps)]
     build_ms = [ev_s[i].elapsed_time(ev_b[i]) for i in range(args.steps)]
+    buildH_ms = [ev_h[i].elapsed_time(ev_b[i]) for i in range(args.steps)]
     solve_ms = [ev_b[i].elapsed_time(ev_e[i]) for i in range(args.steps)]
     total_ms = sum(step_ms)
     total_ms = max_over_ranks(total_ms, world, dev)
@@ -272,7 +311,6 @@ def run_ours(args):
         b.synchronize()
         sp_ms.append(a.elapsed_time(b))
     spmm_ms = statistics.median(sp_ms)
-    hbm, peak_kind, peaks = load_peaks()
     spmm_bytes = algorithmic_bytes("k_spmm", M.dim, M.nnz)
     spmm_gbs = spmm_bytes / (spmm_ms * 1e-3) / 1e9
     # the same product from the half-stored H (upper triangle, atomic updates)
@@ -298,6 +336,7 @@ def run_ours(args):
                    "share": round(v[1] / tot_k, 4)} for k, v in sorted(kern.items(), key=lambda kv: -kv[1][1])}
     gpu_launches = int(sum(v[0] for v in kern.values()))
     roofs = []
+    traffic_of = ncu_traffic() if nnz == 102601752 else {}
     for name, v in kern.items():
         b = algorithmic_bytes(name, dim, nnz)
         if b is None:
@@ -307,11 +346,19 @@ def run_ours(args):
             # inside the solve the SpMM runs on 8-vector blocks and the final
             # residual blocks; take the standalone measurement's bytes model
             pass
-        traffic = NCU_TRAFFIC_C1.get(name) if nnz == 102601752 else None
+        traffic = traffic_of.get(name)
         roofs.append({"kernel": name, "bound": "hbm", "achieved": round(b / avg_s / 1e9, 1), "peak": hbm,
                       "unit": "GB/s", "frac": round(b / avg_s / 1e9 / hbm, 4), "traffic": traffic,
                       "bytes_per_launch": b, "ms_per_launch": round(avg_s * 1e3, 5)})
     dominant = max(kern.items(), key=lambda kv: kv[1][1])[0] if kern else None
+    # the whole ci_build_H call (species filter, count, scan, fill): CUDA
+    # events on the launch stream around it in every timed step
+    bh_ms = statistics.median(buildH_ms)
+    bh_bytes = algorithmic_bytes("build_H", dim, nnz)
+    roofs.append({"kernel": "build_H", "bound": "hbm", "achieved": round(bh_bytes / (bh_ms * 1e-3) / 1e9, 1),
+                  "peak": hbm, "unit": "GB/s", "frac": round(bh_bytes / (bh_ms * 1e-3) / 1e9 / hbm, 4),
+                  "traffic": None, "bytes_per_launch": bh_bytes, "ms_per_launch": round(bh_ms, 5),
+                  "scope": "ci_build_H: species filter (tables staged), count, scan, fill"})
 
     rec = {
         "metric": METRIC, "value": None, "unit": "nnz/s", "n_gpus": world, "steps": args.steps,
@@ -327,9 +374,10 @@ def run_ours(args):
     per_rank_nnz = nnz * args.steps
     rec["value"] = whole_job_rate(per_rank_nnz, world, total_ms)
     rec["ms_per_step"] = total_ms / args.steps
-    rec["phases_ms"] = {"build_median": statistics.median(build_ms), "solve_median": statistics.median(solve_ms),
+    rec["phases_ms"] = {"build_median": statistics.median(build_ms), "build_H_median": bh_ms,
+                        "solve_median": statistics.median(solve_ms),
                         "step_median": statistics.median(step_ms), "wall_total_s": t_wall}
-    rec["build_nnz_per_s"] = nnz / (statistics.median(build_ms) * 1e-3)
+    rec["build_nnz_per_s"] = nnz / (bh_ms * 1e-3)
     rec["solve"] = {"iterations": infos[-1]["iterations"], "restarts": infos[-1]["restarts"],
                     "lowest": [round(float(x), 9) for x in evals], "residual_max": max(infos[-1]["residual"]),
                     "hnorm_est": infos[-1]["hnorm_est"]}
@@ -378,6 +426,14 @@ def run_ours(args):
             rec["serve"] = run_serve_leg(pool)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rec["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    # the headline figures once more at the end of the line (kept by tails)
+    bh = next(r for r in roofs if r["kernel"] == "build_H")
+    rec["summary"] = {"step_ms": rec["ms_per_step"], "build_H_ms": round(bh_ms, 4),
+                      "build_nnz_per_s": rec["build_nnz_per_s"], "build_H_frac_hbm": bh["frac"],
+                      "solve_ms": statistics.median(solve_ms), "spmm_ms": round(spmm_ms, 4),
+                      "spmm_frac_hbm": rec["spmm"]["frac"],
+                      "dominant": {k: rec["roofline"].get(k) for k in ("kernel", "frac")},
+                      "cpu_build_nnz_per_s": (rec.get("cpu_baseline") or {}).get("build_nnz_per_s")}
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
@@ -806,58 +862,151 @@ def run_serve_leg(pool, n_requests=400, n_capacity=300, seed=4):
 
 # ---------------------------------------------------------------- the oracle
 
-def oracle_rows_sample(seconds, start_row=0):
-    """FP64 oracle building consecutive rows of the workload for ~seconds."""
+def _golden_c1():
+    with open(os.path.join(ROOT, "tests", "golden", "golden.json")) as f:
+        return json.load(f)["c1"]
+
+
+def oracle_step_sample(o, i0, build_seconds, matvecs, ncv, chunk=256):
+    """One bounded step of the oracle on rows i0, i0+1, ... of the workload:
+    build rows (Fig. 1 count, scan and fill, the oracle's OpenMP row loops)
+    chunk by chunk until build_seconds have passed, then the per-row work of
+    the oracle's eigensolve on those rows: `matvecs` products of the row slab
+    with a full-length vector (scipy's CSR product, the operator ARPACK
+    applies) each followed by two classical Gram-Schmidt passes against
+    `ncv` basis columns restricted to the slab (ARPACK's
+    reorthogonalisation).  Returns (rows, nnz, build_s, solve_s)."""
+    import numpy as np
+    import scipy.sparse as sps
+    t0 = time.perf_counter()
+    parts = []
+    i = i0
+    while time.perf_counter() - t0 < build_seconds:
+        a = i % o.dim
+        b = min(a + chunk, o.dim)
+        parts.append(o.csr_rows(a, b))
+        i = a + (b - a)
+    t_build = time.perf_counter() - t0
+    rows = sum(len(rp) - 1 for rp, _, _ in parts)
+    nnz = sum(int(rp[-1]) for rp, _, _ in parts)
+    rp = np.concatenate([[0]] + [p[0][1:] + off for p, off in
+                                 zip(parts, np.cumsum([0] + [int(q[0][-1]) for q in parts[:-1]]))])
+    H = sps.csr_matrix((np.concatenate([p[2] for p in parts]), np.concatenate([p[1] for p in parts]), rp),
+                       shape=(rows, o.dim))
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal(o.dim)
+    V = np.linalg.qr(rng.standard_normal((rows, ncv)))[0]
+    t1 = time.perf_counter()
+    for k in range(matvecs):
+        y = H @ x
+        for _ in range(2):
+            y -= V @ (V.T @ y)
+        V[:, k % ncv] = y / (np.linalg.norm(y) + 1e-300)
+    t_solve = time.perf_counter() - t1
+    return rows, nnz, t_build, t_solve
+
+
+def _oracle_for_workload():
     import oracle
     p, sp, eps, T = workload_inputs()
-    o = oracle.OracleProblem(sp, p.Z, p.N, p.nmax, p.twoM, eps, T)
-    t0 = time.perf_counter()
-    rows = 0
-    nnz = 0
-    i = start_row
-    while time.perf_counter() - t0 < seconds:
-        c, v, ab, d = o.row(i % o.dim)
-        nnz += len(c)
-        rows += 1
-        i += 1
-    dt = time.perf_counter() - t0
-    return nnz, rows, dt
+    return oracle.OracleProblem(sp, p.Z, p.N, p.nmax, p.twoM, eps, T)
+
+
+def cpu_sample_main(threads, seconds, i0):
+    """Child process of the CPU baseline: one oracle step sample on
+    `threads` OpenMP threads, printed as one JSON line."""
+    import oracle
+    used = oracle.set_threads(threads)
+    g = _golden_c1()
+    o = _oracle_for_workload()
+    rows, nnz, tb, ts = oracle_step_sample(o, i0, seconds, g["arpack_matvecs"], g["arpack_ncv"])
+    print(json.dumps({"threads": used, "rows": rows, "nnz": nnz, "build_s": tb, "solve_s": ts}))
+
+
+def _cpu_sample(threads, seconds, i0):
+    env = dict(os.environ)
+    if threads == 1:
+        for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            env[k] = "1"
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample", str(threads),
+                          "--cpu-seconds", str(seconds), "--cpu-row0", str(i0)],
+                         capture_output=True, text=True, env=env, timeout=600)
+    if out.returncode != 0:
+        raise RuntimeError("CPU sample failed: " + out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def _phase(r):
+    return {"threads": r["threads"], "rows": r["rows"], "nnz": r["nnz"],
+            "build_nnz_per_s": r["nnz"] / r["build_s"],
+            "solve_nnz_per_s": r["nnz"] / r["solve_s"],
+            "step_nnz_per_s": r["nnz"] / (r["build_s"] + r["solve_s"]),
+            "build_s": round(r["build_s"], 3), "solve_s": round(r["solve_s"], 3)}
 
 
 def cpu_baseline(seconds):
-    nnz, rows, dt = oracle_rows_sample(seconds)
-    return {"value": nnz / dt, "unit": "nnz/s", "cores": 1, "kind": "oracle",
-            "sample": "%d consecutive rows of the same H (%d nonzeros, Slater-Condon FP64, %.1f s), "
-                      "single thread" % (rows, nnz, dt)}
+    """The oracle timed on the host cores, once on one thread and once on
+    all of them, each a bounded sample of the workload's rows (about
+    `seconds` of building, then the eigensolve's per-row work on the same
+    rows).  value: H nonzeros per second of that build + solve sample on all
+    cores, the unit of the GPU value."""
+    nproc = os.cpu_count() or 1
+    one = _phase(_cpu_sample(1, seconds * 0.5, 20000))
+    allc = _phase(_cpu_sample(nproc, seconds * 0.5, 60000))
+    g = _golden_c1()
+    return {"value": allc["step_nnz_per_s"], "unit": "nnz/s", "cores": allc["threads"], "nproc": nproc,
+            "kind": "oracle",
+            "sample": "rows of the same H: FP64 Slater-Condon build (count, scan, fill; OpenMP over rows) "
+                      "of ~%.0f s, then the oracle eigensolve's per-row work on those rows (%d CSR products "
+                      "+ 2x Gram-Schmidt against %d columns, ARPACK's count for the whole H)"
+                      % (seconds * 0.5, g["arpack_matvecs"], g["arpack_ncv"]),
+            "phases": {"one_thread": one, "all_cores": allc},
+            "build_nnz_per_s": allc["build_nnz_per_s"], "build_nnz_per_s_one_thread": one["build_nnz_per_s"]}
 
 
 def run_reference(args):
+    """The oracle, timed as it stands on all host cores: each step is one
+    bounded sample of the workload (rows built, then the eigensolve's work on
+    them), the unit of the GPU arm (H nonzeros per second of build + solve)."""
     rank, world, local = dist_info()
     if rank != 0:
         return
-    per_step = max(2.0, min(20.0, 120.0 / max(args.steps + args.warmup, 1)))
+    import oracle
+    nproc = os.cpu_count() or 1
+    used = oracle.set_threads(nproc)
+    g = _golden_c1()
+    o = _oracle_for_workload()
+    per_step = max(1.0, min(10.0, 60.0 / max(args.steps + args.warmup, 1)))
     for w in range(args.warmup):
-        oracle_rows_sample(min(per_step, 2.0), start_row=1000 * w)
-    tot_nnz, tot_t, tot_rows = 0, 0.0, 0
+        oracle_step_sample(o, 3000 * w, min(per_step, 1.0), g["arpack_matvecs"], g["arpack_ncv"])
+    tot_nnz, tot_t, tot_rows, tb, ts = 0, 0.0, 0, 0.0, 0.0
     for s in range(args.steps):
-        nnz, rows, dt = oracle_rows_sample(per_step, start_row=5000 * (s + 1))
+        rows, nnz, b, sv = oracle_step_sample(o, 7919 * (s + 1), per_step, g["arpack_matvecs"], g["arpack_ncv"])
         tot_nnz += nnz
-        tot_t += dt
         tot_rows += rows
+        tb += b
+        ts += sv
+    tot_t = tb + ts
     v = tot_nnz / tot_t
     rec = {"impl": "reference", "metric": METRIC, "value": v, "unit": "nnz/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": tot_t / args.steps * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "sample": "each step builds ~%.0f s of consecutive rows" % per_step},
-           "cpu_baseline": {"value": v, "unit": "nnz/s", "cores": 1, "kind": "oracle",
-                            "sample": "%d rows, %d nonzeros over %d steps" % (tot_rows, tot_nnz, args.steps)},
+           "config": {"workload": WORKLOAD,
+                      "sample": "each step: ~%.0f s of row builds on %d threads, then %d CSR products of those rows "
+                                "with Gram-Schmidt against %d columns" % (per_step, used, g["arpack_matvecs"],
+                                                                          g["arpack_ncv"])},
+           "cpu_baseline": {"value": v, "unit": "nnz/s", "cores": used, "nproc": nproc, "kind": "oracle",
+                            "sample": "%d rows, %d nonzeros over %d steps" % (tot_rows, tot_nnz, args.steps),
+                            "build_nnz_per_s": tot_nnz / tb, "solve_nnz_per_s": tot_nnz / ts},
            "e2e": {"value": v, "unit": "nnz/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(rec))
 
 
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.cpu_sample:
+        cpu_sample_main(args.cpu_sample, args.cpu_seconds, args.cpu_row0)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -241,7 +241,9 @@ ci_status ci_exclusive_scan(const int32_t *counts, int64_t n, int64_t *offsets, 
  * (512 KB, held by every GPU that loads the library until the process
  * exits), so n is limited to 2^28 counts; larger n returns CI_ERR_CAPACITY.
  * The first call on a device looks up the array's device address (make it
- * before any stream capture).  All calls share the array: calls that
+ * before any stream capture) and keeps it for the life of the process: after
+ * cudaDeviceReset on that device the kept address is stale, and later calls
+ * on that device are invalid.  All calls share the array: calls that
  * overlap on the GPU (other streams, other threads) race and must be
  * serialised by the caller.  Outputs are identical to ci_exclusive_scan. */
 ci_status ci_exclusive_scan_noalloc(const int32_t *counts, int64_t n, int64_t *offsets, void *stream);
@@ -272,10 +274,16 @@ ci_status ci_matrix_info(const ci_matrix *m, int64_t *dim, int64_t *nnz, int32_t
 ci_status ci_matrix_export(const ci_matrix *m, int64_t *row_ptr, int32_t *col,
                            void *val, float *row_scale, void *stream);
 
-/* Fig. 2, optional FMA (Sec. 2): Y = H X for a block of nvec vectors (1..8), X and
- * Y device arrays [dim][nvec] (float for CI_F32 / CI_BF16_ROWSCALE, double
- * for CI_F64), not overlapping.  Each row is accumulated in the value
- * precision in ascending column order within each of 32 lanes. */
+/* Fig. 2, optional FMA (Sec. 2): Y = H X for a block of nvec vectors (1..8, or
+ * 16), X and Y device arrays [dim][nvec] (float for CI_F32 / CI_BF16_ROWSCALE,
+ * double for CI_F64), not overlapping.  Each row is accumulated in the value
+ * precision in ascending column order within each of 32 lanes.  nvec = 16
+ * (full-storage CI_F32 or CI_BF16_ROWSCALE only, 16-byte aligned X and Y) is
+ * the product LOBPCG uses for [X P]: one gather of a 64-byte X row per
+ * nonzero, each row's sum split over 8 lane groups instead of 16, so its
+ * results differ from two 8-vector products in the last FP32 bits.
+ * Errors: CI_ERR_INVALID_ARG (other nvec, misaligned X or Y, nvec = 16 on
+ * a half-stored or FP64 matrix). */
 ci_status ci_apply_H(const ci_matrix *m, const void *X, void *Y, int32_t nvec, void *stream);
 
 /* ---------------------------------------------------------------- eigensolver */
@@ -438,7 +446,11 @@ void ci_batch_destroy(ci_batch *b);
  * arrive while others run overlap with them; each keeps H and its Krylov
  * vectors on the device until it finishes.  A problem's result does not
  * depend on what else runs beside it (per-problem start block and
- * reductions).  The paper has no counterpart. */
+ * reductions).  A request whose basis has at most max_basis + 16 states is
+ * too small for the engine's blocks: the worker builds its FP32 H alone and
+ * solves it at admission with ci_lowest_eigs' whole-space Rayleigh-Ritz
+ * (k must not exceed the dimension; an empty basis fails with
+ * CI_ERR_INVALID_ARG).  The paper has no counterpart. */
 typedef struct {
     size_t mem_budget;    /* device bytes the queue may hold; 0 = 70 % of free memory */
     int32_t max_slots;    /* problems running at once, 1..4096                  [256] */

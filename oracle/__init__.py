@@ -22,9 +22,10 @@ than itself):
   Sec. 2.3-2.4 (plain loops).
 """
 
-from .core import OracleProblem, build_library, count_pairs, exclusive_scan, expectation_values, spmm
+from .core import (OracleProblem, build_library, count_pairs, exclusive_scan, expectation_values, set_threads,
+                   spmm)
 from .eig import lowest_dense, lowest_sparse, dense_from_csr
 from . import brute, motifs, precond
 
-__all__ = ["OracleProblem", "build_library", "count_pairs", "exclusive_scan", "expectation_values", "spmm",
+__all__ = ["OracleProblem", "build_library", "count_pairs", "exclusive_scan", "expectation_values", "set_threads", "spmm",
            "lowest_dense", "lowest_sparse", "dense_from_csr", "brute", "motifs", "precond"]

@@ -32,6 +32,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_MAXA 32
 
@@ -424,10 +427,10 @@ int64_t orc_row(const orc_basis_view *B, int64_t i, int64_t cap, int64_t *cols,
     return c;
 }
 
-/* Number of stored entries of every row (Fig. 1, count step).  Rows that share
- * a proton determinant reuse its difference list (same result as recomputing
- * it per row). */
-void orc_row_counts(const orc_basis_view *B, int64_t *counts)
+/* Number of stored entries of rows i0 <= i < i1 (Fig. 1, count step) into
+ * counts[i - i0].  Rows that share a proton determinant reuse its
+ * difference list (same result as recomputing it per row). */
+void orc_row_counts_range(const orc_basis_view *B, int64_t i0, int64_t i1, int64_t *counts)
 {
     const orc_species *P = B->sp[0], *Nn = B->sp[1];
     #pragma omp parallel
@@ -436,22 +439,29 @@ void orc_row_counts(const orc_basis_view *B, int64_t *counts)
         uint8_t *dn = (uint8_t *)malloc((size_t)(Nn->n ? Nn->n : 1));
         int64_t last_p = -1;
         #pragma omp for schedule(dynamic, 64)
-        for (int64_t i = 0; i < B->dim; ++i) {
+        for (int64_t i = i0; i < i1; ++i) {
             if (B->p_idx[i] != last_p) { species_diffs(P, B->p_idx[i], dp); last_p = B->p_idx[i]; }
             species_diffs(Nn, B->n_idx[i], dn);
             int64_t c = 0;
             for (int64_t j = 0; j < B->dim; ++j)
                 if (dp[B->p_idx[j]] + dn[B->n_idx[j]] <= 4) ++c;
-            counts[i] = c;
+            counts[i - i0] = c;
         }
         free(dp); free(dn);
     }
 }
 
-/* Fill a CSR whose row_ptr the caller has made from orc_row_counts (Fig. 1,
- * fill step).  absums may be NULL. */
-void orc_fill(const orc_basis_view *B, const int64_t *row_ptr, int64_t *cols,
-              double *vals, double *absums)
+/* Number of stored entries of every row. */
+void orc_row_counts(const orc_basis_view *B, int64_t *counts)
+{
+    orc_row_counts_range(B, 0, B->dim, counts);
+}
+
+/* Fill rows i0 <= i < i1 of a CSR whose offsets the caller has made from
+ * orc_row_counts_range and the scan (Fig. 1, fill step): row i goes to
+ * positions [row_ptr[i - i0], row_ptr[i - i0 + 1]).  absums may be NULL. */
+void orc_fill_range(const orc_basis_view *B, int64_t i0, int64_t i1, const int64_t *row_ptr,
+                    int64_t *cols, double *vals, double *absums)
 {
     const orc_species *P = B->sp[0], *Nn = B->sp[1];
     #pragma omp parallel
@@ -459,13 +469,33 @@ void orc_fill(const orc_basis_view *B, const int64_t *row_ptr, int64_t *cols,
         uint8_t *dp = (uint8_t *)malloc((size_t)(P->n ? P->n : 1));
         uint8_t *dn = (uint8_t *)malloc((size_t)(Nn->n ? Nn->n : 1));
         #pragma omp for schedule(dynamic, 64)
-        for (int64_t i = 0; i < B->dim; ++i) {
-            int64_t o = row_ptr[i];
-            orc_row(B, i, row_ptr[i + 1] - o, cols + o, vals + o,
+        for (int64_t i = i0; i < i1; ++i) {
+            int64_t o = row_ptr[i - i0];
+            orc_row(B, i, row_ptr[i - i0 + 1] - o, cols + o, vals + o,
                     absums ? absums + o : NULL, NULL, dp, dn);
         }
         free(dp); free(dn);
     }
+}
+
+/* Fill the whole CSR. */
+void orc_fill(const orc_basis_view *B, const int64_t *row_ptr, int64_t *cols,
+              double *vals, double *absums)
+{
+    orc_fill_range(B, 0, B->dim, row_ptr, cols, vals, absums);
+}
+
+/* Threads of the OpenMP loops above (n <= 0: leave the default); returns
+ * the number the next parallel region will use. */
+int orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }
 
 /* Y = H X in FP64 over a CSR (Fig. 2, optional FMA: H_ij with the j-th

@@ -69,6 +69,10 @@ def _load():
             lib.orc_row.restype = C.c_int64
             lib.orc_row_counts.argtypes = [P(_BasisView), C.c_void_p]
             lib.orc_fill.argtypes = [P(_BasisView)] + [C.c_void_p] * 4
+            lib.orc_row_counts_range.argtypes = [P(_BasisView), C.c_int64, C.c_int64, C.c_void_p]
+            lib.orc_fill_range.argtypes = [P(_BasisView), C.c_int64, C.c_int64] + [C.c_void_p] * 4
+            lib.orc_set_threads.argtypes = [C.c_int]
+            lib.orc_set_threads.restype = C.c_int
             lib.orc_spmm.argtypes = [C.c_int64] + [C.c_void_p] * 5 + [C.c_int]
             lib.orc_exclusive_scan.argtypes = [C.c_void_p, C.c_int64, C.c_void_p]
             lib.orc_count_pairs.argtypes = [C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_void_p, C.c_int64,
@@ -196,6 +200,19 @@ class OracleProblem:
                           _ptr(ab) if with_absums else None)
         return row_ptr, cols[:nnz], vals[:nnz], (ab[:nnz] if with_absums else None)
 
+    def csr_rows(self, i0, i1):
+        """Rows i0 <= i < i1 of H as a CSR slab (row_ptr from 0, global
+        column indices, FP64 values): the count, scan and fill of Fig. 1
+        restricted to those rows."""
+        i0, i1 = int(i0), int(min(i1, self.dim))
+        cnt = np.zeros(max(i1 - i0, 1), np.int64)
+        self.lib.orc_row_counts_range(C.byref(self._bv), i0, i1, _ptr(cnt))
+        row_ptr = exclusive_scan(cnt[: i1 - i0])
+        nnz = int(row_ptr[-1])
+        cols = np.zeros(max(nnz, 1), np.int64); vals = np.zeros(max(nnz, 1))
+        self.lib.orc_fill_range(C.byref(self._bv), i0, i1, _ptr(row_ptr), _ptr(cols), _ptr(vals), None)
+        return row_ptr, cols[:nnz], vals[:nnz]
+
     def count_difference(self, s, a, b):
         occ = self.species(s)["occ"]
         x = np.ascontiguousarray(occ[a]); y = np.ascontiguousarray(occ[b])
@@ -221,6 +238,12 @@ def expectation_values(row_ptr, cols, vals, X, Y=None):
             raise ValueError("X and Y must have the same shape")
     OY = spmm(row_ptr, cols, vals, Y)
     return np.einsum("iv,iv->v", X, OY)
+
+
+def set_threads(n=0):
+    """OpenMP threads of the oracle's row loops (n <= 0 keeps the default);
+    returns the count in use."""
+    return int(_load().orc_set_threads(int(n)))
 
 
 def count_pairs(mbs, rows=None, max_diff=4):

@@ -253,7 +253,7 @@ class Matrix:
 
     # -- Fig. 2, optional FMA -------------------------------------------------------
     def apply_H(self, X, Y, stream=None):
-        """Y = H X for device tensors [dim, nvec] (nvec 1..8)."""
+        """Y = H X for device tensors [dim, nvec] (nvec 1..8 or 16)."""
         nvec = 1 if X.dim() == 1 else int(X.shape[1])
         check(lib().ci_apply_H(self._h, _ptr(X), _ptr(Y), nvec, _stream(stream)), "ci_apply_H")
 

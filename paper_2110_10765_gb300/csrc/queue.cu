@@ -62,6 +62,7 @@ struct Queue {
     void run();
     void admit();
     void harvest();
+    void solve_small(Request *r);
 };
 
 // Device bytes a request holds while it runs.
@@ -130,21 +131,22 @@ void Queue::admit() {
         }
     }
     if (cand.empty()) return;
-    // create and count the candidates together
-    std::vector<Request *> ok;
+    // create and count the candidates together; spaces too small for the
+    // engine's Krylov blocks are solved at once on the single-problem path
+    std::vector<Request *> ok, small;
     for (Request *r : cand) {
         try {
             r->prob.reset(new ci_problem());
             problem_create(&r->desc, &r->prob->impl);
             enumerate_basis(&r->prob->impl, eng.stream);
-            if (r->prob->impl.dim <= (int64_t)eng.MB + 2 * EB)
-                fail(CI_ERR_INVALID_ARG, "served solves need dimension > %d", eng.MB + 2 * EB);
-            ok.push_back(r);
+            if (r->prob->impl.dim <= (int64_t)eng.MB + 2 * EB) small.push_back(r);
+            else ok.push_back(r);
         } catch (const Error &e) {
             std::lock_guard<std::mutex> lk(mu);
             r->status = e.status; r->error = e.what(); r->t_done = qnow(); r->prob.reset();
         }
     }
+    for (Request *r : small) solve_small(r);
     if (ok.empty()) return;
     std::vector<Problem *> ps;
     for (Request *r : ok) ps.push_back(&r->prob->impl);
@@ -229,6 +231,42 @@ void Queue::admit() {
     }
     engine_retile(&eng);
     engine_init_slots(&eng);
+}
+
+// A request whose basis has at most MB + 2 EB states: FP32 H built alone
+// and solved by the single-problem eigensolver (Rayleigh-Ritz on the whole
+// space at this size) on the engine stream, between two engine steps.
+void Queue::solve_small(Request *r) {
+    const double t0 = qnow();
+    try {
+        Problem *p = &r->prob->impl;
+        Matrix m;
+        build_matrix(p, CI_F32, &m, eng.stream);
+        ci_eig_opts o{};
+        o.k = r->k;
+        o.block = EB;
+        o.max_basis = eng.MB;
+        o.tol = d.tol;
+        double ev[32] = {0};
+        ci_eig_info inf{};
+        lowest_eigs(&m, &o, ev, nullptr, &inf, eng.stream);
+        std::lock_guard<std::mutex> lk(mu);
+        for (int j = 0; j < r->k; ++j) { r->evals[j] = ev[j]; r->residual[j] = inf.residual[j]; }
+        r->iterations = inf.iterations;
+        r->dim = m.dim;
+        r->nnz = m.nnz;
+        r->t_admit = t0;
+        r->t_done = qnow();
+        r->status = CI_OK;
+        ++admitted;
+        ++completed;
+    } catch (const Error &e) {
+        std::lock_guard<std::mutex> lk(mu);
+        r->status = e.status;
+        r->error = e.what();
+        r->t_done = qnow();
+    }
+    r->prob.reset();
 }
 
 void Queue::run() {

@@ -408,10 +408,10 @@ void apply_matrix16(const Matrix *m, const float *X, float *Y, cudaStream_t s) {
     const float *scale = m->vtype == CI_BF16_ROWSCALE ? m->row_scale.ptr : nullptr;
     if (m->upper) fail(CI_ERR_INVALID_ARG, "the 16-vector product takes a full-storage matrix");
     if (m->vtype == CI_F32)
-        launch("k_spmm", k_spmm16<float>, grid, 256, 0, s, m->dim, m->row_ptr.ptr, m->col.ptr,
+        launch("k_spmm16", k_spmm16<float>, grid, 256, 0, s, m->dim, m->row_ptr.ptr, m->col.ptr,
                (const float *)m->val.ptr, X, Y, scale);
     else if (m->vtype == CI_BF16_ROWSCALE)
-        launch("k_spmm", k_spmm16<__nv_bfloat16>, grid, 256, 0, s, m->dim, m->row_ptr.ptr, m->col.ptr,
+        launch("k_spmm16", k_spmm16<__nv_bfloat16>, grid, 256, 0, s, m->dim, m->row_ptr.ptr, m->col.ptr,
                (const __nv_bfloat16 *)m->val.ptr, X, Y, scale);
     else
         fail(CI_ERR_INVALID_ARG, "the 16-vector product takes FP32 or BF16 values");
@@ -419,9 +419,13 @@ void apply_matrix16(const Matrix *m, const float *X, float *Y, cudaStream_t s) {
 }
 
 void apply_matrix(const Matrix *m, const void *X, void *Y, int nvec, cudaStream_t s) {
-    if (nvec < 1 || nvec > 8) fail(CI_ERR_INVALID_ARG, "nvec must be 1..8 (got %d)", nvec);
+    if ((nvec < 1 || nvec > 8) && nvec != 16) fail(CI_ERR_INVALID_ARG, "nvec must be 1..8 or 16 (got %d)", nvec);
     if (m->dim == 0) return;
     if (!X || !Y) fail(CI_ERR_INVALID_ARG, "X and Y must be device pointers");
+    if (nvec == 16) {   // two 8-vector blocks side by side, one gather per nonzero
+        apply_matrix16(m, (const float *)X, (float *)Y, s);
+        return;
+    }
     size_t esz = m->vtype == CI_F64 ? 8 : 4;   // X and Y element size (float for F32 and BF16)
     size_t align = (nvec == 8 || nvec == 4) ? 16 : esz;
     if (((uintptr_t)X % align) != 0 || ((uintptr_t)Y % align) != 0)

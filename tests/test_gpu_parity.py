@@ -213,18 +213,55 @@ def test_build_H_nmax2_subspace_fp32():
     _check_matrix(o, M, REL32)
 
 
+def _sha256_i64(a):
+    import hashlib
+    return hashlib.sha256(np.ascontiguousarray(a, dtype="<i8").tobytes()).hexdigest()
+
+
+def _boundary_rows(o):
+    """First and last row of every (2M, q) group of the proton list: the
+    rows where a proton 2M block or a q prefix of the cut begins or ends."""
+    sp = o.species(0)
+    key = sp["twoM"].astype(np.int64)[o.p_idx] * 1024 + sp["q"].astype(np.int64)[o.p_idx]
+    edges = np.flatnonzero(np.diff(key)) + 1
+    starts = np.concatenate([[0], edges])
+    ends = np.concatenate([edges - 1, [o.dim - 1]])
+    return set(starts.tolist()) | set(ends.tolist())
+
+
+@pytest.mark.parametrize("case", ["c0", "c2_sub", "c1"])
+def test_build_H_full_pattern_digest(case):
+    """The whole structural pattern (row_ptr and every column index) against
+    SHA-256 digests of the oracle's full CSR, bit for bit; c1 is the
+    benchmark workload at full size (172,684 rows, 102,601,752 nonzeros)."""
+    inp = preset_inputs(case)
+    g = gpu_problem(inp)
+    M = g.build_H("f64" if case == "c0" else "f32")
+    gd = golden()[case]
+    assert (M.dim, M.nnz) == (gd["dim"], gd["nnz"])
+    rp, col, _, _ = M.export()
+    assert _sha256_i64(rp) == gd["row_ptr_sha256"]
+    assert _sha256_i64(col) == gd["col_sha256"]
+
+
 def test_build_H_config1_full_size_sampled_rows():
-    """Nmax=4, 70 states per species (two-word bit strings), sampled rows."""
+    """Nmax=4, 70 states per species (two-word bit strings): values and
+    patterns of 2,000+ rows against the oracle, among them the first and
+    last row of every (2M, q) group of the proton list."""
     inp = preset_inputs("c1")
     o, g = oracle_problem(inp), gpu_problem(inp)
     M = g.build_H("f32")
     gd = golden()["c1"]
     assert (M.dim, M.nnz) == (gd["dim"], gd["nnz"])
+    edge = _boundary_rows(o)
     rng = np.random.default_rng(11)
-    rows = sorted(set(rng.integers(0, M.dim, 150).tolist()) | {0, M.dim - 1})
+    rows = set(edge) | {0, M.dim - 1}
+    while len(rows) < 2000 + len(edge):
+        rows.add(int(rng.integers(0, M.dim)))
+    rows = sorted(rows)
     rp, col, val = _check_matrix(o, M, REL32, rows)
-    # structural symmetry and value symmetry on the sampled rows
-    for i in rows[:40]:
+    # structural symmetry and value symmetry on sampled rows
+    for i in rows[::50]:
         for j, v in zip(col[rp[i]:rp[i + 1]].tolist(), val[rp[i]:rp[i + 1]].tolist()):
             seg = col[rp[j]:rp[j + 1]]
             k = np.searchsorted(seg, i)

@@ -38,29 +38,52 @@ def _wait(q, tickets, timeout=120.0):
     return out
 
 
+def _batch_alone(case, k):
+    import paper_2110_10765_gb300 as ci
+    a = _args(case)
+    b = ci.Batch([ci.Problem(a["sp"], a["Z"], a["N"], a["nmax"], a["twoM"], a["eps"], seed=a["seed"])], k=[k])
+    b.run()
+    return b.result(0)[0]
+
+
+# a large request (3 protons, 5 neutrons in shells N <= 3, Nmax 4: dim
+# 116,184) that keeps running while the others are submitted
+BIG = (3, 3, 5, 4, 21)
+
+
 def test_queue_matches_batch_and_overlaps():
+    """Requests submitted while a large one runs are admitted before it
+    finishes (their engine steps are shared with it), and every result is
+    bit-identical to the same problem solved alone in a batch."""
     import paper_2110_10765_gb300 as ci
     ks = [5, 3, 6, 4, 2, 5, 4]
-    # reference: each problem alone in a batch
-    ref = []
-    for c, k in zip(CASES, ks):
-        a = _args(c)
-        b = ci.Batch([ci.Problem(a["sp"], a["Z"], a["N"], a["nmax"], a["twoM"], a["eps"], seed=a["seed"])], k=[k])
-        b.run()
-        ref.append(b.result(0)[0])
+    ref_big = _batch_alone(BIG, 5)
+    ref = [_batch_alone(c, k) for c, k in zip(CASES, ks)]
     q = ci.Queue(max_slots=4)
-    first = [q.submit(k=ks[i], **_args(CASES[i])) for i in range(3)]
-    time.sleep(0.01)   # the rest arrives while the first ones run
-    rest = [q.submit(k=ks[i], **_args(CASES[i])) for i in range(3, len(CASES))]
-    res = _wait(q, first + rest)
-    for i, t in enumerate(first + rest):
+    big = q.submit(k=5, **_args(BIG))
+    t0 = time.time()
+    while q.stats()["admitted"] < 1:       # the large request is on the GPU
+        assert time.time() - t0 < 60
+        time.sleep(0.001)
+    st, rb = q.poll(big)
+    assert st == 6, "the large request finished before the others were submitted"
+    steps_before = q.stats()["steps"]
+    late = [q.submit(k=ks[i], **_args(CASES[i])) for i in range(len(CASES))]
+    res = _wait(q, [big] + late)
+    st, rb = res[big]
+    assert st == 0, rb
+    assert np.array_equal(rb["evals"], ref_big), rb["evals"] - ref_big
+    for i, t in enumerate(late):
         st, r = res[t]
         assert st == 0, r
         assert np.array_equal(r["evals"], ref[i]), (i, r["evals"] - ref[i])
         assert r["t_done"] >= r["t_admit"] >= r["t_submit"] and r["latency_s"] > 0
         assert max(r["residual"]) < 1e-3
+        # admitted while the large request was still running: overlap
+        assert r["t_admit"] < rb["t_done"], (i, r["t_admit"], rb["t_done"])
     s = q.stats()
-    assert s["completed"] == len(CASES) and s["admitted"] == len(CASES)
+    assert s["completed"] == len(CASES) + 1 and s["admitted"] == len(CASES) + 1
+    assert s["steps"] > steps_before
     q.close()
 
 
@@ -90,8 +113,32 @@ def test_queue_rejects_bad_requests():
     q = ci.Queue(max_slots=2)
     with pytest.raises(ci.CIError):
         q.submit(k=40, **_args(CASES[0]))
-    small = _args((1, 1, 1, -1, 3))  # dimension 20: too small for the engine
-    t = q.submit(k=2, **small)
-    st, r = _wait(q, [t])[t]
+    bad = q.submit(k=3, **_args((1, 1, 1, -1, 3)) | {"nmax": -1, "twoM": 9})   # empty basis
+    st, r = _wait(q, [bad])[bad]
     assert st == 1   # CI_ERR_INVALID_ARG
+    q.close()
+
+
+@pytest.mark.parametrize("case,k", [((1, 1, 1, -1, 3), 2), ((1, 2, 1, -1, 4), 5), ((2, 1, 1, 0, 5), 1)])
+def test_queue_solves_small_requests(case, k):
+    """Spaces too small for the engine's Krylov blocks (dimension <= 80) are
+    solved on the single-problem path inside the queue, beside a running
+    engine request, and match the oracle's dense eigenvalues."""
+    import oracle
+    import paper_2110_10765_gb300 as ci
+    from helpers import EIG_REL, oracle_problem
+    a = _args(case)
+    q = ci.Queue(max_slots=2)
+    running = q.submit(k=3, **_args(CASES[1]))
+    t = q.submit(k=k, **a)
+    res = _wait(q, [running, t])
+    st, r = res[t]
+    assert st == 0, r
+    assert 0 < r["dim"] <= 80
+    T = synth.tbme_tables(a["sp"], a["seed"], np.float32)
+    inp = dict(sp=a["sp"], Z=a["Z"], N=a["N"], nmax=a["nmax"], twoM=a["twoM"], eps=a["eps"], tables=T)
+    o = oracle_problem(inp)
+    ref = oracle.lowest_dense(oracle.dense_from_csr(*o.csr()[:3], o.dim), k)
+    assert np.all(np.abs(r["evals"] - ref) <= EIG_REL * np.maximum(np.abs(ref), 1)), r["evals"] - ref
+    assert res[running][0] == 0
     q.close()

@@ -206,6 +206,32 @@ def test_pattern_config0_dense_brute_force():
     assert np.array_equal(o2.csr()[0], rp)
 
 
+def test_row_slab_pattern_brute_force_and_thread_count():
+    """The count -> scan -> fill of a row slab (the oracle's bounded CPU
+    baseline): every slab row holds exactly the columns within 4 differing
+    s.p. states (brute-force set differences), and the slab is the same on
+    one thread and on all of them."""
+    import oracle
+    sp, eps, T, o = _problem(1, 4, 4, -1, seed=0)
+    states = [frozenset(s) for s in _states_of(o)]
+    i0, i1 = 37, 311
+    prev = oracle.set_threads(0)
+    try:
+        runs = []
+        for th in (1, prev):
+            assert oracle.set_threads(th) == th
+            runs.append(o.csr_rows(i0, i1))
+    finally:
+        oracle.set_threads(prev)
+    (rp, cols, vals), (rp2, cols2, vals2) = runs
+    assert np.array_equal(rp, rp2) and np.array_equal(cols, cols2) and np.array_equal(vals, vals2)
+    assert len(rp) == i1 - i0 + 1 and rp[0] == 0
+    for k, i in enumerate(range(i0, i1)):
+        ref = [j for j in range(o.dim) if len(states[i] ^ states[j]) <= 4]
+        assert list(cols[rp[k]:rp[k + 1]]) == ref
+    assert len(o.csr_rows(5, 5)[1]) == 0
+
+
 # ---------------------------------------------------------------- values
 
 @pytest.mark.parametrize("nsh,Z,N,nmax", [(1, 2, 2, -1), (1, 3, 2, -1), (1, 2, 1, -1), (1, 1, 3, -1),
