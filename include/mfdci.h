@@ -288,6 +288,32 @@ ci_status ci_apply_H(const ci_matrix *m, const void *X, void *Y, int32_t nvec, v
 
 /* ---------------------------------------------------------------- eigensolver */
 
+/* Sec. 2, Fig. 1 eigensolve: the products of the block Lanczos solver's
+ * full FP64 reorthogonalisation against its basis A (n rows, columns
+ * orthonormal, |A_iu| <= 1), exposed for tests and for callers with a basis
+ * of their own.  Device pointers, row-major, caller-owned:
+ *   op CI_PRODUCT_TN: C [na][nb] = A^T B   (A [n][lda], B [n][ldb])
+ *   op CI_PRODUCT_NN: B = beta B + alpha A C   (C [na][nb], B [n][ldb];
+ *                     beta = 0 does not read B)
+ * method CI_PRODUCT_FP64: FP64 FMAs on the CUDA cores (1 <= na <= 256,
+ * 1 <= nb <= 8).  method CI_PRODUCT_TC: on the tensor cores (tcgen05.mma,
+ * FP16 inputs, FP32 accumulation): each operand is cut into eight balanced
+ * 8-bit digit planes relative to a power-of-two scale (A: 2^0, so
+ * |A| < 1.99 is required; B and C: per vector, above its largest entry),
+ * every plane product is exact, and the planes are recombined in 64- and
+ * 128-bit integers with one or two roundings to FP64 per output.  The result
+ * differs from the exact product by at most about 2^-52 |result| +
+ * 2^-60 n max|B| (TN) or 2^-52 |result| + 2^-60 na max|C| (NN) -- FP64
+ * accuracy -- and needs nb = 8 and na <= 64.
+ * Synchronises the stream.
+ * Errors: CI_ERR_INVALID_ARG (shapes, an entry of A with |a| >= 1.99 or a
+ * non-finite operand for CI_PRODUCT_TC), CI_ERR_TIMEOUT (a tensor-core wait
+ * ran out; the context stays usable). */
+enum { CI_PRODUCT_TN = 0, CI_PRODUCT_NN = 1 };
+enum { CI_PRODUCT_FP64 = 0, CI_PRODUCT_TC = 1 };
+ci_status ci_basis_product(int32_t op, int32_t method, int64_t n, const double *A, int32_t lda, int32_t na,
+                           double *B, int32_t ldb, int32_t nb, double *C, double alpha, double beta, void *stream);
+
 /* Options of ci_lowest_eigs; zero fields take the defaults in brackets. */
 typedef struct {
     int32_t k;            /* eigenpairs wanted, 1..32                      [5]  */
@@ -301,6 +327,10 @@ typedef struct {
     int32_t reorth_passes;/* full Gram-Schmidt passes per step after the
                              projection on the two newest blocks, 1..2    [1]  */
     int32_t check_every;  /* block steps between convergence checks       [2]  */
+    int32_t fp64_products;/* 1: the reorthogonalisation products on the FP64
+                             CUDA cores; 0: on the tensor cores as exact
+                             products of 8-bit digit planes (FP64 accuracy,
+                             see ci_basis_product)                          [0] */
 } ci_eig_opts;
 
 typedef struct {

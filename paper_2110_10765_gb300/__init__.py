@@ -18,7 +18,7 @@ from . import _lib
 from ._lib import (CIError, CI_F32, CI_F64, CI_BF16_ROWSCALE, CI_TBME_TABLES,
                    CI_TBME_SEED, check, lib)
 
-__all__ = ["Problem", "Matrix", "Batch", "Queue", "exclusive_scan", "count_pairs", "COUNT_VARIANTS", "trace_enable", "trace_read", "CIError", "CI_F32", "CI_F64",
+__all__ = ["Problem", "Matrix", "Batch", "Queue", "basis_product", "exclusive_scan", "count_pairs", "COUNT_VARIANTS", "trace_enable", "trace_read", "CIError", "CI_F32", "CI_F64",
            "CI_BF16_ROWSCALE", "VTYPES", "lib", "current_stream"]
 
 VTYPES = {"f32": CI_F32, "f64": CI_F64, "bf16": CI_BF16_ROWSCALE}
@@ -260,15 +260,17 @@ class Matrix:
     # -- Fig. 1, eigensolve ------------------------------------------------------
     def lowest_eigs(self, k=5, block=8, max_basis=0, max_iter=0, tol=0.0, seed=1, reorth_passes=0,
                     check_every=0, evecs=None, stream=None, allow_unconverged=False, method="lanczos",
-                    blocks=None):
+                    blocks=None, fp64_products=False):
         """Lowest k eigenvalues (numpy, ascending) and the solve info dict.
 
         evecs: optional device float64 tensor [dim, k] for the eigenvectors.
         method: "lanczos" (ci_lowest_eigs) or "lobpcg" (ci_lowest_eigs_lobpcg).
         blocks: for LOBPCG, (row_block device int32 tensor, nblocks) from
         ``Problem.orbital_blocks`` for the block-diagonal preconditioner;
-        None for the diagonal one."""
-        o = _lib.EigOpts(k, block, max_basis, max_iter, tol, seed, reorth_passes, check_every)
+        None for the diagonal one.
+        fp64_products: reorthogonalisation products on the FP64 CUDA cores
+        instead of the tensor cores (ci_eig_opts.fp64_products)."""
+        o = _lib.EigOpts(k, block, max_basis, max_iter, tol, seed, reorth_passes, check_every, int(fp64_products))
         ev = np.zeros(k, np.float64)
         info = _lib.EigInfo()
         if method == "lanczos":
@@ -439,6 +441,25 @@ def count_pairs(mbs, S, variant="hybrid", max_diff=4, row_counts=None, stream=No
     check(lib().ci_count_pairs(_ptr(mbs), n, N, int(S), COUNT_VARIANTS.get(variant, variant), int(max_diff),
                                C.byref(total), _ptr(row_counts), _stream(stream)), "ci_count_pairs")
     return total.value
+
+
+def basis_product(op, A, B, Cm, alpha=-1.0, beta=1.0, method="tc", stream=None):
+    """ci_basis_product on float64 device tensors: op "tn" writes
+    Cm = A^T B ([na, nb]); op "nn" updates B = beta B + alpha A Cm.  method
+    "tc" (tensor cores, exact digit-plane products) or "fp64" (CUDA cores).
+    A, B are [n, cols] row-major (their row strides are the leading
+    dimensions)."""
+    import torch
+    opc = {"tn": 0, "nn": 1}[op]
+    mc = {"fp64": 0, "tc": 1}[method]
+    n, na = int(A.shape[0]), int(A.shape[1])
+    nb = int(B.shape[1])
+    for t in (A, B):
+        if t.dim() != 2 or t.stride(1) != 1 or t.dtype != torch.float64 or not t.is_cuda:
+            raise ValueError("A and B must be float64 CUDA matrices with unit column stride")
+    check(lib().ci_basis_product(opc, mc, n, C.c_void_p(A.data_ptr()), int(A.stride(0)), na,
+                                 C.c_void_p(B.data_ptr()), int(B.stride(0)), nb, _ptr(Cm), float(alpha), float(beta),
+                                 _stream(stream)), "ci_basis_product")
 
 
 def exclusive_scan(counts, offsets, stream=None):

@@ -34,7 +34,7 @@ class ProblemDesc(C.Structure):
 class EigOpts(C.Structure):
     _fields_ = [("k", C.c_int32), ("block", C.c_int32), ("max_basis", C.c_int32),
                 ("max_iter", C.c_int32), ("tol", C.c_double), ("seed", C.c_uint64),
-                ("reorth_passes", C.c_int32), ("check_every", C.c_int32)]
+                ("reorth_passes", C.c_int32), ("check_every", C.c_int32), ("fp64_products", C.c_int32)]
 
 
 class EigInfo(C.Structure):
@@ -96,6 +96,8 @@ _SIGS = {
     "ci_matrix_export": (C.c_int, [_P, _P, _P, _P, _P, _P]),
     "ci_apply_H": (C.c_int, [_P, _P, _P, C.c_int32, _P]),
     "ci_lowest_eigs": (C.c_int, [_P, C.POINTER(EigOpts), _P, _P, C.POINTER(EigInfo), _P]),
+    "ci_basis_product": (C.c_int, [C.c_int32, C.c_int32, C.c_int64, _P, C.c_int32, C.c_int32, _P, C.c_int32,
+                                   C.c_int32, _P, C.c_double, C.c_double, _P]),
     "ci_lowest_eigs_lobpcg": (C.c_int, [_P, C.POINTER(EigOpts), _P, C.c_int64, _P, _P, C.POINTER(EigInfo), _P]),
     "ci_orbital_blocks": (C.c_int, [_P, _P, _P, _I64P, _P]),
     "ci_refine_eigs": (C.c_int, [_P, C.c_int32, C.c_int32, _P, _P, _P, _P]),

@@ -197,27 +197,20 @@ __global__ void __launch_bounds__(256) k_nn_rows(int64_t dim, const double *__re
     }
 }
 
-// out[o] = sum_blk part[blk][o]: 32 outputs per block, 8 warps each sum a
-// fixed stride of blocks, then warp 0 adds the 8 partials in order
+// out[o] = sum_blk part[blk][o]: one warp per output, lane l sums blocks
+// l, l + 32, ... in order, then a fixed butterfly adds the 32 lane sums
 // (deterministic).
 __global__ void __launch_bounds__(256) k_reduce_partial(const double *__restrict__ part, int nblk, int n,
                                                         double *__restrict__ out) {
-    __shared__ double red[8][33];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int o = blockIdx.x * 32 + lane;
+    const int lane = threadIdx.x & 31;
+    const int o = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (o >= n) return;
     double s = 0.0;
-    if (o < n) {
 #pragma unroll 4
-        for (int b = w; b < nblk; b += 8) s += part[(int64_t)b * n + o];
-    }
-    red[w][lane] = s;
-    __syncthreads();
-    if (w == 0 && o < n) {
-        double t = 0.0;
+    for (int b = lane; b < nblk; b += 32) s += part[(int64_t)b * n + o];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) t += red[i][lane];
-        out[o] = t;
-    }
+    for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
+    if (lane == 0) out[o] = s;
 }
 
 // W[i][v] = beta W[i][v] + alpha sum_u A[i][u] C[u][v]   (beta == 0: W not read)
@@ -341,6 +334,54 @@ __global__ void k_precond(int64_t dim, int nb, const double *__restrict__ R, con
     }
 }
 
+// ------------------------------------------------------------------ FP64 products
+
+static void set_tn_attributes() {
+    static bool attr = false;
+    if (!attr) {
+        CI_CUDA(cudaFuncSetAttribute(k_tn_partial, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(sizeof(double) * kTR * (kMaxNa + 8))));
+        CI_CUDA(cudaFuncSetAttribute(k_tn_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)std::max(kTnSmem, sizeof(double) * kTnThreads * 8 * 4)));
+        attr = true;
+    }
+}
+
+// part[blk][na][nb] = A^T B over row blocks of rows_per_blk rows, on the
+// FP64 CUDA cores.
+static void fp64_tn(int64_t dim, const double *A, int lda, int na, const double *B, int ldb, int nb, double *part,
+                    int nblk, int64_t rows_per_blk, cudaStream_t s) {
+    set_tn_attributes();
+    const int nap = (na + 3) & ~3;
+    const bool aligned = ((uintptr_t)A % 16 == 0) && ((uintptr_t)B % 16 == 0) && lda % 2 == 0 && ldb % 2 == 0 &&
+                         nap <= lda;
+    if (nb == 8 && aligned) {
+        // two staged tiles, later reused for the slice sums, in at most
+        // kTnSmem bytes
+        const int S = kTnThreads / (nap / 4);
+        int tr = (int)(kTnSmem / sizeof(double)) / (2 * (nap + 8));
+        if (tr > 128) tr = 128;
+        const size_t smem = sizeof(double) * std::max((size_t)2 * tr * (nap + 8), (size_t)S * nap * 8);
+        launch("k_tn_partial", k_tn_tiled, nblk, kTnThreads, smem, s, dim, A, lda, na, B, ldb, part,
+               rows_per_blk, tr);
+    } else {
+        const size_t smem = sizeof(double) * kTR * (na + nb);
+        launch("k_tn_partial", k_tn_partial, nblk, kTnThreads, smem, s, dim, A, lda, na, B, ldb, nb, part,
+               rows_per_blk);
+    }
+}
+
+// W = beta W + alpha A C on the FP64 CUDA cores.
+static void fp64_nn(int64_t dim, const double *A, int lda, int na, const double *C, int nb, double *Wout, int ldw,
+                    double alpha, double beta, cudaStream_t s) {
+    const int grid = nb == 8 ? grid_for(dim, 256, sm_count() * 8) : grid_for(dim * nb, 256, sm_count() * 8);
+    if (nb == 8)
+        launch("k_nn_update", k_nn_rows<8>, grid, 256, 0, s, dim, A, lda, na, C, Wout, ldw, alpha, beta);
+    else
+        launch("k_nn_update", k_nn_update, grid, 256, 0, s, dim, A, lda, na, C, nb, Wout, ldw, alpha, beta);
+    CI_CHECK_LAUNCH();
+}
+
 // ------------------------------------------------------------------ driver
 
 namespace {
@@ -352,6 +393,12 @@ struct Solver {
     int b, k, mmax;
     bool f64;
     int nblk;
+    // basis products on the tensor cores (FP64-exact digit planes) unless
+    // the caller asked for the FP64 CUDA-core kernels
+    bool tc = true;
+    int oz_nblk = 1;
+    DevBuf<int> ozflag;
+    DevBuf<unsigned long long> Qfix;   // fixed-point shadow of Q for the tensor-core products
     int64_t rows_per_blk;
     DevBuf<double> Q, W, tmp, part, Cdev, Mdev, theta_dev, Cacc;
     DevBuf<float> X32, Y32;
@@ -367,21 +414,17 @@ struct Solver {
     Solver(const Matrix *H_, cudaStream_t s_, int b_, int k_, int mmax_)
         : H(H_), s(s_), dim(H_->dim), b(b_), k(k_), mmax(mmax_), f64(H_->vtype == CI_F64) {
         int sms = sm_count();
-        static bool attr = false;
-        if (!attr) {
-            CI_CUDA(cudaFuncSetAttribute(k_tn_partial, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(sizeof(double) * kTR * (kMaxNa + 8))));
-            CI_CUDA(cudaFuncSetAttribute(k_tn_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)std::max(kTnSmem, sizeof(double) * kTnThreads * 8 * 4)));
-            attr = true;
-        }
         nblk = (int)std::min<int64_t>((int64_t)sms * 2, (dim + 63) / 64);
         if (nblk < 1) nblk = 1;
         rows_per_blk = (dim + nblk - 1) / nblk;
+        oz_nblk = oz_tn_blocks(dim);
         Q.alloc((size_t)dim * mmax);
         W.alloc((size_t)dim * b);
         tmp.alloc((size_t)dim * std::max(mmax, b));
-        part.alloc((size_t)nblk * kMaxNa * 8);
+        part.alloc((size_t)std::max(nblk, oz_nblk) * kMaxNa * 8);
+        ozflag.alloc(1);
+        CI_CUDA(cudaMemsetAsync(ozflag.ptr, 0, sizeof(int), s));
+        if (b == 8) Qfix.alloc((size_t)dim * mmax);
         Cdev.alloc((size_t)kMaxNa * 8);
         Mdev.alloc((size_t)kMaxNa * 8);
         theta_dev.alloc(64);
@@ -401,27 +444,37 @@ struct Solver {
     int grid(int64_t work) const { return grid_for(work, 256, sm_count() * 8); }
 
     // C (na x nb) = A^T B over all rows; result in Cout (device) and, if
-    // host != null, copied to host.
-    void tn(const double *A, int lda, int na, const double *B, int ldb, int nb, double *Cout,
-            std::vector<double> *host) {
-        const int nap = (na + 3) & ~3;
-        const bool aligned = ((uintptr_t)A % 16 == 0) && ((uintptr_t)B % 16 == 0) && lda % 2 == 0 && ldb % 2 == 0 &&
-                             nap <= lda;
-        if (nb == 8 && aligned) {
-            // two staged tiles, later reused for the slice sums, in at most
-            // kTnSmem bytes
-            const int S = kTnThreads / (nap / 4);
-            int tr = (int)(kTnSmem / sizeof(double)) / (2 * (nap + 8));
-            if (tr > 128) tr = 128;
-            const size_t smem = sizeof(double) * std::max((size_t)2 * tr * (nap + 8), (size_t)S * nap * 8);
-            launch("k_tn_partial", k_tn_tiled, nblk, kTnThreads, smem, s, dim, A, lda, na, B, ldb, part.ptr,
-                   rows_per_blk, tr);
+    // host != null, copied to host.  basis: A holds orthonormal basis
+    // columns (|A| <= 1), which the tensor-core product takes.
+    bool use_tc(bool basis, int na, int nb) const { return basis && tc && nb == 8 && Qfix.ptr && oz_supported(na); }
+    // the shadow of the basis column that A points at
+    const unsigned long long *shadow(const double *A) const { return Qfix.ptr + (A - Q.ptr); }
+    // Q[:, c0:c0+nc] = src (leading dimension lds), with the shadow
+    void copy_into_basis(const double *src, int lds, int c0, int nc) {
+        if (tc && Qfix.ptr) {
+            oz_copy_fix(dim, nc, src, lds, Q.ptr + c0, mmax, Qfix.ptr + c0, mmax, ozflag.ptr, s);
         } else {
-            const size_t smem = sizeof(double) * kTR * (na + nb);
-            launch("k_tn_partial", k_tn_partial, nblk, kTnThreads, smem, s, dim, A, lda, na, B, ldb, nb, part.ptr,
-                   rows_per_blk);
+            launch("k_copy_cols", k_copy_cols, grid(dim * nc), 256, 0, s, dim, nc, src, lds, Q.ptr + c0, mmax);
         }
-        launch("k_reduce_partial", k_reduce_partial, (na * nb + 31) / 32, 256, 0, s, part.ptr, nblk, na * nb, Cout);
+        CI_CHECK_LAUNCH();
+    }
+
+    void tn(const double *A, int lda, int na, const double *B, int ldb, int nb, double *Cout,
+            std::vector<double> *host, bool basis = false) {
+        if (use_tc(basis, na, nb)) {
+            oz_tn(dim, shadow(A), lda, na, B, ldb, part.ptr, oz_nblk, ozflag.ptr, s);
+            launch("k_reduce_partial", k_reduce_partial, (na * nb + 7) / 8, 256, 0, s, part.ptr, oz_nblk, na * nb,
+                   Cout);
+            CI_CHECK_LAUNCH();
+            if (host) {
+                host->resize((size_t)na * nb);
+                CI_CUDA(cudaMemcpyAsync(host->data(), Cout, sizeof(double) * na * nb, cudaMemcpyDeviceToHost, s));
+                CI_CUDA(cudaStreamSynchronize(s));
+            }
+            return;
+        }
+        fp64_tn(dim, A, lda, na, B, ldb, nb, part.ptr, nblk, rows_per_blk, s);
+        launch("k_reduce_partial", k_reduce_partial, (na * nb + 7) / 8, 256, 0, s, part.ptr, nblk, na * nb, Cout);
         CI_CHECK_LAUNCH();
         if (host) {
             host->resize((size_t)na * nb);
@@ -431,13 +484,13 @@ struct Solver {
     }
 
     void nn(const double *A, int lda, int na, const double *C, int nb, double *Wout, int ldw, double alpha,
-            double beta) {
-        if (nb == 8)
-            launch("k_nn_update", k_nn_rows<8>, grid(dim), 256, 0, s, dim, A, lda, na, C, Wout, ldw, alpha, beta);
-        else
-            launch("k_nn_update", k_nn_update, grid(dim * nb), 256, 0, s, dim, A, lda, na, C, nb, Wout, ldw, alpha,
-                   beta);
-        CI_CHECK_LAUNCH();
+            double beta, bool basis = false) {
+        if (use_tc(basis, na, nb)) {
+            oz_nn(dim, shadow(A), lda, na, C, Wout, ldw, alpha, beta, ozflag.ptr, s);
+            CI_CHECK_LAUNCH();
+            return;
+        }
+        fp64_nn(dim, A, lda, na, C, nb, Wout, ldw, alpha, beta, s);
     }
 
     void upload(const std::vector<double> &h, double *d) {
@@ -488,13 +541,13 @@ struct Solver {
         Cacc.ensure((size_t)(passes + 1) * kMaxNa * 8);
         double *cl = Cacc.ptr;
         if (nl > 0) {
-            tn(Q.ptr + lo, mmax, nl, Wb, nb, nb, cl, nullptr);
-            nn(Q.ptr + lo, mmax, nl, cl, nb, Wb, nb, -1.0, 1.0);
+            tn(Q.ptr + lo, mmax, nl, Wb, nb, nb, cl, nullptr, true);
+            nn(Q.ptr + lo, mmax, nl, cl, nb, Wb, nb, -1.0, 1.0, true);
         }
         for (int p = 0; p < passes; ++p) {
             double *cp = Cacc.ptr + (size_t)(p + 1) * kMaxNa * 8;
-            tn(Q.ptr, mmax, m, Wb, nb, nb, cp, nullptr);
-            nn(Q.ptr, mmax, m, cp, nb, Wb, nb, -1.0, 1.0);
+            tn(Q.ptr, mmax, m, Wb, nb, nb, cp, nullptr, true);
+            nn(Q.ptr, mmax, m, cp, nb, Wb, nb, -1.0, 1.0, true);
         }
         if (!coef) return;
         std::vector<double> h((size_t)(passes + 1) * kMaxNa * 8);
@@ -584,8 +637,11 @@ struct Solver {
             launch("k_copy_cols", k_copy_cols, grid(dim * nr), 256, 0, s, dim, nr, Vr, nr, V + r, mmax);
             CI_CHECK_LAUNCH();
         }
-        // second pass: V <- V G2^{-1/2}, R <- G2^{1/2} R
-        tn(V, mmax, b, V, mmax, b, Cdev.ptr, &G);
+        // second pass: V <- V G2^{-1/2}, R <- G2^{1/2} R.  V is orthonormal up
+        // to rounding now, so its products go through the basis path
+        const bool vtc = tc && Qfix.ptr;
+        if (vtc) oz_fix(dim, b, V, mmax, Qfix.ptr + m, mmax, ozflag.ptr, s);
+        tn(V, mmax, b, V, mmax, b, Cdev.ptr, &G, vtc);
         sym_eig(b, G, w, U);
         std::vector<double> Mi((size_t)b * b, 0.0), Ms((size_t)b * b, 0.0);
         for (int a = 0; a < b; ++a)
@@ -600,9 +656,8 @@ struct Solver {
                 Ms[(size_t)a * b + c] = y;
             }
         upload(Mi, Mdev.ptr);
-        nn(V, mmax, b, Mdev.ptr, b, tmp.ptr, b, 1.0, 0.0);
-        launch("k_copy_cols", k_copy_cols, grid(dim * b), 256, 0, s, dim, b, tmp.ptr, b, V, mmax);
-        CI_CHECK_LAUNCH();
+        nn(V, mmax, b, Mdev.ptr, b, tmp.ptr, b, 1.0, 0.0, vtc);
+        copy_into_basis(tmp.ptr, b, m, b);
         std::vector<double> R2((size_t)b * b, 0.0);
         for (int a = 0; a < b; ++a)
             for (int c = 0; c < b; ++c) {
@@ -727,6 +782,7 @@ void lowest_eigs(const Matrix *H, const ci_eig_opts *opts_in, double *evals, dou
     }
 
     Solver sv(H, s, b, k, mmax);
+    sv.tc = o.fp64_products == 0;
     std::vector<double> T((size_t)mmax * mmax, 0.0);
     std::vector<double> R, coef;
     // start block
@@ -798,12 +854,11 @@ void lowest_eigs(const Matrix *H, const ci_eig_opts *opts_in, double *evals, dou
                 for (int r = 0; r < m_act; ++r)
                     for (int i = 0; i < nc; ++i) Sc[(size_t)r * nc + i] = Sk[(size_t)r * keep + c0 + i];
                 sv.upload(Sc, sv.Mdev.ptr);
-                sv.nn(sv.Q.ptr, mmax, m_act, sv.Mdev.ptr, nc, sv.tmp.ptr + c0, keep, 1.0, 0.0);
+                sv.nn(sv.Q.ptr, mmax, m_act, sv.Mdev.ptr, nc, sv.tmp.ptr + c0, keep, 1.0, 0.0, true);
             }
             // new block Q[:, m_act:m_act+b] -> Q[:, keep:keep+b]; Ritz vectors -> Q[:, 0:keep]
-            launch("k_copy_cols", k_copy_cols, sv.grid(dim * b), 256, 0, s, dim, b, sv.Q.ptr + m_act, mmax, sv.Q.ptr + keep, mmax);
-            launch("k_copy_cols", k_copy_cols, sv.grid(dim * keep), 256, 0, s, dim, keep, sv.tmp.ptr, keep, sv.Q.ptr, mmax);
-            CI_CHECK_LAUNCH();
+            sv.copy_into_basis(sv.Q.ptr + m_act, mmax, keep, b);
+            sv.copy_into_basis(sv.tmp.ptr, keep, 0, keep);
             std::fill(T.begin(), T.end(), 0.0);
             for (int i = 0; i < keep; ++i) T[(size_t)i * mmax + i] = last.theta[i];
             for (int r = 0; r < b; ++r)
@@ -845,7 +900,10 @@ void lowest_eigs(const Matrix *H, const ci_eig_opts *opts_in, double *evals, dou
         for (int i = 0; i < nc; ++i) inf.residual[c0 + i] = std::sqrt(std::max(G[(size_t)i * nc + i], 0.0));
     }
     if (evecs) CI_CUDA(cudaMemcpyAsync(evecs, X, sizeof(double) * dim * k, cudaMemcpyDeviceToDevice, s));
+    int ozf = 0;
+    CI_CUDA(cudaMemcpyAsync(&ozf, sv.ozflag.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
     CI_CUDA(cudaStreamSynchronize(s));
+    if (ozf) fail(CI_ERR_INTERNAL, "tensor-core basis product failed (flag %d)", ozf);
     inf.iterations = it;
     inf.basis_size = m_act;
     inf.hnorm_est = sv.hnorm;
@@ -1324,5 +1382,52 @@ extern "C" ci_status ci_refine_eigs(ci_problem *p, int32_t k, int32_t iters, dou
         cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
         ci::StreamScope scope(s);
         ci::refine_eigs(&p->impl, k, iters, evecs, evals, residuals, s);
+    });
+}
+
+// Sec. 2, Fig. 1 eigensolve: the reorthogonalisation products of the block
+// Lanczos solver, exposed for testing and for callers with their own basis.
+extern "C" ci_status ci_basis_product(int32_t op, int32_t method, int64_t n, const double *A, int32_t lda,
+                                      int32_t na, double *B, int32_t ldb, int32_t nb, double *C, double alpha,
+                                      double beta, void *stream) {
+    return ci::guard([&] {
+        using namespace ci;
+        cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+        StreamScope scope(s);
+        if (op != CI_PRODUCT_TN && op != CI_PRODUCT_NN) fail(CI_ERR_INVALID_ARG, "op must be CI_PRODUCT_TN or _NN");
+        if (method != CI_PRODUCT_FP64 && method != CI_PRODUCT_TC) fail(CI_ERR_INVALID_ARG, "unknown method %d", method);
+        if (n < 0 || !A || !B || !C) fail(CI_ERR_INVALID_ARG, "n >= 0 and A, B, C are required");
+        if (na < 1 || na > kMaxNa || nb < 1 || nb > 8 || lda < na || ldb < nb)
+            fail(CI_ERR_INVALID_ARG, "need 1 <= na <= %d, 1 <= nb <= 8, lda >= na, ldb >= nb", kMaxNa);
+        if (method == CI_PRODUCT_TC && (nb != 8 || !oz_supported(na)))
+            fail(CI_ERR_INVALID_ARG, "the tensor-core product needs nb = 8 and na <= 64");
+        DevBuf<int> flag(1);
+        CI_CUDA(cudaMemsetAsync(flag.ptr, 0, sizeof(int), s));
+        DevBuf<unsigned long long> Y;
+        const int ldy = (na + 1) & ~1;
+        if (method == CI_PRODUCT_TC && n > 0) {   // the fixed-point shadow of A
+            Y.alloc((size_t)n * ldy);
+            oz_fix(n, na, A, lda, Y.ptr, ldy, flag.ptr, s);
+        }
+        if (op == CI_PRODUCT_TN) {
+            if (n == 0) {
+                CI_CUDA(cudaMemsetAsync(C, 0, sizeof(double) * na * nb, s));
+            } else {
+                const int nblk = method == CI_PRODUCT_TC ? oz_tn_blocks(n)
+                                                         : (int)std::min<int64_t>(2 * sm_count(), (n + 63) / 64);
+                DevBuf<double> part((size_t)nblk * na * nb);
+                if (method == CI_PRODUCT_TC) oz_tn(n, Y.ptr, ldy, na, B, ldb, part.ptr, nblk, flag.ptr, s);
+                else fp64_tn(n, A, lda, na, B, ldb, nb, part.ptr, nblk, (n + nblk - 1) / nblk, s);
+                launch("k_reduce_partial", k_reduce_partial, (na * nb + 7) / 8, 256, 0, s, part.ptr, nblk, na * nb, C);
+            }
+        } else if (n > 0) {
+            if (method == CI_PRODUCT_TC) oz_nn(n, Y.ptr, ldy, na, C, B, ldb, alpha, beta, flag.ptr, s);
+            else fp64_nn(n, A, lda, na, C, nb, B, ldb, alpha, beta, s);
+        }
+        int f = 0;
+        CI_CUDA(cudaMemcpyAsync(&f, flag.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CI_CUDA(cudaStreamSynchronize(s));
+        if (f & 1) fail(CI_ERR_INVALID_ARG, "an entry of A (or a non-finite value) is outside the digits' range");
+        if (f & 2) fail(CI_ERR_TIMEOUT, "a tensor-core wait ran out");
     });
 }

@@ -267,6 +267,23 @@ void apply_matrix16(const Matrix *m, const float *X, float *Y, cudaStream_t s);
 // Y8 = H R8 ([dim][8]) in FP64 with every element evaluated on the fly
 void h64_apply(Problem *p, const double *R8, double *Y8, cudaStream_t s);
 void apply_matrix(const Matrix *m, const void *X, void *Y, int nvec, cudaStream_t s);
+// FP64-exact products on the tensor cores (ozaki.cu) for a basis A of
+// na <= 64 orthonormal columns (|A| < 1.99), read in its fixed-point
+// shadow form Y (oz_fix; 16-byte aligned rows, even ldy):
+//   oz_tn: part[blk][na][8] = A[rows of blk]^T B over nblk row blocks
+//   oz_nn: W = beta W + alpha A C, C [na][8]
+// An entry outside the digits' range sets bit 0 of *flag, a tensor-core
+// wait that ran out bit 1.
+bool oz_supported(int na);
+void oz_fix(int64_t dim, int nc, const double *A, int lda, unsigned long long *Y, int ldy, int *flag,
+            cudaStream_t s);
+void oz_copy_fix(int64_t dim, int nc, const double *src, int lds, double *dst, int ldd, unsigned long long *Y, int ldy,
+                 int *flag, cudaStream_t s);
+void oz_tn(int64_t dim, const unsigned long long *Y, int ldy, int na, const double *B, int ldb, double *part,
+           int nblk, int *flag, cudaStream_t s);
+void oz_nn(int64_t dim, const unsigned long long *Y, int ldy, int na, const double *C, double *W, int ldw,
+           double alpha, double beta, int *flag, cudaStream_t s);
+int oz_tn_blocks(int64_t dim);
 void lowest_eigs(const Matrix *H, const ci_eig_opts *opts, double *evals, double *evecs, ci_eig_info *info,
                  cudaStream_t s);
 
