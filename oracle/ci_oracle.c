@@ -25,7 +25,8 @@
  * Hamiltonian:  H = sum_a eps_a a+_a a_a   (both species)
  *                 + 1/4 sum V^pp_abcd a+_a a+_b a_d a_c   (same for nn)
  *                 + sum V^pn_abcd a+_{a,p} a+_{b,n} a_{d,n} a_{c,p}
- * with antisymmetrised V^pp, V^nn and flat tables V[((a*S+b)*S+c)*S+d].
+ * with antisymmetrised V^pp, V^nn and flat tables V[((a*S+b)*S+c)*S+d], or,
+ * without tables, the seeded counter-based draws described at V_seeded.
  * Determinant convention: |p;n> = (prod_{i in p, ascending} a+_{i,p})
  *                                 (prod_{j in n, ascending} a+_{j,n}) |0>.
  */
@@ -43,10 +44,12 @@ typedef struct {
     const int *sp_N;       /* [S] HO shell of each s.p. state             */
     const int *sp_twom;    /* [S] 2m of each s.p. state                   */
     const double *eps;     /* [S] one-body energies                       */
-    const double *Vpp, *Vnn, *Vpn;   /* [S^4] each                        */
+    const double *Vpp, *Vnn, *Vpn;   /* [S^4] each, or all NULL: drawn     */
     int A[2];              /* particles: [0] protons, [1] neutrons         */
     int nmax;              /* -1: no Nmax cut                              */
     int twoM;              /* total 2M                                     */
+    uint64_t seed;         /* with NULL tables: seed of the drawn TBMEs    */
+    int round_f32;         /* with NULL tables: round each draw to float32 */
 } orc_problem;
 
 /* ---------------------------------------------------------------------- */
@@ -248,8 +251,60 @@ static int set_minus(const uint8_t *x, const uint8_t *y, int A, int *out)
 
 static double absd(double x) { return x < 0 ? -x : x; }
 
-static double V4(const double *V, int S, int a, int b, int c, int d)
+/* SplitMix64 output function (Steele, Lea and Flood, OOPSLA 2014). */
+static uint64_t splitmix_mix(uint64_t z)
 {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+/* One seeded TBME draw for pair indices P <= Q of channel ch: twelve
+ * SplitMix64 outputs at stream positions 12c+1 .. 12c+12 of the counter
+ * c = (ch << 32) | (P << 16) | Q, each taken as a uniform (z >> 32) 2^-32,
+ * summed, minus 6 (Irwin-Hall).  The partial sums are exact in binary64. */
+static double seeded_draw(uint64_t seed, int ch, uint64_t P, uint64_t Q)
+{
+    const uint64_t gamma = 0x9E3779B97F4A7C15ull;
+    uint64_t c = ((uint64_t)ch << 32) | (P << 16) | Q;
+    double g = 0.0;
+    for (int k = 1; k <= 12; ++k)
+        g += (double)(splitmix_mix(seed + (12 * c + (uint64_t)k) * gamma) >> 32) * 0x1p-32;
+    return g - 6.0;
+}
+
+/* V_abcd of channel ch (0 pp, 1 nn, 2 pn) when no tables are given: zero
+ * unless m_a + m_b = m_c + m_d; like-particle elements are antisymmetric in
+ * (a, b) and in (c, d) and vanish for a == b or c == d, with a < b pairs
+ * numbered P = b(b-1)/2 + a; pn pairs are numbered P = a S + b; the element
+ * of the unordered pair of pair indices is one draw (V_abcd = V_cdab). */
+static double V_seeded(const orc_problem *pr, int ch, int a, int b, int c, int d)
+{
+    const int *m = pr->sp_twom;
+    if (m[a] + m[b] != m[c] + m[d]) return 0.0;
+    double sign = 1.0;
+    uint64_t P, Q;
+    if (ch < 2) {
+        if (a == b || c == d) return 0.0;
+        if (a > b) { int t = a; a = b; b = t; sign = -sign; }
+        if (c > d) { int t = c; c = d; d = t; sign = -sign; }
+        P = (uint64_t)b * (uint64_t)(b - 1) / 2 + (uint64_t)a;
+        Q = (uint64_t)d * (uint64_t)(d - 1) / 2 + (uint64_t)c;
+    } else {
+        P = (uint64_t)a * (uint64_t)pr->S + (uint64_t)b;
+        Q = (uint64_t)c * (uint64_t)pr->S + (uint64_t)d;
+    }
+    double g = P <= Q ? seeded_draw(pr->seed, ch, P, Q) : seeded_draw(pr->seed, ch, Q, P);
+    if (pr->round_f32) g = (double)(float)g;
+    return sign * g;
+}
+
+/* V_abcd of channel ch from the flat table V[((a*S+b)*S+c)*S+d], or drawn. */
+static double Vch(const orc_problem *pr, int ch, int a, int b, int c, int d)
+{
+    const double *V = ch == 0 ? pr->Vpp : ch == 1 ? pr->Vnn : pr->Vpn;
+    if (!V) return V_seeded(pr, ch, a, b, c, d);
+    const int64_t S = pr->S;
     return V[(((int64_t)a * S + b) * S + c) * S + d];
 }
 
@@ -279,7 +334,7 @@ static int phase_of(const uint8_t *ket, const uint8_t *bra, int A,
 double orc_element(const orc_problem *pr, const uint8_t *pb, const uint8_t *nb,
                    const uint8_t *pk, const uint8_t *nk, double *absum)
 {
-    const int S = pr->S, Ap = pr->A[0], An = pr->A[1];
+    const int Ap = pr->A[0], An = pr->A[1];
     int ap[2], cp[2], an_[2], cn[2];   /* annihilated (ket only), created (bra only) */
     int dp = orc_count_difference(pb, pk, Ap);
     int dn = orc_count_difference(nb, nk, An);
@@ -292,17 +347,17 @@ double orc_element(const orc_problem *pr, const uint8_t *pb, const uint8_t *nb,
         for (int i = 0; i < An; ++i) { v += pr->eps[nk[i]]; ab += absd(pr->eps[nk[i]]); }
         for (int i = 0; i < Ap; ++i)
             for (int j = i + 1; j < Ap; ++j) {
-                double t = V4(pr->Vpp, S, pk[i], pk[j], pk[i], pk[j]);
+                double t = Vch(pr, 0, pk[i], pk[j], pk[i], pk[j]);
                 v += t; ab += absd(t);
             }
         for (int i = 0; i < An; ++i)
             for (int j = i + 1; j < An; ++j) {
-                double t = V4(pr->Vnn, S, nk[i], nk[j], nk[i], nk[j]);
+                double t = Vch(pr, 1, nk[i], nk[j], nk[i], nk[j]);
                 v += t; ab += absd(t);
             }
         for (int i = 0; i < Ap; ++i)
             for (int j = 0; j < An; ++j) {
-                double t = V4(pr->Vpn, S, pk[i], nk[j], pk[i], nk[j]);
+                double t = Vch(pr, 2, pk[i], nk[j], pk[i], nk[j]);
                 v += t; ab += absd(t);
             }
         *absum = ab;
@@ -317,11 +372,11 @@ double orc_element(const orc_problem *pr, const uint8_t *pb, const uint8_t *nb,
         int s = phase_of(pk, pb, Ap, ops, 2);
         for (int i = 0; i < Ap; ++i) {
             if (pk[i] == a) continue;
-            double t = V4(pr->Vpp, S, c, pk[i], a, pk[i]);
+            double t = Vch(pr, 0, c, pk[i], a, pk[i]);
             v += t; ab += absd(t);
         }
         for (int j = 0; j < An; ++j) {
-            double t = V4(pr->Vpn, S, c, nk[j], a, nk[j]);
+            double t = Vch(pr, 2, c, nk[j], a, nk[j]);
             v += t; ab += absd(t);
         }
         *absum = ab;
@@ -334,11 +389,11 @@ double orc_element(const orc_problem *pr, const uint8_t *pb, const uint8_t *nb,
         int s = phase_of(nk, nb, An, ops, 2);
         for (int j = 0; j < An; ++j) {
             if (nk[j] == b) continue;
-            double t = V4(pr->Vnn, S, d, nk[j], b, nk[j]);
+            double t = Vch(pr, 1, d, nk[j], b, nk[j]);
             v += t; ab += absd(t);
         }
         for (int i = 0; i < Ap; ++i) {
-            double t = V4(pr->Vpn, S, pk[i], d, pk[i], b);
+            double t = Vch(pr, 2, pk[i], d, pk[i], b);
             v += t; ab += absd(t);
         }
         *absum = ab;
@@ -349,7 +404,7 @@ double orc_element(const orc_problem *pr, const uint8_t *pb, const uint8_t *nb,
         int a = ap[0], b = ap[1], c = cp[0], d = cp[1];
         int ops[4] = { -(a + 1), -(b + 1), d, c };
         int s = phase_of(pk, pb, Ap, ops, 4);
-        double t = V4(pr->Vpp, S, c, d, a, b);
+        double t = Vch(pr, 0, c, d, a, b);
         *absum = absd(t);
         return s * t;
     }
@@ -357,7 +412,7 @@ double orc_element(const orc_problem *pr, const uint8_t *pb, const uint8_t *nb,
         int a = an_[0], b = an_[1], c = cn[0], d = cn[1];
         int ops[4] = { -(a + 1), -(b + 1), d, c };
         int s = phase_of(nk, nb, An, ops, 4);
-        double t = V4(pr->Vnn, S, c, d, a, b);
+        double t = Vch(pr, 1, c, d, a, b);
         *absum = absd(t);
         return s * t;
     }
@@ -367,7 +422,7 @@ double orc_element(const orc_problem *pr, const uint8_t *pb, const uint8_t *nb,
         int a = ap[0], c = cp[0], b = an_[0], d = cn[0];
         int opp[2] = { -(a + 1), c }, opn[2] = { -(b + 1), d };
         int s = phase_of(pk, pb, Ap, opp, 2) * phase_of(nk, nb, An, opn, 2);
-        double t = V4(pr->Vpn, S, c, d, a, b);
+        double t = Vch(pr, 2, c, d, a, b);
         *absum = absd(t);
         return s * t;
     }

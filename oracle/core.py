@@ -37,7 +37,8 @@ class _Problem(C.Structure):
                 ("sp_twom", C.POINTER(C.c_int)), ("eps", C.POINTER(C.c_double)),
                 ("Vpp", C.POINTER(C.c_double)), ("Vnn", C.POINTER(C.c_double)),
                 ("Vpn", C.POINTER(C.c_double)), ("A", C.c_int * 2),
-                ("nmax", C.c_int), ("twoM", C.c_int)]
+                ("nmax", C.c_int), ("twoM", C.c_int), ("seed", C.c_uint64),
+                ("round_f32", C.c_int)]
 
 
 class _Species(C.Structure):
@@ -97,24 +98,35 @@ class OracleProblem:
     """One CI problem: s.p. table, particle numbers, cuts and interaction.
 
     ``tables`` holds the flat ``pp``, ``nn``, ``pn`` TBME tables in any float
-    dtype; they are widened to float64 exactly.  ``eps`` are the one-body
-    energies [S].
+    dtype; they are widened to float64 exactly.  Without tables, ``seed``
+    draws every TBME on demand from the counter-based SplitMix64 recipe
+    (each draw rounded to float32 when ``round_f32``), so that no S**4 table
+    is held.  ``eps`` are the one-body energies [S].
     """
 
-    def __init__(self, sp, Z, N, nmax, twoM, eps, tables):
+    def __init__(self, sp, Z, N, nmax, twoM, eps, tables=None, seed=None, round_f32=True):
         self.lib = _load()
         self.S = int(len(sp["N"]))
         self.sp_N = np.ascontiguousarray(sp["N"], dtype=np.int32).astype(np.intc)
         self.sp_twom = np.ascontiguousarray(sp["twom"], dtype=np.int32).astype(np.intc)
         self.eps = np.ascontiguousarray(eps, dtype=np.float64)
-        self.V = {k: np.ascontiguousarray(tables[k], dtype=np.float64) for k in ("pp", "nn", "pn")}
-        for k, v in self.V.items():
-            if v.size != self.S ** 4:
-                raise ValueError("table %s must have S**4 entries" % k)
         self.Z, self.N, self.nmax, self.twoM = int(Z), int(N), int(nmax), int(twoM)
+        if tables is not None:
+            self.V = {k: np.ascontiguousarray(tables[k], dtype=np.float64) for k in ("pp", "nn", "pn")}
+            for k, v in self.V.items():
+                if v.size != self.S ** 4:
+                    raise ValueError("table %s must have S**4 entries" % k)
+            vp = [_dptr(self.V[k]) for k in ("pp", "nn", "pn")]
+            seed, round_f32 = 0, False
+        else:
+            if seed is None:
+                raise ValueError("give TBME tables or a seed")
+            self.V = None
+            vp = [None, None, None]
         self._pr = _Problem(self.S, _iptr(self.sp_N), _iptr(self.sp_twom), _dptr(self.eps),
-                            _dptr(self.V["pp"]), _dptr(self.V["nn"]), _dptr(self.V["pn"]),
-                            (C.c_int * 2)(self.Z, self.N), self.nmax, self.twoM)
+                            vp[0], vp[1], vp[2],
+                            (C.c_int * 2)(self.Z, self.N), self.nmax, self.twoM,
+                            int(seed) & 0xFFFFFFFFFFFFFFFF, int(bool(round_f32)))
         self._sp = [_Species(), _Species()]
         for s in (0, 1):
             if self.lib.orc_species_build(C.byref(self._pr), s, C.byref(self._sp[s])) != 0:

@@ -14,7 +14,7 @@ Each independent element is one draw g(seed, channel, P, Q) on the canonical
 pair of pair-indices P <= Q:
 
 * like pairs a < b have index P = b(b-1)/2 + a; pn pairs (a, b) have
-  P = a*S + b (S <= 128, so P < 2**16);
+  P = a*S + b (S <= 256, so P < 2**16);
 * the counter is c = (channel << 32) | (P << 16) | Q;
 * twelve SplitMix64 outputs (Steele, Lea and Flood, OOPSLA 2014) are taken at
   stream positions 12c + 1 ... 12c + 12, i.e. z_k = mix(seed + (12c+k+1)*gamma)
@@ -98,8 +98,8 @@ def tbme_tables(sp, seed, dtype=np.float32):
     """
     twom = np.asarray(sp["twom"])
     S = len(twom)
-    if S > 128:
-        raise ValueError("at most 128 s.p. states per species")
+    if S > 256:
+        raise ValueError("at most 256 s.p. states per species")
     out = {}
     like_groups = _pairs_by_m(twom, like=True)
     pn_groups = _pairs_by_m(twom, like=False)

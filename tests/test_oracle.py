@@ -483,3 +483,59 @@ def test_operator_has_no_one_body_part_and_scales():
     x = np.random.default_rng(2).standard_normal(oh.dim)
     a1 = oracle.expectation_values(rp, col, val, x)[0]
     assert np.isclose(oracle.expectation_values(rp, col, val, 3 * x)[0], 9 * a1, rtol=1e-12)
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_seeded_oracle_matches_flat_tables(dtype):
+    """The oracle's on-demand TBME draws (no S**4 tables) give bit for bit the
+    matrix of the flat tables written by the input generator: same draws, same
+    antisymmetric completion, same float32 rounding."""
+    sp = synth.ho_sp_table(2)
+    eps = synth.sp_energies(sp, 20.0)
+    T = synth.tbme_tables(sp, 17, dtype)
+    a = oracle.OracleProblem(sp, 2, 3, 2, 1, eps, T)
+    b = oracle.OracleProblem(sp, 2, 3, 2, 1, eps, seed=17, round_f32=dtype == np.float32)
+    ra, ca, va, aa = a.csr()
+    rb, cb, vb, ab = b.csr()
+    assert np.array_equal(ra, rb) and np.array_equal(ca, cb)
+    assert np.array_equal(va, vb) and np.array_equal(aa, ab)
+    c = oracle.OracleProblem(sp, 2, 3, 2, 1, eps, seed=18, round_f32=dtype == np.float32)
+    assert not np.array_equal(va, c.csr()[2])
+
+
+def test_seeded_oracle_two_body_elements_above_128_states():
+    """S = 168 (HO shells N <= 6): with one proton and one neutron, the
+    element between (a, b) and (c, d) (a != c, b != d) is the single pn draw
+    V_cdab; with two protons, a < b and c < d all different, it is the pp
+    draw V_cdab with its sign.  Pair
+    indices here reach P = a S + b > 2**14 and states above 127."""
+    sp = synth.ho_sp_table(6)
+    S = len(sp["N"])
+    assert S == 168
+    eps = synth.sp_energies(sp, 20.0)
+    rng = np.random.default_rng(3)
+    o = oracle.OracleProblem(sp, 1, 1, -1, 0, eps, seed=21, round_f32=False)
+    P, Nn = o.species(0)["occ"][:, 0], o.species(1)["occ"][:, 0]
+    hi = np.nonzero((P[o.p_idx] >= 128) & (Nn[o.n_idx] >= 128))[0]
+    rows = np.concatenate([rng.choice(o.dim, 20, replace=False), rng.choice(hi, 20, replace=False)])
+    for i in rows:
+        for j in rng.choice(o.dim, 10, replace=False):
+            a, b = int(P[o.p_idx[j]]), int(Nn[o.n_idx[j]])
+            c, d = int(P[o.p_idx[i]]), int(Nn[o.n_idx[i]])
+            if (a, b) == (c, d) or a == c or b == d:
+                continue
+            v, _ = o.element(i, j)
+            Pi, Pj = c * S + d, a * S + b
+            ref = synth.tbme_gaussian(21, synth.CH_PN, min(Pi, Pj), max(Pi, Pj))
+            assert v == float(ref), (i, j)
+    o2 = oracle.OracleProblem(sp, 2, 0, -1, 0, eps, seed=21, round_f32=True)
+    occ = o2.species(0)["occ"]
+    for i in rng.choice(o2.dim, 30, replace=False):
+        for j in rng.choice(o2.dim, 30, replace=False):
+            (c, d), (a, b) = occ[o2.p_idx[i]], occ[o2.p_idx[j]]
+            if len({a, b, c, d}) < 4:
+                continue
+            v, _ = o2.element(i, j)
+            Pi, Pj = int(d) * (int(d) - 1) // 2 + int(c), int(b) * (int(b) - 1) // 2 + int(a)
+            ref = np.float32(synth.tbme_gaussian(21, synth.CH_PP, min(Pi, Pj), max(Pi, Pj)))
+            assert v == float(ref), (i, j)   # <cd|H|ab> = V_cdab, a < b, c < d
