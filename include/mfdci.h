@@ -31,7 +31,7 @@
  *     stream before returning.
  *   - all matrices and vectors are row-major; indices are 0-based.
  *
- * Single-particle (s.p.) states: the caller lists them (S <= 128 per
+ * Single-particle (s.p.) states: the caller lists them (S <= 256 per
  * species) with their HO shell N and 2m.  A species determinant is a bit
  * string with bit a set when state a is occupied (Sec. 2.1), stored as
  * W = ceil(S/64) little-endian 64-bit words.  A basis state is a pair (p, n)
@@ -90,13 +90,14 @@ typedef struct ci_queue ci_queue;
 
 /* Problem description (Sec. 2: many-body basis of A = Z + N nucleons).
  *
- * n_sp        S, s.p. states per species, 1..128.
+ * n_sp        S, s.p. states per species, 1..256 (|2m| <= 63).
  * sp_N        host [S]: HO shell N of each state (>= 0).
  * sp_twom     host [S]: 2m of each state (odd).
  * sp_energy   host [S]: one-body energies eps_a (both species).
  * Z, N        protons and neutrons, 0..min(S, 16).
  * nmax        Nmax cut on the total excess HO quanta q_p + q_n (q = sum of
- *             shells minus the lowest possible sum); -1 for no cut.
+ *             shells minus the lowest possible sum); -1 for no cut, else
+ *             0..31.
  * twoM        total 2M of the basis.
  * tbme_source CI_TBME_TABLES or CI_TBME_SEED.
  * tbme_dtype  CI_F32 or CI_F64: element type of v_pp / v_nn / v_pn.
@@ -109,7 +110,8 @@ typedef struct ci_queue ci_queue;
  *             1 (nn), 2 (pn); g = sum_{k=0..11} (mix(seed + (12c+k+1)*
  *             0x9E3779B97F4A7C15) >> 32) * 2^-32 - 6 (exact in binary64);
  *             V_abcd = V_cdab = g, completed by antisymmetry for pp, nn;
- *             the float32 table is g rounded to nearest. */
+ *             an FP64 build uses g itself, an FP32 build g rounded to the
+ *             nearest float (the float32 table of the same recipe). */
 typedef struct {
     int32_t n_sp;
     const int32_t *sp_N;
@@ -138,7 +140,9 @@ const char *ci_version(void);
 
 /* Validate desc, copy the s.p. table, and stage the interaction on the
  * current device as compact m-blocked tables.  Errors: INVALID_ARG (bad
- * sizes, S > 128, Z or N > 16 or > S, missing tables), OOM, CUDA. */
+ * sizes, S > 256, Z or N > 16 or > S, missing tables), CAPACITY (nmax > 31,
+ * |2m| > 63, more than 8192 one-particle moves with one change of 2m), OOM,
+ * CUDA. */
 ci_status ci_problem_create(const ci_problem_desc *desc, ci_problem **out);
 void ci_problem_destroy(ci_problem *p);
 

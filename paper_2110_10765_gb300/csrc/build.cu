@@ -171,13 +171,22 @@ __global__ void __launch_bounds__(256) k_count_rows(const RowArgs<T> *args, cons
     }
 }
 
-// sum over the set bits k of a (W-word) bit string of tab[k]
+// sum over the occupied states k of determinant s (W-word bit strings) of tab[k]
 template <class T>
-__device__ __forceinline__ T sum_over_bits(const T *tab, uint64_t w0, uint64_t w1) {
-    T s = 0;
-    while (w0) { int k = __ffsll((long long)w0) - 1; w0 &= w0 - 1; s += tab[k]; }
-    while (w1) { int k = __ffsll((long long)w1) - 1; w1 &= w1 - 1; s += tab[64 + k]; }
-    return s;
+__device__ __forceinline__ T sum_over_bits(const T *tab, const uint64_t *bits, int s, int W) {
+    const uint64_t *b = bits + (int64_t)s * W;
+    T sum = 0;
+    if (W <= 2) {   // S <= 128: both words loaded up front, no loop over words
+        uint64_t w0 = b[0], w1 = W > 1 ? b[1] : 0ull;
+        while (w0) { const int k = __ffsll((long long)w0) - 1; w0 &= w0 - 1; sum += tab[k]; }
+        while (w1) { const int k = __ffsll((long long)w1) - 1; w1 &= w1 - 1; sum += tab[64 + k]; }
+        return sum;
+    }
+    for (int w = 0; w < W; ++w) {
+        uint64_t x = b[w];
+        while (x) { const int k = __ffsll((long long)x) - 1; x &= x - 1; sum += tab[64 * w + k]; }
+    }
+    return sum;
 }
 
 // Row context of the fill.  The bit strings of p and n are only needed by
@@ -186,12 +195,6 @@ struct RowCtx {
     int p, n, n_local;
     int64_t l2b, l4b;
 };
-
-template <class T>
-__device__ __forceinline__ void row_bits(const RowArgs<T> &a, int s, const uint64_t *bits, uint64_t &b0, uint64_t &b1) {
-    b0 = bits[(int64_t)s * a.W];
-    b1 = a.W > 1 ? bits[(int64_t)s * a.W + 1] : 0ull;
-}
 
 // One chunk of up to 32 O2 partners (one per lane: entry ep, segment kind,
 // beg, len; extra = elements of other partners placed before this one's
@@ -241,9 +244,7 @@ __device__ __forceinline__ int fill_chunk(const RowArgs<T> &a, const RowCtx &x, 
                 v = (info_neg(pinfo) ^ info_neg(en.info)) ? -w : w;
             } else {                          // (2,0): neutrons are spectators
                 const T *u = a.Upn + ((int64_t)info_c(pinfo) * S + info_a(pinfo)) * S;
-                uint64_t nb0, nb1;
-                row_bits<T>(a, x.n, a.n_bits, nb0, nb1);
-                const T h = pval + sum_over_bits<T>(u, nb0, nb1);
+                const T h = pval + sum_over_bits<T>(u, a.n_bits, x.n, a.W);
                 v = info_neg(pinfo) ? -h : h;
             }
             em.put(a, jpos + k, jcol + en.local, v);
@@ -265,20 +266,17 @@ __device__ __forceinline__ int fill_chunk(const RowArgs<T> &a, const RowCtx &x, 
                 v = en.val;
             } else if (dn == 1) {             // (0,2): protons are spectators
                 const T *w = a.Wpn + ((int64_t)info_c(en.info) * S + info_a(en.info)) * S;
-                uint64_t pb0, pb1;
-                row_bits<T>(a, x.p, a.p_bits, pb0, pb1);
-                const T h = en.val + sum_over_bits<T>(w, pb0, pb1);
+                const T h = en.val + sum_over_bits<T>(w, a.p_bits, x.p, a.W);
                 v = info_neg(en.info) ? -h : h;
             } else {                          // diagonal
                 T h = pval2 + en.val;
-                uint64_t x0, x1, nb0, nb1;
-                row_bits<T>(a, x.p, a.p_bits, x0, x1);
-                row_bits<T>(a, x.n, a.n_bits, nb0, nb1);
-                while (x0 | x1) {
-                    int kp;
-                    if (x0) { kp = __ffsll((long long)x0) - 1; x0 &= x0 - 1; }
-                    else { kp = 64 + __ffsll((long long)x1) - 1; x1 &= x1 - 1; }
-                    h += sum_over_bits<T>(a.Dpn + (int64_t)kp * S, nb0, nb1);
+                for (int w = 0; w < a.W; ++w) {   // pn diagonal: every occupied proton state with every neutron state
+                    uint64_t xp = a.p_bits[(int64_t)x.p * a.W + w];
+                    while (xp) {
+                        const int kp = 64 * w + __ffsll((long long)xp) - 1;
+                        xp &= xp - 1;
+                        h += sum_over_bits<T>(a.Dpn + (int64_t)kp * S, a.n_bits, x.n, a.W);
+                    }
                 }
                 v = h;
             }
@@ -311,6 +309,7 @@ __device__ __forceinline__ void load_partner(const RowArgs<T> &a, const RowCtx &
 // for the expectation values of Fig. 1, observables step.
 template <class T>
 struct StoreEmit {
+    static constexpr int kMinBlocks = 4;   // 64 registers: 32 warps per SM hide the gathers' latency
     __device__ __forceinline__ void init() {}
     __device__ __forceinline__ void put(const RowArgs<T> &a, int64_t pos, int c, T v) {
         a.col[pos] = c;
@@ -324,6 +323,7 @@ struct StoreEmit {
 // tot += L[i] * y_i (lane 0); at the end the block's tot goes to part.
 template <class T>
 struct ApplyEmit {
+    static constexpr int kMinBlocks = 1;
     const double *R = nullptr;   // right vectors [dim][8], gathered by column
     const double *L = nullptr;   // left vectors [dim][8], one row per row end
     double acc[8], tot[8];
@@ -366,7 +366,7 @@ struct ApplyEmit {
 };
 
 template <class T, class Emit>
-__global__ void __launch_bounds__(256) k_rows(const RowArgs<T> *args, const int64_t *row_off, int G, Emit em,
+__global__ void __launch_bounds__(256, Emit::kMinBlocks) k_rows(const RowArgs<T> *args, const int64_t *row_off, int G, Emit em,
                                               double *part) {
     em.init();
     const int lane = threadIdx.x & 31;
@@ -540,6 +540,7 @@ void fill_group(const std::vector<Problem *> &ps, GroupCSR *g, cudaStream_t s) {
 // stored), written to Y [dim][8]: the FP64 product of the Ritz refinement.
 template <class T>
 struct ProductEmit {
+    static constexpr int kMinBlocks = 1;
     const double *R = nullptr;   // [dim][8], gathered by column
     double *Y = nullptr;         // [dim][8]
     double acc[8];

@@ -141,10 +141,10 @@ int sm_count();
 
 // ------------------------------------------------------------------ bits
 
-constexpr int kMaxWords = 2;   // S <= 128
+constexpr int kMaxWords = 4;   // S <= 256
 constexpr int kMaxA = 16;      // particles per species
 
-// Bit string of one species determinant (W <= 2 words).
+// Bit string of one species determinant (W <= 4 words).
 struct Bits {
     uint64_t w[kMaxWords];
 };

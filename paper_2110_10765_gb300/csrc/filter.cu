@@ -91,7 +91,7 @@ __device__ __forceinline__ ConnEntry<T> make_entry(const FilterArgs<T> &a, int m
                 if (o[i] != ao) h += u[o[i]];
             e.info = make_info(1, par & 1, ao, co);
             if (proton) e.local = a.tr_base[co * S + ao];
-            else e.info |= (uint32_t)a.tr_idx[co * S + ao] << 17;
+            else e.info = info_with_tcol(e.info, a.tr_idx[co * S + ao]);
             e.val = h;
         } else {
             // d == 4: (a<b) -> (c<d), operator a+_c a+_d a_b a_a on the ket
@@ -118,7 +118,7 @@ __device__ __forceinline__ ConnEntry<T> make_entry(const FilterArgs<T> &a, int m
         // basis row, q, change of 2M) instead of t itself
         e.tgt = (int32_t)a.p_row_base[t];
         const int dslot = (a.twoM[t] - a.twoM[s]) / 2;
-        e.info = (e.info & 0x1FFFFu) | ((uint32_t)a.q[t] << 17) | ((uint32_t)(dslot + 64) << 25);
+        e.info = info_with_partner(e.info, a.q[t], dslot);
     }
     return e;
 }
@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(256) k_filter(const FilterArgs<T> *jobs, const
         for (int c0 = 0; c0 < nt; c0 += 32) {
             const int tl = c0 + lane;
             const bool tv = tl < nt;
-            uint64_t bt[kMaxWords] = {0ull, 0ull};
+            uint64_t bt[kMaxWords] = {};
 #pragma unroll
             for (int w = 0; w < W; ++w) bt[w] = tv ? sbits[tl * W + w] : 0ull;
             const int mt = tv ? sm2[tl] : 0;
@@ -256,13 +256,13 @@ __global__ void __launch_bounds__(256) k_entries(const FilterArgs<T> *jobs, cons
         const FilterArgs<T> &a = jobs[lo];
         const int mode = __ffs(a.modes) - 1;
         const int64_t s = gr - job_row[lo];
-        uint64_t bs[kMaxWords] = {0ull, 0ull};
+        uint64_t bs[kMaxWords] = {};
 #pragma unroll
         for (int w = 0; w < W; ++w) bs[w] = a.bits[s * W + w];
         const int64_t e1 = a.ptr[mode][s + 1];
         for (int64_t e = a.ptr[mode][s] + lane; e < e1; e += 32) {
             const int64_t t = a.tgt[e];
-            uint64_t bt[kMaxWords] = {0ull, 0ull};
+            uint64_t bt[kMaxWords] = {};
             int d = 0;
 #pragma unroll
             for (int w = 0; w < W; ++w) {
@@ -289,19 +289,32 @@ static void launch_entries(const std::vector<FilterArgs<T>> &jobs, cudaStream_t 
 }
 
 template <class T>
+static void launch_entries_all(const std::vector<FilterArgs<T>> (&ejw)[kMaxWords], cudaStream_t s) {
+    launch_entries<T, 1>(ejw[0], s);
+    launch_entries<T, 2>(ejw[1], s);
+    launch_entries<T, 3>(ejw[2], s);
+    launch_entries<T, 4>(ejw[3], s);
+}
+
+template <class T>
 static void filter_pass(const std::vector<FilterArgs<T>> &jobs, int pass, cudaStream_t s) {
     // rows per warp: 2 only when that still leaves every SM 16 blocks of
     // 8 warps (the sweep is latency bound, so more warps beat more reuse)
-    std::vector<FilterArgs<T>> j1, j2;
+    std::vector<FilterArgs<T>> jw[kMaxWords];
     int64_t rows = 0;
     for (auto &j : jobs) {
         if (j.n == 0) continue;
-        (j.W == 1 ? j1 : j2).push_back(j);
+        jw[j.W - 1].push_back(j);
         rows += j.n;
     }
     const bool wide = rows >= (int64_t)sm_count() * 16 * 16;
-    if (wide) { launch_filter<T, 1, 2>(j1, pass, s); launch_filter<T, 2, 2>(j2, pass, s); }
-    else { launch_filter<T, 1, 1>(j1, pass, s); launch_filter<T, 2, 1>(j2, pass, s); }
+    if (wide) {
+        launch_filter<T, 1, 2>(jw[0], pass, s); launch_filter<T, 2, 2>(jw[1], pass, s);
+        launch_filter<T, 3, 2>(jw[2], pass, s); launch_filter<T, 4, 2>(jw[3], pass, s);
+    } else {
+        launch_filter<T, 1, 1>(jw[0], pass, s); launch_filter<T, 2, 1>(jw[1], pass, s);
+        launch_filter<T, 3, 1>(jw[2], pass, s); launch_filter<T, 4, 1>(jw[3], pass, s);
+    }
 }
 
 // Segment tables of one problem's lists (c: a cap on q, ds: a 2M slot,
@@ -540,15 +553,14 @@ void species_filter_group(const std::vector<Problem *> &ps_in, cudaStream_t s) {
         j.tgt = tgts->ptr;
     }
     filter_pass<T>(jobs, 1, s);
-    std::vector<FilterArgs<T>> ej1, ej2;
+    std::vector<FilterArgs<T>> ejw[kMaxWords];
     for (size_t i = 0; i < lists.size(); ++i) {
         FilterArgs<T> j = jobs[list_job[i]];
         j.modes = 1 << list_mode[i];
         j.n = lists[i]->n;
-        (j.W == 1 ? ej1 : ej2).push_back(j);
+        ejw[j.W - 1].push_back(j);
     }
-    launch_entries<T, 1>(ej1, s);
-    launch_entries<T, 2>(ej2, s);
+    launch_entries_all<T>(ejw, s);
     // segment tables
     std::vector<SegJob<T>> sj;
     std::vector<int64_t> soff(1, 0);
@@ -610,7 +622,7 @@ template <class T>
 void operator_entries(Problem *p, const Tables<T> &t, ConnEntry<T> *ents, cudaStream_t s) {
     Connectivity<T> &c = p->conn<T>();
     if (!c.ready) fail(CI_ERR_STATE, "species connectivity not built");
-    std::vector<FilterArgs<T>> ej1, ej2;
+    std::vector<FilterArgs<T>> ejw[kMaxWords];
     const ConnList<T> *ls[kModes] = {&c.outer, &c.l2, &c.l4, &c.outer4};
     for (int m = 0; m < kModes; ++m) {
         const bool prot = m == CONN_OUTER || m == CONN_O4;
@@ -619,10 +631,9 @@ void operator_entries(Problem *p, const Tables<T> &t, ConnEntry<T> *ents, cudaSt
         j.ptr[m] = ls[m]->ptr;
         j.ent = ents;
         j.tgt = const_cast<int32_t *>(ls[m]->tgt);
-        (j.W == 1 ? ej1 : ej2).push_back(j);
+        ejw[j.W - 1].push_back(j);
     }
-    launch_entries<T, 1>(ej1, s);
-    launch_entries<T, 2>(ej2, s);
+    launch_entries_all<T>(ejw, s);
 }
 
 template void operator_entries<float>(Problem *, const Tables<float> &, ConnEntry<float> *, cudaStream_t);

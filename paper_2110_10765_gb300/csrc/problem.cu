@@ -254,13 +254,14 @@ static PairGroups make_transitions(const std::vector<int32_t> &twom) {
 
 void problem_create(const ci_problem_desc *d, Problem *p) {
     if (!d) fail(CI_ERR_INVALID_ARG, "desc is NULL");
-    if (d->n_sp < 1 || d->n_sp > 128) fail(CI_ERR_INVALID_ARG, "n_sp must be 1..128 (got %d)", d->n_sp);
+    if (d->n_sp < 1 || d->n_sp > 64 * kMaxWords)
+        fail(CI_ERR_INVALID_ARG, "n_sp must be 1..%d (got %d)", 64 * kMaxWords, d->n_sp);
     if (!d->sp_N || !d->sp_twom || !d->sp_energy)
         fail(CI_ERR_INVALID_ARG, "sp_N, sp_twom and sp_energy are required");
     if (d->Z < 0 || d->N < 0 || d->Z > kMaxA || d->N > kMaxA || d->Z > d->n_sp || d->N > d->n_sp)
         fail(CI_ERR_INVALID_ARG, "Z and N must be 0..min(S,%d)", kMaxA);
     if (d->nmax < -1) fail(CI_ERR_INVALID_ARG, "nmax must be >= -1");
-    if (d->nmax > 64) fail(CI_ERR_CAPACITY, "nmax above 64 is not supported");
+    if (d->nmax > 31) fail(CI_ERR_CAPACITY, "nmax above 31 is not supported");
     if (d->tbme_source != CI_TBME_TABLES && d->tbme_source != CI_TBME_SEED)
         fail(CI_ERR_INVALID_ARG, "tbme_source must be CI_TBME_TABLES or CI_TBME_SEED");
     if (d->tbme_source == CI_TBME_TABLES) {
@@ -295,6 +296,8 @@ void problem_create(const ci_problem_desc *d, Problem *p) {
         }
     }
     PairGroups lg = make_like_pairs(p->sp_twom), tg = make_transitions(p->sp_twom);
+    for (int32_t c : tg.col)
+        if (c >= kMaxTcol) fail(CI_ERR_CAPACITY, "a 2m-transfer class holds more than %d one-particle moves", kMaxTcol);
     p->like_row.upload(lg.row, s); p->like_col.upload(lg.col, s);
     p->tr_base.upload(tg.row, s); p->tr_idx.upload(tg.col, s);
     p->like_size = lg.grp_off.back();
@@ -433,7 +436,7 @@ static void enumerate_species(const Problem *p, int A, SpeciesList *L) {
     }
     const int nmin = suffix_min[0][A];
     const int64_t cap = 1ll << 26;
-    struct Tmp { int twoM, q; uint64_t w[2]; uint8_t occ[kMaxA]; };
+    struct Tmp { int twoM, q; uint64_t w[kMaxWords]; uint8_t occ[kMaxA]; };
     struct Walk {
         const Problem *p;
         const std::vector<std::vector<int>> &suffix_min;
@@ -446,7 +449,7 @@ static void enumerate_species(const Problem *p, int A, SpeciesList *L) {
                 Tmp t;
                 t.twoM = msum;
                 t.q = Nsum - nmin;
-                t.w[0] = t.w[1] = 0;
+                for (int w = 0; w < kMaxWords; ++w) t.w[w] = 0;
                 for (int k = 0; k < A; ++k) { t.occ[k] = occ[k]; t.w[occ[k] >> 6] |= 1ull << (occ[k] & 63); }
                 out.push_back(t);
                 if ((int64_t)out.size() > cap) fail(CI_ERR_CAPACITY, "species list larger than 2^26 determinants");
@@ -467,7 +470,8 @@ static void enumerate_species(const Problem *p, int A, SpeciesList *L) {
     std::sort(out.begin(), out.end(), [](const Tmp &x, const Tmp &y) {
         if (x.twoM != y.twoM) return x.twoM < y.twoM;
         if (x.q != y.q) return x.q < y.q;
-        if (x.w[1] != y.w[1]) return x.w[1] < y.w[1];
+        for (int w = kMaxWords - 1; w > 0; --w)
+            if (x.w[w] != y.w[w]) return x.w[w] < y.w[w];
         return x.w[0] < y.w[0];
     });
     L->n = (int64_t)out.size();

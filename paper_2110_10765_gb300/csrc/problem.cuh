@@ -59,10 +59,11 @@ struct Tables {
 
 // One entry of a species connectivity list (row determinant s = bra,
 // partner s' = ket).  info: bits 0-1 difference code (0: d=0, 1: d=2,
-// 2: d=4), bit 2 sign (1: negative), bits 3-9 state a (in s' only), bits
-// 10-16 state c (in s only).  Neutron lists: bits 17-31 of d=2 entries hold
-// the column index of the move a -> c in the pn transition table.  Proton
-// list: bits 17-24 hold q(s'), bits 25-31 (2M(s') - 2M(s))/2 + 64.
+// 2: d=4), bit 2 sign (1: negative), bits 3-10 state a (in s' only), bits
+// 11-18 state c (in s only).  Neutron lists: bits 19-31 of d=2 entries hold
+// the column index of the move a -> c in the pn transition table (< 8192).
+// Proton list: bits 19-23 hold q(s') (capped at 31; only read under an
+// Nmax cut, which is <= 31), bits 24-31 (2M(s') - 2M(s))/2 + 128.
 // tgt: neutron lists, the partner s'; proton list, the first basis row of
 // s' (p_row_base[s']), the partner index itself being kept in ConnList::tgt.
 // local: neutron lists, index of s' inside its 2M block; proton list, for
@@ -77,15 +78,21 @@ struct ConnEntry {
     T val;
 };
 
+constexpr int kMaxTcol = 1 << 13;   // pn transition-table columns an entry can address
+
 __host__ __device__ inline int info_dcode(uint32_t i) { return (int)(i & 3u); }
 __host__ __device__ inline int info_neg(uint32_t i) { return (int)((i >> 2) & 1u); }
-__host__ __device__ inline int info_a(uint32_t i) { return (int)((i >> 3) & 127u); }
-__host__ __device__ inline int info_c(uint32_t i) { return (int)((i >> 10) & 127u); }
-__host__ __device__ inline int info_tcol(uint32_t i) { return (int)(i >> 17); }
-__host__ __device__ inline int info_q(uint32_t i) { return (int)((i >> 17) & 255u); }
-__host__ __device__ inline int info_dslot(uint32_t i) { return (int)(i >> 25) - 64; }
+__host__ __device__ inline int info_a(uint32_t i) { return (int)((i >> 3) & 255u); }
+__host__ __device__ inline int info_c(uint32_t i) { return (int)((i >> 11) & 255u); }
+__host__ __device__ inline int info_tcol(uint32_t i) { return (int)(i >> 19); }
+__host__ __device__ inline int info_q(uint32_t i) { return (int)((i >> 19) & 31u); }
+__host__ __device__ inline int info_dslot(uint32_t i) { return (int)(i >> 24) - 128; }
 __host__ __device__ inline uint32_t make_info(int dcode, int neg, int a, int c) {
-    return (uint32_t)dcode | ((uint32_t)neg << 2) | ((uint32_t)a << 3) | ((uint32_t)c << 10);
+    return (uint32_t)dcode | ((uint32_t)neg << 2) | ((uint32_t)a << 3) | ((uint32_t)c << 11);
+}
+__host__ __device__ inline uint32_t info_with_tcol(uint32_t i, int tcol) { return i | ((uint32_t)tcol << 19); }
+__host__ __device__ inline uint32_t info_with_partner(uint32_t i, int q, int dslot) {
+    return (i & 0x7FFFFu) | ((uint32_t)(q < 31 ? q : 31) << 19) | ((uint32_t)(dslot + 128) << 24);
 }
 
 // A species list inside a group allocation: ptr [n+1] holds absolute

@@ -350,7 +350,7 @@ ci_status ci_submit(ci_queue *q, const ci_request *req, uint64_t *ticket) {
         if (!q || !req || !ticket) fail(CI_ERR_INVALID_ARG, "queue, request and ticket are required");
         Queue &Q = q->impl;
         const ci_problem_desc &d = req->desc;
-        if (d.n_sp < 1 || d.n_sp > 128 || !d.sp_N || !d.sp_twom || !d.sp_energy)
+        if (d.n_sp < 1 || d.n_sp > 64 * kMaxWords || !d.sp_N || !d.sp_twom || !d.sp_energy)
             fail(CI_ERR_INVALID_ARG, "bad s.p. table");
         if (req->k < 1 || req->k > EKMAX || 2 * (req->k + EB) > Q.d.max_basis)
             fail(CI_ERR_INVALID_ARG, "k must be 1..%d with 2(k+8) <= max_basis", EKMAX);

@@ -472,7 +472,7 @@ def _sp128():
 
 
 def test_maximum_sp_states_seeded_tables():
-    """S = 128 (the ABI's maximum, both 64-bit words full) with TBMEs from the
+    """S = 128 (two 64-bit words, both full) with TBMEs from the
     seeded generator (no flat tables): one proton and one neutron, no Nmax
     cut, so every basis pair is within four differences.  The matrix is
     symmetric, dense, and the solver agrees with LAPACK on it."""
@@ -492,6 +492,48 @@ def test_maximum_sp_states_seeded_tables():
     ev, info = M.lowest_eigs(k=5)
     ref = np.linalg.eigvalsh(H)[:5]
     assert np.allclose(ev, ref, rtol=0, atol=1e-8 * np.abs(ref).max())
+
+
+def _sp_first(n_shell, S):
+    import synth
+    return {k: v[:S].copy() for k, v in synth.ho_sp_table(n_shell).items()}
+
+
+@pytest.mark.parametrize("case", [(6, 168, 2, 2, 6, 0), (7, 240, 2, 1, 7, 1), (8, 256, 1, 2, 8, 1),
+                                  (7, 200, 1, 1, -1, 0)])
+def test_sp_states_above_128(case):
+    """S = 168, 200, 240, 256 s.p. states (three and four 64-bit words; HO
+    shells up to N = 8) with TBMEs drawn by the counter-based generator on
+    both sides: species lists bit-exact, the whole CSR pattern bit-exact,
+    FP64 and FP32 values within their bounds, the SpMM, and the lowest
+    eigenvalues against the oracle's Lanczos."""
+    n_shell, S, Z, N, nmax, twoM = case
+    sp = _sp_first(n_shell, S)
+    import synth
+    eps = synth.sp_energies(sp, 20.0)
+    o = oracle.OracleProblem(sp, Z, N, nmax, twoM, eps, seed=31, round_f32=False)   # exact draws
+    g = gpu_problem(dict(sp=sp, Z=Z, N=N, nmax=nmax, twoM=twoM, eps=eps), seed=31)
+    assert g.enumerate_basis() == o.dim > 0
+    W = (S + 63) // 64
+    for s in (0, 1):
+        _species_eq(o, g, s)
+        assert g.species(s)["bits"].shape[1] == W
+    occ = np.concatenate([o.species(0)["occ"].ravel(), o.species(1)["occ"].ravel()])
+    assert occ.max() >= 64 * (W - 1)                        # the top word is in use
+    M = g.build_H("f64")
+    rp, col, val = _check_matrix(o, M, REL64)
+    M32 = g.build_H("f32")
+    _check_matrix(o, M32, REL32)
+    X = np.random.default_rng(2).standard_normal((o.dim, 8))
+    Y = torch.empty((o.dim, 8), dtype=torch.float64, device="cuda")
+    M.apply_H(torch.from_numpy(X).cuda(), Y)
+    orp, ocol, oval, oab = o.csr()
+    ref = oracle.spmm(orp, ocol, oval, X)
+    bound = oracle.spmm(orp, ocol, np.maximum(np.abs(oval), oab), np.abs(X))
+    assert np.all(np.abs(Y.cpu().numpy() - ref) <= 1e-11 * bound + 1e-300)
+    ev, info = M.lowest_eigs(k=4)
+    ref_ev = oracle.lowest_sparse(orp, ocol, oval, o.dim, 4)
+    assert np.allclose(ev, ref_ev, rtol=0, atol=1e-8 * max(1.0, np.abs(ref_ev).max()))
 
 
 def test_maximum_sp_states_zero_interaction_closed_form():
