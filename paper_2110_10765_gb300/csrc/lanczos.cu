@@ -1415,8 +1415,17 @@ extern "C" ci_status ci_basis_product(int32_t op, int32_t method, int64_t n, con
             } else {
                 const int nblk = method == CI_PRODUCT_TC ? oz_tn_blocks(n)
                                                          : (int)std::min<int64_t>(2 * sm_count(), (n + 63) / 64);
-                DevBuf<double> part((size_t)nblk * na * nb);
-                if (method == CI_PRODUCT_TC) oz_tn(n, Y.ptr, ldy, na, B, ldb, part.ptr, nblk, flag.ptr, s);
+                DevBuf<double> part((size_t)nblk * na * nb), Bc;
+                const double *Bt = B;
+                int ldbt = ldb;
+                if (method == CI_PRODUCT_TC && (ldb & 1)) {   // the tensor copies want an even row stride
+                    Bc.alloc((size_t)n * 8);
+                    launch("k_copy_cols", k_copy_cols, grid_for((int64_t)n * 8, 256, sm_count() * 8), 256, 0, s,
+                           (int64_t)n, 8, B, ldb, Bc.ptr, 8);
+                    Bt = Bc.ptr;
+                    ldbt = 8;
+                }
+                if (method == CI_PRODUCT_TC) oz_tn(n, Y.ptr, ldy, na, Bt, ldbt, part.ptr, nblk, flag.ptr, s);
                 else fp64_tn(n, A, lda, na, B, ldb, nb, part.ptr, nblk, (n + nblk - 1) / nblk, s);
                 launch("k_reduce_partial", k_reduce_partial, (na * nb + 7) / 8, 256, 0, s, part.ptr, nblk, na * nb, C);
             }

@@ -276,8 +276,10 @@ void h64_apply(Problem *p, const double *R8, double *Y8, cudaStream_t s);
 void apply_matrix(const Matrix *m, const void *X, void *Y, int nvec, cudaStream_t s);
 // FP64-exact products on the tensor cores (ozaki.cu) for a basis A of
 // na <= 64 orthonormal columns (|A| < 1.99), read in its fixed-point
-// shadow form Y (oz_fix; 16-byte aligned rows, even ldy):
-//   oz_tn: part[blk][na][8] = A[rows of blk]^T B over nblk row blocks
+// shadow form Y (oz_fix; even ldy, so rows are 16-byte aligned; A may start
+// at an odd column).
+//   oz_tn: part[blk][na][8] = A[rows of blk]^T B over nblk row blocks (B
+//          8-byte aligned, ldb even)
 //   oz_nn: W = beta W + alpha A C, C [na][8]
 // An entry outside the digits' range sets bit 0 of *flag, a tensor-core
 // wait that ran out bit 1.

@@ -52,6 +52,35 @@ __device__ __forceinline__ void mbar_init(uint64_t *mbar, uint32_t count) {
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
 }
 
+// One arrival of this thread (release: its earlier shared-memory writes are
+// visible to whoever waits on the phase).
+__device__ __forceinline__ void mbar_arrive(uint64_t *mbar) {
+    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];\n" ::"r"(smem_addr(mbar)) : "memory");
+}
+
+// One arrival that also announces `bytes` of bulk copies completing on the
+// current phase.
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(mbar)), "r"(bytes)
+                 : "memory");
+}
+
+// Tensor (TMA) copy of the box at column x (x * element size a multiple of
+// 16 bytes), row y of a 2-D tensor map into shared memory, completing on the
+// mbarrier; elements outside the tensor are filled with zeros.
+__device__ __forceinline__ void tma_2d(void *dst_smem, const void *map, int x, int y, uint64_t *mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(
+            smem_addr(dst_smem)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(mbar))
+        : "memory");
+}
+
+// Barrier `id` (1..15) over `nthreads` threads (whole warps) of the CTA.
+__device__ __forceinline__ void named_sync(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(nthreads) : "memory");
+}
+
 // Wait for phase `parity` of the mbarrier to complete, at most max_iter
 // polls; returns false when the limit ran out.
 __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, int max_iter) {
@@ -81,62 +110,60 @@ __device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence
 // Generic-proxy stores to shared memory become visible to the tensor core.
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
 
-// 64 consecutive 32-bit TMEM columns of this thread's lane (warp w reads
-// lanes 32 (w % 4) .. 32 (w % 4) + 31), waited for before the values are
-// returned.
-__device__ __forceinline__ void ld64(uint32_t taddr, float v[64]) {
-    uint32_t r[64];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];\n"
-        "tcgen05.wait::ld.sync.aligned;\n"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
-        : "r"(taddr)
-        : "memory");
+// NV (2 or 4) consecutive columns at each of taddr + 8 t (t = 0..7) of this
+// thread's lane, waited for: v[NV t + c] = column taddr + 8 t + c.
+template <int NV>
+__device__ __forceinline__ void ld8xN(uint32_t taddr, float v[8 * NV]) {
+    static_assert(NV == 2 || NV == 4, "two or four columns");
+    uint32_t r[8 * NV];
+    if constexpr (NV == 4) {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%32 + 0];\n"
+            "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%4,%5,%6,%7}, [%32 + 8];\n"
+            "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%8,%9,%10,%11}, [%32 + 16];\n"
+            "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%12,%13,%14,%15}, [%32 + 24];\n"
+            "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%16,%17,%18,%19}, [%32 + 32];\n"
+            "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%20,%21,%22,%23}, [%32 + 40];\n"
+            "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%24,%25,%26,%27}, [%32 + 48];\n"
+            "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%28,%29,%30,%31}, [%32 + 56];\n"
+            "tcgen05.wait::ld.sync.aligned;\n"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+            : "r"(taddr)
+            : "memory");
+    } else {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%16 + 0];\n"
+            "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%2,%3}, [%16 + 8];\n"
+            "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%4,%5}, [%16 + 16];\n"
+            "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%6,%7}, [%16 + 24];\n"
+            "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%8,%9}, [%16 + 32];\n"
+            "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%10,%11}, [%16 + 40];\n"
+            "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%12,%13}, [%16 + 48];\n"
+            "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%14,%15}, [%16 + 56];\n"
+            "tcgen05.wait::ld.sync.aligned;\n"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(taddr)
+            : "memory");
+    }
 #pragma unroll
-    for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
+    for (int i = 0; i < 8 * NV; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Four consecutive columns at each of taddr + 8 j (j = 0..7) of this
-// thread's lane, waited for before the values are returned:
-// v[4 j + c] = column taddr + 8 j + c.
-__device__ __forceinline__ void ld8x4(uint32_t taddr, float v[32]) {
+// Eight consecutive columns at each of taddr + 64 p (p = 0..3) of this
+// thread's lane, waited for: v[8 p + c] = column taddr + 64 p + c.
+__device__ __forceinline__ void ld4x8(uint32_t taddr, float v[32]) {
     uint32_t r[32];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%32 + 0];\n"
-        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%4,%5,%6,%7}, [%32 + 8];\n"
-        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%8,%9,%10,%11}, [%32 + 16];\n"
-        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%12,%13,%14,%15}, [%32 + 24];\n"
-        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%16,%17,%18,%19}, [%32 + 32];\n"
-        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%20,%21,%22,%23}, [%32 + 40];\n"
-        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%24,%25,%26,%27}, [%32 + 48];\n"
-        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%28,%29,%30,%31}, [%32 + 56];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%32 + 0];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%32 + 64];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16,%17,%18,%19,%20,%21,%22,%23}, [%32 + 128];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%24,%25,%26,%27,%28,%29,%30,%31}, [%32 + 192];\n"
         "tcgen05.wait::ld.sync.aligned;\n"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(taddr)
         : "memory");
 #pragma unroll
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// Two consecutive columns at each of taddr + 8 j (j = 0..7) of this
-// thread's lane, waited for: v[2 j + c] = column taddr + 8 j + c.
-__device__ __forceinline__ void ld8x2(uint32_t taddr, float v[16]) {
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%16 + 0];\n"
-        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%2,%3}, [%16 + 8];\n"
-        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%4,%5}, [%16 + 16];\n"
-        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%6,%7}, [%16 + 24];\n"
-        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%8,%9}, [%16 + 32];\n"
-        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%10,%11}, [%16 + 40];\n"
-        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%12,%13}, [%16 + 48];\n"
-        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%14,%15}, [%16 + 56];\n"
-        "tcgen05.wait::ld.sync.aligned;\n"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr)
-        : "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 }  // namespace tc

@@ -73,6 +73,56 @@ def test_nn_tensor_cores_fp64_accuracy(n, na, beta):
         assert np.all(err <= bound), (method, float(np.max(err / bound)))
 
 
+@pytest.mark.parametrize("na", [5, 40, 64])
+def test_tensor_core_products_long_rows(na):
+    """400,003 rows: every SM's share of A^T B spans several 1024-row
+    accumulation segments, and W = W - A C runs through the stage ring and
+    both accumulators many times per SM."""
+    import paper_2110_10765_gb300 as ci
+    n = 400_003
+    rng = np.random.default_rng(na)
+    A = rng.uniform(-1, 1, (n, na)) / np.sqrt(n)
+    B = _vectors(n, rng)
+    Ad = torch.zeros((n, 64), dtype=torch.float64, device="cuda")
+    Ad[:, :na] = torch.from_numpy(A)
+    Bd = torch.from_numpy(B).cuda()
+    C = torch.full((na, 8), float("nan"), dtype=torch.float64, device="cuda")
+    ci.basis_product("tn", Ad[:, :na], Bd, C, method="tc")
+    ref = _tn_ref(A, B)
+    bound = 8 * U * _tn_ref(np.abs(A), np.abs(B)) + n * 2.0 ** -58 * np.abs(A).max() * np.abs(B).max(axis=0)
+    err = np.abs(C.cpu().numpy().astype(np.longdouble) - ref)
+    assert np.all(err <= bound), float(np.max(err / bound))
+    Cm = rng.standard_normal((na, 8))
+    W = torch.from_numpy(B).cuda()
+    ci.basis_product("nn", Ad[:, :na], W, torch.from_numpy(Cm).cuda(), alpha=-1.0, beta=1.0, method="tc")
+    rows = np.concatenate([np.arange(300), rng.choice(n, 3000, replace=False), np.arange(n - 300, n)])
+    AC = np.einsum("ku,uv->kv", A[rows].astype(np.longdouble), Cm.astype(np.longdouble))
+    refw = B[rows].astype(np.longdouble) - AC
+    bw = 8 * U * (np.abs(B[rows]) + np.abs(A[rows]) @ np.abs(Cm)) + na * 2.0 ** -58 * np.abs(Cm).max(axis=0)[None, :]
+    errw = np.abs(W.cpu().numpy()[rows].astype(np.longdouble) - refw)
+    assert np.all(errw <= bw), float(np.max(errw / bw))
+
+
+@pytest.mark.parametrize("col0", [0, 1])
+def test_tn_tensor_cores_strided_operands(col0):
+    """A^T B with B a column slice of a wider array (odd row stride) and A
+    starting at an odd or even column of its own wider array."""
+    import paper_2110_10765_gb300 as ci
+    n, na = 7001, 21
+    rng = np.random.default_rng(7 + col0)
+    A = rng.uniform(-1, 1, (n, na)) / np.sqrt(n)
+    Bw = rng.standard_normal((n, 9))
+    Ad = torch.zeros((n, 40), dtype=torch.float64, device="cuda")
+    Ad[:, col0:col0 + na] = torch.from_numpy(A)
+    Bd = torch.from_numpy(Bw).cuda()
+    C = torch.full((na, 8), float("nan"), dtype=torch.float64, device="cuda")
+    ci.basis_product("tn", Ad[:, col0:col0 + na], Bd[:, 1:9], C, method="tc")
+    ref = _tn_ref(A, Bw[:, 1:9])
+    bound = 8 * U * _tn_ref(np.abs(A), np.abs(Bw[:, 1:9])) + n * 2.0 ** -58 * np.abs(Bw).max()
+    err = np.abs(C.cpu().numpy().astype(np.longdouble) - ref)
+    assert np.all(err <= bound), float(np.max(err / bound))
+
+
 def test_tensor_core_product_range_and_shapes():
     import paper_2110_10765_gb300 as ci
     A = torch.zeros((300, 64), dtype=torch.float64, device="cuda")
