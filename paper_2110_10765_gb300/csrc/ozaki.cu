@@ -472,20 +472,21 @@ __global__ void __launch_bounds__(kNnThreads, 1) k_oz_nn(const __grid_constant__
 
 // One CTA per SM sums its contiguous rows [q0, q1) of A^T B, in 64-row
 // stages (the MMA's K) grouped into segments of at most 1024 rows.  The M
-// dimension of an operand stacks two digit planes of A^T (M-row 64 h + m
-// holds plane 2 p + h of column m; operand p = 0..3), the B operand holds
+// dimension of an operand stacks PP = 128 / MC digit planes of A^T, MC =
+// 16, 32 or 64 the columns of A rounded up (M-row MC h + m holds plane
+// PP p + h of column m; operands p = 0 .. 8 / PP - 1), the B operand holds
 // the digit planes of the eight vectors side by side (N = 8 n + j).
-// Accumulator p of a segment (TMEM columns 64 p ..) collects D[2p + h][m][n][j]
+// Accumulator p of a segment (TMEM columns 64 p ..) collects D[PP p + h][m][n][j]
 // over the segment's rows; at most 1024 rows keep |D| <= 2^24 exact.  Two
 // segment accumulators (2 x 256 columns) alternate, so the epilogue of a
 // segment runs while the next one is multiplied.  Roles as in k_oz_nn: the
 // loader copies a stage's rows of the shadow, converters (8 warps) cut them
 // and the stage's rows of B into the digit planes (two plane stages), one
 // thread issues the MMAs, four epilogue warps (one TMEM lane each: plane
-// parity h, column m) add up the plane pairs of equal weight i + j <= 7 of a
+// offset h, column m) add up the plane pairs of equal weight i + j <= 7 of a
 // segment in 32-bit integers and keep the weighted sum over segments in
-// 128-bit integers; at the end the two parities are added and the block's
-// part is rounded once.
+// 128-bit integers; at the end the lanes of a column are added and the
+// block's part is rounded once.
 constexpr int kTnConvWarps = 8;
 constexpr int kTnEpiWarps = 4;
 constexpr int kTnThreads = 32 * (kTnConvWarps + kTnEpiWarps + 2);   // + MMA warp + loader warp
@@ -499,6 +500,7 @@ constexpr uint32_t kTnRawBytes = 83968u;   // the raw ring: A's rows and B's row
 // ymap: boxes of bc columns x 64 rows of the shadow; bmap: boxes of bw
 // columns x 64 rows of B from its 16-byte aligned column at or below B's
 // first (B's vector n at raw column n + mb).
+template <int MC>
 __global__ void __launch_bounds__(kTnThreads, 1) k_oz_tn(const __grid_constant__ CUtensorMap ymap,
                                                   const __grid_constant__ CUtensorMap bmap, int m, int bc, int mb,
                                                   int bw, int64_t dim, int na, const double *__restrict__ B, int ldb,
@@ -509,8 +511,11 @@ __global__ void __launch_bounds__(kTnThreads, 1) k_oz_tn(const __grid_constant__
     __shared__ int emax[8];
     __shared__ volatile int abort_;
     unsigned char *raw = sm + 2 * kTnStage;
-    __int128 *red = reinterpret_cast<__int128 *>(raw);   // [64][8]: the h = 1 sums, once the ring is idle
+    __int128 *red = reinterpret_cast<__int128 *>(raw);   // [PP - 1][MC][8]: the h >= 1 sums, once the ring is idle
     constexpr int KG = kOzTnRows / 8;
+    constexpr int PP = 128 / MC, NOP = 8 / PP;             // planes per operand, operands
+    constexpr int ITEMS = 8 * MC;                          // (column, 8-row group) pieces of a stage
+    constexpr int NIT = (ITEMS + 32 * kTnConvWarps - 1) / (32 * kTnConvWarps);
     const uint32_t stride = 8u * (uint32_t)bc;
     const uint32_t aslot = kOzTnRows * stride, slotb = aslot + kOzTnRows * 8u * (uint32_t)bw;
     const int R = min(kMaxRaw, (int)(kTnRawBytes / slotb));
@@ -566,10 +571,9 @@ __global__ void __launch_bounds__(kTnThreads, 1) k_oz_tn(const __grid_constant__
     for (int n = 0; n < 8; ++n) sc[n] = emax[n] < -10000 ? 0 : emax[n] + 1;
 
     if (warp < kTnConvWarps) {
-        // ---- converters: A columns cp and cp + 32 of stage rows 8 rg .. 8 rg + 7; B vector bn of rows brl, brl + 1
-        const int cp = tid & 31, rg = tid >> 5;
+        // ---- converters: A pieces it = tid + 256 u (column it % MC of stage rows 8 (it / MC) ..
+        // + 7); B vector bn of rows brl, brl + 1
         const int bn = tid & 7, brl = 2 * (tid >> 3);
-        const bool ok0 = cp < na, ok1 = cp + 32 < na;
         for (int s = 0; s < nst; ++s) {
             const int slot = s % R, pst = s & 1;
             if (abort_ || !pipe_wait(&rfull[slot], (s / R) & 1, &abort_, flag)) break;
@@ -577,30 +581,31 @@ __global__ void __launch_bounds__(kTnThreads, 1) k_oz_tn(const __grid_constant__
             const unsigned char *rb = raw + slot * slotb + aslot + 8 * (bn + mb);   // B rows (zero past dim)
             const double wa = t0 + brl < q1 ? *reinterpret_cast<const double *>(rb + brl * (8 * bw)) : 0.0;
             const double wb = t0 + brl + 1 < q1 ? *reinterpret_cast<const double *>(rb + (brl + 1) * (8 * bw)) : 0.0;
-            const unsigned char *rs = raw + slot * slotb + (8 * rg) * stride + 8 * (cp + m);
-            unsigned long long y0[8], y1[8];
+            unsigned long long y[NIT][8];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                y0[k] = ok0 ? *reinterpret_cast<const unsigned long long *>(rs + k * stride) : kBias;
-                y1[k] = ok1 ? *reinterpret_cast<const unsigned long long *>(rs + k * stride + 256) : kBias;
+            for (int u = 0; u < NIT; ++u) {
+                const int it = tid + 32 * kTnConvWarps * u, mc = it % MC;
+                if (it >= ITEMS || mc >= na) continue;
+                const unsigned char *rs = raw + slot * slotb + (8 * (it / MC)) * stride + 8 * (mc + m);
+#pragma unroll
+                for (int k = 0; k < 8; ++k) y[u][k] = *reinterpret_cast<const unsigned long long *>(rs + k * stride);
             }
             tc::mbar_arrive(&rempty[slot]);
             if (s >= 2 && !pipe_wait(&empty[pst], ((s >> 1) - 1) & 1, &abort_, flag)) break;
             unsigned char *sa = sm + pst * kTnStage, *sb = sa + 4 * kTnAop;
             // the 8 rows of column mc are one 16-byte row of each plane; plane i of
-            // column mc sits in operand i >> 1 at M-row 64 (i & 1) + mc
+            // column mc sits in operand i / PP at M-row MC (i % PP) + mc
 #pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                if (!(c ? ok1 : ok0)) continue;
-                const unsigned long long *y = c ? y1 : y0;
-                uint32_t h[4][8];
+            for (int u = 0; u < NIT; ++u) {
+                const int it = tid + 32 * kTnConvWarps * u, mc = it % MC, rg = it / MC;
+                if (it >= ITEMS || mc >= na) continue;
+                uint32_t hp[4][8];
 #pragma unroll
-                for (int p = 0; p < 4; ++p) oz_pack2(y[2 * p], y[2 * p + 1], h[p]);
-                const int mc = cp + 32 * c;
+                for (int p = 0; p < 4; ++p) oz_pack2(y[u][2 * p], y[u][2 * p + 1], hp[p]);
 #pragma unroll
                 for (int i = 0; i < 8; ++i)
-                    *reinterpret_cast<uint4 *>(sa + (i >> 1) * kTnAop + tile_off(64 * (i & 1) + mc, 8 * rg, KG)) =
-                        make_uint4(h[0][i], h[1][i], h[2][i], h[3][i]);
+                    *reinterpret_cast<uint4 *>(sa + (i / PP) * kTnAop + tile_off(MC * (i % PP) + mc, 8 * rg, KG)) =
+                        make_uint4(hp[0][i], hp[1][i], hp[2][i], hp[3][i]);
             }
             int bad = 0;
             uint32_t h[8];
@@ -612,10 +617,10 @@ __global__ void __launch_bounds__(kTnThreads, 1) k_oz_tn(const __grid_constant__
             tc::mbar_arrive(&full[pst]);
         }
     } else if (warp < kTnConvWarps + kTnEpiWarps) {
-        // ---- epilogue: TMEM lane L = 32 q + lane is (h = L >> 6, column m = L & 63); it holds
-        // D[i][m][n][j] of the planes i = 2 p + h at columns 256 buf + 64 p + 8 n + j
+        // ---- epilogue: TMEM lane L = 32 q + lane is (h = L / MC, column m = L % MC); it holds
+        // D[i][m][n][j] of the planes i = PP p + h at columns 256 buf + 64 p + 8 n + j
         const int q = warp - kTnConvWarps;
-        const int L = 32 * q + lane, h = L >> 6, mc = L & 63;
+        const int L = 32 * q + lane, h = L / MC, mc = L % MC;
         __int128 acc[8];
 #pragma unroll
         for (int n = 0; n < 8; ++n) acc[n] = 0;
@@ -625,43 +630,44 @@ __global__ void __launch_bounds__(kTnThreads, 1) k_oz_tn(const __grid_constant__
             tc::fence_after_sync();
 #pragma unroll 1
             for (int n = 0; n < 8; ++n) {
-                float v[32];   // v[8 p + j] = D[2 p + h][mc][n][j]
+                float v[32];   // v[8 p + j] = D[PP p + h][mc][n][j] (p < NOP)
                 tc::ld4x8(tmem + ((uint32_t)(32 * q) << 16) + 256u * buf + 8u * n, v);
-                // U_k = sum over the pairs with 2 p + j = k, i.e. i + j = k + h, of the
+                // U_k = sum over the pairs with PP p + j = k, i.e. i + j = k + h, of the
                 // segment's exact integer sums (|U_k| <= 4 * 2^24); the pairs with
                 // i + j > 7 lie below the digits' resolution and are left out
                 int U[8];
 #pragma unroll
                 for (int k = 0; k < 8; ++k) U[k] = 0;
 #pragma unroll
-                for (int p = 0; p < 4; ++p)
+                for (int p = 0; p < NOP; ++p)
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
-                        const int k = 2 * p + j;
+                        const int k = PP * p + j;
                         if (k <= 7 && k <= 7 - h) U[k] += __float2int_rn(v[8 * p + j]);
                     }
                 // sum_k U_k 2^(56 - 8 k) = I 2^24 + R; in units of 2^(s_n - 68) the
-                // pairs contribute that times 2^(-8 h) (exact: U_7 = 0 when h = 1)
+                // pairs contribute that times 2^(-8 h) (exact: U_k = 0 for k > 7 - h)
                 const long long I = ((long long)U[0] << 32) + ((long long)U[1] << 24) + ((long long)U[2] << 16) +
                                     ((long long)U[3] << 8) + (long long)U[4];
                 const long long Rr = ((long long)U[5] << 16) + ((long long)U[6] << 8) + (long long)U[7];
                 __int128 x = ((__int128)I << 24) + (__int128)Rr;
-                if (h) x >>= 8;
+                x >>= 8 * h;
                 acc[n] += x;
             }
             tc::fence_before_sync();
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(&tempty[buf]);
         }
-        if (h == 1) {
+        if (h > 0) {
 #pragma unroll
-            for (int n = 0; n < 8; ++n) red[mc * 8 + n] = acc[n];
+            for (int n = 0; n < 8; ++n) red[((h - 1) * MC + mc) * 8 + n] = acc[n];
         }
         tc::named_sync(1, 32 * kTnEpiWarps);
         if (h == 0 && mc < na) {
 #pragma unroll
             for (int n = 0; n < 8; ++n) {
-                const __int128 t = acc[n] + red[mc * 8 + n];
+                __int128 t = acc[n];
+                for (int g = 1; g < PP; ++g) t += red[((g - 1) * MC + mc) * 8 + n];
                 const long long hi = (long long)(t >> 64);
                 const unsigned long long lo = (unsigned long long)t;
                 const int e = sc[n] - 68;
@@ -679,7 +685,7 @@ __global__ void __launch_bounds__(kTnThreads, 1) k_oz_tn(const __grid_constant__
                 if (!pipe_wait(&full[pst], (s >> 1) & 1, &abort_, flag)) break;
                 tc::fence_after_sync();
                 const unsigned char *sa = sm + pst * kTnStage, *sb = sa + 4 * kTnAop;
-                for (int p = 0; p < 4; ++p)
+                for (int p = 0; p < NOP; ++p)
 #pragma unroll
                     for (int ks = 0; ks < kOzTnRows / 16; ++ks) {
                         const uint64_t ad = tc::desc_kmajor(tc::smem_addr(sa + p * kTnAop + ks * 256), 128, KG * 128);
@@ -720,7 +726,7 @@ static size_t oz_nn_smem(int na) {
     return (size_t)2 * kNnStage + kNnRawBytes + (size_t)8 * KGB * 128;   // plane stages, raw ring, C planes
 }
 constexpr size_t kOzTnSmem = (size_t)2 * kTnStage + kTnRawBytes;
-static_assert(kTnRawBytes >= 64 * 8 * sizeof(__int128), "the final sums reuse the raw ring");
+static_assert(kTnRawBytes >= 112 * 8 * sizeof(__int128), "the final sums reuse the raw ring");
 
 bool oz_supported(int na) { return na >= 1 && na <= 64; }
 
@@ -803,7 +809,9 @@ void oz_tn(int64_t dim, const unsigned long long *Y, int ldy, int na, const doub
            int nblk, int *flag, cudaStream_t s) {
     static bool attr = false;
     if (!attr) {
-        CI_CUDA(cudaFuncSetAttribute(k_oz_tn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOzTnSmem));
+        CI_CUDA(cudaFuncSetAttribute(k_oz_tn<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOzTnSmem));
+        CI_CUDA(cudaFuncSetAttribute(k_oz_tn<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOzTnSmem));
+        CI_CUDA(cudaFuncSetAttribute(k_oz_tn<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOzTnSmem));
         attr = true;
     }
     const int bc = (int)((na + (((uintptr_t)Y >> 3) & 1) + 1) & ~1);   // A's columns from the aligned one
@@ -812,8 +820,8 @@ void oz_tn(int64_t dim, const unsigned long long *Y, int ldy, int na, const doub
     const CUtensorMap ymap = rows_map(Y, ldy, std::max<int64_t>(dim, 1), na, bc, kOzTnRows, m);
     const CUtensorMap bmap = rows_map(B, ldb, std::max<int64_t>(dim, 1), 8, bw, kOzTnRows, mb);
     const int64_t rpb = (dim + nblk - 1) / nblk;
-    launch("k_oz_tn", k_oz_tn, nblk, kTnThreads, kOzTnSmem, s, ymap, bmap, m, bc, mb, bw, dim, na, B, ldb, part, rpb,
-           flag);
+    auto kern = na <= 16 ? k_oz_tn<16> : (na <= 32 ? k_oz_tn<32> : k_oz_tn<64>);
+    launch("k_oz_tn", kern, nblk, kTnThreads, kOzTnSmem, s, ymap, bmap, m, bc, mb, bw, dim, na, B, ldb, part, rpb, flag);
 }
 
 }  // namespace ci
