@@ -41,7 +41,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "H nonzeros built/s + SpMM % HBM peak; served solves/s, p50/p99 latency"
 WORKLOAD = ("4p+4n HO shells N<=4 (70 m-states/species), Nmax=4, 2M=0: dim 172684, nnz 102601752; "
-            "FP32 H, block Lanczos k=5 b=8 FP64 reorth")
+            "FP32 H, block Lanczos k=5 b=8, FP64-exact reorth on tensor cores")
 
 
 def parse():
@@ -66,6 +66,9 @@ def parse():
     ap.add_argument("--no-c2", action="store_true", help="skip the Nmax=6 precision-study leg")
     ap.add_argument("--no-eigensolvers", action="store_true", help="skip the Lanczos / LOBPCG comparison leg")
     ap.add_argument("--no-motifs", action="store_true", help="skip the scan / fill / array-reduction motif leg")
+    ap.add_argument("--no-products", action="store_true", help="skip the reorthogonalisation-product leg")
+    ap.add_argument("--products-only", action="store_true",
+                    help="run only the reorthogonalisation-product leg and print its JSON (a small profiling case)")
     ap.add_argument("--obs-m", type=int, default=16, help="operators of the observables leg")
     return ap.parse_args()
 
@@ -418,6 +421,8 @@ def run_ours(args):
         rec["eigensolvers"] = run_eigensolver_leg(sp, p, eps, dtab)
     if not args.no_motifs:
         rec["motifs"] = run_motifs_leg(hbm, (clk or {}).get("sm_mhz"))
+    if not args.no_products:
+        rec["products"] = run_products_leg(hbm)
     if not args.no_c2:
         rec["c2_precision"] = run_c2_leg(hbm)
     if not args.no_batch:
@@ -516,6 +521,48 @@ def run_c2_leg(hbm):
 # FP32 FMAs per clock per SM (CUDA arithmetic-throughput table): the ALU
 # roofline of the array-reduction motif
 FMA32_PER_CLK_SM = 128
+
+
+def run_products_leg(hbm, dim=172684, widths=(8, 16, 32, 64), reps=10):
+    """The block Lanczos reorthogonalisation products through ci_basis_product
+    at the c1 dimension: Q^T W and W - Q C for a basis of `na` columns (row
+    stride 64, as in the solver) and an 8-vector block, on the tensor cores
+    (FP64-exact digit planes) and on the FP64 CUDA cores.  Kernel time from
+    CUDA events on the launch stream; algorithmic bytes: the na columns of the
+    basis (the tensor-core form reads its 8-byte fixed-point shadow) plus W
+    (read, and for W - Q C written)."""
+    import numpy as np
+    import torch
+    import paper_2110_10765_gb300 as ci
+    rng = np.random.default_rng(5)
+    A = torch.from_numpy(rng.uniform(-1, 1, (dim, 64)) / np.sqrt(dim)).cuda()
+    B = torch.from_numpy(rng.standard_normal((dim, 8))).cuda()
+    Cm = torch.from_numpy(rng.standard_normal((64, 8)) * 1e-3).cuda()
+    out = {"dim": dim, "forms": {}}
+    names = {"tc": ("k_oz_tn", "k_oz_nn"), "fp64": ("k_tn_partial", "k_nn_update")}
+    for method in ("tc", "fp64"):
+        rows = []
+        for na in widths:
+            C = torch.zeros((na, 8), dtype=torch.float64, device="cuda")
+            for _ in range(2):
+                ci.basis_product("tn", A[:, :na], B, C, method=method)
+            ci.trace_enable(True)
+            ci.trace_read(True)
+            for _ in range(reps):
+                ci.basis_product("tn", A[:, :na], B, C, method=method)
+                ci.basis_product("nn", A[:, :na], B, Cm[:na], alpha=-1.0, beta=1.0, method=method)
+            t = ci.trace_read(True)
+            ci.trace_enable(False)
+            kt, kn = names[method]
+            tn_us = t[kt][1] / t[kt][0] * 1e3
+            nn_us = t[kn][1] / t[kn][0] * 1e3
+            btn, bnn = dim * (8 * na + 64), dim * (8 * na + 128)
+            rows.append({"na": na, "tn_us": round(tn_us, 2), "nn_us": round(nn_us, 2),
+                         "tn_frac_hbm": round(btn / (tn_us * 1e-6) / 1e9 / hbm, 4),
+                         "nn_frac_hbm": round(bnn / (nn_us * 1e-6) / 1e9 / hbm, 4)})
+        out["forms"][method] = rows
+    del A, B, Cm
+    return out
 
 
 def run_motifs_leg(hbm, clock_mhz=None, reps=5):
@@ -1006,6 +1053,10 @@ def main():
     args = parse()
     if args.cpu_sample:
         cpu_sample_main(args.cpu_sample, args.cpu_seconds, args.cpu_row0)
+    elif args.products_only:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps({"products": run_products_leg(load_peaks()[0])}))
     elif args.impl == "reference":
         run_reference(args)
     else:
