@@ -281,6 +281,65 @@ __global__ void k_zero_cols(int64_t dim, int nb, double *dst, int ldd) {
 }
 
 // Uniform(-1, 1) entries from SplitMix64 at position (i*nb + v) of stream seed.
+// Second block-QR pass on the device.  G (b x b) is the Gram matrix of a
+// block whose columns are orthogonal up to rounding (completion columns may
+// have any length); with D = diag(G)^{-1/2} and G' = D G D (unit diagonal),
+// the coupled Newton-Schulz iteration Y <- Y T, Z <- T Z, T = (3I - Z Y)/2
+// from Y = G', Z = I converges quadratically to Y = G'^{1/2}, Z = G'^{-1/2}
+// (the eigenvalues of G' lie in (0, 3) here).  Then V Mi with Mi = D Z is
+// orthonormal, and the block's coupling becomes R2 = Y D^{-1} R.  One thread
+// per entry (b*b <= 64); bit 2 of *flag when 40 iterations leave T off the
+// identity or a column has no length.
+__global__ void k_qr2(const double *__restrict__ G, int b, double *__restrict__ Mi, const double *__restrict__ R,
+                      double *__restrict__ R2, int *flag) {
+    __shared__ double Y[64], Z[64], Tm[64], d[8];
+    const int t = threadIdx.x, i = t / b, j = t % b;
+    const bool on = t < b * b;
+    if (t < b) {
+        const double g = G[t * b + t];
+        d[t] = g > 0.0 ? 1.0 / sqrt(g) : 1.0;
+        if (!(g > 0.0)) atomicOr(flag, 4);
+    }
+    __syncthreads();
+    if (on) {
+        Y[t] = d[i] * (0.5 * (G[i * b + j] + G[j * b + i])) * d[j];
+        Z[t] = i == j ? 1.0 : 0.0;
+    }
+    bool conv = false;
+    for (int it = 0; it < 40 && !conv; ++it) {
+        __syncthreads();
+        double dev = 0.0;
+        if (on) {
+            double zy = 0.0;
+            for (int k = 0; k < b; ++k) zy = fma(Z[i * b + k], Y[k * b + j], zy);
+            const double e = (i == j ? 1.0 : 0.0) - zy;   // T = I + E/2, E = I - Z Y
+            Tm[t] = (i == j ? 1.0 : 0.0) + 0.5 * e;
+            dev = fabs(e);
+        }
+        __syncthreads();
+        double yn = 0.0, zn = 0.0;
+        if (on) {
+            for (int k = 0; k < b; ++k) {
+                yn = fma(Y[i * b + k], Tm[k * b + j], yn);
+                zn = fma(Tm[i * b + k], Z[k * b + j], zn);
+            }
+        }
+        conv = !__syncthreads_or(dev > 1e-15);
+        if (on) {
+            Y[t] = yn;
+            Z[t] = zn;
+        }
+    }
+    __syncthreads();
+    if (!conv && t == 0) atomicOr(flag, 4);
+    if (on) {
+        Mi[t] = d[i] * Z[t];
+        double x = 0.0;
+        for (int k = 0; k < b; ++k) x = fma(Y[i * b + k], R[k * b + j] / d[k], x);
+        R2[t] = x;
+    }
+}
+
 __global__ void k_random_cols(int64_t dim, int nb, uint64_t seed, double *dst, int ldd) {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < dim * nb; t += (int64_t)gridDim.x * blockDim.x) {
         uint64_t z = seed + (uint64_t)(t + 1) * 0x9E3779B97F4A7C15ull;
@@ -408,6 +467,11 @@ struct Solver {
     // after the next host sync instead of a sync of its own
     double *pin_coef = nullptr;
     size_t pin_len = 0;
+    // the block QR's coupling R of the last two block steps: computed on the
+    // device by the second pass, copied to pinned memory, read by take_R
+    DevBuf<double> Rdev, R2dev;
+    double *pin_R = nullptr;   // [2][64]
+    cudaEvent_t ev_R[2] = {nullptr, nullptr};
     int pend_m = 0, pend_lo = 0, pend_nb = 0, pend_passes = 0;
     bool pend = false;
 
@@ -433,6 +497,12 @@ struct Solver {
     }
 
     ~Solver() {
+        if (pin_R) {
+            cudaStreamSynchronize(s);
+            cudaFreeHost(pin_R);
+        }
+        for (cudaEvent_t &e : ev_R)
+            if (e) cudaEventDestroy(e);
         if (pin_coef) {
             cudaStreamSynchronize(s);
             cudaFreeHost(pin_coef);
@@ -596,8 +666,12 @@ struct Solver {
     // Q[:, m:m+b].  R (b x b, row-major) receives the coupling Wb = V R.
     // Directions below the deflation threshold are replaced by random
     // vectors orthogonal to Q and V (their coupling is zero).
-    void block_qr(double *Wb, int m, uint64_t seed, std::vector<double> &R) {
-        std::vector<double> G, w, U;
+    // The first pass synchronises on the Gram matrix of Wb (its eigenvalues
+    // decide the deflation); the second pass runs on the device (k_qr2) and
+    // leaves its R in pinned slot `par`, read by take_R(par) after event
+    // ev_R[par].
+    void block_qr(double *Wb, int m, uint64_t seed, int par) {
+        std::vector<double> G, w, U, R;
         tn(Wb, b, b, Wb, b, b, Cdev.ptr, &G);
         sym_eig(b, G, w, U);
         const double lmax = std::max(w[b - 1], 0.0);
@@ -616,7 +690,14 @@ struct Solver {
             ++r;
         }
         double *V = Q.ptr + m;
+        if (!pin_R) {
+            CI_CUDA(cudaMallocHost(&pin_R, sizeof(double) * 2 * 64));
+            for (cudaEvent_t &e : ev_R) CI_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            Rdev.alloc(64);
+            R2dev.alloc(64);
+        }
         upload(M, Mdev.ptr);
+        upload(R, Rdev.ptr);
         nn(Wb, b, b, Mdev.ptr, b, V, mmax, 1.0, 0.0);
         if (r < b) {
             // random completion of columns r..b-1
@@ -641,31 +722,18 @@ struct Solver {
         // to rounding now, so its products go through the basis path
         const bool vtc = tc && Qfix.ptr;
         if (vtc) oz_fix(dim, b, V, mmax, Qfix.ptr + m, mmax, ozflag.ptr, s);
-        tn(V, mmax, b, V, mmax, b, Cdev.ptr, &G, vtc);
-        sym_eig(b, G, w, U);
-        std::vector<double> Mi((size_t)b * b, 0.0), Ms((size_t)b * b, 0.0);
-        for (int a = 0; a < b; ++a)
-            for (int c = 0; c < b; ++c) {
-                double x = 0.0, y = 0.0;
-                for (int i = 0; i < b; ++i) {
-                    double wi = std::max(w[i], 1e-300);
-                    x += U[(size_t)a * b + i] * U[(size_t)c * b + i] / std::sqrt(wi);
-                    y += U[(size_t)a * b + i] * U[(size_t)c * b + i] * std::sqrt(wi);
-                }
-                Mi[(size_t)a * b + c] = x;
-                Ms[(size_t)a * b + c] = y;
-            }
-        upload(Mi, Mdev.ptr);
+        tn(V, mmax, b, V, mmax, b, Cdev.ptr, nullptr, vtc);
+        launch("k_qr2", k_qr2, 1, 64, 0, s, Cdev.ptr, b, Mdev.ptr, Rdev.ptr, R2dev.ptr, ozflag.ptr);
         nn(V, mmax, b, Mdev.ptr, b, tmp.ptr, b, 1.0, 0.0, vtc);
         copy_into_basis(tmp.ptr, b, m, b);
-        std::vector<double> R2((size_t)b * b, 0.0);
-        for (int a = 0; a < b; ++a)
-            for (int c = 0; c < b; ++c) {
-                double x = 0.0;
-                for (int i = 0; i < b; ++i) x += Ms[(size_t)a * b + i] * R[(size_t)i * b + c];
-                R2[(size_t)a * b + c] = x;
-            }
-        R.swap(R2);
+        CI_CUDA(cudaMemcpyAsync(pin_R + 64 * par, R2dev.ptr, sizeof(double) * b * b, cudaMemcpyDeviceToHost, s));
+        CI_CUDA(cudaEventRecord(ev_R[par], s));
+    }
+
+    // R of the block QR that wrote pinned slot par (waits for its copy)
+    void take_R(int par, std::vector<double> &R) {
+        CI_CUDA(cudaEventSynchronize(ev_R[par]));
+        R.assign(pin_R + 64 * par, pin_R + 64 * par + (size_t)b * b);
     }
 };
 
@@ -784,11 +852,11 @@ void lowest_eigs(const Matrix *H, const ci_eig_opts *opts_in, double *evals, dou
     Solver sv(H, s, b, k, mmax);
     sv.tc = o.fp64_products == 0;
     std::vector<double> T((size_t)mmax * mmax, 0.0);
-    std::vector<double> R, coef;
-    // start block
+    std::vector<double> coef;
+    // start block (its R is not needed: pinned slot 1, never read)
     launch("k_random_cols", k_random_cols, sv.grid(dim * b), 256, 0, s, dim, b, o.seed, sv.W.ptr, b);
     CI_CHECK_LAUNCH();
-    sv.block_qr(sv.W.ptr, 0, o.seed ^ 0x5bd1e995ull, R);
+    sv.block_qr(sv.W.ptr, 0, o.seed ^ 0x5bd1e995ull, 1);
     int m_cur = b, j0 = 0;
     int it = 0, since_check = 0;
     bool converged = false;
@@ -796,6 +864,20 @@ void lowest_eigs(const Matrix *H, const ci_eig_opts *opts_in, double *evals, dou
     int m_act = 0;
     std::vector<double> Rlast;
     bool applied = false;   // H V_j already enqueued (before the last host Ritz check)
+    // The coupling R of a block step comes from the device: it is read at the
+    // step's Ritz check (after the next product is enqueued), else after the
+    // next step's block-QR sync; until then its block of T is pending.
+    int par = 0, pend_row = 0, pend_col = 0, pend_par = 0;
+    bool pend_R = false;
+    auto resolve_R = [&]() {
+        sv.take_R(pend_par, Rlast);
+        for (int r = 0; r < b; ++r)
+            for (int c = 0; c < b; ++c) {
+                T[(size_t)(pend_row + r) * mmax + pend_col + c] = Rlast[(size_t)r * b + c];
+                T[(size_t)(pend_col + c) * mmax + pend_row + r] = Rlast[(size_t)r * b + c];
+            }
+        pend_R = false;
+    };
     while (true) {
         // W = H V_j, orthogonalised against the whole basis
         if (!applied) sv.apply(sv.Q.ptr + j0, mmax, b, sv.W.ptr);
@@ -803,8 +885,10 @@ void lowest_eigs(const Matrix *H, const ci_eig_opts *opts_in, double *evals, dou
         sv.project_deferred(sv.W.ptr, b, m_cur, std::max(0, j0 - b), o.reorth_passes);
         ++it;
         // next block (its Gram matrix is the step's one host sync; the
-        // projection coefficients copied before it are then on the host)
-        sv.block_qr(sv.W.ptr, m_cur, o.seed + 0x9E37ull * (uint64_t)(it + 1), Rlast);
+        // projection coefficients and the previous step's R copied before it
+        // are then on the host)
+        sv.block_qr(sv.W.ptr, m_cur, o.seed + 0x9E37ull * (uint64_t)(it + 1), par);
+        if (pend_R) resolve_R();
         sv.take_coef(&coef, true);
         for (int i = 0; i < j0; ++i)
             for (int v = 0; v < b; ++v) {
@@ -815,11 +899,11 @@ void lowest_eigs(const Matrix *H, const ci_eig_opts *opts_in, double *evals, dou
             for (int v = 0; v < b; ++v)
                 T[(size_t)(j0 + u) * mmax + j0 + v] =
                     0.5 * (coef[(size_t)(j0 + u) * b + v] + coef[(size_t)(j0 + v) * b + u]);
-        for (int r = 0; r < b; ++r)
-            for (int c = 0; c < b; ++c) {
-                T[(size_t)(m_cur + r) * mmax + j0 + c] = Rlast[(size_t)r * b + c];
-                T[(size_t)(j0 + c) * mmax + m_cur + r] = Rlast[(size_t)r * b + c];
-            }
+        pend_R = true;
+        pend_row = m_cur;
+        pend_col = j0;
+        pend_par = par;
+        par ^= 1;
         m_act = m_cur;
         j0 = m_cur;
         m_cur += b;
@@ -834,6 +918,7 @@ void lowest_eigs(const Matrix *H, const ci_eig_opts *opts_in, double *evals, dou
                 sv.apply(sv.Q.ptr + j0, mmax, b, sv.W.ptr);
                 applied = true;
             }
+            resolve_R();
             last = ritz(T, mmax, m_act, b, Rlast, k);
             sv.hnorm = std::max(sv.hnorm, std::max(std::fabs(last.theta.front()), std::fabs(last.theta.back())));
             converged = (int)last.res.size() >= k;
@@ -903,7 +988,7 @@ void lowest_eigs(const Matrix *H, const ci_eig_opts *opts_in, double *evals, dou
     int ozf = 0;
     CI_CUDA(cudaMemcpyAsync(&ozf, sv.ozflag.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
     CI_CUDA(cudaStreamSynchronize(s));
-    if (ozf) fail(CI_ERR_INTERNAL, "tensor-core basis product failed (flag %d)", ozf);
+    if (ozf) fail(CI_ERR_INTERNAL, "a tensor-core basis product or the device block QR failed (flag %d)", ozf);
     inf.iterations = it;
     inf.basis_size = m_act;
     inf.hnorm_est = sv.hnorm;
