@@ -330,7 +330,7 @@ typedef struct {
     uint64_t seed;        /* seed of the start block                      [1]  */
     int32_t reorth_passes;/* full Gram-Schmidt passes per step after the
                              projection on the two newest blocks, 1..2    [1]  */
-    int32_t check_every;  /* block steps between convergence checks       [2]  */
+    int32_t check_every;  /* block steps between convergence checks       [1]  */
     int32_t fp64_products;/* 1: the reorthogonalisation products on the FP64
                              CUDA cores; 0: on the tensor cores as exact
                              products of 8-bit digit planes (FP64 accuracy,

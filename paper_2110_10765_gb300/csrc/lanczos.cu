@@ -776,7 +776,7 @@ void lowest_eigs(const Matrix *H, const ci_eig_opts *opts_in, double *evals, dou
     if (o.tol == 0.0) o.tol = H->vtype == CI_F64 ? 1e-10 : 1e-6;
     if (o.seed == 0) o.seed = 1;
     if (o.reorth_passes == 0) o.reorth_passes = 1;
-    if (o.check_every == 0) o.check_every = 2;
+    if (o.check_every == 0) o.check_every = 1;   // the host check overlaps the next product
     if (o.k < 1 || o.k > 32) fail(CI_ERR_INVALID_ARG, "k must be 1..32");
     if (o.block < 1 || o.block > 8) fail(CI_ERR_INVALID_ARG, "block must be 1..8");
     if (o.reorth_passes < 1 || o.reorth_passes > 2) fail(CI_ERR_INVALID_ARG, "reorth_passes must be 1..2");
