@@ -288,8 +288,9 @@ __global__ void k_zero_cols(int64_t dim, int nb, double *dst, int ldd) {
 // from Y = G', Z = I converges quadratically to Y = G'^{1/2}, Z = G'^{-1/2}
 // (the eigenvalues of G' lie in (0, 3) here).  Then V Mi with Mi = D Z is
 // orthonormal, and the block's coupling becomes R2 = Y D^{-1} R.  One thread
-// per entry (b*b <= 64); bit 2 of *flag when 40 iterations leave T off the
-// identity or a column has no length.
+// per entry (b*b <= 64); the iteration stops after the update made with
+// |I - Z Y| <= 1e-12, whose error is of second order; bit 2 of *flag when 40
+// iterations leave T off the identity or a column has no length.
 __global__ void k_qr2(const double *__restrict__ G, int b, double *__restrict__ Mi, const double *__restrict__ R,
                       double *__restrict__ R2, int *flag) {
     __shared__ double Y[64], Z[64], Tm[64], d[8];
@@ -324,7 +325,7 @@ __global__ void k_qr2(const double *__restrict__ G, int b, double *__restrict__ 
                 zn = fma(Tm[i * b + k], Z[k * b + j], zn);
             }
         }
-        conv = !__syncthreads_or(dev > 1e-15);
+        conv = !__syncthreads_or(dev > 1e-12);   // this last update leaves O(dev^2): rounding level
         if (on) {
             Y[t] = yn;
             Z[t] = zn;
