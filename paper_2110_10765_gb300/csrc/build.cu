@@ -640,6 +640,7 @@ void build_matrix(Problem *p, int vtype, Matrix *m, cudaStream_t s) {
     m->nnz = g.nnz;
     m->row_ptr = std::move(g.row_ptr);
     m->col = std::move(g.col);
+    spmm_prepare(m, s);
     if (vtype != CI_BF16_ROWSCALE) {
         m->val = std::move(g.val);
         return;

@@ -198,6 +198,10 @@ struct Matrix {
     DevBuf<unsigned char> val;       // float, double or bf16 bits
     DevBuf<float> row_scale;         // BF16 only
     bool upper = false;              // only the upper triangle (col >= row) is stored
+    // row ranges of balanced work for the 8-vector SpMM (spmm_prepare):
+    // range b is rows [spmm_bnd[b], spmm_bnd[b+1]), b < spmm_nb
+    DevBuf<int64_t> spmm_bnd;
+    int64_t spmm_nb = 0;
 };
 
 // Block-diagonal preconditioner over many-body basis orbitals: sub-blocks of
@@ -274,6 +278,8 @@ void apply_matrix16(const Matrix *m, const float *X, float *Y, cudaStream_t s);
 // Y8 = H R8 ([dim][8]) in FP64 with every element evaluated on the fly
 void h64_apply(Problem *p, const double *R8, double *Y8, cudaStream_t s);
 void apply_matrix(const Matrix *m, const void *X, void *Y, int nvec, cudaStream_t s);
+// The row ranges of a full-storage matrix's 8-vector SpMM (after its CSR is final).
+void spmm_prepare(Matrix *m, cudaStream_t s);
 // FP64-exact products on the tensor cores (ozaki.cu) for a basis A of
 // na <= 64 orthonormal columns (|A| < 1.99), read in its fixed-point
 // shadow form Y (oz_fix; even ldy, so rows are 16-byte aligned; A may start

@@ -113,20 +113,23 @@ __global__ void __launch_bounds__(256) k_spmm(int64_t dim, const int64_t *__rest
 // warp instruction touches 16 rows of X (one sector each) instead of
 // issuing two loads per row.  Lanes accumulate their four components over
 // the row's nonzeros j, j+16, ... in ascending order, then reduce over the
-// 16 lanes of the same parity.
+// 16 lanes of the same parity.  CTA b takes the consecutive rows
+// [bnd[b], bnd[b+1]) (about kSpmmWork nonzeros, see k_spmm_bounds) and its
+// eight warps interleave over them: the rows a CTA holds at once mostly
+// belong to one proton-state block, whose rows share many X rows (reused
+// from L1), and many short CTAs of even work keep every SM busy to the end.
 
 // row_scale: null, or a per-row factor of the stored values (BF16 form)
 template <class TV>
-__global__ void __launch_bounds__(256) k_spmm8_half(int64_t dim, const int64_t *__restrict__ rp,
+__global__ void __launch_bounds__(256) k_spmm8_half(const int64_t *__restrict__ bnd, const int64_t *__restrict__ rp,
                                                     const int32_t *__restrict__ col, const TV *__restrict__ val,
                                                     const float *__restrict__ X, float *__restrict__ Y,
                                                     const float *__restrict__ row_scale) {
     constexpr int U = 4;  // nonzeros in flight per lane pair
     const int lane = threadIdx.x & 31, half = lane & 1, pair = lane >> 1;
-    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t r_end = bnd[blockIdx.x + 1];
     const float4 *X4 = reinterpret_cast<const float4 *>(X);
-    for (int64_t r = warp; r < dim; r += nwarps) {
+    for (int64_t r = bnd[blockIdx.x] + (threadIdx.x >> 5); r < r_end; r += blockDim.x >> 5) {
         float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
         const int64_t e1 = rp[r + 1];
         int64_t e = rp[r] + pair;
@@ -237,6 +240,39 @@ __global__ void k_spmm_upper(int64_t dim, const int64_t *__restrict__ rp, const 
     }
 }
 
+// Work of rows [0, r): nonzeros plus kSpmmRowCost per row (a row also costs
+// its pointers and its Y store), strictly increasing in r.  Range b starts
+// at the first row whose work reaches b / nb of the total; the last range
+// ends at dim, so trailing empty rows are covered too.
+constexpr int64_t kSpmmWork = 10240, kSpmmRowCost = 16;
+__global__ void k_spmm_bounds(int64_t dim, const int64_t *__restrict__ rp, int64_t nb, int64_t *__restrict__ bnd) {
+    const int64_t total = rp[dim] + kSpmmRowCost * dim;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g <= nb; g += (int64_t)gridDim.x * blockDim.x) {
+        if (g == nb) {
+            bnd[g] = dim;
+            continue;
+        }
+        const int64_t target = total / nb * g + total % nb * g / nb;   // floor(total * g / nb)
+        int64_t lo = 0, hi = dim;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (rp[mid] + kSpmmRowCost * mid < target) lo = mid + 1; else hi = mid;
+        }
+        bnd[g] = lo;
+    }
+}
+
+void spmm_prepare(Matrix *m, cudaStream_t s) {
+    if (m->upper) return;
+    const int64_t total = m->nnz + kSpmmRowCost * m->dim;
+    m->spmm_nb = std::max<int64_t>(1, (total + kSpmmWork - 1) / kSpmmWork);
+    if (m->spmm_nb > INT32_MAX) fail(CI_ERR_CAPACITY, "matrix too large for the SpMM's row ranges");
+    m->spmm_bnd.alloc((size_t)m->spmm_nb + 1);
+    launch("k_spmm_bounds", k_spmm_bounds, grid_for(m->spmm_nb + 1, 256), 256, 0, s, m->dim, m->row_ptr.ptr,
+           m->spmm_nb, m->spmm_bnd.ptr);
+    CI_CHECK_LAUNCH();
+}
+
 template <class TV, class TX, int NV>
 static void launch_spmm_upper(const Matrix *m, const void *X, void *Y, cudaStream_t s) {
     CI_CUDA(cudaMemsetAsync(Y, 0, sizeof(TX) * (size_t)m->dim * NV, s));
@@ -259,7 +295,8 @@ static void launch_spmm(const Matrix *m, const void *X, void *Y, cudaStream_t s)
     int grid = grid_for(m->dim * 32, 256, sm_count() * 8);
     const float *scale = m->vtype == CI_BF16_ROWSCALE ? m->row_scale.ptr : nullptr;
     if (NV == 8 && sizeof(TX) == 4) {
-        launch("k_spmm", k_spmm8_half<TV>, grid, 256, 0, s, m->dim, m->row_ptr.ptr, m->col.ptr,
+        if (!m->spmm_bnd.ptr) fail(CI_ERR_INTERNAL, "matrix without SpMM row ranges");
+        launch("k_spmm", k_spmm8_half<TV>, (int)m->spmm_nb, 256, 0, s, (const int64_t *)m->spmm_bnd.ptr, m->row_ptr.ptr, m->col.ptr,
                (const TV *)m->val.ptr, (const float *)X, (float *)Y, (const float *)scale);
         return;
     }
