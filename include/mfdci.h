@@ -345,13 +345,21 @@ typedef struct {
     double hnorm_est;     /* estimate of ||H||_2 (largest |Ritz value| seen)    */
     double residual[32];  /* ||H x_i - theta_i x_i||_2, FP64, with the stored H */
     double seconds;       /* wall time of the call                              */
+    int32_t host_qr;      /* block Lanczos: block steps whose block QR fell back
+                             from the device (Cholesky) path to the host's
+                             rank-revealing one (deflation, random completion) */
+    int32_t reserved;
 } ci_eig_info;
 
 /* Fig. 1, eigensolve (Sec. 2): lowest k eigenvalues of H by block Lanczos with
  * full FP64 reorthogonalisation (classical Gram-Schmidt against the two
  * newest blocks, then reorth_passes passes over the whole basis) and thick
- * restart.  SpMM in the matrix's
- * precision, everything else in FP64.  evals: host [k], ascending.  evecs:
+ * restart.  SpMM in the matrix's precision, everything else in FP64.  Each
+ * new block is orthonormalised on the device (Cholesky QR, then a
+ * Newton-Schulz pass) without a host sync; a numerically rank-deficient
+ * block is redone by the host's rank-revealing QR (info->host_qr counts
+ * those).  The host reads the projection coefficients and the coupling
+ * while the next product runs.  evals: host [k], ascending.  evecs:
  * nullable device double [dim][k], unit norm.  info: nullable.  Returns
  * CI_ERR_NOT_CONVERGED (with the best estimates written) if max_iter is hit. */
 ci_status ci_lowest_eigs(const ci_matrix *m, const ci_eig_opts *opts, double *evals,

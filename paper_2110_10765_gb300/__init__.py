@@ -287,7 +287,8 @@ class Matrix:
             check(st, "ci_lowest_eigs" if method == "lanczos" else "ci_lowest_eigs_lobpcg")
         out = {"iterations": info.iterations, "restarts": info.restarts, "converged": info.converged,
                "basis_size": info.basis_size, "hnorm_est": info.hnorm_est,
-               "residual": list(info.residual)[:k], "seconds": info.seconds, "status": st}
+               "residual": list(info.residual)[:k], "seconds": info.seconds, "host_qr": info.host_qr,
+               "status": st}
         return ev, out
 
 

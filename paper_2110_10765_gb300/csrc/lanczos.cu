@@ -280,7 +280,61 @@ __global__ void k_zero_cols(int64_t dim, int nb, double *dst, int ldd) {
         dst[(t / nb) * ldd + t % nb] = 0.0;
 }
 
-// Uniform(-1, 1) entries from SplitMix64 at position (i*nb + v) of stream seed.
+// First block-QR pass on the device (Cholesky QR): the Gram matrix G = W^T W
+// (b x b, b <= 8) of a block that is already orthogonal to the basis is
+// factored as G = L L^T; then W M with M = L^{-T} has orthonormal columns up
+// to the conditioning of G, and W = (W M) R with R = L^T.  One thread per
+// entry: column c of the right-looking factorisation, then thread c solves
+// L x = e_c for column c of L^{-1}.  *stat = 1 (else 0) when a pivot is not
+// above 1e-12 of the largest diagonal entry, nor above 1e-20 max(hnorm^2,
+// that entry) (the host path's deflation level), or is not finite: the
+// block is then left to the rank-revealing host path.
+__global__ void k_qr1(const double *__restrict__ G, int b, double hnorm, double *__restrict__ M,
+                      double *__restrict__ R, int *stat) {
+    __shared__ double A[64], Li[64], rd[8];
+    __shared__ int bad;
+    const int t = threadIdx.x, i = t / b, j = t % b;
+    const bool on = t < b * b;
+    if (on) A[t] = 0.5 * (G[i * b + j] + G[j * b + i]);
+    if (t == 0) bad = 0;
+    __syncthreads();
+    double gmax = 0.0;
+    for (int q = 0; q < b; ++q) gmax = fmax(gmax, A[q * b + q]);
+    const double thr = fmax(1e-12 * gmax, 1e-20 * fmax(hnorm * hnorm, gmax)) + 1e-300;
+    for (int c = 0; c < b; ++c) {
+        double d = A[c * b + c];   // Schur complement pivot
+        const bool ok = d > thr && d < 1e300;
+        if (!ok) d = 1.0;          // any finite pivot: the result is not used
+        const double l = sqrt(d), il = 1.0 / l;
+        double lic = 0.0, ljc = 0.0;
+        if (on && i > c && j > c) {
+            lic = A[i * b + c] * il;
+            ljc = A[j * b + c] * il;
+        }
+        __syncthreads();           // column c read by everyone
+        if (t == 0) {
+            rd[c] = il;
+            if (!ok) bad = 1;
+        }
+        if (on && i > c && j > c) A[t] -= lic * ljc;
+        if (on && j == c && i >= c) A[t] = i == c ? l : A[t] * il;
+        __syncthreads();
+    }
+    if (t < b) {   // column t of L^{-1}
+        for (int r = 0; r < b; ++r) {
+            double x = r == t ? 1.0 : 0.0;
+            for (int k = t; k < r; ++k) x -= A[r * b + k] * Li[k * b + t];
+            Li[r * b + t] = r < t ? 0.0 : x * rd[r];
+        }
+    }
+    __syncthreads();
+    if (on) {
+        M[i * b + j] = Li[j * b + i];                  // M = L^{-T}
+        R[i * b + j] = j >= i ? A[j * b + i] : 0.0;    // R = L^T
+    }
+    if (t == 0) *stat = bad;
+}
+
 // Second block-QR pass on the device.  G (b x b) is the Gram matrix of a
 // block whose columns are orthogonal up to rounding (completion columns may
 // have any length); with D = diag(G)^{-1/2} and G' = D G D (unit diagonal),
@@ -289,17 +343,17 @@ __global__ void k_zero_cols(int64_t dim, int nb, double *dst, int ldd) {
 // (the eigenvalues of G' lie in (0, 3) here).  Then V Mi with Mi = D Z is
 // orthonormal, and the block's coupling becomes R2 = Y D^{-1} R.  One thread
 // per entry (b*b <= 64); the iteration stops after the update made with
-// |I - Z Y| <= 1e-12, whose error is of second order; bit 2 of *flag when 40
+// |I - Z Y| <= 1e-12, whose error is of second order; *flag |= fail when 40
 // iterations leave T off the identity or a column has no length.
 __global__ void k_qr2(const double *__restrict__ G, int b, double *__restrict__ Mi, const double *__restrict__ R,
-                      double *__restrict__ R2, int *flag) {
+                      double *__restrict__ R2, int *flag, int fail) {
     __shared__ double Y[64], Z[64], Tm[64], d[8];
     const int t = threadIdx.x, i = t / b, j = t % b;
     const bool on = t < b * b;
     if (t < b) {
         const double g = G[t * b + t];
         d[t] = g > 0.0 ? 1.0 / sqrt(g) : 1.0;
-        if (!(g > 0.0)) atomicOr(flag, 4);
+        if (!(g > 0.0)) atomicOr(flag, fail);
     }
     __syncthreads();
     if (on) {
@@ -332,7 +386,7 @@ __global__ void k_qr2(const double *__restrict__ G, int b, double *__restrict__ 
         }
     }
     __syncthreads();
-    if (!conv && t == 0) atomicOr(flag, 4);
+    if (!conv && t == 0) atomicOr(flag, fail);
     if (on) {
         Mi[t] = d[i] * Z[t];
         double x = 0.0;
@@ -341,6 +395,7 @@ __global__ void k_qr2(const double *__restrict__ G, int b, double *__restrict__ 
     }
 }
 
+// Uniform(-1, 1) entries from SplitMix64 at position (i*nb + v) of stream seed.
 __global__ void k_random_cols(int64_t dim, int nb, uint64_t seed, double *dst, int ldd) {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < dim * nb; t += (int64_t)gridDim.x * blockDim.x) {
         uint64_t z = seed + (uint64_t)(t + 1) * 0x9E3779B97F4A7C15ull;
@@ -460,7 +515,7 @@ struct Solver {
     DevBuf<int> ozflag;
     DevBuf<unsigned long long> Qfix;   // fixed-point shadow of Q for the tensor-core products
     int64_t rows_per_blk;
-    DevBuf<double> Q, W, tmp, part, Cdev, Mdev, theta_dev, Cacc;
+    DevBuf<double> Q, W, W2, tmp, part, Cdev, Mdev, theta_dev, Cacc;
     DevBuf<float> X32, Y32;
     DevBuf<double> X64;
     double hnorm = 0.0;
@@ -468,10 +523,14 @@ struct Solver {
     // after the next host sync instead of a sync of its own
     double *pin_coef = nullptr;
     size_t pin_len = 0;
+    cudaEvent_t ev_coef = nullptr;   // after their copy
     // the block QR's coupling R of the last two block steps: computed on the
-    // device by the second pass, copied to pinned memory, read by take_R
+    // device by the second pass, copied to pinned memory with the device
+    // pass's status, read by take_R
     DevBuf<double> Rdev, R2dev;
+    DevBuf<int> qstat;
     double *pin_R = nullptr;   // [2][64]
+    int *pin_stat = nullptr;   // [2]
     cudaEvent_t ev_R[2] = {nullptr, nullptr};
     int pend_m = 0, pend_lo = 0, pend_nb = 0, pend_passes = 0;
     bool pend = false;
@@ -485,6 +544,7 @@ struct Solver {
         oz_nblk = oz_tn_blocks(dim);
         Q.alloc((size_t)dim * mmax);
         W.alloc((size_t)dim * b);
+        W2.alloc((size_t)dim * b);
         tmp.alloc((size_t)dim * std::max(mmax, b));
         part.alloc((size_t)std::max(nblk, oz_nblk) * kMaxNa * 8);
         ozflag.alloc(1);
@@ -501,9 +561,11 @@ struct Solver {
         if (pin_R) {
             cudaStreamSynchronize(s);
             cudaFreeHost(pin_R);
+            cudaFreeHost(pin_stat);
         }
         for (cudaEvent_t &e : ev_R)
             if (e) cudaEventDestroy(e);
+        if (ev_coef) cudaEventDestroy(ev_coef);
         if (pin_coef) {
             cudaStreamSynchronize(s);
             cudaFreeHost(pin_coef);
@@ -521,9 +583,10 @@ struct Solver {
     // the shadow of the basis column that A points at
     const unsigned long long *shadow(const double *A) const { return Qfix.ptr + (A - Q.ptr); }
     // Q[:, c0:c0+nc] = src (leading dimension lds), with the shadow
-    void copy_into_basis(const double *src, int lds, int c0, int nc) {
+    // (an entry out of the shadow's range sets bit 0 of *flag, ozflag by default)
+    void copy_into_basis(const double *src, int lds, int c0, int nc, int *flag = nullptr) {
         if (tc && Qfix.ptr) {
-            oz_copy_fix(dim, nc, src, lds, Q.ptr + c0, mmax, Qfix.ptr + c0, mmax, ozflag.ptr, s);
+            oz_copy_fix(dim, nc, src, lds, Q.ptr + c0, mmax, Qfix.ptr + c0, mmax, flag ? flag : ozflag.ptr, s);
         } else {
             launch("k_copy_cols", k_copy_cols, grid(dim * nc), 256, 0, s, dim, nc, src, lds, Q.ptr + c0, mmax);
         }
@@ -637,8 +700,7 @@ struct Solver {
     }
 
     // project() whose coefficients are copied to pinned memory without a
-    // sync; take_coef() reads them after the stream has been synchronised
-    // (block_qr synchronises on its Gram matrix).
+    // sync; take_coef() reads them once the copy's event has passed.
     void project_deferred(double *Wb, int nb, int m, int lo, int passes) {
         project(Wb, nb, m, lo, passes, nullptr);
         if (m == 0) return;
@@ -653,24 +715,36 @@ struct Solver {
             pin_len = len;
         }
         CI_CUDA(cudaMemcpyAsync(pin_coef, Cacc.ptr, sizeof(double) * len, cudaMemcpyDeviceToHost, s));
+        if (!ev_coef) CI_CUDA(cudaEventCreateWithFlags(&ev_coef, cudaEventDisableTiming));
+        CI_CUDA(cudaEventRecord(ev_coef, s));
         pend = true;
         pend_m = m; pend_lo = lo; pend_nb = nb; pend_passes = passes;
     }
-    void take_coef(std::vector<double> *coef, bool synced) {
+    void take_coef(std::vector<double> *coef) {
         if (!pend) { coef->assign((size_t)pend_m * pend_nb, 0.0); return; }
-        if (!synced) CI_CUDA(cudaStreamSynchronize(s));
+        CI_CUDA(cudaEventSynchronize(ev_coef));
         fold_coef(pin_coef, pend_nb, pend_m, pend_lo, pend_passes, coef);
         pend = false;
     }
 
+    void ensure_qr_buffers() {
+        if (pin_R) return;
+        CI_CUDA(cudaMallocHost(&pin_R, sizeof(double) * 2 * 64));
+        CI_CUDA(cudaMallocHost(&pin_stat, sizeof(int) * 2));
+        for (cudaEvent_t &e : ev_R) CI_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        Rdev.alloc(64);
+        R2dev.alloc(64);
+        qstat.alloc(1);
+    }
+
     // Orthonormalise Wb [dim][b] (already orthogonal to Q[:, 0:m]) into
-    // Q[:, m:m+b].  R (b x b, row-major) receives the coupling Wb = V R.
-    // Directions below the deflation threshold are replaced by random
-    // vectors orthogonal to Q and V (their coupling is zero).
-    // The first pass synchronises on the Gram matrix of Wb (its eigenvalues
-    // decide the deflation); the second pass runs on the device (k_qr2) and
-    // leaves its R in pinned slot `par`, read by take_R(par) after event
-    // ev_R[par].
+    // Q[:, m:m+b] on the host path.  R (b x b, row-major) receives the
+    // coupling Wb = V R.  Directions below the deflation threshold are
+    // replaced by random vectors orthogonal to Q and V (their coupling is
+    // zero).  The first pass synchronises on the Gram matrix of Wb (its
+    // eigenvalues decide the deflation); the second pass runs on the device
+    // (k_qr2) and leaves its R in pinned slot `par`, read by take_R(par)
+    // after event ev_R[par].
     void block_qr(double *Wb, int m, uint64_t seed, int par) {
         std::vector<double> G, w, U, R;
         tn(Wb, b, b, Wb, b, b, Cdev.ptr, &G);
@@ -691,12 +765,7 @@ struct Solver {
             ++r;
         }
         double *V = Q.ptr + m;
-        if (!pin_R) {
-            CI_CUDA(cudaMallocHost(&pin_R, sizeof(double) * 2 * 64));
-            for (cudaEvent_t &e : ev_R) CI_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-            Rdev.alloc(64);
-            R2dev.alloc(64);
-        }
+        ensure_qr_buffers();
         upload(M, Mdev.ptr);
         upload(R, Rdev.ptr);
         nn(Wb, b, b, Mdev.ptr, b, V, mmax, 1.0, 0.0);
@@ -719,22 +788,49 @@ struct Solver {
             launch("k_copy_cols", k_copy_cols, grid(dim * nr), 256, 0, s, dim, nr, Vr, nr, V + r, mmax);
             CI_CHECK_LAUNCH();
         }
-        // second pass: V <- V G2^{-1/2}, R <- G2^{1/2} R.  V is orthonormal up
-        // to rounding now, so its products go through the basis path
+        CI_CUDA(cudaMemsetAsync(qstat.ptr, 0, sizeof(int), s));
+        second_pass(m, par, ozflag.ptr, 4);
+    }
+
+    // Second pass of either path: V = Q[:, m:m+b] <- V G2^{-1/2} and
+    // R2 = G2^{1/2} R (Rdev), with G2 the Gram matrix of V (k_qr2; a failure
+    // sets `fail` in *flag, and so does bit 0 for an entry of V out of the
+    // shadow's range).  V is orthonormal up to rounding or the conditioning
+    // of the first pass, so its products go through the basis path.  R2 and
+    // the status word go to pinned slot par, then ev_R[par].
+    void second_pass(int m, int par, int *flag, int fail) {
+        double *V = Q.ptr + m;
         const bool vtc = tc && Qfix.ptr;
-        if (vtc) oz_fix(dim, b, V, mmax, Qfix.ptr + m, mmax, ozflag.ptr, s);
+        if (vtc) oz_fix(dim, b, V, mmax, Qfix.ptr + m, mmax, flag, s);
         tn(V, mmax, b, V, mmax, b, Cdev.ptr, nullptr, vtc);
-        launch("k_qr2", k_qr2, 1, 64, 0, s, Cdev.ptr, b, Mdev.ptr, Rdev.ptr, R2dev.ptr, ozflag.ptr);
+        launch("k_qr2", k_qr2, 1, 64, 0, s, Cdev.ptr, b, Mdev.ptr, Rdev.ptr, R2dev.ptr, flag, fail);
         nn(V, mmax, b, Mdev.ptr, b, tmp.ptr, b, 1.0, 0.0, vtc);
-        copy_into_basis(tmp.ptr, b, m, b);
+        copy_into_basis(tmp.ptr, b, m, b, flag);
         CI_CUDA(cudaMemcpyAsync(pin_R + 64 * par, R2dev.ptr, sizeof(double) * b * b, cudaMemcpyDeviceToHost, s));
+        CI_CUDA(cudaMemcpyAsync(pin_stat + par, qstat.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
         CI_CUDA(cudaEventRecord(ev_R[par], s));
     }
 
-    // R of the block QR that wrote pinned slot par (waits for its copy)
-    void take_R(int par, std::vector<double> &R) {
+    // The same on the device without a host sync: G = Wb^T Wb, Cholesky
+    // first pass (k_qr1), V = Wb M, then the second pass.  A block that is
+    // numerically rank deficient, or whose second pass does not settle, is
+    // reported in its status word (take_R): the caller then redoes it with
+    // block_qr from the same Wb.
+    void block_qr_dev(const double *Wb, int m, int par) {
+        ensure_qr_buffers();
+        tn(Wb, b, b, Wb, b, b, Cdev.ptr, nullptr);
+        launch("k_qr1", k_qr1, 1, 64, 0, s, Cdev.ptr, b, hnorm, Mdev.ptr, Rdev.ptr, qstat.ptr);
+        CI_CHECK_LAUNCH();
+        nn(Wb, b, b, Mdev.ptr, b, Q.ptr + m, mmax, 1.0, 0.0);
+        second_pass(m, par, qstat.ptr, 2);
+    }
+
+    // R of the block QR that wrote pinned slot par (waits for its copy) and
+    // that pass's status: 0, else the device path left the block undone
+    int take_R(int par, std::vector<double> &R) {
         CI_CUDA(cudaEventSynchronize(ev_R[par]));
         R.assign(pin_R + 64 * par, pin_R + 64 * par + (size_t)b * b);
+        return pin_stat[par];
     }
 };
 
@@ -865,32 +961,20 @@ void lowest_eigs(const Matrix *H, const ci_eig_opts *opts_in, double *evals, dou
     int m_act = 0;
     std::vector<double> Rlast;
     bool applied = false;   // H V_j already enqueued (before the last host Ritz check)
-    // The coupling R of a block step comes from the device: it is read at the
-    // step's Ritz check (after the next product is enqueued), else after the
-    // next step's block-QR sync; until then its block of T is pending.
-    int par = 0, pend_row = 0, pend_col = 0, pend_par = 0;
-    bool pend_R = false;
-    auto resolve_R = [&]() {
-        sv.take_R(pend_par, Rlast);
-        for (int r = 0; r < b; ++r)
-            for (int c = 0; c < b; ++c) {
-                T[(size_t)(pend_row + r) * mmax + pend_col + c] = Rlast[(size_t)r * b + c];
-                T[(size_t)(pend_col + c) * mmax + pend_row + r] = Rlast[(size_t)r * b + c];
-            }
-        pend_R = false;
-    };
+    // W = H V_j alternates between two buffers, so that a step's W is still
+    // there when its block QR has to be redone on the host path
+    double *Wcur = sv.W.ptr, *Wnext = sv.W2.ptr;
+    int par = 0, host_qr = 0;
     while (true) {
         // W = H V_j, orthogonalised against the whole basis
-        if (!applied) sv.apply(sv.Q.ptr + j0, mmax, b, sv.W.ptr);
+        if (!applied) sv.apply(sv.Q.ptr + j0, mmax, b, Wcur);
         applied = false;
-        sv.project_deferred(sv.W.ptr, b, m_cur, std::max(0, j0 - b), o.reorth_passes);
+        sv.project_deferred(Wcur, b, m_cur, std::max(0, j0 - b), o.reorth_passes);
         ++it;
-        // next block (its Gram matrix is the step's one host sync; the
-        // projection coefficients and the previous step's R copied before it
-        // are then on the host)
-        sv.block_qr(sv.W.ptr, m_cur, o.seed + 0x9E37ull * (uint64_t)(it + 1), par);
-        if (pend_R) resolve_R();
-        sv.take_coef(&coef, true);
+        // next block, on the device: no host sync before the next product
+        // is enqueued
+        sv.block_qr_dev(Wcur, m_cur, par);
+        sv.take_coef(&coef);
         for (int i = 0; i < j0; ++i)
             for (int v = 0; v < b; ++v) {
                 T[(size_t)i * mmax + j0 + v] = coef[(size_t)i * b + v];
@@ -900,26 +984,37 @@ void lowest_eigs(const Matrix *H, const ci_eig_opts *opts_in, double *evals, dou
             for (int v = 0; v < b; ++v)
                 T[(size_t)(j0 + u) * mmax + j0 + v] =
                     0.5 * (coef[(size_t)(j0 + u) * b + v] + coef[(size_t)(j0 + v) * b + u]);
-        pend_R = true;
-        pend_row = m_cur;
-        pend_col = j0;
-        pend_par = par;
+        const int row0 = m_cur, col0 = j0, qpar = par;
         par ^= 1;
         m_act = m_cur;
         j0 = m_cur;
         m_cur += b;
         const bool full = m_cur + b > mmax;
+        // the next product only needs the new block: the GPU computes it
+        // while the host reads the coupling and solves the projected problem
+        // (wasted once, at convergence)
+        if (!full && it < o.max_iter) {
+            sv.apply(sv.Q.ptr + j0, mmax, b, Wnext);
+            applied = true;
+        }
+        if (sv.take_R(qpar, Rlast) != 0) {
+            // rank deficient (or the second pass did not settle): the
+            // rank-revealing host path redoes the block from the same W, and
+            // the product just enqueued is redone with the new block
+            sv.block_qr(Wcur, row0, o.seed + 0x9E37ull * (uint64_t)(it + 1), qpar);
+            sv.take_R(qpar, Rlast);
+            applied = false;
+            ++host_qr;
+        }
+        for (int r = 0; r < b; ++r)
+            for (int c = 0; c < b; ++c) {
+                T[(size_t)(row0 + r) * mmax + col0 + c] = Rlast[(size_t)r * b + c];
+                T[(size_t)(col0 + c) * mmax + row0 + r] = Rlast[(size_t)r * b + c];
+            }
+        std::swap(Wcur, Wnext);
         ++since_check;
         if (since_check >= o.check_every || full || it >= o.max_iter) {
             since_check = 0;
-            // the next product only needs the new block: the GPU computes it
-            // while the host solves the projected problem (wasted once, at
-            // convergence)
-            if (!full && it < o.max_iter) {
-                sv.apply(sv.Q.ptr + j0, mmax, b, sv.W.ptr);
-                applied = true;
-            }
-            resolve_R();
             last = ritz(T, mmax, m_act, b, Rlast, k);
             sv.hnorm = std::max(sv.hnorm, std::max(std::fabs(last.theta.front()), std::fabs(last.theta.back())));
             converged = (int)last.res.size() >= k;
@@ -993,6 +1088,7 @@ void lowest_eigs(const Matrix *H, const ci_eig_opts *opts_in, double *evals, dou
     inf.iterations = it;
     inf.basis_size = m_act;
     inf.hnorm_est = sv.hnorm;
+    inf.host_qr = host_qr;
     inf.converged = 0;
     for (int i = 0; i < k; ++i)
         if (last.res[i] <= o.tol * sv.hnorm) ++inf.converged;

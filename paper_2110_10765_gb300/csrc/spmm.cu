@@ -55,15 +55,14 @@ __device__ __forceinline__ double load_as<double, double>(const double *p) { ret
 
 // row_scale: null, or a per-row factor of the stored values (BF16 form)
 template <class TV, class TX, int NV>
-__global__ void __launch_bounds__(256) k_spmm(int64_t dim, const int64_t *__restrict__ rp,
+__global__ void __launch_bounds__(256) k_spmm(const int64_t *__restrict__ bnd, const int64_t *__restrict__ rp,
                                               const int32_t *__restrict__ col, const TV *__restrict__ val,
                                               const TX *__restrict__ X, TX *__restrict__ Y,
                                               const float *__restrict__ row_scale) {
     constexpr int U = 4;  // nonzeros in flight per lane
     const int lane = threadIdx.x & 31;
-    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t r = warp; r < dim; r += nwarps) {
+    const int64_t r_end = bnd[blockIdx.x + 1];   // rows as in k_spmm8_half
+    for (int64_t r = bnd[blockIdx.x] + (threadIdx.x >> 5); r < r_end; r += blockDim.x >> 5) {
         TX acc[NV];
 #pragma unroll
         for (int i = 0; i < NV; ++i) acc[i] = 0;
@@ -292,16 +291,17 @@ static void launch_spmm(const Matrix *m, const void *X, void *Y, cudaStream_t s)
         launch_spmm_upper<TV, TX, NV>(m, X, Y, s);
         return;
     }
-    int grid = grid_for(m->dim * 32, 256, sm_count() * 8);
+    if (!m->spmm_bnd.ptr) fail(CI_ERR_INTERNAL, "matrix without SpMM row ranges");
+    const int grid = (int)m->spmm_nb;
+    const int64_t *bnd = m->spmm_bnd.ptr;
     const float *scale = m->vtype == CI_BF16_ROWSCALE ? m->row_scale.ptr : nullptr;
     if (NV == 8 && sizeof(TX) == 4) {
-        if (!m->spmm_bnd.ptr) fail(CI_ERR_INTERNAL, "matrix without SpMM row ranges");
-        launch("k_spmm", k_spmm8_half<TV>, (int)m->spmm_nb, 256, 0, s, (const int64_t *)m->spmm_bnd.ptr, m->row_ptr.ptr, m->col.ptr,
-               (const TV *)m->val.ptr, (const float *)X, (float *)Y, (const float *)scale);
+        launch("k_spmm", k_spmm8_half<TV>, grid, 256, 0, s, bnd, m->row_ptr.ptr, m->col.ptr, (const TV *)m->val.ptr,
+               (const float *)X, (float *)Y, (const float *)scale);
         return;
     }
-    launch("k_spmm", k_spmm<TV, TX, NV>, grid, 256, 0, s, m->dim, m->row_ptr.ptr, m->col.ptr,
-           (const TV *)m->val.ptr, (const TX *)X, (TX *)Y, (const float *)scale);
+    launch("k_spmm", k_spmm<TV, TX, NV>, grid, 256, 0, s, bnd, m->row_ptr.ptr, m->col.ptr, (const TV *)m->val.ptr,
+           (const TX *)X, (TX *)Y, (const float *)scale);
 }
 
 template <class TV, class TX>
@@ -399,15 +399,14 @@ void upper_matrix(const Matrix *full, Matrix *out, cudaStream_t s) {
 // eight nonzeros per warp step.  One gather serves twice the vectors of the
 // 8-wide kernel for the same L2 transactions.
 template <class TV>
-__global__ void __launch_bounds__(256) k_spmm16(int64_t dim, const int64_t *__restrict__ rp,
+__global__ void __launch_bounds__(256) k_spmm16(const int64_t *__restrict__ bnd, const int64_t *__restrict__ rp,
                                                 const int32_t *__restrict__ col, const TV *__restrict__ val,
                                                 const float *__restrict__ X, float *__restrict__ Y,
                                                 const float *__restrict__ row_scale) {
     const int lane = threadIdx.x & 31, q = lane & 3, grp = lane >> 2;
-    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t r_end = bnd[blockIdx.x + 1];   // rows as in k_spmm8_half
     const float4 *X4 = reinterpret_cast<const float4 *>(X);
-    for (int64_t r = warp; r < dim; r += nwarps) {
+    for (int64_t r = bnd[blockIdx.x] + (threadIdx.x >> 5); r < r_end; r += blockDim.x >> 5) {
         float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
         const int64_t e1 = rp[r + 1];
         int64_t e = rp[r] + grp;
@@ -441,14 +440,16 @@ __global__ void __launch_bounds__(256) k_spmm16(int64_t dim, const int64_t *__re
 void apply_matrix16(const Matrix *m, const float *X, float *Y, cudaStream_t s) {
     if (m->dim == 0) return;
     if (((uintptr_t)X % 16) != 0 || ((uintptr_t)Y % 16) != 0) fail(CI_ERR_INVALID_ARG, "X and Y must be 16-byte aligned");
-    const int grid = grid_for(m->dim * 32, 256, sm_count() * 8);
     const float *scale = m->vtype == CI_BF16_ROWSCALE ? m->row_scale.ptr : nullptr;
     if (m->upper) fail(CI_ERR_INVALID_ARG, "the 16-vector product takes a full-storage matrix");
+    if (!m->spmm_bnd.ptr) fail(CI_ERR_INTERNAL, "matrix without SpMM row ranges");
+    const int grid = (int)m->spmm_nb;
+    const int64_t *bnd = m->spmm_bnd.ptr;
     if (m->vtype == CI_F32)
-        launch("k_spmm16", k_spmm16<float>, grid, 256, 0, s, m->dim, m->row_ptr.ptr, m->col.ptr,
+        launch("k_spmm16", k_spmm16<float>, grid, 256, 0, s, bnd, m->row_ptr.ptr, m->col.ptr,
                (const float *)m->val.ptr, X, Y, scale);
     else if (m->vtype == CI_BF16_ROWSCALE)
-        launch("k_spmm16", k_spmm16<__nv_bfloat16>, grid, 256, 0, s, m->dim, m->row_ptr.ptr, m->col.ptr,
+        launch("k_spmm16", k_spmm16<__nv_bfloat16>, grid, 256, 0, s, bnd, m->row_ptr.ptr, m->col.ptr,
                (const __nv_bfloat16 *)m->val.ptr, X, Y, scale);
     else
         fail(CI_ERR_INVALID_ARG, "the 16-vector product takes FP32 or BF16 values");

@@ -338,11 +338,15 @@ def test_lowest_eigs_config0_fp64():
 
 
 def test_lowest_eigs_degenerate_closed_form():
-    """Zero interaction: lowest five levels are all 320 MeV (51-fold)."""
+    """Zero interaction: lowest five levels are all 320 MeV (51-fold).  The
+    Krylov space of a diagonal H with few distinct levels runs out, so a
+    block turns rank deficient: the device block QR hands it to the host's
+    rank-revealing path (deflation and random completion)."""
     inp = inputs(1, 4, 4, -1, zero=True, dtype=np.float64)
     M = gpu_problem(inp).build_H("f64")
     ev, info = M.lowest_eigs(k=5)
     assert np.allclose(ev, 320.0, rtol=0, atol=1e-8)
+    assert info["host_qr"] >= 1
 
 
 def test_lowest_eigs_nmax2_subspace_fp32():
@@ -363,6 +367,7 @@ def test_lowest_eigs_config1_fp32():
     ref = np.array(golden()["c1"]["lowest"])
     assert np.all(np.abs(ev - ref) <= EIG_REL * np.maximum(np.abs(ref), 1)), ev - ref
     assert max(info["residual"]) <= 1e-4 * info["hnorm_est"]
+    assert info["host_qr"] == 0   # every block step orthonormalised on the device
 
 
 @pytest.mark.parametrize("case", [(1, 2, 2, -1), (2, 2, 1, 1), (1, 1, 1, -1)])
