@@ -178,6 +178,36 @@ bool trace_on();
 void trace_begin(const char *name, cudaStream_t s, void **token);
 void trace_end(void *token, cudaStream_t s);
 
+// Programmatic dependent launch: a kernel launched by launch_pdl may be
+// set up while the kernel before it on the stream drains, so it must call
+// pdl_wait() before its first access to memory that kernel wrote (every
+// kernel launched this way calls it first thing; without the launch
+// attribute the wait returns at once).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <class K, class... Args>
+inline void launch_pdl(const char *name, K kernel, dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args... args) {
+    void *tok = nullptr;
+    if (trace_on()) trace_begin(name, s, &tok);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, args...);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (tok) trace_end(tok, s);
+    if (e != cudaSuccess)
+        fail(e == cudaErrorMemoryAllocation ? CI_ERR_OOM : CI_ERR_CUDA, "launch of %s failed: %s", name,
+             cudaGetErrorString(e));
+}
+
 template <class K, class... Args>
 inline void launch(const char *name, K kernel, dim3 grid, dim3 block, size_t smem, cudaStream_t s,
                    Args... args) {

@@ -30,6 +30,7 @@ constexpr size_t kTnSmem = 96 * 1024;   // shared memory of the tiled product
 __global__ void __launch_bounds__(kTnThreads) k_tn_partial(int64_t dim, const double *__restrict__ A, int lda, int na,
                                                            const double *__restrict__ B, int ldb, int nb,
                                                            double *__restrict__ part, int64_t rows_per_blk) {
+    pdl_wait();
     extern __shared__ double sm[];
     double *As = sm;             // [kTR][na]
     double *Bs = sm + kTR * na;  // [kTR][nb]
@@ -93,6 +94,7 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 __global__ void __launch_bounds__(kTnThreads) k_tn_tiled(int64_t dim, const double *__restrict__ A, int lda, int na,
                                                          const double *__restrict__ B, int ldb,
                                                          double *__restrict__ part, int64_t rows_per_blk, int tr) {
+    pdl_wait();
     extern __shared__ double sm[];
     const int nap = (na + 3) & ~3;
     const int rowlen = nap + 8;                  // one staged row: A part, then B part
@@ -177,6 +179,7 @@ template <int NB>
 __global__ void __launch_bounds__(256) k_nn_rows(int64_t dim, const double *__restrict__ A, int lda, int na,
                                                  const double *__restrict__ C, double *__restrict__ W, int ldw,
                                                  double alpha, double beta) {
+    pdl_wait();
     __shared__ double Cs[kMaxNa * NB];
     for (int e = threadIdx.x; e < na * NB; e += blockDim.x) Cs[e] = C[e];
     __syncthreads();
@@ -202,6 +205,7 @@ __global__ void __launch_bounds__(256) k_nn_rows(int64_t dim, const double *__re
 // (deterministic).
 __global__ void __launch_bounds__(256) k_reduce_partial(const double *__restrict__ part, int nblk, int n,
                                                         double *__restrict__ out) {
+    pdl_wait();
     const int lane = threadIdx.x & 31;
     const int o = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (o >= n) return;
@@ -217,6 +221,7 @@ __global__ void __launch_bounds__(256) k_reduce_partial(const double *__restrict
 __global__ void __launch_bounds__(256) k_nn_update(int64_t dim, const double *__restrict__ A, int lda, int na,
                                                    const double *__restrict__ C, int nb, double *__restrict__ W,
                                                    int ldw, double alpha, double beta) {
+    pdl_wait();
     __shared__ double Cs[kMaxNa * 8];
     for (int e = threadIdx.x; e < na * nb; e += blockDim.x) Cs[e] = C[e];
     __syncthreads();
@@ -234,11 +239,13 @@ __global__ void __launch_bounds__(256) k_nn_update(int64_t dim, const double *__
 }
 
 __global__ void k_cvt_to_f32(int64_t dim, int nb, const double *__restrict__ src, int lds, float *__restrict__ dst) {
+    pdl_wait();
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < dim * nb; t += (int64_t)gridDim.x * blockDim.x)
         dst[t] = (float)src[(t / nb) * lds + t % nb];
 }
 
 __global__ void k_cvt_to_f64(int64_t dim, int nb, const float *__restrict__ src, double *__restrict__ dst, int ldd) {
+    pdl_wait();
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < dim * nb; t += (int64_t)gridDim.x * blockDim.x)
         dst[(t / nb) * ldd + t % nb] = (double)src[t];
 }
@@ -265,6 +272,7 @@ __global__ void k_unpack16(int64_t dim, const float *__restrict__ Y16, double *_
 
 __global__ void k_copy_cols(int64_t dim, int nb, const double *__restrict__ src, int lds, double *__restrict__ dst,
                             int ldd) {
+    pdl_wait();
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < dim * nb; t += (int64_t)gridDim.x * blockDim.x)
         dst[(t / nb) * ldd + t % nb] = src[(t / nb) * lds + t % nb];
 }
@@ -291,6 +299,7 @@ __global__ void k_zero_cols(int64_t dim, int nb, double *dst, int ldd) {
 // block is then left to the rank-revealing host path.
 __global__ void k_qr1(const double *__restrict__ G, int b, double hnorm, double *__restrict__ M,
                       double *__restrict__ R, int *stat) {
+    pdl_wait();
     __shared__ double A[64], Li[64], rd[8];
     __shared__ int bad;
     const int t = threadIdx.x, i = t / b, j = t % b;
@@ -347,6 +356,7 @@ __global__ void k_qr1(const double *__restrict__ G, int b, double hnorm, double 
 // iterations leave T off the identity or a column has no length.
 __global__ void k_qr2(const double *__restrict__ G, int b, double *__restrict__ Mi, const double *__restrict__ R,
                       double *__restrict__ R2, int *flag, int fail) {
+    pdl_wait();
     __shared__ double Y[64], Z[64], Tm[64], d[8];
     const int t = threadIdx.x, i = t / b, j = t % b;
     const bool on = t < b * b;
@@ -477,11 +487,11 @@ static void fp64_tn(int64_t dim, const double *A, int lda, int na, const double 
         int tr = (int)(kTnSmem / sizeof(double)) / (2 * (nap + 8));
         if (tr > 128) tr = 128;
         const size_t smem = sizeof(double) * std::max((size_t)2 * tr * (nap + 8), (size_t)S * nap * 8);
-        launch("k_tn_partial", k_tn_tiled, nblk, kTnThreads, smem, s, dim, A, lda, na, B, ldb, part,
+        launch_pdl("k_tn_partial", k_tn_tiled, nblk, kTnThreads, smem, s, dim, A, lda, na, B, ldb, part,
                rows_per_blk, tr);
     } else {
         const size_t smem = sizeof(double) * kTR * (na + nb);
-        launch("k_tn_partial", k_tn_partial, nblk, kTnThreads, smem, s, dim, A, lda, na, B, ldb, nb, part,
+        launch_pdl("k_tn_partial", k_tn_partial, nblk, kTnThreads, smem, s, dim, A, lda, na, B, ldb, nb, part,
                rows_per_blk);
     }
 }
@@ -491,9 +501,9 @@ static void fp64_nn(int64_t dim, const double *A, int lda, int na, const double 
                     double alpha, double beta, cudaStream_t s) {
     const int grid = nb == 8 ? grid_for(dim, 256, sm_count() * 8) : grid_for(dim * nb, 256, sm_count() * 8);
     if (nb == 8)
-        launch("k_nn_update", k_nn_rows<8>, grid, 256, 0, s, dim, A, lda, na, C, Wout, ldw, alpha, beta);
+        launch_pdl("k_nn_update", k_nn_rows<8>, grid, 256, 0, s, dim, A, lda, na, C, Wout, ldw, alpha, beta);
     else
-        launch("k_nn_update", k_nn_update, grid, 256, 0, s, dim, A, lda, na, C, nb, Wout, ldw, alpha, beta);
+        launch_pdl("k_nn_update", k_nn_update, grid, 256, 0, s, dim, A, lda, na, C, nb, Wout, ldw, alpha, beta);
     CI_CHECK_LAUNCH();
 }
 
@@ -588,7 +598,7 @@ struct Solver {
         if (tc && Qfix.ptr) {
             oz_copy_fix(dim, nc, src, lds, Q.ptr + c0, mmax, Qfix.ptr + c0, mmax, flag ? flag : ozflag.ptr, s);
         } else {
-            launch("k_copy_cols", k_copy_cols, grid(dim * nc), 256, 0, s, dim, nc, src, lds, Q.ptr + c0, mmax);
+            launch_pdl("k_copy_cols", k_copy_cols, grid(dim * nc), 256, 0, s, dim, nc, src, lds, Q.ptr + c0, mmax);
         }
         CI_CHECK_LAUNCH();
     }
@@ -597,7 +607,7 @@ struct Solver {
             std::vector<double> *host, bool basis = false) {
         if (use_tc(basis, na, nb)) {
             oz_tn(dim, shadow(A), lda, na, B, ldb, part.ptr, oz_nblk, ozflag.ptr, s);
-            launch("k_reduce_partial", k_reduce_partial, (na * nb + 7) / 8, 256, 0, s, part.ptr, oz_nblk, na * nb,
+            launch_pdl("k_reduce_partial", k_reduce_partial, (na * nb + 7) / 8, 256, 0, s, part.ptr, oz_nblk, na * nb,
                    Cout);
             CI_CHECK_LAUNCH();
             if (host) {
@@ -608,7 +618,7 @@ struct Solver {
             return;
         }
         fp64_tn(dim, A, lda, na, B, ldb, nb, part.ptr, nblk, rows_per_blk, s);
-        launch("k_reduce_partial", k_reduce_partial, (na * nb + 7) / 8, 256, 0, s, part.ptr, nblk, na * nb, Cout);
+        launch_pdl("k_reduce_partial", k_reduce_partial, (na * nb + 7) / 8, 256, 0, s, part.ptr, nblk, na * nb, Cout);
         CI_CHECK_LAUNCH();
         if (host) {
             host->resize((size_t)na * nb);
@@ -634,12 +644,12 @@ struct Solver {
     // Wout [dim][nb] (contiguous) = H V, V with leading dimension ldv.
     void apply(const double *V, int ldv, int nb, double *Wout) {
         if (f64) {
-            launch("k_copy_cols", k_copy_cols, grid(dim * nb), 256, 0, s, dim, nb, V, ldv, X64.ptr, nb);
+            launch_pdl("k_copy_cols", k_copy_cols, grid(dim * nb), 256, 0, s, dim, nb, V, ldv, X64.ptr, nb);
             apply_matrix(H, X64.ptr, Wout, nb, s);
         } else {
-            launch("k_cvt_to_f32", k_cvt_to_f32, grid(dim * nb), 256, 0, s, dim, nb, V, ldv, X32.ptr);
+            launch_pdl("k_cvt_to_f32", k_cvt_to_f32, grid(dim * nb), 256, 0, s, dim, nb, V, ldv, X32.ptr);
             apply_matrix(H, X32.ptr, Y32.ptr, nb, s);
-            launch("k_cvt_to_f64", k_cvt_to_f64, grid(dim * nb), 256, 0, s, dim, nb, Y32.ptr, Wout, nb);
+            launch_pdl("k_cvt_to_f64", k_cvt_to_f64, grid(dim * nb), 256, 0, s, dim, nb, Y32.ptr, Wout, nb);
         }
         CI_CHECK_LAUNCH();
     }
@@ -785,7 +795,7 @@ struct Solver {
                     nn(V, mmax, r, Cdev.ptr, nr, Vr, nr, -1.0, 1.0);
                 }
             }
-            launch("k_copy_cols", k_copy_cols, grid(dim * nr), 256, 0, s, dim, nr, Vr, nr, V + r, mmax);
+            launch_pdl("k_copy_cols", k_copy_cols, grid(dim * nr), 256, 0, s, dim, nr, Vr, nr, V + r, mmax);
             CI_CHECK_LAUNCH();
         }
         CI_CUDA(cudaMemsetAsync(qstat.ptr, 0, sizeof(int), s));
@@ -803,7 +813,7 @@ struct Solver {
         const bool vtc = tc && Qfix.ptr;
         if (vtc) oz_fix(dim, b, V, mmax, Qfix.ptr + m, mmax, flag, s);
         tn(V, mmax, b, V, mmax, b, Cdev.ptr, nullptr, vtc);
-        launch("k_qr2", k_qr2, 1, 64, 0, s, Cdev.ptr, b, Mdev.ptr, Rdev.ptr, R2dev.ptr, flag, fail);
+        launch_pdl("k_qr2", k_qr2, 1, 64, 0, s, Cdev.ptr, b, Mdev.ptr, Rdev.ptr, R2dev.ptr, flag, fail);
         nn(V, mmax, b, Mdev.ptr, b, tmp.ptr, b, 1.0, 0.0, vtc);
         copy_into_basis(tmp.ptr, b, m, b, flag);
         CI_CUDA(cudaMemcpyAsync(pin_R + 64 * par, R2dev.ptr, sizeof(double) * b * b, cudaMemcpyDeviceToHost, s));
@@ -819,7 +829,7 @@ struct Solver {
     void block_qr_dev(const double *Wb, int m, int par) {
         ensure_qr_buffers();
         tn(Wb, b, b, Wb, b, b, Cdev.ptr, nullptr);
-        launch("k_qr1", k_qr1, 1, 64, 0, s, Cdev.ptr, b, hnorm, Mdev.ptr, Rdev.ptr, qstat.ptr);
+        launch_pdl("k_qr1", k_qr1, 1, 64, 0, s, Cdev.ptr, b, hnorm, Mdev.ptr, Rdev.ptr, qstat.ptr);
         CI_CHECK_LAUNCH();
         nn(Wb, b, b, Mdev.ptr, b, Q.ptr + m, mmax, 1.0, 0.0);
         second_pass(m, par, qstat.ptr, 2);
@@ -1335,7 +1345,7 @@ void lowest_eigs_lobpcg(const Matrix *H, const ci_eig_opts *opts_in, const int32
         project_out(X.ptr, nullptr, Wd.ptr, nullptr);
         bool useW = chol_qr(Wd, nullptr, &wn);
         if (!useW) {   // the preconditioned residuals lie in span(X) (e.g. diagonal H): take R itself
-            launch("k_copy_cols", k_copy_cols, sv.grid(dim * nb), 256, 0, s, dim, nb, R.ptr, nb, Wd.ptr, nb);
+            launch_pdl("k_copy_cols", k_copy_cols, sv.grid(dim * nb), 256, 0, s, dim, nb, R.ptr, nb, Wd.ptr, nb);
             project_out(X.ptr, nullptr, Wd.ptr, nullptr);
             project_out(X.ptr, nullptr, Wd.ptr, nullptr);
             useW = chol_qr(Wd, nullptr, nullptr);
@@ -1410,7 +1420,7 @@ void lowest_eigs_lobpcg(const Matrix *H, const ci_eig_opts *opts_in, const int32
         inf.residual[i] = std::sqrt(std::max(h[(size_t)i * nb + i], 0.0));
     }
     if (evecs) {
-        launch("k_copy_cols", k_copy_cols, sv.grid(dim * k), 256, 0, s, dim, k, X.ptr, nb, evecs, k);
+        launch_pdl("k_copy_cols", k_copy_cols, sv.grid(dim * k), 256, 0, s, dim, k, X.ptr, nb, evecs, k);
         CI_CHECK_LAUNCH();
     }
     CI_CUDA(cudaStreamSynchronize(s));
@@ -1450,9 +1460,9 @@ void refine_eigs(Problem *P, int k, int iters, double *X, double *evals, double 
         for (int g = 0; g < nc; g += 8) {
             const int m = std::min(8, nc - g);
             CI_CUDA(cudaMemsetAsync(T8.ptr, 0, sizeof(double) * dim * 8, s));
-            launch("k_copy_cols", k_copy_cols, sv.grid(dim * m), 256, 0, s, dim, m, S.ptr + c0 + g, n2, T8.ptr, 8);
+            launch_pdl("k_copy_cols", k_copy_cols, sv.grid(dim * m), 256, 0, s, dim, m, S.ptr + c0 + g, n2, T8.ptr, 8);
             h64_apply(P, T8.ptr, Y8.ptr, s);
-            launch("k_copy_cols", k_copy_cols, sv.grid(dim * m), 256, 0, s, dim, m, Y8.ptr, 8, HS.ptr + c0 + g, n2);
+            launch_pdl("k_copy_cols", k_copy_cols, sv.grid(dim * m), 256, 0, s, dim, m, Y8.ptr, 8, HS.ptr + c0 + g, n2);
         }
     };
     auto gram = [&](const double *A, const double *B, int n, std::vector<double> &h) {
@@ -1462,9 +1472,9 @@ void refine_eigs(Problem *P, int k, int iters, double *X, double *evals, double 
     auto rotate = [&](int n, const std::vector<double> &C) {
         sv.upload(C, sv.Cdev.ptr);
         sv.nn(S.ptr, n2, n, sv.Cdev.ptr, k, Tmp.ptr, k, 1.0, 0.0);
-        launch("k_copy_cols", k_copy_cols, sv.grid(dim * k), 256, 0, s, dim, k, Tmp.ptr, k, S.ptr, n2);
+        launch_pdl("k_copy_cols", k_copy_cols, sv.grid(dim * k), 256, 0, s, dim, k, Tmp.ptr, k, S.ptr, n2);
         sv.nn(HS.ptr, n2, n, sv.Cdev.ptr, k, Tmp.ptr, k, 1.0, 0.0);
-        launch("k_copy_cols", k_copy_cols, sv.grid(dim * k), 256, 0, s, dim, k, Tmp.ptr, k, HS.ptr, n2);
+        launch_pdl("k_copy_cols", k_copy_cols, sv.grid(dim * k), 256, 0, s, dim, k, Tmp.ptr, k, HS.ptr, n2);
     };
     std::vector<double> theta(k), C, ga, gb;
     // Rayleigh-Ritz on n columns of S (pencil S^T H S, S^T S)
@@ -1480,17 +1490,17 @@ void refine_eigs(Problem *P, int k, int iters, double *X, double *evals, double 
         rotate(n, C);
         return true;
     };
-    launch("k_copy_cols", k_copy_cols, sv.grid(dim * k), 256, 0, s, dim, k, X, k, S.ptr, n2);
+    launch_pdl("k_copy_cols", k_copy_cols, sv.grid(dim * k), 256, 0, s, dim, k, X, k, S.ptr, n2);
     apply_cols(0, k);
     if (!rayleigh_ritz(k)) fail(CI_ERR_INVALID_ARG, "the k vectors are linearly dependent");
     std::vector<double> rn(k, 0.0);
     auto residuals = [&]() {
         sv.upload(theta, sv.theta_dev.ptr);
         // R = HX - X Theta into the second half of S (HX made contiguous first)
-        launch("k_copy_cols", k_copy_cols, sv.grid(dim * k), 256, 0, s, dim, k, HS.ptr, n2, Tmp.ptr, k);
+        launch_pdl("k_copy_cols", k_copy_cols, sv.grid(dim * k), 256, 0, s, dim, k, HS.ptr, n2, Tmp.ptr, k);
         launch("k_residual", k_residual<double>, sv.grid(dim * k), 256, 0, s, dim, k, Tmp.ptr, S.ptr, n2,
                sv.theta_dev.ptr, Rb.ptr);
-        launch("k_copy_cols", k_copy_cols, sv.grid(dim * k), 256, 0, s, dim, k, Rb.ptr, k, S.ptr + k, n2);
+        launch_pdl("k_copy_cols", k_copy_cols, sv.grid(dim * k), 256, 0, s, dim, k, Rb.ptr, k, S.ptr + k, n2);
         std::vector<double> h;
         gram(S.ptr + k, S.ptr + k, k, h);
         for (int v = 0; v < k; ++v) rn[v] = std::sqrt(std::max(h[(size_t)v * k + v], 0.0));
@@ -1523,12 +1533,12 @@ void refine_eigs(Problem *P, int k, int iters, double *X, double *evals, double 
             for (int c = 0; c < k; ++c) Mi[(size_t)i * k + c] *= dsc[i];
         sv.upload(Mi, sv.Cdev.ptr);
         sv.nn(S.ptr + k, n2, k, sv.Cdev.ptr, k, Tmp.ptr, k, 1.0, 0.0);
-        launch("k_copy_cols", k_copy_cols, sv.grid(dim * k), 256, 0, s, dim, k, Tmp.ptr, k, S.ptr + k, n2);
+        launch_pdl("k_copy_cols", k_copy_cols, sv.grid(dim * k), 256, 0, s, dim, k, Tmp.ptr, k, S.ptr + k, n2);
         apply_cols(k, k);
         if (!rayleigh_ritz(n2)) break;
     }
     residuals();
-    launch("k_copy_cols", k_copy_cols, sv.grid(dim * k), 256, 0, s, dim, k, S.ptr, n2, X, k);
+    launch_pdl("k_copy_cols", k_copy_cols, sv.grid(dim * k), 256, 0, s, dim, k, S.ptr, n2, X, k);
     CI_CUDA(cudaStreamSynchronize(s));
     for (int v = 0; v < k; ++v) {
         evals[v] = theta[v];
@@ -1602,14 +1612,14 @@ extern "C" ci_status ci_basis_product(int32_t op, int32_t method, int64_t n, con
                 int ldbt = ldb;
                 if (method == CI_PRODUCT_TC && (ldb & 1)) {   // the tensor copies want an even row stride
                     Bc.alloc((size_t)n * 8);
-                    launch("k_copy_cols", k_copy_cols, grid_for((int64_t)n * 8, 256, sm_count() * 8), 256, 0, s,
+                    launch_pdl("k_copy_cols", k_copy_cols, grid_for((int64_t)n * 8, 256, sm_count() * 8), 256, 0, s,
                            (int64_t)n, 8, B, ldb, Bc.ptr, 8);
                     Bt = Bc.ptr;
                     ldbt = 8;
                 }
                 if (method == CI_PRODUCT_TC) oz_tn(n, Y.ptr, ldy, na, Bt, ldbt, part.ptr, nblk, flag.ptr, s);
                 else fp64_tn(n, A, lda, na, B, ldb, nb, part.ptr, nblk, (n + nblk - 1) / nblk, s);
-                launch("k_reduce_partial", k_reduce_partial, (na * nb + 7) / 8, 256, 0, s, part.ptr, nblk, na * nb, C);
+                launch_pdl("k_reduce_partial", k_reduce_partial, (na * nb + 7) / 8, 256, 0, s, part.ptr, nblk, na * nb, C);
             }
         } else if (n > 0) {
             if (method == CI_PRODUCT_TC) oz_nn(n, Y.ptr, ldy, na, C, B, ldb, alpha, beta, flag.ptr, s);

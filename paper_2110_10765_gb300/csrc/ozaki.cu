@@ -122,6 +122,7 @@ constexpr int kWaitPolls = 1 << 22;   // bounded mbarrier waits (error flag 2 wh
 // element, consecutive threads along a row (32-bit indices: dim * nc < 2^31).
 __global__ void k_oz_fix(int dim, int nc, const double *__restrict__ A, int lda, unsigned long long *__restrict__ Y,
                          int ldy, int *flag) {
+    pdl_wait();
     int bad = 0;
     const int total = dim * nc;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
@@ -135,6 +136,7 @@ __global__ void k_oz_fix(int dim, int nc, const double *__restrict__ A, int lda,
 // column copy into the basis that keeps the shadow current.
 __global__ void k_oz_copy_fix(int dim, int nc, const double *__restrict__ src, int lds, double *__restrict__ dst,
                               int ldd, unsigned long long *__restrict__ Y, int ldy, int *flag) {
+    pdl_wait();
     int bad = 0;
     const int total = dim * nc;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
@@ -223,6 +225,7 @@ __global__ void __launch_bounds__(kNnThreads, 1) k_oz_nn(const __grid_constant__
                                                   int64_t dim, int na, const double *__restrict__ C,
                                                   double *__restrict__ W, int ldw, double alpha, double beta,
                                                   int *flag) {
+    pdl_wait();
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ __align__(8) uint64_t rfull[kMaxRaw], rempty[kMaxRaw], full[2], empty[2], tfull[2], tempty[2], done;
     __shared__ uint32_t tmem_base;
@@ -505,6 +508,7 @@ __global__ void __launch_bounds__(kTnThreads, 1) k_oz_tn(const __grid_constant__
                                                   const __grid_constant__ CUtensorMap bmap, int m, int bc, int mb,
                                                   int bw, int64_t dim, int na, const double *__restrict__ B, int ldb,
                                                   double *__restrict__ part, int64_t rows_per_blk, int *flag) {
+    pdl_wait();
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ __align__(8) uint64_t rfull[kMaxRaw], rempty[kMaxRaw], full[2], empty[2], tfull[2], tempty[2], done;
     __shared__ uint32_t tmem_base;
@@ -770,7 +774,7 @@ void oz_fix(int64_t dim, int nc, const double *A, int lda, unsigned long long *Y
             cudaStream_t s) {
     if (dim == 0 || nc == 0) return;
     if (dim * nc >= ((int64_t)1 << 31)) fail(CI_ERR_CAPACITY, "basis shadow: %lld entries", (long long)(dim * nc));
-    launch("k_oz_fix", k_oz_fix, grid_for(dim * nc, 256, sm_count() * 16), 256, 0, s, (int)dim, nc, A, lda, Y, ldy,
+    launch_pdl("k_oz_fix", k_oz_fix, grid_for(dim * nc, 256, sm_count() * 16), 256, 0, s, (int)dim, nc, A, lda, Y, ldy,
            flag);
 }
 
@@ -778,7 +782,7 @@ void oz_copy_fix(int64_t dim, int nc, const double *src, int lds, double *dst, i
                  int *flag, cudaStream_t s) {
     if (dim == 0 || nc == 0) return;
     if (dim * nc >= ((int64_t)1 << 31)) fail(CI_ERR_CAPACITY, "basis shadow: %lld entries", (long long)(dim * nc));
-    launch("k_copy_cols", k_oz_copy_fix, grid_for(dim * nc, 256, sm_count() * 16), 256, 0, s, (int)dim, nc, src, lds,
+    launch_pdl("k_copy_cols", k_oz_copy_fix, grid_for(dim * nc, 256, sm_count() * 16), 256, 0, s, (int)dim, nc, src, lds,
            dst, ldd, Y, ldy, flag);
 }
 
@@ -795,7 +799,7 @@ void oz_nn(int64_t dim, const unsigned long long *Y, int ldy, int na, const doub
     const CUtensorMap map = rows_map(Y, ldy, dim, na, bc, 128, m);
     const int64_t ntiles = (dim + 127) / 128;
     const int grid = (int)std::min<int64_t>(ntiles, sm_count());
-    launch("k_oz_nn", k_oz_nn, grid, kNnThreads, oz_nn_smem(na), s, map, m, bc, dim, na, C, W, ldw, alpha, beta,
+    launch_pdl("k_oz_nn", k_oz_nn, grid, kNnThreads, oz_nn_smem(na), s, map, m, bc, dim, na, C, W, ldw, alpha, beta,
            flag);
 }
 
@@ -821,7 +825,7 @@ void oz_tn(int64_t dim, const unsigned long long *Y, int ldy, int na, const doub
     const CUtensorMap bmap = rows_map(B, ldb, std::max<int64_t>(dim, 1), 8, bw, kOzTnRows, mb);
     const int64_t rpb = (dim + nblk - 1) / nblk;
     auto kern = na <= 16 ? k_oz_tn<16> : (na <= 32 ? k_oz_tn<32> : k_oz_tn<64>);
-    launch("k_oz_tn", kern, nblk, kTnThreads, kOzTnSmem, s, ymap, bmap, m, bc, mb, bw, dim, na, B, ldb, part, rpb, flag);
+    launch_pdl("k_oz_tn", kern, nblk, kTnThreads, kOzTnSmem, s, ymap, bmap, m, bc, mb, bw, dim, na, B, ldb, part, rpb, flag);
 }
 
 }  // namespace ci

@@ -59,6 +59,7 @@ __global__ void __launch_bounds__(256) k_spmm(const int64_t *__restrict__ bnd, c
                                               const int32_t *__restrict__ col, const TV *__restrict__ val,
                                               const TX *__restrict__ X, TX *__restrict__ Y,
                                               const float *__restrict__ row_scale) {
+    pdl_wait();
     constexpr int U = 4;  // nonzeros in flight per lane
     const int lane = threadIdx.x & 31;
     const int64_t r_end = bnd[blockIdx.x + 1];   // rows as in k_spmm8_half
@@ -124,6 +125,7 @@ __global__ void __launch_bounds__(256) k_spmm8_half(const int64_t *__restrict__ 
                                                     const int32_t *__restrict__ col, const TV *__restrict__ val,
                                                     const float *__restrict__ X, float *__restrict__ Y,
                                                     const float *__restrict__ row_scale) {
+    pdl_wait();
     constexpr int U = 4;  // nonzeros in flight per lane pair
     const int lane = threadIdx.x & 31, half = lane & 1, pair = lane >> 1;
     const int64_t r_end = bnd[blockIdx.x + 1];
@@ -296,11 +298,11 @@ static void launch_spmm(const Matrix *m, const void *X, void *Y, cudaStream_t s)
     const int64_t *bnd = m->spmm_bnd.ptr;
     const float *scale = m->vtype == CI_BF16_ROWSCALE ? m->row_scale.ptr : nullptr;
     if (NV == 8 && sizeof(TX) == 4) {
-        launch("k_spmm", k_spmm8_half<TV>, grid, 256, 0, s, bnd, m->row_ptr.ptr, m->col.ptr, (const TV *)m->val.ptr,
+        launch_pdl("k_spmm", k_spmm8_half<TV>, grid, 256, 0, s, bnd, m->row_ptr.ptr, m->col.ptr, (const TV *)m->val.ptr,
                (const float *)X, (float *)Y, (const float *)scale);
         return;
     }
-    launch("k_spmm", k_spmm<TV, TX, NV>, grid, 256, 0, s, bnd, m->row_ptr.ptr, m->col.ptr, (const TV *)m->val.ptr,
+    launch_pdl("k_spmm", k_spmm<TV, TX, NV>, grid, 256, 0, s, bnd, m->row_ptr.ptr, m->col.ptr, (const TV *)m->val.ptr,
            (const TX *)X, (TX *)Y, (const float *)scale);
 }
 
