@@ -209,14 +209,16 @@ def ncu_traffic():
     return out
 
 
-def algorithmic_bytes(kernel, dim, nnz, nvec=8):
-    """Algorithmic DRAM bytes of one launch of the kernels with a byte roofline."""
+def algorithmic_bytes(kernel, dim, nnz, nvec=8, y_bytes=4):
+    """Algorithmic DRAM bytes of one launch of the kernels with a byte roofline
+    (y_bytes: 4 for the standalone FP32 product, 8 inside the solve, where the
+    SpMM writes the Lanczos block W in FP64)."""
     if kernel == "k_fill_rows":      # col i32 + val f32 written, row_ptr read
         return 8 * nnz + 8 * (dim + 1)
     if kernel == "build_H":          # col + val written, row counts written and read, row_ptr written
         return 8 * nnz + 12 * dim + 8
-    if kernel == "k_spmm":           # CSR streamed once, X read once, Y written
-        return 8 * nnz + 8 * (dim + 1) + 2 * 4 * nvec * dim
+    if kernel == "k_spmm":           # CSR streamed once, X (FP32) read once, Y written
+        return 8 * nnz + 8 * (dim + 1) + 4 * nvec * dim + y_bytes * nvec * dim
     if kernel == "k_spmm16":         # the same with 16-vector X and Y rows
         return 8 * nnz + 8 * (dim + 1) + 2 * 4 * 16 * dim
     return None   # k_count_rows walks per-row segment tables: latency-bound, no byte roofline
@@ -341,14 +343,12 @@ def run_ours(args):
     roofs = []
     traffic_of = ncu_traffic() if nnz == 102601752 else {}
     for name, v in kern.items():
-        b = algorithmic_bytes(name, dim, nnz)
+        b = algorithmic_bytes(name, dim, nnz, y_bytes=8)
         if b is None:
             continue
         avg_s = v[1] / max(v[0], 1) * 1e-3
-        if name == "k_spmm":
-            # inside the solve the SpMM runs on 8-vector blocks and the final
-            # residual blocks; take the standalone measurement's bytes model
-            pass
+        # inside the solve the SpMM runs on the 8-vector blocks (Y in FP64),
+        # once per solve on the final residual block
         traffic = traffic_of.get(name)
         roofs.append({"kernel": name, "bound": "hbm", "achieved": round(b / avg_s / 1e9, 1), "peak": hbm,
                       "unit": "GB/s", "frac": round(b / avg_s / 1e9 / hbm, 4), "traffic": traffic,

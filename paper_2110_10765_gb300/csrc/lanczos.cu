@@ -527,6 +527,7 @@ struct Solver {
     int64_t rows_per_blk;
     DevBuf<double> Q, W, W2, tmp, part, Cdev, Mdev, theta_dev, Cacc;
     DevBuf<float> X32, Y32;
+    int x32_col = -1;   // X32 holds Q[:, x32_col : x32_col + b] in FP32 (else -1)
     DevBuf<double> X64;
     double hnorm = 0.0;
     // pinned copy of the projection coefficients of the latest step, read
@@ -593,10 +594,14 @@ struct Solver {
     // the shadow of the basis column that A points at
     const unsigned long long *shadow(const double *A) const { return Qfix.ptr + (A - Q.ptr); }
     // Q[:, c0:c0+nc] = src (leading dimension lds), with the shadow
-    // (an entry out of the shadow's range sets bit 0 of *flag, ozflag by default)
-    void copy_into_basis(const double *src, int lds, int c0, int nc, int *flag = nullptr) {
+    // (an entry out of the shadow's range sets bit 0 of *flag, ozflag by
+    // default).  x32: nullable, also receives the columns in FP32 (the next
+    // SpMM's input; x32_col records which block it holds).
+    void copy_into_basis(const double *src, int lds, int c0, int nc, int *flag = nullptr, float *x32 = nullptr) {
+        x32_col = -1;
         if (tc && Qfix.ptr) {
-            oz_copy_fix(dim, nc, src, lds, Q.ptr + c0, mmax, Qfix.ptr + c0, mmax, flag ? flag : ozflag.ptr, s);
+            oz_copy_fix(dim, nc, src, lds, Q.ptr + c0, mmax, Qfix.ptr + c0, mmax, x32, flag ? flag : ozflag.ptr, s);
+            if (x32) x32_col = c0;
         } else {
             launch_pdl("k_copy_cols", k_copy_cols, grid(dim * nc), 256, 0, s, dim, nc, src, lds, Q.ptr + c0, mmax);
         }
@@ -647,9 +652,14 @@ struct Solver {
             launch_pdl("k_copy_cols", k_copy_cols, grid(dim * nb), 256, 0, s, dim, nb, V, ldv, X64.ptr, nb);
             apply_matrix(H, X64.ptr, Wout, nb, s);
         } else {
-            launch_pdl("k_cvt_to_f32", k_cvt_to_f32, grid(dim * nb), 256, 0, s, dim, nb, V, ldv, X32.ptr);
-            apply_matrix(H, X32.ptr, Y32.ptr, nb, s);
-            launch_pdl("k_cvt_to_f64", k_cvt_to_f64, grid(dim * nb), 256, 0, s, dim, nb, Y32.ptr, Wout, nb);
+            // a block just written by the second pass comes with its FP32 copy
+            if (!(nb == b && ldv == mmax && x32_col >= 0 && V == Q.ptr + x32_col))
+                launch_pdl("k_cvt_to_f32", k_cvt_to_f32, grid(dim * nb), 256, 0, s, dim, nb, V, ldv, X32.ptr);
+            x32_col = -1;
+            if (!(nb == 8 && apply_matrix8_f64out(H, X32.ptr, Wout, s))) {
+                apply_matrix(H, X32.ptr, Y32.ptr, nb, s);
+                launch_pdl("k_cvt_to_f64", k_cvt_to_f64, grid(dim * nb), 256, 0, s, dim, nb, Y32.ptr, Wout, nb);
+            }
         }
         CI_CHECK_LAUNCH();
     }
@@ -815,7 +825,7 @@ struct Solver {
         tn(V, mmax, b, V, mmax, b, Cdev.ptr, nullptr, vtc);
         launch_pdl("k_qr2", k_qr2, 1, 64, 0, s, Cdev.ptr, b, Mdev.ptr, Rdev.ptr, R2dev.ptr, flag, fail);
         nn(V, mmax, b, Mdev.ptr, b, tmp.ptr, b, 1.0, 0.0, vtc);
-        copy_into_basis(tmp.ptr, b, m, b, flag);
+        copy_into_basis(tmp.ptr, b, m, b, flag, f64 ? nullptr : X32.ptr);
         CI_CUDA(cudaMemcpyAsync(pin_R + 64 * par, R2dev.ptr, sizeof(double) * b * b, cudaMemcpyDeviceToHost, s));
         CI_CUDA(cudaMemcpyAsync(pin_stat + par, qstat.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
         CI_CUDA(cudaEventRecord(ev_R[par], s));

@@ -133,9 +133,12 @@ __global__ void k_oz_fix(int dim, int nc, const double *__restrict__ A, int lda,
 }
 
 // dst[r][c] = src[r][c] and Y[r][c] = its biased fixed point, c < nc: a
-// column copy into the basis that keeps the shadow current.
+// column copy into the basis that keeps the shadow current; x32 (nullable,
+// [dim][nc]) also receives the columns rounded to FP32 (the input of the
+// next FP32 SpMM).
 __global__ void k_oz_copy_fix(int dim, int nc, const double *__restrict__ src, int lds, double *__restrict__ dst,
-                              int ldd, unsigned long long *__restrict__ Y, int ldy, int *flag) {
+                              int ldd, unsigned long long *__restrict__ Y, int ldy, float *__restrict__ x32,
+                              int *flag) {
     pdl_wait();
     int bad = 0;
     const int total = dim * nc;
@@ -144,6 +147,7 @@ __global__ void k_oz_copy_fix(int dim, int nc, const double *__restrict__ src, i
         const double x = __ldg(src + (int64_t)r * lds + c);
         dst[(int64_t)r * ldd + c] = x;
         Y[(int64_t)r * ldy + c] = oz_fix(x, 0, bad);
+        if (x32) x32[t] = (float)x;
     }
     if (bad) atomicOr(flag, 1);
 }
@@ -779,11 +783,11 @@ void oz_fix(int64_t dim, int nc, const double *A, int lda, unsigned long long *Y
 }
 
 void oz_copy_fix(int64_t dim, int nc, const double *src, int lds, double *dst, int ldd, unsigned long long *Y, int ldy,
-                 int *flag, cudaStream_t s) {
+                 float *x32, int *flag, cudaStream_t s) {
     if (dim == 0 || nc == 0) return;
     if (dim * nc >= ((int64_t)1 << 31)) fail(CI_ERR_CAPACITY, "basis shadow: %lld entries", (long long)(dim * nc));
     launch_pdl("k_copy_cols", k_oz_copy_fix, grid_for(dim * nc, 256, sm_count() * 16), 256, 0, s, (int)dim, nc, src, lds,
-           dst, ldd, Y, ldy, flag);
+               dst, ldd, Y, ldy, x32, flag);
 }
 
 void oz_nn(int64_t dim, const unsigned long long *Y, int ldy, int na, const double *C, double *W, int ldw,

@@ -280,6 +280,10 @@ void h64_apply(Problem *p, const double *R8, double *Y8, cudaStream_t s);
 void apply_matrix(const Matrix *m, const void *X, void *Y, int nvec, cudaStream_t s);
 // The row ranges of a full-storage matrix's 8-vector SpMM (after its CSR is final).
 void spmm_prepare(Matrix *m, cudaStream_t s);
+// W = H X for 8 FP32 vectors with the result in FP64 ([dim][8]) of a
+// full-storage FP32 or BF16 matrix; false (nothing launched) for other
+// matrices.
+bool apply_matrix8_f64out(const Matrix *m, const float *X, double *W, cudaStream_t s);
 // FP64-exact products on the tensor cores (ozaki.cu) for a basis A of
 // na <= 64 orthonormal columns (|A| < 1.99), read in its fixed-point
 // shadow form Y (oz_fix; even ldy, so rows are 16-byte aligned; A may start
@@ -292,8 +296,9 @@ void spmm_prepare(Matrix *m, cudaStream_t s);
 bool oz_supported(int na);
 void oz_fix(int64_t dim, int nc, const double *A, int lda, unsigned long long *Y, int ldy, int *flag,
             cudaStream_t s);
+// x32: nullable [dim][nc], the copied columns rounded to FP32
 void oz_copy_fix(int64_t dim, int nc, const double *src, int lds, double *dst, int ldd, unsigned long long *Y, int ldy,
-                 int *flag, cudaStream_t s);
+                 float *x32, int *flag, cudaStream_t s);
 void oz_tn(int64_t dim, const unsigned long long *Y, int ldy, int na, const double *B, int ldb, double *part,
            int nblk, int *flag, cudaStream_t s);
 void oz_nn(int64_t dim, const unsigned long long *Y, int ldy, int na, const double *C, double *W, int ldw,

@@ -120,10 +120,11 @@ __global__ void __launch_bounds__(256) k_spmm(const int64_t *__restrict__ bnd, c
 // from L1), and many short CTAs of even work keep every SM busy to the end.
 
 // row_scale: null, or a per-row factor of the stored values (BF16 form)
-template <class TV>
+// TY: float, or double for Y written in FP64 (the Lanczos block W).
+template <class TV, class TY = float>
 __global__ void __launch_bounds__(256) k_spmm8_half(const int64_t *__restrict__ bnd, const int64_t *__restrict__ rp,
                                                     const int32_t *__restrict__ col, const TV *__restrict__ val,
-                                                    const float *__restrict__ X, float *__restrict__ Y,
+                                                    const float *__restrict__ X, TY *__restrict__ Y,
                                                     const float *__restrict__ row_scale) {
     pdl_wait();
     constexpr int U = 4;  // nonzeros in flight per lane pair
@@ -171,7 +172,13 @@ __global__ void __launch_bounds__(256) k_spmm8_half(const int64_t *__restrict__ 
         }
         if (lane < 2) {
             const float sc = row_scale ? row_scale[r] : 1.f;
-            reinterpret_cast<float4 *>(Y)[r * 2 + half] = make_float4(a0 * sc, a1 * sc, a2 * sc, a3 * sc);
+            if constexpr (sizeof(TY) == 4) {
+                reinterpret_cast<float4 *>(Y)[r * 2 + half] = make_float4(a0 * sc, a1 * sc, a2 * sc, a3 * sc);
+            } else {
+                double2 *y = reinterpret_cast<double2 *>(Y) + r * 4 + half * 2;
+                y[0] = make_double2(a0 * sc, a1 * sc);
+                y[1] = make_double2(a2 * sc, a3 * sc);
+            }
         }
     }
 }
@@ -304,6 +311,22 @@ static void launch_spmm(const Matrix *m, const void *X, void *Y, cudaStream_t s)
     }
     launch_pdl("k_spmm", k_spmm<TV, TX, NV>, grid, 256, 0, s, bnd, m->row_ptr.ptr, m->col.ptr, (const TV *)m->val.ptr,
            (const TX *)X, (TX *)Y, (const float *)scale);
+}
+
+bool apply_matrix8_f64out(const Matrix *m, const float *X, double *W, cudaStream_t s) {
+    if (m->upper || (m->vtype != CI_F32 && m->vtype != CI_BF16_ROWSCALE)) return false;
+    if (m->dim == 0) return true;
+    if (!m->spmm_bnd.ptr) fail(CI_ERR_INTERNAL, "matrix without SpMM row ranges");
+    if (((uintptr_t)X % 16) != 0 || ((uintptr_t)W % 16) != 0) fail(CI_ERR_INVALID_ARG, "X and W must be 16-byte aligned");
+    const int grid = (int)m->spmm_nb;
+    if (m->vtype == CI_F32)
+        launch_pdl("k_spmm", k_spmm8_half<float, double>, grid, 256, 0, s, (const int64_t *)m->spmm_bnd.ptr,
+                   m->row_ptr.ptr, m->col.ptr, (const float *)m->val.ptr, X, W, (const float *)nullptr);
+    else
+        launch_pdl("k_spmm", k_spmm8_half<__nv_bfloat16, double>, grid, 256, 0, s, (const int64_t *)m->spmm_bnd.ptr,
+                   m->row_ptr.ptr, m->col.ptr, (const __nv_bfloat16 *)m->val.ptr, X, W, (const float *)m->row_scale.ptr);
+    CI_CHECK_LAUNCH();
+    return true;
 }
 
 template <class TV, class TX>
