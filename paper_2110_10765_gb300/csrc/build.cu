@@ -171,15 +171,36 @@ __global__ void __launch_bounds__(256) k_count_rows(const RowArgs<T> *args, cons
     }
 }
 
-// sum over the occupied states k of determinant s (W-word bit strings) of tab[k]
+// sum over the occupied states k of determinant s (W-word bit strings) of
+// tab[k], in ascending k.  For S <= 128 the states are taken four at a time
+// and their four loads issued before the adds (the same order of adds).
 template <class T>
 __device__ __forceinline__ T sum_over_bits(const T *tab, const uint64_t *bits, int s, int W) {
     const uint64_t *b = bits + (int64_t)s * W;
     T sum = 0;
     if (W <= 2) {   // S <= 128: both words loaded up front, no loop over words
         uint64_t w0 = b[0], w1 = W > 1 ? b[1] : 0ull;
-        while (w0) { const int k = __ffsll((long long)w0) - 1; w0 &= w0 - 1; sum += tab[k]; }
-        while (w1) { const int k = __ffsll((long long)w1) - 1; w1 &= w1 - 1; sum += tab[64 + k]; }
+        while (w0 | w1) {
+            int k[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (w0) {
+                    k[u] = __ffsll((long long)w0) - 1;
+                    w0 &= w0 - 1;
+                } else if (w1) {
+                    k[u] = 64 + __ffsll((long long)w1) - 1;
+                    w1 &= w1 - 1;
+                } else {
+                    k[u] = -1;
+                }
+            }
+            T x[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) x[u] = k[u] >= 0 ? tab[k[u]] : (T)0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (k[u] >= 0) sum += x[u];
+        }
         return sum;
     }
     for (int w = 0; w < W; ++w) {
@@ -216,6 +237,13 @@ __device__ __forceinline__ int fill_chunk(const RowArgs<T> &a, const RowCtx &x, 
     const int colbase = ep.tgt;   // first basis row of the proton partner
     // 0. four protons moved: the neutrons stay, one element
     if (kind == 0 && len == 1) em.put(a, pos, colbase + x.n_local, ep.val);
+    // (2,0) elements below (one proton moved, the neutrons spectators) take a
+    // value that depends on the partner alone: its lane forms it here, once
+    T hspec = 0;
+    if (kind == 1 && len > 0 && info_dslot(ep.info) == 0) {
+        const T *u = a.Upn + ((int64_t)info_c(ep.info) * S + info_a(ep.info)) * S;
+        hspec = ep.val + sum_over_bits<T>(u, a.n_bits, x.n, a.W);
+    }
     // 1. one proton moved (a -> c): L2(n)[beg, beg+len)
     const int len1 = kind == 1 ? len : 0;
     const int incl1 = warp_incl_scan_i32(len1);
@@ -234,7 +262,7 @@ __device__ __forceinline__ int fill_chunk(const RowArgs<T> &a, const RowCtx &x, 
         const int jcol = __shfl_sync(0xffffffffu, colbase, j);
         const int jtb = __shfl_sync(0xffffffffu, ep.local, j);
         const uint32_t pinfo = __shfl_sync(0xffffffffu, ep.info, j);
-        const T pval = __shfl_sync(0xffffffffu, ep.val, j);
+        const T hj = __shfl_sync(0xffffffffu, hspec, j);
         const int jbeg = __shfl_sync(0xffffffffu, beg, j);
         if (t < total1) {
             const ConnEntry<T> en = a.l2_ent[x.l2b + jbeg + k];
@@ -242,10 +270,8 @@ __device__ __forceinline__ int fill_chunk(const RowArgs<T> &a, const RowCtx &x, 
             if (info_dcode(en.info) != 0) {   // (2,2): V^pn_{c_p c_n, a_p a_n}
                 const T w = a.Tpn[jtb + info_tcol(en.info)];
                 v = (info_neg(pinfo) ^ info_neg(en.info)) ? -w : w;
-            } else {                          // (2,0): neutrons are spectators
-                const T *u = a.Upn + ((int64_t)info_c(pinfo) * S + info_a(pinfo)) * S;
-                const T h = pval + sum_over_bits<T>(u, a.n_bits, x.n, a.W);
-                v = info_neg(pinfo) ? -h : h;
+            } else {                          // (2,0): neutrons are spectators (n' = n, same 2M)
+                v = info_neg(pinfo) ? -hj : hj;
             }
             em.put(a, jpos + k, jcol + en.local, v);
         }
