@@ -349,7 +349,7 @@ struct StoreEmit {
 // tot += L[i] * y_i (lane 0); at the end the block's tot goes to part.
 template <class T>
 struct ApplyEmit {
-    static constexpr int kMinBlocks = 1;
+    static constexpr int kMinBlocks = 2;   // <= 128 registers: two blocks per SM
     const double *R = nullptr;   // right vectors [dim][8], gathered by column
     const double *L = nullptr;   // left vectors [dim][8], one row per row end
     double acc[8], tot[8];
