@@ -348,7 +348,9 @@ typedef struct {
     int32_t host_qr;      /* block Lanczos: block steps whose block QR fell back
                              from the device (Cholesky) path to the host's
                              rank-revealing one (deflation, random completion) */
-    int32_t reserved;
+    int32_t qr_one_pass;  /* block Lanczos: block steps whose first (device)
+                             block-QR pass already left the block orthonormal
+                             to 1e-13, so the second pass formed no product */
 } ci_eig_info;
 
 /* Fig. 1, eigensolve (Sec. 2): lowest k eigenvalues of H by block Lanczos with

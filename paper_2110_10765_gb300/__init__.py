@@ -288,6 +288,7 @@ class Matrix:
         out = {"iterations": info.iterations, "restarts": info.restarts, "converged": info.converged,
                "basis_size": info.basis_size, "hnorm_est": info.hnorm_est,
                "residual": list(info.residual)[:k], "seconds": info.seconds, "host_qr": info.host_qr,
+               "qr_one_pass": info.qr_one_pass,
                "status": st}
         return ev, out
 

@@ -41,7 +41,7 @@ class EigInfo(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("restarts", C.c_int32), ("converged", C.c_int32),
                 ("basis_size", C.c_int32), ("hnorm_est", C.c_double),
                 ("residual", C.c_double * 32), ("seconds", C.c_double), ("host_qr", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("qr_one_pass", C.c_int32)]
 
 
 class QueueDesc(C.Structure):

@@ -353,13 +353,30 @@ __global__ void k_qr1(const double *__restrict__ G, int b, double hnorm, double 
 // orthonormal, and the block's coupling becomes R2 = Y D^{-1} R.  One thread
 // per entry (b*b <= 64); the iteration stops after the update made with
 // |I - Z Y| <= 1e-12, whose error is of second order; *flag |= fail when 40
-// iterations leave T off the identity or a column has no length.
+// iterations leave T off the identity or a column has no length.  skip
+// (nullable): set to 1 when every entry of G is within kOrthSkip of the
+// identity's (V orthonormal already: Mi = I, R2 = R, and the caller's
+// V Mi product and copy read V itself), else to 0.
+constexpr double kOrthSkip = 1e-13;
 __global__ void k_qr2(const double *__restrict__ G, int b, double *__restrict__ Mi, const double *__restrict__ R,
-                      double *__restrict__ R2, int *flag, int fail) {
+                      double *__restrict__ R2, int *flag, int fail, int *skip) {
     pdl_wait();
     __shared__ double Y[64], Z[64], Tm[64], d[8];
     const int t = threadIdx.x, i = t / b, j = t % b;
     const bool on = t < b * b;
+    if (skip) {
+        const double e = on ? fabs(0.5 * (G[i * b + j] + G[j * b + i]) - (i == j ? 1.0 : 0.0)) : 0.0;
+        const bool far = __syncthreads_or(on && !(e <= kOrthSkip));
+        if (!far) {
+            if (on) {
+                Mi[t] = i == j ? 1.0 : 0.0;
+                R2[t] = R[t];
+            }
+            if (t == 0) *skip = 1;
+            return;
+        }
+        if (t == 0) *skip = 0;
+    }
     if (t < b) {
         const double g = G[t * b + t];
         d[t] = g > 0.0 ? 1.0 / sqrt(g) : 1.0;
@@ -539,9 +556,10 @@ struct Solver {
     // device by the second pass, copied to pinned memory with the device
     // pass's status, read by take_R
     DevBuf<double> Rdev, R2dev;
-    DevBuf<int> qstat;
+    DevBuf<int> qstat, qskip;
     double *pin_R = nullptr;   // [2][64]
-    int *pin_stat = nullptr;   // [2]
+    int *pin_stat = nullptr;   // [2][2]: status, second-pass product skipped
+    int last_skip = 0;
     cudaEvent_t ev_R[2] = {nullptr, nullptr};
     int pend_m = 0, pend_lo = 0, pend_nb = 0, pend_passes = 0;
     bool pend = false;
@@ -596,11 +614,14 @@ struct Solver {
     // Q[:, c0:c0+nc] = src (leading dimension lds), with the shadow
     // (an entry out of the shadow's range sets bit 0 of *flag, ozflag by
     // default).  x32: nullable, also receives the columns in FP32 (the next
-    // SpMM's input; x32_col records which block it holds).
-    void copy_into_basis(const double *src, int lds, int c0, int nc, int *flag = nullptr, float *x32 = nullptr) {
+    // SpMM's input; x32_col records which block it holds).  skip: nullable
+    // device flag, when set the source is alt (leading dimension ld_alt).
+    void copy_into_basis(const double *src, int lds, int c0, int nc, int *flag = nullptr, float *x32 = nullptr,
+                         const double *alt = nullptr, int ld_alt = 0, const int *skip = nullptr) {
         x32_col = -1;
         if (tc && Qfix.ptr) {
-            oz_copy_fix(dim, nc, src, lds, Q.ptr + c0, mmax, Qfix.ptr + c0, mmax, x32, flag ? flag : ozflag.ptr, s);
+            oz_copy_fix(dim, nc, src, lds, Q.ptr + c0, mmax, Qfix.ptr + c0, mmax, x32, flag ? flag : ozflag.ptr, s,
+                        alt, ld_alt, skip);
             if (x32) x32_col = c0;
         } else {
             launch_pdl("k_copy_cols", k_copy_cols, grid(dim * nc), 256, 0, s, dim, nc, src, lds, Q.ptr + c0, mmax);
@@ -632,10 +653,11 @@ struct Solver {
         }
     }
 
+    // skip: nullable device flag that cancels the (tensor-core) product
     void nn(const double *A, int lda, int na, const double *C, int nb, double *Wout, int ldw, double alpha,
-            double beta, bool basis = false) {
+            double beta, bool basis = false, const int *skip = nullptr) {
         if (use_tc(basis, na, nb)) {
-            oz_nn(dim, shadow(A), lda, na, C, Wout, ldw, alpha, beta, ozflag.ptr, s);
+            oz_nn(dim, shadow(A), lda, na, C, Wout, ldw, alpha, beta, ozflag.ptr, s, skip);
             CI_CHECK_LAUNCH();
             return;
         }
@@ -750,11 +772,13 @@ struct Solver {
     void ensure_qr_buffers() {
         if (pin_R) return;
         CI_CUDA(cudaMallocHost(&pin_R, sizeof(double) * 2 * 64));
-        CI_CUDA(cudaMallocHost(&pin_stat, sizeof(int) * 2));
+        CI_CUDA(cudaMallocHost(&pin_stat, sizeof(int) * 4));
         for (cudaEvent_t &e : ev_R) CI_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         Rdev.alloc(64);
         R2dev.alloc(64);
         qstat.alloc(1);
+        qskip.alloc(1);
+        CI_CUDA(cudaMemsetAsync(qskip.ptr, 0, sizeof(int), s));
     }
 
     // Orthonormalise Wb [dim][b] (already orthogonal to Q[:, 0:m]) into
@@ -818,16 +842,20 @@ struct Solver {
     // shadow's range).  V is orthonormal up to rounding or the conditioning
     // of the first pass, so its products go through the basis path.  R2 and
     // the status word go to pinned slot par, then ev_R[par].
+    // On the tensor-core path a block that the first pass left orthonormal to
+    // kOrthSkip skips the product V G2^{-1/2} (k_qr2 decides on the device).
     void second_pass(int m, int par, int *flag, int fail) {
         double *V = Q.ptr + m;
         const bool vtc = tc && Qfix.ptr;
+        int *sk = vtc ? qskip.ptr : nullptr;
         if (vtc) oz_fix(dim, b, V, mmax, Qfix.ptr + m, mmax, flag, s);
         tn(V, mmax, b, V, mmax, b, Cdev.ptr, nullptr, vtc);
-        launch_pdl("k_qr2", k_qr2, 1, 64, 0, s, Cdev.ptr, b, Mdev.ptr, Rdev.ptr, R2dev.ptr, flag, fail);
-        nn(V, mmax, b, Mdev.ptr, b, tmp.ptr, b, 1.0, 0.0, vtc);
-        copy_into_basis(tmp.ptr, b, m, b, flag, f64 ? nullptr : X32.ptr);
+        launch_pdl("k_qr2", k_qr2, 1, 64, 0, s, Cdev.ptr, b, Mdev.ptr, Rdev.ptr, R2dev.ptr, flag, fail, sk);
+        nn(V, mmax, b, Mdev.ptr, b, tmp.ptr, b, 1.0, 0.0, vtc, sk);
+        copy_into_basis(tmp.ptr, b, m, b, flag, f64 ? nullptr : X32.ptr, V, mmax, sk);
         CI_CUDA(cudaMemcpyAsync(pin_R + 64 * par, R2dev.ptr, sizeof(double) * b * b, cudaMemcpyDeviceToHost, s));
-        CI_CUDA(cudaMemcpyAsync(pin_stat + par, qstat.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CI_CUDA(cudaMemcpyAsync(pin_stat + 2 * par, qstat.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CI_CUDA(cudaMemcpyAsync(pin_stat + 2 * par + 1, qskip.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
         CI_CUDA(cudaEventRecord(ev_R[par], s));
     }
 
@@ -850,7 +878,8 @@ struct Solver {
     int take_R(int par, std::vector<double> &R) {
         CI_CUDA(cudaEventSynchronize(ev_R[par]));
         R.assign(pin_R + 64 * par, pin_R + 64 * par + (size_t)b * b);
-        return pin_stat[par];
+        last_skip = pin_stat[2 * par + 1];
+        return pin_stat[2 * par];
     }
 };
 
@@ -984,7 +1013,7 @@ void lowest_eigs(const Matrix *H, const ci_eig_opts *opts_in, double *evals, dou
     // W = H V_j alternates between two buffers, so that a step's W is still
     // there when its block QR has to be redone on the host path
     double *Wcur = sv.W.ptr, *Wnext = sv.W2.ptr;
-    int par = 0, host_qr = 0;
+    int par = 0, host_qr = 0, one_pass = 0;
     while (true) {
         // W = H V_j, orthogonalised against the whole basis
         if (!applied) sv.apply(sv.Q.ptr + j0, mmax, b, Wcur);
@@ -1017,7 +1046,9 @@ void lowest_eigs(const Matrix *H, const ci_eig_opts *opts_in, double *evals, dou
             sv.apply(sv.Q.ptr + j0, mmax, b, Wnext);
             applied = true;
         }
-        if (sv.take_R(qpar, Rlast) != 0) {
+        if (sv.take_R(qpar, Rlast) == 0) {
+            one_pass += sv.last_skip;
+        } else {
             // rank deficient (or the second pass did not settle): the
             // rank-revealing host path redoes the block from the same W, and
             // the product just enqueued is redone with the new block
@@ -1109,6 +1140,7 @@ void lowest_eigs(const Matrix *H, const ci_eig_opts *opts_in, double *evals, dou
     inf.basis_size = m_act;
     inf.hnorm_est = sv.hnorm;
     inf.host_qr = host_qr;
+    inf.qr_one_pass = one_pass;
     inf.converged = 0;
     for (int i = 0; i < k; ++i)
         if (last.res[i] <= o.tol * sv.hnorm) ++inf.converged;

@@ -135,16 +135,21 @@ __global__ void k_oz_fix(int dim, int nc, const double *__restrict__ A, int lda,
 // dst[r][c] = src[r][c] and Y[r][c] = its biased fixed point, c < nc: a
 // column copy into the basis that keeps the shadow current; x32 (nullable,
 // [dim][nc]) also receives the columns rounded to FP32 (the input of the
-// next FP32 SpMM).
-__global__ void k_oz_copy_fix(int dim, int nc, const double *__restrict__ src, int lds, double *__restrict__ dst,
-                              int ldd, unsigned long long *__restrict__ Y, int ldy, float *__restrict__ x32,
-                              int *flag) {
+// next FP32 SpMM).  When skip (nullable) is set, alt (leading dimension
+// ld_alt) is the source instead (it may be dst itself).
+__global__ void k_oz_copy_fix(int dim, int nc, const double *src, int lds, double *dst, int ldd,
+                              unsigned long long *__restrict__ Y, int ldy, float *__restrict__ x32, int *flag,
+                              const double *alt, int ld_alt, const int *skip) {
     pdl_wait();
+    if (skip && *skip) {
+        src = alt;
+        lds = ld_alt;
+    }
     int bad = 0;
     const int total = dim * nc;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
         const int r = t / nc, c = t - r * nc;
-        const double x = __ldg(src + (int64_t)r * lds + c);
+        const double x = src[(int64_t)r * lds + c];   // plain load: src may be dst
         dst[(int64_t)r * ldd + c] = x;
         Y[(int64_t)r * ldy + c] = oz_fix(x, 0, bad);
         if (x32) x32[t] = (float)x;
@@ -225,11 +230,13 @@ static uint32_t nn_raw_stride(int na, int m) {
 }
 
 // ymap: boxes of bc columns x 128 rows (bc = raw row stride / 8).
+// skip: nullable; when *skip is set the kernel returns at once (W untouched).
 __global__ void __launch_bounds__(kNnThreads, 1) k_oz_nn(const __grid_constant__ CUtensorMap ymap, int m, int bc,
                                                   int64_t dim, int na, const double *__restrict__ C,
                                                   double *__restrict__ W, int ldw, double alpha, double beta,
-                                                  int *flag) {
+                                                  int *flag, const int *skip) {
     pdl_wait();
+    if (skip && *skip) return;
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ __align__(8) uint64_t rfull[kMaxRaw], rempty[kMaxRaw], full[2], empty[2], tfull[2], tempty[2], done;
     __shared__ uint32_t tmem_base;
@@ -783,15 +790,15 @@ void oz_fix(int64_t dim, int nc, const double *A, int lda, unsigned long long *Y
 }
 
 void oz_copy_fix(int64_t dim, int nc, const double *src, int lds, double *dst, int ldd, unsigned long long *Y, int ldy,
-                 float *x32, int *flag, cudaStream_t s) {
+                 float *x32, int *flag, cudaStream_t s, const double *alt, int ld_alt, const int *skip) {
     if (dim == 0 || nc == 0) return;
     if (dim * nc >= ((int64_t)1 << 31)) fail(CI_ERR_CAPACITY, "basis shadow: %lld entries", (long long)(dim * nc));
     launch_pdl("k_copy_cols", k_oz_copy_fix, grid_for(dim * nc, 256, sm_count() * 16), 256, 0, s, (int)dim, nc, src, lds,
-               dst, ldd, Y, ldy, x32, flag);
+               dst, ldd, Y, ldy, x32, flag, alt, ld_alt, skip);
 }
 
 void oz_nn(int64_t dim, const unsigned long long *Y, int ldy, int na, const double *C, double *W, int ldw,
-           double alpha, double beta, int *flag, cudaStream_t s) {
+           double alpha, double beta, int *flag, cudaStream_t s, const int *skip) {
     static bool attr = false;
     if (!attr) {
         CI_CUDA(cudaFuncSetAttribute(k_oz_nn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_nn_smem(64)));
@@ -804,7 +811,7 @@ void oz_nn(int64_t dim, const unsigned long long *Y, int ldy, int na, const doub
     const int64_t ntiles = (dim + 127) / 128;
     const int grid = (int)std::min<int64_t>(ntiles, sm_count());
     launch_pdl("k_oz_nn", k_oz_nn, grid, kNnThreads, oz_nn_smem(na), s, map, m, bc, dim, na, C, W, ldw, alpha, beta,
-           flag);
+               flag, skip);
 }
 
 // Row blocks of oz_tn: one per SM (a block takes any number of rows in

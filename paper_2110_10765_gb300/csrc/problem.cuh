@@ -296,13 +296,17 @@ bool apply_matrix8_f64out(const Matrix *m, const float *X, double *W, cudaStream
 bool oz_supported(int na);
 void oz_fix(int64_t dim, int nc, const double *A, int lda, unsigned long long *Y, int ldy, int *flag,
             cudaStream_t s);
-// x32: nullable [dim][nc], the copied columns rounded to FP32
+// x32: nullable [dim][nc], the copied columns rounded to FP32; skip:
+// nullable, when set on the device the source is alt (leading dimension
+// ld_alt) instead of src
 void oz_copy_fix(int64_t dim, int nc, const double *src, int lds, double *dst, int ldd, unsigned long long *Y, int ldy,
-                 float *x32, int *flag, cudaStream_t s);
+                 float *x32, int *flag, cudaStream_t s, const double *alt = nullptr, int ld_alt = 0,
+                 const int *skip = nullptr);
 void oz_tn(int64_t dim, const unsigned long long *Y, int ldy, int na, const double *B, int ldb, double *part,
            int nblk, int *flag, cudaStream_t s);
+// skip: nullable, when set on the device the product is not formed
 void oz_nn(int64_t dim, const unsigned long long *Y, int ldy, int na, const double *C, double *W, int ldw,
-           double alpha, double beta, int *flag, cudaStream_t s);
+           double alpha, double beta, int *flag, cudaStream_t s, const int *skip = nullptr);
 int oz_tn_blocks(int64_t dim);
 void lowest_eigs(const Matrix *H, const ci_eig_opts *opts, double *evals, double *evecs, ci_eig_info *info,
                  cudaStream_t s);

@@ -368,6 +368,7 @@ def test_lowest_eigs_config1_fp32():
     assert np.all(np.abs(ev - ref) <= EIG_REL * np.maximum(np.abs(ref), 1)), ev - ref
     assert max(info["residual"]) <= 1e-4 * info["hnorm_est"]
     assert info["host_qr"] == 0   # every block step orthonormalised on the device
+    assert 0 <= info["qr_one_pass"] <= info["iterations"]
 
 
 @pytest.mark.parametrize("case", [(1, 2, 2, -1), (2, 2, 1, 1), (1, 1, 1, -1)])
