@@ -358,7 +358,9 @@ typedef struct {
  * newest blocks, then reorth_passes passes over the whole basis) and thick
  * restart.  SpMM in the matrix's precision, everything else in FP64.  Each
  * new block is orthonormalised on the device (Cholesky QR, then a
- * Newton-Schulz pass) without a host sync; a numerically rank-deficient
+ * Newton-Schulz pass, whose product is skipped when the block's Gram matrix
+ * is already the identity to 1e-13) without a host sync; a numerically
+ * rank-deficient
  * block is redone by the host's rank-revealing QR (info->host_qr counts
  * those).  The host reads the projection coefficients and the coupling
  * while the next product runs.  evals: host [k], ascending.  evecs:
