@@ -355,8 +355,9 @@ __global__ void k_qr1(const double *__restrict__ G, int b, double hnorm, double 
 // |I - Z Y| <= 1e-12, whose error is of second order; *flag |= fail when 40
 // iterations leave T off the identity or a column has no length.  skip
 // (nullable): set to 1 when every entry of G is within kOrthSkip of the
-// identity's (V orthonormal already: Mi = I, R2 = R, and the caller's
-// V Mi product and copy read V itself), else to 0.
+// identity's (V orthonormal already: Mi = I, R2 = R, and the caller skips
+// the product V Mi and the copy, leaving the block, its shadow and its FP32
+// copy as the first pass made them), else to 0.
 constexpr double kOrthSkip = 1e-13;
 __global__ void k_qr2(const double *__restrict__ G, int b, double *__restrict__ Mi, const double *__restrict__ R,
                       double *__restrict__ R2, int *flag, int fail, int *skip) {
@@ -615,13 +616,14 @@ struct Solver {
     // (an entry out of the shadow's range sets bit 0 of *flag, ozflag by
     // default).  x32: nullable, also receives the columns in FP32 (the next
     // SpMM's input; x32_col records which block it holds).  skip: nullable
-    // device flag, when set the source is alt (leading dimension ld_alt).
+    // device flag, when set nothing is copied (the columns, shadow and FP32
+    // copy are already in place).
     void copy_into_basis(const double *src, int lds, int c0, int nc, int *flag = nullptr, float *x32 = nullptr,
-                         const double *alt = nullptr, int ld_alt = 0, const int *skip = nullptr) {
+                         const int *skip = nullptr) {
         x32_col = -1;
         if (tc && Qfix.ptr) {
             oz_copy_fix(dim, nc, src, lds, Q.ptr + c0, mmax, Qfix.ptr + c0, mmax, x32, flag ? flag : ozflag.ptr, s,
-                        alt, ld_alt, skip);
+                        skip);
             if (x32) x32_col = c0;
         } else {
             launch_pdl("k_copy_cols", k_copy_cols, grid(dim * nc), 256, 0, s, dim, nc, src, lds, Q.ptr + c0, mmax);
@@ -848,11 +850,14 @@ struct Solver {
         double *V = Q.ptr + m;
         const bool vtc = tc && Qfix.ptr;
         int *sk = vtc ? qskip.ptr : nullptr;
-        if (vtc) oz_fix(dim, b, V, mmax, Qfix.ptr + m, mmax, flag, s);
+        float *x32 = f64 ? nullptr : X32.ptr;
+        // the shadow (and FP32 copy) of the first pass's block: final when
+        // the product below is skipped, else rewritten by the copy
+        if (vtc) oz_fix(dim, b, V, mmax, Qfix.ptr + m, mmax, flag, s, x32);
         tn(V, mmax, b, V, mmax, b, Cdev.ptr, nullptr, vtc);
         launch_pdl("k_qr2", k_qr2, 1, 64, 0, s, Cdev.ptr, b, Mdev.ptr, Rdev.ptr, R2dev.ptr, flag, fail, sk);
         nn(V, mmax, b, Mdev.ptr, b, tmp.ptr, b, 1.0, 0.0, vtc, sk);
-        copy_into_basis(tmp.ptr, b, m, b, flag, f64 ? nullptr : X32.ptr, V, mmax, sk);
+        copy_into_basis(tmp.ptr, b, m, b, flag, x32, sk);
         CI_CUDA(cudaMemcpyAsync(pin_R + 64 * par, R2dev.ptr, sizeof(double) * b * b, cudaMemcpyDeviceToHost, s));
         CI_CUDA(cudaMemcpyAsync(pin_stat + 2 * par, qstat.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
         CI_CUDA(cudaMemcpyAsync(pin_stat + 2 * par + 1, qskip.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));

@@ -118,16 +118,19 @@ constexpr int kWaitPolls = 1 << 22;   // bounded mbarrier waits (error flag 2 wh
 // ---------------------------------------------------------------- the shadow
 
 // Y[r][c] = biased fixed point of A[r][c] (scale 2^0) for c < nc; bit 0 of
-// *flag when an entry has |a| >= 1.99 or is not finite.  One thread per
+// *flag when an entry has |a| >= 1.99 or is not finite; x32 (nullable,
+// [dim][nc]) also receives the entries rounded to FP32.  One thread per
 // element, consecutive threads along a row (32-bit indices: dim * nc < 2^31).
 __global__ void k_oz_fix(int dim, int nc, const double *__restrict__ A, int lda, unsigned long long *__restrict__ Y,
-                         int ldy, int *flag) {
+                         int ldy, int *flag, float *__restrict__ x32) {
     pdl_wait();
     int bad = 0;
     const int total = dim * nc;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
         const int r = t / nc, c = t - r * nc;
-        Y[(int64_t)r * ldy + c] = oz_fix(__ldg(A + (int64_t)r * lda + c), 0, bad);
+        const double x = __ldg(A + (int64_t)r * lda + c);
+        Y[(int64_t)r * ldy + c] = oz_fix(x, 0, bad);
+        if (x32) x32[t] = (float)x;
     }
     if (bad) atomicOr(flag, 1);
 }
@@ -135,21 +138,18 @@ __global__ void k_oz_fix(int dim, int nc, const double *__restrict__ A, int lda,
 // dst[r][c] = src[r][c] and Y[r][c] = its biased fixed point, c < nc: a
 // column copy into the basis that keeps the shadow current; x32 (nullable,
 // [dim][nc]) also receives the columns rounded to FP32 (the input of the
-// next FP32 SpMM).  When skip (nullable) is set, alt (leading dimension
-// ld_alt) is the source instead (it may be dst itself).
-__global__ void k_oz_copy_fix(int dim, int nc, const double *src, int lds, double *dst, int ldd,
-                              unsigned long long *__restrict__ Y, int ldy, float *__restrict__ x32, int *flag,
-                              const double *alt, int ld_alt, const int *skip) {
+// next FP32 SpMM).  When skip (nullable) is set the kernel returns at once
+// (the columns, their shadow and their FP32 copy are already in place).
+__global__ void k_oz_copy_fix(int dim, int nc, const double *__restrict__ src, int lds, double *__restrict__ dst,
+                              int ldd, unsigned long long *__restrict__ Y, int ldy, float *__restrict__ x32, int *flag,
+                              const int *skip) {
     pdl_wait();
-    if (skip && *skip) {
-        src = alt;
-        lds = ld_alt;
-    }
+    if (skip && *skip) return;
     int bad = 0;
     const int total = dim * nc;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
         const int r = t / nc, c = t - r * nc;
-        const double x = src[(int64_t)r * lds + c];   // plain load: src may be dst
+        const double x = __ldg(src + (int64_t)r * lds + c);
         dst[(int64_t)r * ldd + c] = x;
         Y[(int64_t)r * ldy + c] = oz_fix(x, 0, bad);
         if (x32) x32[t] = (float)x;
@@ -782,19 +782,19 @@ static CUtensorMap rows_map(const void *P, int ld, int64_t rows, int ncols, int 
 }
 
 void oz_fix(int64_t dim, int nc, const double *A, int lda, unsigned long long *Y, int ldy, int *flag,
-            cudaStream_t s) {
+            cudaStream_t s, float *x32) {
     if (dim == 0 || nc == 0) return;
     if (dim * nc >= ((int64_t)1 << 31)) fail(CI_ERR_CAPACITY, "basis shadow: %lld entries", (long long)(dim * nc));
     launch_pdl("k_oz_fix", k_oz_fix, grid_for(dim * nc, 256, sm_count() * 16), 256, 0, s, (int)dim, nc, A, lda, Y, ldy,
-           flag);
+               flag, x32);
 }
 
 void oz_copy_fix(int64_t dim, int nc, const double *src, int lds, double *dst, int ldd, unsigned long long *Y, int ldy,
-                 float *x32, int *flag, cudaStream_t s, const double *alt, int ld_alt, const int *skip) {
+                 float *x32, int *flag, cudaStream_t s, const int *skip) {
     if (dim == 0 || nc == 0) return;
     if (dim * nc >= ((int64_t)1 << 31)) fail(CI_ERR_CAPACITY, "basis shadow: %lld entries", (long long)(dim * nc));
     launch_pdl("k_copy_cols", k_oz_copy_fix, grid_for(dim * nc, 256, sm_count() * 16), 256, 0, s, (int)dim, nc, src, lds,
-               dst, ldd, Y, ldy, x32, flag, alt, ld_alt, skip);
+               dst, ldd, Y, ldy, x32, flag, skip);
 }
 
 void oz_nn(int64_t dim, const unsigned long long *Y, int ldy, int na, const double *C, double *W, int ldw,

@@ -294,14 +294,13 @@ bool apply_matrix8_f64out(const Matrix *m, const float *X, double *W, cudaStream
 // An entry outside the digits' range sets bit 0 of *flag, a tensor-core
 // wait that ran out bit 1.
 bool oz_supported(int na);
+// x32: nullable [dim][nc], the entries rounded to FP32
 void oz_fix(int64_t dim, int nc, const double *A, int lda, unsigned long long *Y, int ldy, int *flag,
-            cudaStream_t s);
+            cudaStream_t s, float *x32 = nullptr);
 // x32: nullable [dim][nc], the copied columns rounded to FP32; skip:
-// nullable, when set on the device the source is alt (leading dimension
-// ld_alt) instead of src
+// nullable, when set on the device nothing is copied
 void oz_copy_fix(int64_t dim, int nc, const double *src, int lds, double *dst, int ldd, unsigned long long *Y, int ldy,
-                 float *x32, int *flag, cudaStream_t s, const double *alt = nullptr, int ld_alt = 0,
-                 const int *skip = nullptr);
+                 float *x32, int *flag, cudaStream_t s, const int *skip = nullptr);
 void oz_tn(int64_t dim, const unsigned long long *Y, int ldy, int na, const double *B, int ldb, double *part,
            int nblk, int *flag, cudaStream_t s);
 // skip: nullable, when set on the device the product is not formed
