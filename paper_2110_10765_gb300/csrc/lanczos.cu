@@ -574,7 +574,6 @@ struct Solver {
         oz_nblk = oz_tn_blocks(dim);
         Q.alloc((size_t)dim * mmax);
         W.alloc((size_t)dim * b);
-        W2.alloc((size_t)dim * b);
         tmp.alloc((size_t)dim * std::max(mmax, b));
         part.alloc((size_t)std::max(nblk, oz_nblk) * kMaxNa * 8);
         ozflag.alloc(1);
@@ -1017,6 +1016,7 @@ void lowest_eigs(const Matrix *H, const ci_eig_opts *opts_in, double *evals, dou
     bool applied = false;   // H V_j already enqueued (before the last host Ritz check)
     // W = H V_j alternates between two buffers, so that a step's W is still
     // there when its block QR has to be redone on the host path
+    sv.W2.alloc((size_t)dim * b);
     double *Wcur = sv.W.ptr, *Wnext = sv.W2.ptr;
     int par = 0, host_qr = 0, one_pass = 0;
     while (true) {
